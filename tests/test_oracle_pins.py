@@ -1,0 +1,429 @@
+"""Pins of the FP64 oracle against closed forms, invariants and independent routines.
+
+Each test fixes one stage of the oracle to something other than itself, so that a dropped
+term, a sign or index error or a transposed operand in that stage fails here:
+
+* FFT: numpy.fft (independent implementation), all radices used (2, 5 and others).
+* Spot: exact discrete Dirichlet form of a flat square subaperture; Parseval; an integer tilt
+  rolls the image exactly; elongation equals circular convolution with the periodised
+  Gaussian (Poisson summation) along the stated direction.
+* Binning and centroid: hand-built images with known answers.
+* Bilinear sampling: exact on affine screens (asymmetric coefficients catch transposition).
+* Cone projection: a linear layer seen by a laser star at finite height gives
+  b.(x (1 - h/H) + h theta + t v) exactly.
+* DM: single poke equals the Gaussian closed form with g(pitch) = coupling; the separable
+  evaluation equals the brute-force double sum on a non-square actuator grid.
+* Science: zero residual gives Strehl 1 and a unit PSF peak; Parseval of the PSF; Marechal
+  regime exp(-sigma^2) for a small random phase.
+* Integrator: with a static DM-shaped aberration and R = -pinv(D), the command error decays as
+  (1 - g)^k.
+* Noise: Poisson and read-noise moments; float exp/log/cos against libm.
+* Screens: structure function against the quadrature of the von Karman spectrum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_00386_gb300 import inputs
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# ------------------------------------------------------------------------------------------ FFT
+@pytest.mark.parametrize("n", [1, 2, 7, 14, 16, 32, 64, 243, 256, 1000, 1280])
+def test_fft1_matches_numpy(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ref = np.fft.fft(x)
+    assert np.max(np.abs(oracle.fft1(x) - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(oracle.fft1(x, inverse=True) - np.fft.ifft(x))) <= 1e-13 * max(1.0, n)
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 40])
+def test_fft2_matches_numpy(n):
+    rng = np.random.default_rng(100 + n)
+    x = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    ref = np.fft.fft2(x)
+    assert np.max(np.abs(oracle.fft2(x) - ref)) <= 1e-11 * np.max(np.abs(ref))
+    assert np.max(np.abs(oracle.fft2(x, inverse=True) - np.fft.ifft2(x))) <= 1e-13 * n
+
+
+# ------------------------------------------------------------------------------------------ spot
+def _dirichlet(kp, n, N):
+    return (np.sin(np.pi * kp * n / N) / np.sin(np.pi * kp / N)) ** 2
+
+
+@pytest.mark.parametrize("n,N", [(8, 16), (8, 32), (32, 64), (5, 20)])
+def test_flat_spot_is_dirichlet(n, N):
+    img = oracle.sh_image(np.ones((n, n)), np.zeros((n, n)), N)
+    kp = (np.arange(N) - N / 2) + 0.5          # half-bin centring: peak at N/2 - 1/2
+    d = _dirichlet(kp, n, N)
+    ref = np.outer(d, d)
+    assert np.max(np.abs(img - ref)) <= 1e-10 * ref.max()
+    assert img.sum() == pytest.approx(N * N * n * n, rel=1e-12)
+
+
+@pytest.mark.parametrize("sigma", [0.0, 1.7])
+def test_spot_parseval(sigma):
+    rng = np.random.default_rng(5)
+    n, N = 8, 32
+    amp = (rng.random((n, n)) > 0.2).astype(float)
+    ph = rng.standard_normal((n, n)) * 2.0
+    img = oracle.sh_image(amp, ph, N, sigma, (0.6, 0.8))
+    assert abs(img.sum() - N * N * (amp ** 2).sum()) <= 1e-10 * img.sum()
+
+
+@pytest.mark.parametrize("m,axis", [(3, 1), (-5, 1), (2, 0), (-1, 0)])
+def test_integer_tilt_rolls_spot(m, axis):
+    rng = np.random.default_rng(9)
+    n, N = 8, 32
+    amp = (rng.random((n, n)) > 0.1).astype(float)
+    base = rng.standard_normal((n, n)) * 0.7
+    y, x = np.mgrid[0:n, 0:n]
+    ramp = 2 * np.pi * m * (x if axis == 1 else y) / N
+    i0 = oracle.sh_image(amp, base, N)
+    i1 = oracle.sh_image(amp, base + ramp, N)
+    assert np.max(np.abs(i1 - np.roll(i0, m, axis=axis))) <= 1e-10 * i0.max()
+
+
+def _periodised_gaussian(N, sigma):
+    j = np.arange(N)
+    k = np.zeros(N)
+    for p in range(-6, 7):
+        t = j - p * N
+        k += np.exp(-t * t / (2 * sigma * sigma))
+    return k / (math.sqrt(2 * math.pi) * sigma)
+
+
+@pytest.mark.parametrize("direction,axis", [((1.0, 0.0), 1), ((0.0, 1.0), 0), ((-1.0, 0.0), 1)])
+def test_elongation_is_periodic_gaussian_convolution(direction, axis):
+    n, N, sigma = 8, 32, 2.5
+    rng = np.random.default_rng(3)
+    amp = np.ones((n, n))
+    ph = rng.standard_normal((n, n)) * 0.5
+    plain = oracle.sh_image(amp, ph, N)
+    elong = oracle.sh_image(amp, ph, N, sigma, direction)
+    K = _periodised_gaussian(N, sigma)
+    # circular convolution along the elongation axis
+    ref = np.zeros_like(plain)
+    for s in range(N):
+        ref += K[s] * np.roll(plain, s, axis=axis)
+    assert np.max(np.abs(elong - ref)) <= 1e-8 * plain.max()
+
+
+def test_elongation_direction_symmetry():
+    n, N, sigma = 8, 32, 3.0
+    flat = np.zeros((n, n))
+    amp = np.ones((n, n))
+    d = 1 / math.sqrt(2)
+    a = oracle.sh_image(amp, flat, N, sigma, (d, d))
+    b = oracle.sh_image(amp, flat, N, sigma, (d, -d))
+    assert np.max(np.abs(a - a.T)) <= 1e-9 * a.max()
+    # mirror x -> N-1-x maps the (1,1) streak onto the (1,-1) streak (flat spot centre N/2-1/2)
+    assert np.max(np.abs(b - a[:, ::-1])) <= 1e-9 * a.max()
+    assert not np.allclose(a, b, rtol=1e-3)
+
+
+def test_binning_and_cog():
+    img = np.arange(64.0).reshape(8, 8)
+    out = oracle.bin_image(img, 2)
+    ref = img.reshape(4, 2, 4, 2).sum(axis=(1, 3))
+    assert np.array_equal(out, ref)
+    d = np.zeros((16, 16))
+    d[3, 12] = 5.0
+    sx, sy = oracle.cog(d)
+    assert sx == pytest.approx(12 - 7.5) and sy == pytest.approx(3 - 7.5)
+    assert oracle.cog(np.zeros((8, 8))) == (0.0, 0.0)
+    e = np.zeros((8, 8))
+    e[2, 2] = 1.0
+    e[2, 5] = 3.0
+    sx, sy = oracle.cog(e)
+    assert sx == pytest.approx((1.0 * (2 - 3.5) + 3.0 * (5 - 3.5)) / 4.0)
+    assert sy == pytest.approx(2 - 3.5)
+
+
+def test_cog_antisymmetric_and_linear_in_small_tilt():
+    n, N, b = 8, 32, 2
+    amp = np.ones((n, n))
+    x = np.mgrid[0:n, 0:n][1]
+    res = []
+    for a in (-0.2, -0.1, 0.1, 0.2):  # tilt in FFT bins
+        img = oracle.bin_image(oracle.sh_image(amp, 2 * np.pi * a * x / N, N), b)
+        res.append(oracle.cog(img)[0])
+    assert res[0] == pytest.approx(-res[3], abs=1e-12)
+    assert res[1] == pytest.approx(-res[2], abs=1e-12)
+    # gain close to 1/b detector pixel per FFT bin, linear in the tilt
+    assert res[3] / 0.2 == pytest.approx(1.0 / b, rel=0.15)
+    assert res[3] / res[2] == pytest.approx(2.0, rel=0.01)
+
+
+# ------------------------------------------------------------------------------------------ geometry
+def test_bilinear_affine_exact_and_periodic():
+    n = 40
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    s = 0.3 + 1.7 * x - 0.9 * y
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        fx, fy = rng.uniform(0, n - 1.001, 2)
+        assert oracle.bilinear_periodic(s, fx, fy) == pytest.approx(0.3 + 1.7 * fx - 0.9 * fy, abs=1e-11)
+    r = rng.standard_normal((n, n))
+    assert oracle.bilinear_periodic(r, 5.0, 7.0) == r[7, 5]
+    assert oracle.bilinear_periodic(r, n - 0.5, 3.0) == pytest.approx(0.5 * (r[3, n - 1] + r[3, 0]))
+    assert oracle.bilinear_periodic(r, -1.0, -2.0) == r[n - 2, n - 1]
+
+
+def test_valid_subaps_brute_force():
+    for D, obs, ns, npx, expect in [(8.0, 0.0, 16, 8, None), (39.0, 0.28, 80, 8, None), (39.0, 0.28, 2, 32, 4)]:
+        A = oracle.pupil(D, obs, ns * npx)
+        n = ns * npx
+        cnt = 0
+        for sy in range(ns):
+            for sx in range(ns):
+                inside = 0
+                for yy in range(npx):
+                    yv = (sy * npx + yy - 0.5 * (n - 1)) * (D / n)
+                    xv = (sx * npx + np.arange(npx) - 0.5 * (n - 1)) * (D / n)
+                    r2 = xv * xv + yv * yv
+                    inside += int(np.sum((r2 <= (D / 2) ** 2) & (r2 >= (obs * D / 2) ** 2)))
+                cnt += inside * 2 >= npx * npx
+        c2, vmap, _ = oracle.valid_subaps(A, ns, npx, 0.5)
+        assert c2 == cnt
+        assert np.array_equal(vmap, vmap[::-1, :]) and np.array_equal(vmap, vmap.T)
+        if expect is not None:
+            assert c2 == expect
+
+
+def _small_cfg(alt=5000.0, kind="lgs", theta=(10 * inputs.ARCSEC, -5 * inputs.ARCSEC)):
+    cfg = {
+        "name": "probe", "D": 4.0, "obstruction": 0.0, "lambda_ref": 500e-9, "dt": 0.01, "gain": 0.5,
+        "seed": 3, "noise": False, "psf_every": 1,
+        "wfs": [inputs._wfs(kind, theta, 4, 8, 16, 2, 600e-9, 100.0, height=90e3 if kind == "lgs" else 0.0)],
+        "science": [{"theta": (0.0, 0.0), "lambda": 2.2e-6, "n_px": 32, "pad": 2}],
+        "layers": [{"n": 256, "pixel": 0.125, "alt": alt, "vx": 2.0, "vy": -1.0, "r0": 0.2, "L0": 25.0, "seed": 1}],
+    }
+    cfg["dms"] = [inputs.dm_spec(cfg, 0.0, 0.5, 0.3, nx=9)]
+    return cfg
+
+
+@pytest.mark.parametrize("kind", ["lgs", "ngs"])
+def test_cone_projection_of_linear_layer(kind):
+    cfg = _small_cfg(kind=kind)
+    n = 256
+    X = (np.arange(n) - 0.5 * (n - 1)) * 0.125
+    bx, by = 0.37, -0.21
+    scr = (bx * X[None, :] + by * X[:, None]).astype(np.float32)
+    sim = oracle.Sim(cfg, [scr])
+    sim.k = 3
+    ph = sim.wfs_phase(0)
+    N = 32
+    x = (np.arange(N) - 0.5 * (N - 1)) * (4.0 / N)
+    h, H = 5000.0, 90e3
+    f = 1 - h / H if kind == "lgs" else 1.0
+    th = cfg["wfs"][0]["theta"]
+    t = 3 * 0.01
+    u = x[None, :] * f + h * th[0] + t * 2.0
+    v = x[:, None] * f + h * th[1] + t * -1.0
+    # the screen holds float32-rounded values of the linear function: compare within that rounding
+    ref = bx * u + by * v
+    assert np.max(np.abs(ph - ref)) < 2e-6
+
+
+def test_dm_single_poke_closed_form_and_subtraction():
+    pitch, coup = 0.5, 0.3
+    sig = oracle.if_sigma(pitch, coup)
+    assert math.exp(-pitch ** 2 / (2 * sig ** 2)) == pytest.approx(coup, rel=1e-14)
+    nx = 7
+    Cg = np.zeros((nx, nx))
+    Cg[2, 4] = 1.3
+    n, dx = 30, 0.125
+    S = oracle.dm_surface(Cg, pitch, coup, n, dx)
+    g = (np.arange(n) - 0.5 * (n - 1)) * dx
+    xa, yb = (4 - 3) * pitch, (2 - 3) * pitch
+    ref = 1.3 * np.exp(-((g[None, :] - xa) ** 2 + (g[:, None] - yb) ** 2) / (2 * sig ** 2))
+    assert np.max(np.abs(S - ref)) < 1e-13
+    # subtraction sign: a DM poke lowers the residual phase by the DM surface
+    cfg = _small_cfg(alt=0.0, kind="ngs", theta=(0.0, 0.0))
+    sim = oracle.Sim(cfg, [np.zeros((256, 256), np.float32)])
+    c = np.zeros(sim.n_cmd)
+    c[sim.n_cmd // 2] = 2.0
+    sim.set_commands(c)
+    ph = sim.wfs_phase(0)
+    assert ph.min() < -1.0 and ph.max() <= 1e-15
+
+
+def test_dm_separable_equals_direct_sum_nonsquare():
+    rng = np.random.default_rng(4)
+    nx, ny, pitch, coup, n, dx = 5, 4, 0.6, 0.25, 14, 0.17
+    Cg = rng.standard_normal((ny, nx))
+    S = oracle.dm_surface(Cg, pitch, coup, n, dx)
+    sig = pitch / math.sqrt(2 * math.log(1 / coup))
+    g = (np.arange(n) - 0.5 * (n - 1)) * dx
+    ref = np.zeros((n, n))
+    for b in range(ny):
+        for a in range(nx):
+            xa = (a - 0.5 * (nx - 1)) * pitch
+            yb = (b - 0.5 * (ny - 1)) * pitch
+            for j in range(n):
+                for i in range(n):
+                    ref[j, i] += Cg[b, a] * math.exp(-((g[i] - xa) ** 2 + (g[j] - yb) ** 2) / (2 * sig * sig))
+    assert np.max(np.abs(S - ref)) < 1e-12
+
+
+# ------------------------------------------------------------------------------------------ science
+def test_flat_residual_strehl_one_and_psf_parseval():
+    cfg = inputs.scao_tiny()
+    sim = oracle.Sim(cfg, [np.zeros((256, 256), np.float32)],
+                     np.zeros((inputs.n_commands(cfg), 416), np.float32))
+    sim.step(2)
+    psf, srl, srk = sim.psf()
+    assert srl == pytest.approx(1.0, abs=1e-12) and srk == pytest.approx(1.0, abs=1e-12)
+    assert psf.max() == pytest.approx(1.0, abs=1e-12)
+    M = psf.shape[0]
+    assert np.unravel_index(np.argmax(psf), psf.shape) == (M // 2, M // 2)
+    A = oracle.pupil(8.0, 0.0, 128)
+    assert psf.sum() == pytest.approx(M * M / A.sum(), rel=1e-10)
+
+
+def test_marechal_small_phase():
+    cfg = inputs.scao_tiny()
+    rng = np.random.default_rng(11)
+    sig_sci = 0.1
+    scr = (rng.standard_normal((256, 256)) * sig_sci * (2.2e-6 / 500e-9)).astype(np.float32)
+    sim = oracle.Sim(cfg, [scr], np.zeros((inputs.n_commands(cfg), 416), np.float32))
+    ph = sim.wfs_phase(0) * (500e-9 / 2.2e-6)
+    A = oracle.pupil(8.0, 0.0, 128)
+    p = ph[A > 0]
+    var = np.mean((p - p.mean()) ** 2)
+    sim.step(1)
+    _, srl, _ = sim.psf()
+    assert abs(srl - math.exp(-var)) <= var * var
+    # the exact definition for the same samples
+    assert srl == pytest.approx(abs(np.mean(np.exp(1j * p))) ** 2, rel=1e-12)
+
+
+# ------------------------------------------------------------------------------------------ loop
+def test_integrator_decay_static_dm_aberration():
+    cfg = inputs.scao_tiny()
+    cfg["layers"][0]["vx"] = 0.0
+    zero = [np.zeros((256, 256), np.float32)]
+    sim = oracle.Sim(cfg, zero)
+    n = sim.n_cmd
+    d = 0.05
+    D = np.zeros((sim.n_slopes, n))
+    for j in range(n):
+        c = np.zeros(n)
+        c[j] = d
+        sim.set_commands(c)
+        sp = sim.measure()
+        c[j] = -d
+        sim.set_commands(c)
+        D[:, j] = (sp - sim.measure()) / (2 * d)
+    U, S, Vt = np.linalg.svd(D, full_matrices=False)
+    keep = S > 1e-2 * S[0]
+    R = -(Vt[keep].T / S[keep]) @ U[:, keep].T
+    # target commands in the controlled subspace, small enough for the linear regime
+    rng = np.random.default_rng(8)
+    cstar = Vt[keep].T @ (Vt[keep] @ rng.standard_normal(n)) * 0.01
+    sim.set_commands(cstar)
+    surf = sim.dm_surface(0)
+    scr = np.zeros((256, 256))
+    # the DM grid (132 samples) and the layer (256) share the 0.0625 m pitch and both centre
+    # on the axis, so the DM shape is written into the layer sample for sample
+    off = (256 - 132) // 2
+    scr[off:off + 132, off:off + 132] = surf
+    loop = oracle.Sim(cfg, [scr.astype(np.float32)], R.astype(np.float32))
+    g = cfg["gain"]
+    for k in range(1, 7):
+        loop.step(1)
+        err = np.linalg.norm(loop.commands() - cstar) / np.linalg.norm(cstar)
+        assert err == pytest.approx((1 - g) ** k, abs=2e-3)
+
+
+# ------------------------------------------------------------------------------------------ noise
+@pytest.mark.parametrize("x", [-15.9, -10.0, -3.3, -1.0, -0.25, -1e-3, 0.0])
+def test_exp_f32_accuracy(x):
+    assert oracle.exp_f32(x) == pytest.approx(math.exp(np.float32(x)), rel=4e-7)
+
+
+def test_log_cos_f32_accuracy():
+    rng = np.random.default_rng(1)
+    for u in list(rng.random(300)) + [2 ** -25, 0.5, 0.7071, 0.99999994]:
+        u = float(np.float32(u))
+        assert oracle.log_f32(u) == pytest.approx(math.log(u), rel=4e-7, abs=4e-7)
+        assert oracle.cos2pi_f32(u) == pytest.approx(math.cos(2 * math.pi * u), abs=6e-7)
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.7, 5.0, 15.9, 16.0, 40.0, 250.0])
+def test_poisson_moments(lam):
+    n = 200_000
+    fr = oracle.noise_frame(np.full(n, lam, np.float32), 0.0, 0, 17, 2, 12345)
+    m, v = fr.mean(), fr.var()
+    tol_m = 5 * math.sqrt(max(lam, 1e-3) / n)
+    assert abs(m - lam) <= tol_m + (0.51 if lam >= 16 else 0.0) * 0 + 1e-12
+    if lam > 0:
+        tol_v = 6 * lam * math.sqrt(2.0 / n) + 6 * math.sqrt(lam / n)
+        extra = 1.0 / 12.0 if lam >= 16 else 0.0  # rounding of the normal approximation
+        assert abs(v - (lam + extra)) <= tol_v + 0.05
+    else:
+        assert np.all(fr == 0)
+
+
+def test_read_noise_moments_and_determinism():
+    n = 200_000
+    fr = oracle.noise_frame(np.zeros(n, np.float32), 3.0, 0, 1, 0, 99)
+    assert abs(fr.mean()) < 5 * 3.0 / math.sqrt(n)
+    assert fr.var() == pytest.approx(9.0 + 1.0 / 12.0, rel=0.02)
+    again = oracle.noise_frame(np.zeros(n, np.float32), 3.0, 0, 1, 0, 99)
+    assert np.array_equal(fr, again)
+    other = oracle.noise_frame(np.zeros(n, np.float32), 3.0, 0, 2, 0, 99)
+    assert not np.array_equal(fr, other)
+
+
+def test_philox_counter_and_key_dependence():
+    base = oracle.philox([0, 0, 0, 0], [0, 0])
+    seen = {tuple(base)}
+    for i in range(4):
+        c = [0, 0, 0, 0]
+        c[i] = 1
+        o = oracle.philox(c, [0, 0])
+        # one flipped input bit changes about half of the 128 output bits
+        flips = sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(o, base))
+        assert 40 < flips < 88
+        seen.add(tuple(o))
+    for i in range(2):
+        k = [0, 0]
+        k[i] = 1
+        seen.add(tuple(oracle.philox([0, 0, 0, 0], k)))
+    assert len(seen) == 7
+    # uniformity of the top byte over many counters
+    words = np.array([oracle.philox([i, 5, 6, 0], [7, 8])[i % 4] for i in range(20000)], dtype=np.uint64)
+    hist = np.bincount((words >> 24).astype(np.int64), minlength=256)
+    chi2 = (((hist - 20000 / 256) ** 2) / (20000 / 256)).sum()
+    assert chi2 < 350
+
+
+# ------------------------------------------------------------------------------------------ screens
+def test_screen_structure_function_matches_von_karman_quadrature():
+    from scipy import integrate, special
+    n, pixel, r0, L0 = 512, 0.125, 0.2, 25.0
+    lags = [2, 4, 8, 16]
+    acc = np.zeros(len(lags))
+    seeds = range(6)
+    for sd in seeds:
+        s = inputs.phase_screen(n, pixel, r0, L0, 1000 + sd).astype(np.float64)
+        for i, L in enumerate(lags):
+            acc[i] += 0.5 * (np.mean((s[:, L:] - s[:, :-L]) ** 2) + np.mean((s[L:, :] - s[:-L, :]) ** 2))
+    acc /= len(seeds)
+    for i, L in enumerate(lags):
+        r = L * pixel
+
+        def f(k):
+            return 2 * inputs.von_karman_psd(k, r0, L0) * (1 - special.j0(2 * np.pi * k * r)) * 2 * np.pi * k
+
+        th, _ = integrate.quad(f, 0, np.inf, limit=500)
+        assert acc[i] == pytest.approx(th, rel=0.10)
+        if r / L0 < 0.02:
+            # Kolmogorov limit 6.88 (r/r0)^(5/3) with the leading outer-scale correction
+            assert th == pytest.approx(6.88 * (r / r0) ** (5 / 3), rel=0.35)
