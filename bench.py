@@ -1,0 +1,321 @@
+"""Throughput of the MCAO closed-loop step on GB300 (one JSON line on stdout, rank 0).
+
+Workload: the E-ELT-shaped 6-LGS MCAO step (39 m pupil, 28 % obstruction, six sodium LGS with
+80 x 80 Shack-Hartmann subapertures and 10 km sodium elongation, three 2 x 2 NGS low-order
+sensors, ten 2048^2 frozen-flow layers, three DMs, dense float32 reconstructor
+n_cmd x 55608, on-axis K-band PSF 1280^2 accumulated every step), synthetic seeded inputs.
+
+A "step" is one pass of the whole hot path: DM surfaces, propagation + spot formation +
+centroids for all nine sensors, reconstructor product + integrator, science Strehl and PSF.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mcao|reference]
+
+N > 1 runs under torchrun: each rank advances its own independent realization (replicas, weak
+scaling, no collective on the data path); the time is the maximum over ranks.
+``--impl reference`` times the FP64 CPU oracle on this host's cores on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "6-LGS MCAO loop steps/s, plain FP32 vs batched/BF16, at ≤1% Strehl error"
+UNIT = "steps/s"
+RECON_SIGMA = 1e-4
+
+
+def workload():
+    from paper_1608_00386_gb300 import inputs
+    cfg = inputs.eelt_mcao()
+    screens = inputs.make_screens(cfg)
+    n_cmd = inputs.n_commands(cfg)
+    return cfg, screens, n_cmd
+
+
+def config_block(cfg, n_cmd, n_slopes):
+    dm_counts = [int(d["valid"].sum()) for d in cfg["dms"]]
+    return {
+        "workload": (f"eelt_mcao_6lgs: D=39 m obstr 0.28, 6 LGS 80x80 (8 px, 32^2 FFT, 16^2 det, Na 10 km) + "
+                     f"3 NGS 2x2 (32 px, 64^2 FFT), 10 layers 2048^2, 3 DMs {dm_counts} act, "
+                     f"R {n_cmd}x{n_slopes} fp32, K-band PSF 1280^2 every step"),
+        "n_cmd": n_cmd, "n_slopes": n_slopes, "steps_per_realization": "K",
+        "reconstructor": f"dense fp32, N(0,{RECON_SIGMA:g}) entries (throughput run)",
+        "l2": "inputs larger than L2: the 1.79 GB reconstructor is streamed from HBM every step",
+        "graph": "one CUDA graph per step (3 streams)",
+    }
+
+
+def step_algorithmic_bytes(cfg, recon_bytes):
+    """Bytes one step must move at least: the reconstructor product (R, s, c), the DM surfaces
+    written once, each layer's pupil-sized footprint read once, and the long-exposure PSF
+    accumulator read and written (double)."""
+    dm = sum(4.0 * d["surf_n"] ** 2 for d in cfg["dms"])
+    npup = cfg["wfs"][0]["n_sub"] * cfg["wfs"][0]["n_px"]
+    layers = 4.0 * npup * npup * len(cfg["layers"])
+    psf = sum(16.0 * (s["n_px"] * s["pad"]) ** 2 for s in cfg["science"])
+    return recon_bytes + dm + layers + psf
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recon_traffic():
+    """dram bytes per launch of the reconstructor kernel from the committed ncu summary, or None
+    if the kernel source changed since that capture."""
+    prof = os.path.join(ROOT, "profiles", "recon_gemv_eelt_traffic.json")
+    src = os.path.join(ROOT, "paper_1608_00386_gb300", "csrc", "k_recon.cu")
+    if not os.path.exists(prof):
+        return None
+    d = json.load(open(prof))
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if d.get("k_recon_sha256") != sha:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores, bounded sample of the same workload per step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    from paper_1608_00386_gb300 import inputs
+    cfg, screens, n_cmd = workload()
+    R = inputs.random_reconstructor(n_cmd, 55608, RECON_SIGMA, 3)
+    sim = oracle.Sim(cfg, screens, R)
+    n_slopes = sim.n_slopes
+    for _ in range(max(0, min(args.warmup, 1))):
+        sim.step(1)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max(1, min(args.steps, 3)):
+        sim.step(1)
+        steps += 1
+        if time.perf_counter() - t0 > 30.0:
+            break
+    dt = time.perf_counter() - t0
+    v = steps / dt
+    cores = oracle.num_threads()
+    sample = f"{steps} full steps of the workload (oracle, FP64, OpenMP)"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": steps,
+            "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(cfg, n_cmd, n_slopes),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(cfg, screens, R, budget_s=20.0):
+    import oracle
+    oracle.build()
+    sim = oracle.Sim(cfg, screens, R)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        sim.step(1)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s or steps >= 4:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} full steps of the same workload, FP64 oracle ({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="mcao", choices=["mcao", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1608_00386_gb300 import build, inputs, mcao
+    build.build()
+
+    cfg, screens, n_cmd = workload()
+    cfg = dict(cfg, seed=7 + rank)
+    R = inputs.random_reconstructor(n_cmd, 55608, RECON_SIGMA, 3)
+    # inputs resident in HBM before the timed region
+    d_screens = [torch.from_numpy(s).cuda() for s in screens]
+    d_R = torch.from_numpy(R).cuda()
+    sim = mcao.make_sim(cfg, d_screens, d_R)
+    n_slopes = sim.query(mcao.Q_SLOPES)
+    sim.step(args.warmup)
+    sim.sync()
+
+    clocks = Clocks(local)
+    sim.set_profiling(True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    sim.sync()
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    ck = clocks.stop()
+    ms, cnt, lps = sim.get_profile()
+    sim.set_profiling(False)
+    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    value = ws * args.steps / elapsed
+
+    # dominant kernel roofline (reconstructor product)
+    recon_ms = ms["recon"] / max(1, cnt["recon"])
+    alg_bytes = 4.0 * (n_cmd * n_slopes + n_slopes + 2 * n_cmd)
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (recon_ms * 1e-3) / 1e9
+    step_bytes = step_algorithmic_bytes(cfg, alg_bytes)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": recon_traffic(), "kernel": "recon_gemv_kernel", "peak_source": f"{peak_kind} hbm_gbs",
+            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": recon_ms}
+    step_ms = 1e3 * elapsed / args.steps
+    stage_ms = {k: v / max(1, cnt[k]) for k, v in ms.items()}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(cfg, screens, R, min(args.steps, 200), dist)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(config_block(cfg, n_cmd, n_slopes), parallelism=f"replicas x{ws}"),
+            "roofline": roof,
+            "step_roofline": {"alg_bytes_per_step": step_bytes,
+                              "frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak},
+            "stage_ms": stage_ms, "gpu_launches": int(lps * args.steps), "clocks": ck, "e2e": e2e}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, screens, R)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def measure_e2e(cfg, screens, R, steps, dist):
+    """Same metric through the public API with host buffers: create, load the screens and the
+    reconstructor from pinned host memory, then every step read the commands and the Strehl
+    back to the host; the PSF is read at the end."""
+    import torch
+    from paper_1608_00386_gb300 import mcao
+    p_screens = [torch.from_numpy(s).pin_memory() for s in screens]
+    p_R = torch.from_numpy(R).pin_memory()
+    h_scr = [s.numpy() for s in p_screens]
+    h_R = p_R.numpy()
+    n_cmd = R.shape[0]
+    out = np.empty(n_cmd, np.float32)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    sim = mcao.make_sim(cfg, h_scr, h_R)
+    for _ in range(steps):
+        sim.step(1)
+        sim.commands(out)
+        sim.psf(0, with_image=False)
+    psf, _, _ = sim.psf(0)
+    elapsed = time.perf_counter() - t0
+    sim.close()
+    h2d = sum(s.nbytes for s in screens) + R.nbytes + sum(d["valid"].nbytes for d in cfg["dms"])
+    d2h = n_cmd * 4 + 3 * 8 + 8
+    return {"value": steps / elapsed, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h + psf.nbytes / steps, "steps": steps,
+            "note": "timed: create + loads from pinned host memory + steps with per-step command/Strehl reads + PSF read"}
+
+
+if __name__ == "__main__":
+    main()

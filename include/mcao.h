@@ -1,0 +1,261 @@
+/*
+ * mcao.h -- C ABI of the GB300 MCAO closed-loop step library (libmcao.so).
+ *
+ * The library advances an end-to-end multi-conjugate adaptive optics Monte-Carlo loop one
+ * time step at a time, as described in arXiv:1608.00386 ("The numerical simulation tool for
+ * the MAORY multiconjugate adaptive optics system"):
+ *   - frozen-flow turbulence layers, static screens translated by the wind
+ *     ("The atmospheric layers generation");
+ *   - open-loop wavefront along each guide star by geometric projection, laser guide stars at
+ *     finite distance ("The open loop wave-front measurements");
+ *   - DMs as linear combinations of analytic (Gaussian) influence functions
+ *     ("Influence function and modal base");
+ *   - Shack-Hartmann X/Y slopes of the residual phase (open-loop wavefront minus DMs), the
+ *     slope vector times the control matrix giving differential commands added to the mirror
+ *     shape, pure integrator ("The closed loop");
+ *   - science PSF at a user wavelength and Strehl ratio ("The Point Spread Functions (PSFs)").
+ * Every stage runs in the library's own CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *   - Every call returns mcao_status; no C++ exception crosses the boundary.  On failure the
+ *     handle keeps a message readable with mcao_last_error() until the next failing call.
+ *   - A handle is not thread-safe: use it from one host thread at a time.
+ *   - Arrays are row-major, [y][x] with x fastest.  Phases are in radians at the reference
+ *     wavelength cfg.lambda_ref (500 nm in the shipped configurations); DM surfaces and commands
+ *     use the same unit (wavefront-equivalent radians).
+ *   - Pupil sample i of a grid of n samples across the diameter D sits at (i - (n-1)/2) D/n;
+ *     the pupil amplitude is 1 for obstruction*D/2 <= r <= D/2 and 0 elsewhere.
+ *   - Host pointers are read during the call and not kept, unless a struct says on_device = 1,
+ *     in which case the pointer is a device address that the caller keeps valid until
+ *     mcao_sim_destroy (the library adopts it without copying).
+ *   - Output buffers are host memory of the stated capacity n (in elements); a smaller n gives
+ *     MCAO_E_SHAPE.  mcao_query() returns the element count each getter needs.
+ *   - Work is queued on library-owned CUDA streams.  mcao_set_stream() names a caller stream
+ *     (for example PyTorch's current stream) that every call orders itself after and that
+ *     waits for the call's device work.  Getters synchronise before returning.
+ */
+#ifndef MCAO_H
+#define MCAO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MCAO_OK = 0,
+    MCAO_E_INVALID_ARG = 1,   /* null pointer, non-finite or out-of-range value              */
+    MCAO_E_SHAPE = 2,         /* size or count does not match the configuration             */
+    MCAO_E_STATE = 3,         /* call out of order (e.g. step before every load_*)          */
+    MCAO_E_CUDA = 4,          /* a CUDA runtime call failed; message holds its error string */
+    MCAO_E_OOM = 5,           /* device allocation failed                                   */
+    MCAO_E_TIMEOUT = 6,       /* a bounded device-side wait gave up                         */
+    MCAO_E_UNSUPPORTED = 7    /* valid request that this build has no kernel for            */
+} mcao_status;
+
+enum { MCAO_WFS_NGS = 0, MCAO_WFS_LGS = 1 };
+enum { MCAO_DTYPE_F32 = 0 };
+
+/* One Shack-Hartmann wavefront sensor.  Its pupil grid has n_sub * n_px samples across D.
+ * Each valid subaperture (illuminated fraction >= valid_thr) forms an n_fft x n_fft spot
+ * (zero-padded field, requires n_fft >= 2 n_px), binned n_bin x n_bin into
+ * (n_fft/n_bin)^2 detector pixels.  Sodium elongation (laser stars, na_fwhm > 0): Gaussian of
+ * FWHM b * na_fwhm / height^2 rad along the launch-to-subaperture direction, b that
+ * distance.  Flux: n_photons times the illuminated fraction per frame. */
+typedef struct {
+    int type;                 /* MCAO_WFS_NGS (source at infinity) or MCAO_WFS_LGS           */
+    int n_sub, n_px, n_fft, n_bin;
+    double theta_x, theta_y;  /* direction, rad                                              */
+    double height;            /* laser star height above the telescope, m                    */
+    double lambda;            /* sensing wavelength, m                                        */
+    double n_photons;         /* photons per fully illuminated subaperture per frame         */
+    double read_noise;        /* e- rms per detector pixel                                    */
+    double valid_thr;         /* minimum illuminated fraction                                 */
+    double na_fwhm;           /* sodium layer FWHM thickness, m (0: no elongation)            */
+    double launch_x, launch_y;/* launch position in the pupil, m                             */
+} mcao_wfs;
+
+/* One science direction: n_px pupil samples across D, PSF FFT of pad * n_px points (pixel
+ * lambda / (pad D)), on-axis Strehl |sum A e^{i phi}|^2 / (sum A)^2 every step. */
+typedef struct {
+    int n_px, pad;
+    double theta_x, theta_y;  /* rad                                                          */
+    double lambda;            /* m                                                            */
+} mcao_science;
+
+typedef struct {
+    size_t struct_size;       /* sizeof(mcao_config), checked                                 */
+    double D;                 /* telescope diameter, m                                        */
+    double obstruction;       /* central obstruction, fraction of D                           */
+    double lambda_ref;        /* wavelength of the phase unit, m                              */
+    double dt;                /* loop period, s                                               */
+    double gain;              /* integrator gain g in c <- c + g R s                          */
+    uint64_t seed;            /* Philox key of the detector noise                             */
+    int noise;                /* 1: photon + read noise on the detector frames                */
+    int psf_every;            /* accumulate the PSF every psf_every steps (0: never)          */
+    int keep_frames;          /* 1: keep the last step's intensities and frames (tests)       */
+    int n_wfs;
+    const mcao_wfs* wfs;
+    int n_sci;
+    const mcao_science* sci;
+} mcao_config;
+
+/* A periodic n x n phase screen with square samples of pixel_m metres, at altitude alt_m,
+ * moving so that step k samples it shifted by (k dt)(vx, vy) metres. */
+typedef struct {
+    int n;
+    double pixel_m, alt_m, vx, vy;
+    const float* phase;       /* [n][n] rad at lambda_ref                                     */
+    int on_device;
+} mcao_layer;
+
+/* A DM conjugated at alt_m: nx * ny actuators at pitch_m (actuator a at
+ * (a - (nx-1)/2) pitch), Gaussian influence functions with g(pitch) = coupling; the surface is
+ * held on a surf_n x surf_n grid of pitch surf_dx centred on the axis and sampled bilinearly
+ * (indices clamped to the grid).  Commands of the valid actuators, in row-major order, form
+ * this DM's block of the command vector; blocks follow the DM order. */
+typedef struct {
+    double alt_m, pitch_m, coupling;
+    int nx, ny;
+    const uint8_t* valid;     /* [ny][nx] host array, nonzero = valid actuator                */
+    int surf_n;
+    double surf_dx;
+} mcao_dm;
+
+typedef struct mcao_sim mcao_sim;
+
+/* What mcao_query() sizes. */
+typedef enum {
+    MCAO_Q_SLOPES = 0,        /* length of the slope vector                                   */
+    MCAO_Q_COMMANDS = 1,      /* length of the command vector (after mcao_load_dms)           */
+    MCAO_Q_VALID = 2,         /* valid subapertures of WFS `index`                            */
+    MCAO_Q_FRAME = 3,         /* detector pixels of WFS `index` (valid subaps x n_det^2)      */
+    MCAO_Q_WFS_PHASE = 4,     /* pupil samples of WFS `index`                                 */
+    MCAO_Q_DM_SURFACE = 5,    /* surface samples of DM `index`                                */
+    MCAO_Q_PSF = 6,           /* PSF pixels of science direction `index`                      */
+    MCAO_Q_STATE = 7          /* bytes of a checkpoint                                        */
+} mcao_query_kind;
+
+/* Create a simulation for a configuration ("Numerical Simulation Tool": the high-level system
+ * configuration).  Validates it, derives pupils and valid subapertures, allocates device
+ * state.  *out receives the handle (NULL on failure).  Errors: MCAO_E_INVALID_ARG,
+ * MCAO_E_UNSUPPORTED (no kernel for a WFS shape), MCAO_E_CUDA, MCAO_E_OOM. */
+mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out);
+
+/* Free every device and host resource of the handle (NULL is accepted). */
+mcao_status mcao_sim_destroy(mcao_sim* sim);
+
+/* Message of the last failing call on this handle ("" if none); valid until the next call. */
+const char* mcao_last_error(const mcao_sim* sim);
+
+/* Message of the last mcao_sim_create failure in this thread. */
+const char* mcao_create_error(void);
+
+/* Order every later call after work queued on `stream` (a cudaStream_t, NULL = legacy
+ * default stream) and make that stream wait for each call's device work. */
+mcao_status mcao_set_stream(mcao_sim* sim, void* stream);
+
+/* Load the turbulence layers ("The atmospheric layers generation"): copies each screen to the
+ * device (or adopts it when on_device = 1).  Replaces previously loaded layers.  Errors:
+ * MCAO_E_INVALID_ARG (n < 2, pixel <= 0, null phase), MCAO_E_OOM, MCAO_E_CUDA. */
+mcao_status mcao_load_atmosphere(mcao_sim* sim, int n_layers, const mcao_layer* layers);
+
+/* Load the DMs ("Influence function and modal base"): actuator maps, influence-function
+ * tables and surface buffers; resets the commands to zero.  Errors: MCAO_E_INVALID_ARG,
+ * MCAO_E_OOM, MCAO_E_CUDA. */
+mcao_status mcao_load_dms(mcao_sim* sim, int n_dms, const mcao_dm* dms);
+
+/* Load the control matrix R [n_cmd][n_slopes] (row-major float32) and the reference slopes
+ * s_ref [n_slopes] (NULL = zeros) ("Control Matrix"; "The calibration of the interaction
+ * matrices": reference slope vector).  The library keeps its own copy in a padded layout.
+ * on_device = 1: R and s_ref are device addresses.  Errors: MCAO_E_STATE (DMs not loaded),
+ * MCAO_E_SHAPE (n_cmd or n_slopes differ from the configuration), MCAO_E_UNSUPPORTED
+ * (dtype other than MCAO_DTYPE_F32), MCAO_E_OOM, MCAO_E_CUDA. */
+mcao_status mcao_load_reconstructor(mcao_sim* sim, int n_cmd, int n_slopes, const float* R,
+                                    const float* s_ref, int dtype, int on_device);
+
+/* Advance the closed loop n_steps steps ("The closed loop"): for step k, DM surfaces from
+ * c_k, residual phase along every guide star, Shack-Hartmann frames (photon and read noise if
+ * enabled), centre-of-gravity slopes s_k minus s_ref, science Strehl (and PSF every psf_every
+ * steps), then c_{k+1} = c_k + gain R s_k.  Asynchronous: returns once the work is queued.
+ * Errors: MCAO_E_STATE (a load_* missing), MCAO_E_INVALID_ARG (n_steps < 0), MCAO_E_CUDA. */
+mcao_status mcao_step(mcao_sim* sim, int n_steps);
+
+/* Wait for all queued work of the handle. */
+mcao_status mcao_sync(mcao_sim* sim);
+
+/* Element count (bytes for MCAO_Q_STATE) a getter needs; index selects the WFS, DM or
+ * science direction.  Errors: MCAO_E_INVALID_ARG (bad kind or index), MCAO_E_STATE. */
+mcao_status mcao_query(const mcao_sim* sim, int kind, int index, size_t* n);
+
+/* Number of completed steps. */
+mcao_status mcao_get_step_index(mcao_sim* sim, int64_t* k);
+
+/* Last slopes s_k (pixels, reference subtracted): for each WFS in order, the x slopes of its
+ * valid subapertures in row-major subaperture order, then their y slopes. */
+mcao_status mcao_get_slopes(mcao_sim* sim, float* out, size_t n);
+
+/* Current commands c (after the last step's update). */
+mcao_status mcao_get_commands(mcao_sim* sim, float* out, size_t n);
+
+/* Overwrite the commands (calibration pokes, tests). */
+mcao_status mcao_set_commands(mcao_sim* sim, const float* in, size_t n);
+
+/* Row-major subaperture index sy*n_sub+sx of every valid subaperture of WFS `wfs`. */
+mcao_status mcao_get_valid(mcao_sim* sim, int wfs, int32_t* out, size_t n);
+
+/* Residual phase of WFS `wfs` on its full pupil grid at the current step index and commands
+ * (layers minus DMs, radians at lambda_ref), evaluated by the propagation kernel. */
+mcao_status mcao_get_wfs_phase(mcao_sim* sim, int wfs, float* out, size_t n);
+
+/* Surface of DM `dm` for the current commands (radians at lambda_ref). */
+mcao_status mcao_get_dm_surface(mcao_sim* sim, int dm, float* out, size_t n);
+
+/* Last step's detector data of WFS `wfs`, [valid subap][n_det][n_det]: noise-free expected
+ * photo-electrons lambda (float) and, with noise on, the integer frames.  Needs
+ * keep_frames = 1 (else MCAO_E_STATE).  Either pointer may be NULL. */
+mcao_status mcao_get_frames(mcao_sim* sim, int wfs, float* lambda, int32_t* frames, size_t n);
+
+/* Long-exposure PSF of science direction `sci` ([pad n_px]^2, centred, divided by the
+ * diffraction-limited peak and by the number of accumulated frames, so a perfect wavefront
+ * peaks at 1), the long-exposure Strehl (mean of the per-step on-axis Strehl) and the last
+ * step's Strehl.  out may be NULL to read only the Strehl values. */
+mcao_status mcao_get_psf(mcao_sim* sim, int sci, double* out, size_t n, double* sr_long,
+                         double* sr_last);
+
+/* Reset the PSF and Strehl accumulators (for example after a convergence period). */
+mcao_status mcao_reset_psf(mcao_sim* sim);
+
+/* Checkpoint: step index, commands, last slopes, PSF and Strehl accumulators.  Noise is
+ * counter-based on (seed, step, WFS, pixel), so resuming from a checkpoint reproduces the
+ * same frames.  buf needs mcao_query(MCAO_Q_STATE) bytes. */
+mcao_status mcao_get_state(mcao_sim* sim, void* buf, size_t n);
+mcao_status mcao_set_state(mcao_sim* sim, const void* buf, size_t n);
+
+/* Stages timed by the profiler. */
+enum {
+    MCAO_STAGE_DM = 0,          /* DM surfaces                                                  */
+    MCAO_STAGE_WFS_MAIN = 1,    /* wavefront-sensor kernel of the largest group (laser stars)   */
+    MCAO_STAGE_WFS_AUX = 2,     /* other wavefront-sensor kernels (concurrent stream)           */
+    MCAO_STAGE_RECON = 3,       /* reconstructor product R s                                    */
+    MCAO_STAGE_RECON_REDUCE = 4,/* partial-sum reduction and integrator                         */
+    MCAO_STAGE_SCIENCE = 5,     /* science field, Strehl and PSF (concurrent stream)            */
+    MCAO_N_STAGES = 6
+};
+
+/* Profiling on: every later mcao_step records a CUDA event pair around each stage of each
+ * step, on the stream that stage runs on.  Off (default): no events are kept. */
+mcao_status mcao_set_profiling(mcao_sim* sim, int on);
+
+/* Synchronise and return, per stage, the summed device milliseconds and the number of timed
+ * steps since profiling was switched on or last read; launches_per_step receives the number
+ * of kernel launches of one step.  Any pointer may be NULL.  Resets the records. */
+mcao_status mcao_get_profile(mcao_sim* sim, double* ms, int64_t* counts, int n_stages,
+                             int64_t* launches_per_step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCAO_H */

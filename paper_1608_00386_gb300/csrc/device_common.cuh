@@ -1,0 +1,334 @@
+// Device helpers shared by the wavefront-sensor and science kernels: cone-beam sampling of
+// layers and DM surfaces, in-shared-memory Stockham FFT stages, and the detector-noise sampler.
+#pragma once
+
+#include <stdint.h>
+
+#include "mcao_internal.h"
+
+namespace mcao {
+
+// ---------------------------------------------------------------------------------------------
+// Geometric propagation ("The open loop wave-front measurements" of arXiv:1608.00386: geometric
+// projection of each layer, laser guide star at finite distance).  A pupil point x seen along
+// direction theta from a source at height H crosses altitude h at x (1 - h/H) + h theta
+// (H infinite for natural stars); layers move by (k dt) v.  For a tile of pupil samples with
+// origin (i0, j0) the grid index of sample (i0 + x, j0 + y) is base + frac + x * step, where the
+// origin part is evaluated in double once per tile and the in-tile offset in float.
+// ---------------------------------------------------------------------------------------------
+struct Coef {
+    const float* data;
+    int n, periodic;
+    int bx, by;          // integer part of the origin's grid index (wrapped for layers)
+    float fx, fy;        // fractional part, in [0, 1)
+    float step;          // grid samples per pupil sample
+    float sign;          // +1 layer, -1 DM
+};
+
+__device__ __forceinline__ Coef make_coef(const GridDev& g, double N, double dxp, double thx,
+                                          double thy, double H, double t, int i0, int j0) {
+    Coef c;
+    double f = (H > 0.0) ? 1.0 - g.alt / H : 1.0;
+    double u0 = ((double)i0 - 0.5 * (N - 1.0)) * dxp * f + g.alt * thx + t * g.vx;
+    double v0 = ((double)j0 - 0.5 * (N - 1.0)) * dxp * f + g.alt * thy + t * g.vy;
+    double gx = u0 / g.pixel + 0.5 * (double)(g.n - 1);
+    double gy = v0 / g.pixel + 0.5 * (double)(g.n - 1);
+    double flx = floor(gx), fly = floor(gy);
+    long long ix = (long long)flx, iy = (long long)fly;
+    if (g.periodic) {
+        ix %= g.n; if (ix < 0) ix += g.n;
+        iy %= g.n; if (iy < 0) iy += g.n;
+    }
+    c.data = g.data;
+    c.n = g.n;
+    c.periodic = g.periodic;
+    c.bx = (int)ix;
+    c.by = (int)iy;
+    c.fx = (float)(gx - flx);
+    c.fy = (float)(gy - fly);
+    c.step = (float)(dxp * f / g.pixel);
+    c.sign = g.sign;
+    return c;
+}
+
+// bilinear sample of one grid at in-tile offset (x, y); periodic wrap for layers, index clamp
+// into [0, n-1] for DM surfaces
+__device__ __forceinline__ float sample_coef(const Coef& c, float x, float y) {
+    float px = fmaf(x, c.step, c.fx), py = fmaf(y, c.step, c.fy);
+    float flx = floorf(px), fly = floorf(py);
+    float tx = px - flx, ty = py - fly;
+    int ix = c.bx + (int)flx, iy = c.by + (int)fly;
+    int n = c.n;
+    int ix1, iy1;
+    if (c.periodic) {
+        while (ix >= n) ix -= n;
+        while (iy >= n) iy -= n;
+        ix1 = (ix + 1 == n) ? 0 : ix + 1;
+        iy1 = (iy + 1 == n) ? 0 : iy + 1;
+    } else {
+        if (ix < 0) { ix = 0; tx = 0.0f; } else if (ix >= n - 1) { ix = n - 2; tx = 1.0f; }
+        if (iy < 0) { iy = 0; ty = 0.0f; } else if (iy >= n - 1) { iy = n - 2; ty = 1.0f; }
+        ix1 = ix + 1;
+        iy1 = iy + 1;
+    }
+    const float* r0 = c.data + (long long)iy * n;
+    const float* r1 = c.data + (long long)iy1 * n;
+    float a = __ldg(r0 + ix), b = __ldg(r0 + ix1), d = __ldg(r1 + ix), e = __ldg(r1 + ix1);
+    float top = fmaf(tx, b - a, a);
+    float bot = fmaf(tx, e - d, d);
+    return c.sign * fmaf(ty, bot - top, top);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Stockham autosort FFT stage in shared memory (forward, exp(-2 pi i ...)), batched.
+// Stage with radix R and current sub-transform length ns: for j < N/R, inputs
+// src[j + r N/R], twiddle exp(-2 pi i r (j mod ns) / (ns R)), R-point DFT, outputs to
+// dst[(j/ns) ns R + (j mod ns) + r ns].  W holds exp(-2 pi i m / N), m < N.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+template <int R>
+__device__ __forceinline__ void small_dft(float2* v);
+
+template <>
+__device__ __forceinline__ void small_dft<2>(float2* v) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void small_dft<4>(float2* v) {
+    float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    float2 a2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+    float2 a3 = make_float2(d.y, -d.x);  // -i (v1 - v3)
+    v[0] = cadd(a0, a2);
+    v[2] = csub(a0, a2);
+    v[1] = cadd(a1, a3);
+    v[3] = csub(a1, a3);
+}
+
+template <>
+__device__ __forceinline__ void small_dft<3>(float2* v) {
+    const float c = -0.5f, s = -0.866025403784438647f;  // exp(-2 pi i / 3)
+    float2 a = v[0], b = v[1], d = v[2];
+    float2 sum = cadd(b, d), dif = csub(b, d);
+    v[0] = cadd(a, sum);
+    float2 m = make_float2(a.x + c * sum.x, a.y + c * sum.y);
+    float2 rot = make_float2(-s * dif.y, s * dif.x);  // i s (b - d)
+    v[1] = cadd(m, rot);
+    v[2] = csub(m, rot);
+}
+
+template <>
+__device__ __forceinline__ void small_dft<5>(float2* v) {
+    // exp(-2 pi i q / 5), q = 0..4
+    const float cr[5] = {1.0f, 0.309016994374947424f, -0.809016994374947424f, -0.809016994374947424f,
+                         0.309016994374947424f};
+    const float ci[5] = {0.0f, -0.951056516295153572f, -0.587785252292473129f, 0.587785252292473129f,
+                         0.951056516295153572f};
+    float2 in[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) in[q] = v[q];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            int m = (q * r) % 5;
+            acc.x += in[q].x * cr[m] - in[q].y * ci[m];
+            acc.y += in[q].x * ci[m] + in[q].y * cr[m];
+        }
+        v[r] = acc;
+    }
+}
+
+// One stage for `batch` transforms of length N; transform f starts at f * fstride and its
+// element e sits at e * estride (both in float2 units).
+template <int R>
+__device__ __forceinline__ void stockham_stage(const float2* src, float2* dst, int N, int ns, int batch,
+                                               int fstride, int estride, const float2* W, int tid,
+                                               int nthr) {
+    const int NR = N / R;
+    const int twstep = N / (ns * R);
+    for (int idx = tid; idx < batch * NR; idx += nthr) {
+        int f = idx / NR, j = idx - f * NR;
+        const float2* s = src + (long long)f * fstride;
+        float2* d = dst + (long long)f * fstride;
+        int k = j % ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[(j + r * NR) * estride];
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], W[(r * k * twstep) % N]);
+        small_dft<R>(v);
+        int base = (j / ns) * ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[(base + r * ns) * estride] = v[r];
+    }
+}
+
+// Full transform through the radix list; returns the buffer holding the result (a or b).
+// Every stage is followed by a block-wide barrier.
+__device__ __forceinline__ float2* stockham_fft(float2* a, float2* b, int N, const int* radices,
+                                                int n_radices, int batch, int fstride, int estride,
+                                                const float2* W, int tid, int nthr) {
+    int ns = 1;
+    float2* src = a;
+    float2* dst = b;
+    for (int q = 0; q < n_radices; ++q) {
+        int R = radices[q];
+        if (R == 4) stockham_stage<4>(src, dst, N, ns, batch, fstride, estride, W, tid, nthr);
+        else if (R == 2) stockham_stage<2>(src, dst, N, ns, batch, fstride, estride, W, tid, nthr);
+        else if (R == 5) stockham_stage<5>(src, dst, N, ns, batch, fstride, estride, W, tid, nthr);
+        else stockham_stage<3>(src, dst, N, ns, batch, fstride, estride, W, tid, nthr);
+        __syncthreads();
+        ns *= R;
+        float2* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Detector noise.  Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by the
+// seed, counter (pixel, step, WFS, 0); float sampler with a fixed operation order written with
+// round-to-nearest intrinsics (never contracted), so one float intensity maps to one integer:
+//   lambda < 16: Poisson by inversion, p0 = exp(-lambda), p_{k+1} = p_k lambda / (k+1), smallest
+//                k with u <= F_k (k <= 64), u from word 0;
+//   lambda >= 16: max(0, rint(lambda + sqrt(lambda) z)), z = Box-Muller(words 0, 1);
+//   read noise rint(sigma z'), z' = Box-Muller(words 2, 3).
+// exp: Cody-Waite reduction by ln 2 (two-part constant) and a degree-7 Taylor polynomial; log:
+// mantissa in [sqrt(1/2), sqrt(2)) and the atanh series to s^9; cos(2 pi u): octant reduction
+// and Taylor polynomials of sin / cos on [-pi/4, pi/4].
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        if (r < 9) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
+}
+
+__device__ __forceinline__ float nz_uniform(uint32_t w) {
+    return __fmul_rn(__fadd_rn(__uint2float_rn(w >> 8), 0.5f), 5.9604644775390625e-8f);
+}
+
+__device__ __forceinline__ float nz_exp(float x) {
+    float kf = rintf(__fmul_rn(x, 1.44269502f));
+    float r = __fmaf_rn(-kf, 0.693145752f, x);
+    r = __fmaf_rn(-kf, 1.42860677e-06f, r);
+    float p = 1.98412701e-04f;            // 1/5040
+    p = __fmaf_rn(p, r, 1.38888892e-03f); // 1/720
+    p = __fmaf_rn(p, r, 8.33333377e-03f); // 1/120
+    p = __fmaf_rn(p, r, 4.16666679e-02f); // 1/24
+    p = __fmaf_rn(p, r, 1.66666672e-01f); // 1/6
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    int k = (int)kf;
+    if (k < -126) return 0.0f;
+    return __fmul_rn(p, __uint_as_float((uint32_t)(k + 127) << 23));
+}
+
+__device__ __forceinline__ float nz_log(float u) {
+    uint32_t b = __float_as_uint(u);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+    if (m > 1.41421356f) {
+        m = __fmul_rn(m, 0.5f);
+        e += 1;
+    }
+    float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    float s2 = __fmul_rn(s, s);
+    float p = 1.11111112e-01f;              // 1/9
+    p = __fmaf_rn(p, s2, 1.42857149e-01f);  // 1/7
+    p = __fmaf_rn(p, s2, 2.00000003e-01f);  // 1/5
+    p = __fmaf_rn(p, s2, 3.33333343e-01f);  // 1/3
+    p = __fmaf_rn(p, s2, 1.0f);
+    float lm = __fmul_rn(__fmul_rn(2.0f, s), p);
+    float ef = (float)e;
+    return __fmaf_rn(ef, 0.693145752f, __fmaf_rn(ef, 1.42860677e-06f, lm));
+}
+
+__device__ __forceinline__ float nz_sin_poly(float y) {
+    float y2 = __fmul_rn(y, y);
+    float p = 2.75573188e-06f;               // 1/362880
+    p = __fmaf_rn(p, y2, -1.98412701e-04f);  // -1/5040
+    p = __fmaf_rn(p, y2, 8.33333377e-03f);   // 1/120
+    p = __fmaf_rn(p, y2, -1.66666672e-01f);  // -1/6
+    return __fmaf_rn(__fmul_rn(p, y2), y, y);
+}
+
+__device__ __forceinline__ float nz_cos_poly(float y) {
+    float y2 = __fmul_rn(y, y);
+    float p = 2.48015876e-05f;               // 1/40320
+    p = __fmaf_rn(p, y2, -1.38888892e-03f);  // -1/720
+    p = __fmaf_rn(p, y2, 4.16666679e-02f);   // 1/24
+    p = __fmaf_rn(p, y2, -0.5f);
+    return __fmaf_rn(p, y2, 1.0f);
+}
+
+__device__ __forceinline__ float nz_cos2pi(float u) {
+    const float twopi = 6.28318548f;
+    float t = fabsf(__fsub_rn(u, rintf(u)));
+    if (t <= 0.125f) return nz_cos_poly(__fmul_rn(t, twopi));
+    if (t <= 0.375f) return nz_sin_poly(__fmul_rn(__fsub_rn(0.25f, t), twopi));
+    return -nz_cos_poly(__fmul_rn(__fsub_rn(0.5f, t), twopi));
+}
+
+__device__ __forceinline__ float nz_box_muller(float u0, float u1) {
+    float rad = __fsqrt_rn(__fmul_rn(-2.0f, nz_log(u0)));
+    return __fmul_rn(rad, nz_cos2pi(u1));
+}
+
+__device__ __forceinline__ int noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1,
+                                            uint32_t c2, unsigned long long seed) {
+    uint32_t w[4] = {c0, c1, c2, 0u};
+    philox4x32_10(w, (uint32_t)seed, (uint32_t)(seed >> 32));
+    int n;
+    if (lam < 16.0f) {
+        float u = nz_uniform(w[0]);
+        float p = nz_exp(-lam), F = p;
+        int k = 0;
+        while (F < u && k < 64) {
+            k += 1;
+            p = __fdiv_rn(__fmul_rn(p, lam), (float)k);
+            F = __fadd_rn(F, p);
+        }
+        n = k;
+    } else {
+        float z = nz_box_muller(nz_uniform(w[0]), nz_uniform(w[1]));
+        float v = __fmaf_rn(__fsqrt_rn(lam), z, lam);
+        n = __float2int_rn(v);
+        if (n < 0) n = 0;
+    }
+    if (read_noise > 0.0f) {
+        float z2 = nz_box_muller(nz_uniform(w[2]), nz_uniform(w[3]));
+        n += __float2int_rn(__fmul_rn(read_noise, z2));
+    }
+    return n;
+}
+
+// warp sum
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace mcao

@@ -1,0 +1,167 @@
+// Science path ("The Point Spread Functions (PSFs)" of arXiv:1608.00386: PSF at a user
+// wavelength and pixel scale computed on the GPU; Strehl ratio from the PSF or the residual):
+//   field E = A exp(i (lambda_ref / lambda) phi) along the science direction (source at
+//   infinity), on-axis Strehl |sum E|^2 / (sum A)^2 every step, and every psf_every steps the
+//   long-exposure PSF += |FFT2(E zero-padded to M x M)|^2 accumulated in double.
+// The 2-D FFT runs as two passes of batched radix-4/5/2 Stockham FFTs in shared memory: rows of
+// the field (zero-padded) written transposed, then rows of the transposed array; the PSF
+// accumulator is therefore held transposed and unshifted, [kx][ky] (the host reorders it).
+#include "device_common.cuh"
+#include "mcao_internal.h"
+
+namespace mcao {
+
+namespace {
+
+constexpr int kRowsPerBlock = 4;
+
+__global__ void __launch_bounds__(256) sci_field_kernel(SciLaunch L) {
+    __shared__ Coef s_cf[8][kMaxEntries];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = L.N / 8;
+    const int tile = blockIdx.x * 8 + warp;
+    if (tile >= tiles_x * tiles_x) return;
+    const int i0 = (tile % tiles_x) * 8, j0 = (tile / tiles_x) * 8;
+    Coef* cf = s_cf[warp];
+    if (lane < L.ctx.n_grids) {
+        double t = (double)L.ctx.st->k * L.ctx.dt;
+        cf[lane] = make_coef(L.ctx.grids[lane], (double)L.N, L.dx, L.theta_x, L.theta_y, 0.0, t, i0, j0);
+    }
+    __syncwarp();
+    float sr = 0.0f, si = 0.0f;
+    for (int q = lane; q < 64; q += 32) {
+        int x = q % 8, y = q / 8;
+        float phi = 0.0f;
+        for (int g = 0; g < L.ctx.n_grids; ++g) phi += sample_coef(cf[g], (float)x, (float)y);
+        float a = __ldg(L.amp + (long long)(j0 + y) * L.N + i0 + x);
+        float sn, cs;
+        sincosf(L.scale * phi, &sn, &cs);
+        float2 e = make_float2(a * cs, a * sn);
+        L.field[(long long)(j0 + y) * L.N + i0 + x] = e;
+        sr += e.x;
+        si += e.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) L.sr_part[tile] = make_float2(sr, si);
+}
+
+__device__ __forceinline__ bool psf_step(const SciLaunch& L) {
+    return L.psf_every > 0 && (L.ctx.st->k % L.psf_every) == 0;
+}
+
+__global__ void __launch_bounds__(256) sci_rows_kernel(SciLaunch L) {
+    extern __shared__ float4 smem_raw[];
+    float2* A = reinterpret_cast<float2*>(smem_raw);
+    float2* B = A + kRowsPerBlock * L.M;
+    float2* W = B + kRowsPerBlock * L.M;
+    double* red = reinterpret_cast<double*>(W + L.M);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+
+    if (blockIdx.x == 0) {
+        // Strehl of this step from the field partial sums (fixed order, double)
+        double sr = 0.0, si = 0.0;
+        for (int q = tid; q < L.n_tiles; q += nthr) {
+            float2 p = L.sr_part[q];
+            sr += p.x;
+            si += p.y;
+        }
+        red[tid] = sr;
+        red[nthr + tid] = si;
+        __syncthreads();
+        for (int o = nthr / 2; o > 0; o >>= 1) {
+            if (tid < o) {
+                red[tid] += red[tid + o];
+                red[nthr + tid] += red[nthr + tid + o];
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            double s = (red[0] * red[0] + red[nthr] * red[nthr]) / (L.sum_amp * L.sum_amp);
+            L.acc->sr_sum += s;
+            L.acc->sr_last = s;
+            L.acc->n_sr += 1;
+        }
+        __syncthreads();
+    }
+    if (!psf_step(L)) return;
+
+    const int row0 = blockIdx.x * kRowsPerBlock;
+    for (int q = tid; q < L.M; q += nthr) W[q] = L.w[q];
+    for (int q = tid; q < kRowsPerBlock * L.M; q += nthr) {
+        int r = q / L.M, c = q - r * L.M;
+        int row = row0 + r;
+        A[q] = (row < L.N && c < L.N) ? L.field[(long long)row * L.N + c] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    float2* R = stockham_fft(A, B, L.M, L.radices, L.n_radices, kRowsPerBlock, L.M, 1, W, tid, nthr);
+    // transposed store: ft[c][row], four consecutive rows per column
+    for (int q = tid; q < kRowsPerBlock * L.M; q += nthr) {
+        int c = q / kRowsPerBlock, r = q - c * kRowsPerBlock;
+        int row = row0 + r;
+        if (row < L.N) L.ft[(long long)c * L.N + row] = R[r * L.M + c];
+    }
+}
+
+__global__ void __launch_bounds__(256) sci_cols_kernel(SciLaunch L) {
+    if (!psf_step(L)) return;
+    extern __shared__ float4 smem_raw[];
+    float2* A = reinterpret_cast<float2*>(smem_raw);
+    float2* B = A + kRowsPerBlock * L.M;
+    float2* W = B + kRowsPerBlock * L.M;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int c0 = blockIdx.x * kRowsPerBlock;
+    for (int q = tid; q < L.M; q += nthr) W[q] = L.w[q];
+    for (int q = tid; q < kRowsPerBlock * L.M; q += nthr) {
+        int r = q / L.M, j = q - r * L.M;
+        A[q] = (j < L.N) ? L.ft[(long long)(c0 + r) * L.N + j] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    float2* R = stockham_fft(A, B, L.M, L.radices, L.n_radices, kRowsPerBlock, L.M, 1, W, tid, nthr);
+    for (int q = tid; q < kRowsPerBlock * L.M; q += nthr) {
+        int r = q / L.M, j = q - r * L.M;
+        float2 v = R[q];
+        double p = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        L.psf_t[(long long)(c0 + r) * L.M + j] += p;
+    }
+    if (blockIdx.x == 0 && tid == 0) L.acc->n_psf += 1;
+}
+
+size_t fft_smem_bytes(int M) {
+    return sizeof(float2) * (2 * kRowsPerBlock * (size_t)M + M) + sizeof(double) * 2 * 256;
+}
+
+cudaError_t set_smem(const void* fn, size_t bytes) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+cudaError_t launch_sci_field(const SciLaunch& L, cudaStream_t s) {
+    int tiles = (L.N / 8) * (L.N / 8);
+    sci_field_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t sci_prepare(int M) {
+    size_t sm = fft_smem_bytes(M);
+    cudaError_t e = set_smem((const void*)sci_rows_kernel, sm);
+    if (e != cudaSuccess) return e;
+    return set_smem((const void*)sci_cols_kernel, sm);
+}
+
+size_t sci_smem_bytes(int M) { return fft_smem_bytes(M); }
+
+cudaError_t launch_sci_rows(const SciLaunch& L, cudaStream_t s) {
+    size_t sm = fft_smem_bytes(L.M);
+    sci_rows_kernel<<<(unsigned)((L.N + kRowsPerBlock - 1) / kRowsPerBlock), 256, sm, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sci_cols(const SciLaunch& L, cudaStream_t s) {
+    size_t sm = fft_smem_bytes(L.M);
+    sci_cols_kernel<<<(unsigned)(L.M / kRowsPerBlock), 256, sm, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace mcao

@@ -1,0 +1,1213 @@
+// Host side of libmcao: the C ABI declared in include/mcao.h.  Validates the configuration,
+// derives geometry (pupils, valid subapertures, elongation, influence-function tables), owns the
+// device state, and issues one closed-loop step as a CUDA graph with three branches:
+//   s0: DM surfaces -> main WFS kernel -> reconstructor product -> reduction/integrator
+//   s1: other WFS kernels (joined before the reconstructor)
+//   s2: science field, row FFT (+ Strehl), column FFT (+ PSF accumulation)
+// Every stage is a kernel of this library (k_dm.cu, k_wfs.cu, k_recon.cu, k_science.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mcao.h"
+#include "mcao_internal.h"
+
+using namespace mcao;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Group {                 // WFSs sharing one kernel variant
+    int n_px, n_fft, n_bin;
+    std::vector<int> wfs;
+    SubapDev* d_subaps = nullptr;
+    int n_subaps = 0;
+};
+
+struct Science {
+    mcao_science p;
+    int N, M;
+    double dx, sum_amp;
+    float* d_amp = nullptr;
+    float2* d_field = nullptr;
+    float2* d_ft = nullptr;
+    double* d_psf_t = nullptr;
+    float2* d_sr_part = nullptr;
+    float2* d_w = nullptr;
+    int n_tiles;
+    std::vector<int> radices;
+};
+
+struct WfsHost {
+    mcao_wfs p;
+    int N, n_det, n_valid, slope0, frame0;
+    double dx;
+    std::vector<float> amp;
+    std::vector<int> valid;        // subaperture index sy*n_sub+sx
+    std::vector<double> frac;
+    std::vector<SubapDev> subaps;
+};
+
+// profiling stages
+enum { ST_DM = 0, ST_WFS_MAIN, ST_WFS_AUX, ST_RECON, ST_REDUCE, ST_SCIENCE, ST_COUNT };
+
+}  // namespace
+
+struct mcao_sim {
+    mcao_config cfg{};
+    std::vector<WfsHost> wfs;
+    std::vector<Science> sci;
+    std::vector<Group> groups;
+    std::string err;
+    int device = 0;
+    int n_slopes = 0, n_frame_px = 0;
+
+    cudaStream_t s0 = nullptr, s1 = nullptr, s2 = nullptr;
+    cudaStream_t user = nullptr;
+    bool user_set = false;
+    cudaEvent_t ev_fork = nullptr, ev_join1 = nullptr, ev_join2 = nullptr, ev_user = nullptr, ev_done = nullptr;
+
+    // wfs
+    WfsDev* d_wfs = nullptr;
+    float* d_amp_all = nullptr;
+    float* d_slopes = nullptr;
+    float* d_sref = nullptr;
+    float* d_lam = nullptr;
+    int* d_frames = nullptr;
+
+    // atmosphere
+    int n_layers = 0;
+    std::vector<mcao_layer> layers;
+    std::vector<float*> d_layer_owned;
+    std::vector<const float*> d_layer_ptr;
+    bool atm_loaded = false;
+
+    // DMs
+    int n_dms = 0;
+    std::vector<mcao_dm> dms;
+    std::vector<DmDesc> dm_desc;
+    std::vector<int> dm_ncmd;
+    DmDesc* d_dm_desc = nullptr;
+    float* d_dm_g = nullptr;
+    int2* d_dm_band = nullptr;
+    int* d_dm_map = nullptr;
+    float* d_dm_tmp = nullptr;
+    float* d_dm_surf = nullptr;
+    long long dm_tmp_total = 0, dm_surf_total = 0;
+    long long dm_tmp_start[kMaxDms] = {0}, dm_surf_start[kMaxDms] = {0};
+    int n_cmd = 0;
+    bool dms_loaded = false;
+
+    // grids = layers then DMs
+    GridDev* d_grids = nullptr;
+    int n_grids = 0;
+
+    // reconstructor
+    float* d_R = nullptr;
+    int ld = 0, rows_pad = 0;
+    float* d_c = nullptr;
+    float* d_partial = nullptr;
+    bool recon_loaded = false;
+
+    StepState* d_st = nullptr;
+    SciAcc* d_acc = nullptr;
+
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_dirty = true;
+    cudaGraphNode_t prof_node[2 * ST_COUNT] = {nullptr};  // event-record node of each slot
+    cudaEvent_t prof_tpl[2 * ST_COUNT] = {nullptr};
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_pool;
+    size_t prof_used = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_records;
+    int launches_per_step = 0;
+};
+
+namespace {
+
+mcao_status fail(mcao_sim* s, mcao_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define CK(expr)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            if (e_ == cudaErrorMemoryAllocation)                                            \
+                return fail(S, MCAO_E_OOM, "%s: %s", #expr, cudaGetErrorString(e_));        \
+            return fail(S, MCAO_E_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));           \
+        }                                                                                   \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+// pupil amplitude on an n x n grid across D (sample i at (i - (n-1)/2) D/n), annulus rule
+std::vector<float> pupil(double D, double obs, int n) {
+    std::vector<float> A((size_t)n * n);
+    double d = D / (double)n, R2 = 0.25 * D * D, ro2 = 0.25 * obs * obs * D * D;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            double x = ((double)i - 0.5 * (double)(n - 1)) * d;
+            double y = ((double)j - 0.5 * (double)(n - 1)) * d;
+            double r2 = x * x + y * y;
+            A[(size_t)j * n + i] = (r2 <= R2 && r2 >= ro2) ? 1.0f : 0.0f;
+        }
+    return A;
+}
+
+std::vector<int> factor_fft(int M) {
+    std::vector<int> r;
+    int n = M;
+    while (n % 4 == 0) { r.push_back(4); n /= 4; }
+    while (n % 2 == 0) { r.push_back(2); n /= 2; }
+    while (n % 5 == 0) { r.push_back(5); n /= 5; }
+    while (n % 3 == 0) { r.push_back(3); n /= 3; }
+    if (n != 1) r.clear();
+    return r;
+}
+
+void release_graph(mcao_sim* S) {
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    S->exec = nullptr;
+    S->graph = nullptr;
+    S->graph_dirty = true;
+    for (auto& n : S->prof_node) n = nullptr;
+}
+
+Ctx make_ctx(mcao_sim* S) {
+    Ctx c;
+    c.grids = S->d_grids;
+    c.n_grids = S->n_grids;
+    c.wfs = S->d_wfs;
+    c.st = S->d_st;
+    c.dt = S->cfg.dt;
+    c.seed = S->cfg.seed;
+    c.noise = S->cfg.noise;
+    return c;
+}
+
+DmLaunch make_dm_launch(mcao_sim* S) {
+    DmLaunch L{};
+    L.n_dm = S->n_dms;
+    L.desc = S->d_dm_desc;
+    L.g = S->d_dm_g;
+    L.band = S->d_dm_band;
+    L.act_map = S->d_dm_map;
+    L.c = S->d_c;
+    L.tmp = S->d_dm_tmp;
+    L.surf = S->d_dm_surf;
+    L.tmp_total = S->dm_tmp_total;
+    L.surf_total = S->dm_surf_total;
+    for (int m = 0; m < kMaxDms; ++m) {
+        L.tmp_start[m] = S->dm_tmp_start[m];
+        L.surf_start[m] = S->dm_surf_start[m];
+    }
+    L.st = S->d_st;
+    return L;
+}
+
+ReconLaunch make_recon_launch(mcao_sim* S) {
+    ReconLaunch L{};
+    L.R = S->d_R;
+    L.n_cmd = S->n_cmd;
+    L.n_slopes = S->n_slopes;
+    L.ld = S->ld;
+    L.rows_pad = S->rows_pad;
+    L.s = S->d_slopes;
+    L.partial = S->d_partial;
+    L.c = S->d_c;
+    L.gain = (float)S->cfg.gain;
+    L.st = S->d_st;
+    return L;
+}
+
+SciLaunch make_sci_launch(mcao_sim* S, int q) {
+    Science& C = S->sci[q];
+    SciLaunch L{};
+    L.ctx = make_ctx(S);
+    L.N = C.N;
+    L.M = C.M;
+    L.dx = C.dx;
+    L.theta_x = C.p.theta_x;
+    L.theta_y = C.p.theta_y;
+    L.scale = (float)(S->cfg.lambda_ref / C.p.lambda);
+    L.amp = C.d_amp;
+    L.field = C.d_field;
+    L.ft = C.d_ft;
+    L.psf_t = C.d_psf_t;
+    L.sr_part = C.d_sr_part;
+    L.n_tiles = C.n_tiles;
+    L.sum_amp = C.sum_amp;
+    L.psf_every = S->cfg.psf_every;
+    L.w = C.d_w;
+    L.n_radices = (int)C.radices.size();
+    for (int i = 0; i < L.n_radices && i < 8; ++i) L.radices[i] = C.radices[i];
+    L.st = S->d_st;
+    L.acc = S->d_acc + q;
+    return L;
+}
+
+WfsLaunch make_wfs_launch(mcao_sim* S, const Group& g) {
+    WfsLaunch L{};
+    L.ctx = make_ctx(S);
+    L.subaps = g.d_subaps;
+    L.n_subaps = g.n_subaps;
+    L.s_ref = S->d_sref;
+    L.slopes = S->d_slopes;
+    L.lam_out = S->cfg.keep_frames ? S->d_lam : nullptr;
+    L.frame_out = (S->cfg.keep_frames && S->cfg.noise) ? S->d_frames : nullptr;
+    return L;
+}
+
+// Rebuild the grid table (layers, then DM surfaces) after either set changes.
+mcao_status rebuild_grids(mcao_sim* S) {
+    std::vector<GridDev> g;
+    for (int l = 0; l < S->n_layers; ++l) {
+        GridDev d{};
+        d.data = S->d_layer_ptr[l];
+        d.n = S->layers[l].n;
+        d.periodic = 1;
+        d.pixel = S->layers[l].pixel_m;
+        d.alt = S->layers[l].alt_m;
+        d.vx = S->layers[l].vx;
+        d.vy = S->layers[l].vy;
+        d.sign = 1.0f;
+        g.push_back(d);
+    }
+    for (int m = 0; m < S->n_dms; ++m) {
+        GridDev d{};
+        d.data = S->d_dm_surf + S->dm_desc[m].surf_off;
+        d.n = S->dms[m].surf_n;
+        d.periodic = 0;
+        d.pixel = S->dms[m].surf_dx;
+        d.alt = S->dms[m].alt_m;
+        d.vx = 0.0;
+        d.vy = 0.0;
+        d.sign = -1.0f;
+        g.push_back(d);
+    }
+    if ((int)g.size() > kMaxEntries)
+        return fail(S, MCAO_E_UNSUPPORTED, "layers + DMs = %d exceeds %d", (int)g.size(), kMaxEntries);
+    dfree(S->d_grids);
+    S->n_grids = (int)g.size();
+    CK(dalloc(&S->d_grids, g.size()));
+    if (!g.empty()) CK(cudaMemcpy(S->d_grids, g.data(), sizeof(GridDev) * g.size(), cudaMemcpyHostToDevice));
+    release_graph(S);
+    return MCAO_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// step issue
+// ---------------------------------------------------------------------------------------------
+void prof_mark(mcao_sim* S, int slot, cudaStream_t st) {
+    cudaEventRecordWithFlags(S->prof_tpl[slot], st, cudaEventRecordExternal);
+}
+
+// Queue one step on s0/s1/s2 (captured into the graph).  Returns the first launch error.
+cudaError_t enqueue_step(mcao_sim* S, int* launches) {
+    cudaError_t e;
+    int nl = 0;
+    prof_mark(S, 2 * ST_DM, S->s0);
+    DmLaunch dl = make_dm_launch(S);
+    if ((e = launch_dm_surfaces(dl, S->s0)) != cudaSuccess) return e;
+    nl += S->n_dms > 0 ? 2 : 1;
+    prof_mark(S, 2 * ST_DM + 1, S->s0);
+    if ((e = cudaEventRecord(S->ev_fork, S->s0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(S->s1, S->ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(S->s2, S->ev_fork, 0)) != cudaSuccess) return e;
+
+    // auxiliary WFS groups on s1
+    prof_mark(S, 2 * ST_WFS_AUX, S->s1);
+    for (size_t gi = 1; gi < S->groups.size(); ++gi) {
+        const Group& g = S->groups[gi];
+        if ((e = launch_wfs(make_wfs_launch(S, g), g.n_px, g.n_fft, g.n_bin, S->s1)) != cudaSuccess) return e;
+        ++nl;
+    }
+    prof_mark(S, 2 * ST_WFS_AUX + 1, S->s1);
+    if ((e = cudaEventRecord(S->ev_join1, S->s1)) != cudaSuccess) return e;
+
+    // science on s2
+    prof_mark(S, 2 * ST_SCIENCE, S->s2);
+    for (size_t q = 0; q < S->sci.size(); ++q) {
+        SciLaunch L = make_sci_launch(S, (int)q);
+        if ((e = launch_sci_field(L, S->s2)) != cudaSuccess) return e;
+        if ((e = launch_sci_rows(L, S->s2)) != cudaSuccess) return e;
+        if ((e = launch_sci_cols(L, S->s2)) != cudaSuccess) return e;
+        nl += 3;
+    }
+    prof_mark(S, 2 * ST_SCIENCE + 1, S->s2);
+    if ((e = cudaEventRecord(S->ev_join2, S->s2)) != cudaSuccess) return e;
+
+    // main WFS group on s0
+    prof_mark(S, 2 * ST_WFS_MAIN, S->s0);
+    if (!S->groups.empty()) {
+        const Group& g = S->groups[0];
+        if ((e = launch_wfs(make_wfs_launch(S, g), g.n_px, g.n_fft, g.n_bin, S->s0)) != cudaSuccess) return e;
+        ++nl;
+    }
+    prof_mark(S, 2 * ST_WFS_MAIN + 1, S->s0);
+    if ((e = cudaStreamWaitEvent(S->s0, S->ev_join1, 0)) != cudaSuccess) return e;
+
+    ReconLaunch rl = make_recon_launch(S);
+    prof_mark(S, 2 * ST_RECON, S->s0);
+    if ((e = launch_recon(rl, S->s0)) != cudaSuccess) return e;
+    prof_mark(S, 2 * ST_RECON + 1, S->s0);
+    prof_mark(S, 2 * ST_REDUCE, S->s0);
+    if ((e = launch_recon_reduce(rl, S->s0)) != cudaSuccess) return e;
+    prof_mark(S, 2 * ST_REDUCE + 1, S->s0);
+    nl += (S->n_cmd > 0 ? 2 : 1);
+    if ((e = cudaStreamWaitEvent(S->s0, S->ev_join2, 0)) != cudaSuccess) return e;
+    if (launches) *launches = nl;
+    return cudaSuccess;
+}
+
+mcao_status build_graph(mcao_sim* S) {
+    release_graph(S);
+    CK(cudaStreamBeginCapture(S->s0, cudaStreamCaptureModeThreadLocal));
+    int nl = 0;
+    cudaError_t e = enqueue_step(S, &nl);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(S->s0, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(S, MCAO_E_CUDA, "step capture: %s", cudaGetErrorString(e));
+    }
+    if (e2 != cudaSuccess) return fail(S, MCAO_E_CUDA, "end capture: %s", cudaGetErrorString(e2));
+    S->graph = g;
+    CK(cudaGraphInstantiate(&S->exec, S->graph, 0));
+    // locate the profiling event-record nodes
+    size_t n = 0;
+    CK(cudaGraphGetNodes(S->graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    CK(cudaGraphGetNodes(S->graph, nodes.data(), &n));
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nodes[i], &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        CK(cudaGraphEventRecordNodeGetEvent(nodes[i], &ev));
+        for (int slot = 0; slot < 2 * ST_COUNT; ++slot)
+            if (S->prof_tpl[slot] == ev) S->prof_node[slot] = nodes[i];
+    }
+    S->launches_per_step = nl;
+    S->graph_dirty = false;
+    return MCAO_OK;
+}
+
+mcao_status order_after_user(mcao_sim* S) {
+    if (!S->user_set) return MCAO_OK;
+    CK(cudaEventRecord(S->ev_user, S->user));
+    CK(cudaStreamWaitEvent(S->s0, S->ev_user, 0));
+    return MCAO_OK;
+}
+
+mcao_status signal_user(mcao_sim* S) {
+    if (!S->user_set) return MCAO_OK;
+    CK(cudaEventRecord(S->ev_done, S->s0));
+    CK(cudaStreamWaitEvent(S->user, S->ev_done, 0));
+    return MCAO_OK;
+}
+
+mcao_status sync_all(mcao_sim* S) {
+    CK(cudaStreamSynchronize(S->s0));
+    CK(cudaStreamSynchronize(S->s1));
+    CK(cudaStreamSynchronize(S->s2));
+    return MCAO_OK;
+}
+
+void destroy_all(mcao_sim* S) {
+    if (!S) return;
+    cudaSetDevice(S->device);
+    if (S->s0) cudaStreamSynchronize(S->s0);
+    if (S->s1) cudaStreamSynchronize(S->s1);
+    if (S->s2) cudaStreamSynchronize(S->s2);
+    release_graph(S);
+    for (auto& g : S->groups) dfree(g.d_subaps);
+    for (auto& c : S->sci) {
+        dfree(c.d_amp); dfree(c.d_field); dfree(c.d_ft); dfree(c.d_psf_t); dfree(c.d_sr_part); dfree(c.d_w);
+    }
+    dfree(S->d_wfs); dfree(S->d_amp_all); dfree(S->d_slopes); dfree(S->d_sref); dfree(S->d_lam);
+    dfree(S->d_frames);
+    for (auto p : S->d_layer_owned) cudaFree(p);
+    S->d_layer_owned.clear();
+    dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map); dfree(S->d_dm_tmp);
+    dfree(S->d_dm_surf); dfree(S->d_grids); dfree(S->d_R); dfree(S->d_c); dfree(S->d_partial);
+    dfree(S->d_st); dfree(S->d_acc);
+    for (auto& e : S->prof_tpl) if (e) cudaEventDestroy(e);
+    for (auto e : S->prof_pool) cudaEventDestroy(e);
+    cudaEvent_t evs[] = {S->ev_fork, S->ev_join1, S->ev_join2, S->ev_user, S->ev_done};
+    for (auto e : evs) if (e) cudaEventDestroy(e);
+    if (S->s0) cudaStreamDestroy(S->s0);
+    if (S->s1) cudaStreamDestroy(S->s1);
+    if (S->s2) cudaStreamDestroy(S->s2);
+    delete S;
+}
+
+mcao_status validate_config(const mcao_config* c) {
+    mcao_sim* S = nullptr;
+    if (!c) return fail(S, MCAO_E_INVALID_ARG, "cfg is NULL");
+    if (c->struct_size != sizeof(mcao_config))
+        return fail(S, MCAO_E_INVALID_ARG, "struct_size %zu != %zu", c->struct_size, sizeof(mcao_config));
+    if (!(is_fin(c->D) && c->D > 0)) return fail(S, MCAO_E_INVALID_ARG, "D must be > 0");
+    if (!(is_fin(c->obstruction) && c->obstruction >= 0 && c->obstruction < 1))
+        return fail(S, MCAO_E_INVALID_ARG, "obstruction must be in [0, 1)");
+    if (!(is_fin(c->lambda_ref) && c->lambda_ref > 0)) return fail(S, MCAO_E_INVALID_ARG, "lambda_ref must be > 0");
+    if (!(is_fin(c->dt) && c->dt >= 0)) return fail(S, MCAO_E_INVALID_ARG, "dt must be >= 0");
+    if (!is_fin(c->gain)) return fail(S, MCAO_E_INVALID_ARG, "gain must be finite");
+    if (c->psf_every < 0) return fail(S, MCAO_E_INVALID_ARG, "psf_every must be >= 0");
+    if (c->n_wfs < 1 || !c->wfs) return fail(S, MCAO_E_INVALID_ARG, "at least one WFS is required");
+    if (c->n_sci < 0 || (c->n_sci > 0 && !c->sci)) return fail(S, MCAO_E_INVALID_ARG, "bad science list");
+    for (int w = 0; w < c->n_wfs; ++w) {
+        const mcao_wfs& p = c->wfs[w];
+        if (p.type != MCAO_WFS_NGS && p.type != MCAO_WFS_LGS) return fail(S, MCAO_E_INVALID_ARG, "wfs %d: bad type", w);
+        if (p.n_sub < 1 || p.n_px < 1 || p.n_fft < 1 || p.n_bin < 1)
+            return fail(S, MCAO_E_INVALID_ARG, "wfs %d: sizes must be positive", w);
+        if (p.n_fft < 2 * p.n_px) return fail(S, MCAO_E_UNSUPPORTED, "wfs %d: n_fft must be >= 2 n_px", w);
+        if (p.n_fft % p.n_bin) return fail(S, MCAO_E_INVALID_ARG, "wfs %d: n_bin must divide n_fft", w);
+        if (!(is_fin(p.lambda) && p.lambda > 0)) return fail(S, MCAO_E_INVALID_ARG, "wfs %d: lambda must be > 0", w);
+        if (!(is_fin(p.n_photons) && p.n_photons >= 0) || !(is_fin(p.read_noise) && p.read_noise >= 0))
+            return fail(S, MCAO_E_INVALID_ARG, "wfs %d: flux and read noise must be >= 0", w);
+        if (!(is_fin(p.valid_thr) && p.valid_thr >= 0 && p.valid_thr <= 1))
+            return fail(S, MCAO_E_INVALID_ARG, "wfs %d: valid_thr must be in [0, 1]", w);
+        if (!is_fin(p.theta_x) || !is_fin(p.theta_y) || !is_fin(p.launch_x) || !is_fin(p.launch_y))
+            return fail(S, MCAO_E_INVALID_ARG, "wfs %d: non-finite direction or launch", w);
+        if (p.type == MCAO_WFS_LGS && !(is_fin(p.height) && p.height > 0))
+            return fail(S, MCAO_E_INVALID_ARG, "wfs %d: LGS height must be > 0", w);
+        if (!(is_fin(p.na_fwhm) && p.na_fwhm >= 0)) return fail(S, MCAO_E_INVALID_ARG, "wfs %d: na_fwhm must be >= 0", w);
+        bool el = p.type == MCAO_WFS_LGS && p.na_fwhm > 0;
+        if (!wfs_variant_supported(p.n_px, p.n_fft, p.n_bin, el))
+            return fail(S, MCAO_E_UNSUPPORTED, "wfs %d: no kernel for n_px=%d n_fft=%d n_bin=%d%s", w, p.n_px,
+                        p.n_fft, p.n_bin, el ? " with elongation" : "");
+    }
+    for (int q = 0; q < c->n_sci; ++q) {
+        const mcao_science& p = c->sci[q];
+        if (p.n_px < 8 || p.n_px % 8 || p.pad < 1)
+            return fail(S, MCAO_E_UNSUPPORTED, "science %d: n_px must be a multiple of 8, pad >= 1", q);
+        if (!(is_fin(p.lambda) && p.lambda > 0)) return fail(S, MCAO_E_INVALID_ARG, "science %d: lambda must be > 0", q);
+        int M = p.n_px * p.pad;
+        if (factor_fft(M).empty() || M > 4096)
+            return fail(S, MCAO_E_UNSUPPORTED, "science %d: FFT size %d must factor into 2,3,5 and be <= 4096", q, M);
+    }
+    return MCAO_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+const char* mcao_create_error(void) { return g_create_error.c_str(); }
+
+const char* mcao_last_error(const mcao_sim* sim) { return sim ? sim->err.c_str() : "null handle"; }
+
+mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, MCAO_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    mcao_status vs = validate_config(cfg);
+    if (vs != MCAO_OK) return vs;
+    mcao_sim* S = new mcao_sim();
+    S->cfg = *cfg;
+    auto bail = [&](mcao_status s) {
+        g_create_error = S->err;
+        destroy_all(S);
+        return s;
+    };
+#define CKC(expr)                                                                                \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            fail(S, e_ == cudaErrorMemoryAllocation ? MCAO_E_OOM : MCAO_E_CUDA, "%s: %s", #expr,  \
+                 cudaGetErrorString(e_));                                                        \
+            return bail(e_ == cudaErrorMemoryAllocation ? MCAO_E_OOM : MCAO_E_CUDA);             \
+        }                                                                                        \
+    } while (0)
+    CKC(cudaGetDevice(&S->device));
+    CKC(cudaStreamCreateWithFlags(&S->s0, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&S->s1, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&S->s2, cudaStreamNonBlocking));
+    cudaEvent_t* evs[] = {&S->ev_fork, &S->ev_join1, &S->ev_join2, &S->ev_user, &S->ev_done};
+    for (auto e : evs) CKC(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    for (auto& e : S->prof_tpl) CKC(cudaEventCreate(&e));
+    CKC(wfs_prepare());
+
+    // ---- wavefront sensors
+    int ns = 0, nframe = 0;
+    std::vector<WfsDev> wdev;
+    std::vector<float> amp_all;
+    std::vector<size_t> amp_off;
+    for (int w = 0; w < cfg->n_wfs; ++w) {
+        WfsHost H;
+        H.p = cfg->wfs[w];
+        H.N = H.p.n_sub * H.p.n_px;
+        H.dx = cfg->D / (double)H.N;
+        H.n_det = H.p.n_fft / H.p.n_bin;
+        H.amp = pupil(cfg->D, cfg->obstruction, H.N);
+        const int npx = H.p.n_px;
+        for (int sy = 0; sy < H.p.n_sub; ++sy)
+            for (int sx = 0; sx < H.p.n_sub; ++sx) {
+                double s = 0.0;
+                for (int y = 0; y < npx; ++y)
+                    for (int x = 0; x < npx; ++x) s += H.amp[(size_t)(sy * npx + y) * H.N + sx * npx + x];
+                double f = s / (double)(npx * npx);
+                if (f >= H.p.valid_thr) {
+                    H.valid.push_back(sy * H.p.n_sub + sx);
+                    H.frac.push_back(f);
+                }
+            }
+        H.n_valid = (int)H.valid.size();
+        H.slope0 = ns;
+        ns += 2 * H.n_valid;
+        H.frame0 = nframe;
+        nframe += H.n_valid * H.n_det * H.n_det;
+        bool el = H.p.type == MCAO_WFS_LGS && H.p.na_fwhm > 0;
+        double pix_rad = H.p.lambda / ((double)H.p.n_fft * H.dx);
+        for (int v = 0; v < H.n_valid; ++v) {
+            SubapDev d{};
+            d.wfs = w;
+            d.sx = H.valid[v] % H.p.n_sub;
+            d.sy = H.valid[v] / H.p.n_sub;
+            d.rank = v;
+            d.frac = (float)H.frac[v];
+            if (el) {
+                double cx = ((double)d.sx - 0.5 * (double)(H.p.n_sub - 1)) * npx * H.dx - H.p.launch_x;
+                double cy = ((double)d.sy - 0.5 * (double)(H.p.n_sub - 1)) * npx * H.dx - H.p.launch_y;
+                double b = std::sqrt(cx * cx + cy * cy);
+                if (b > 0.0) {
+                    double fwhm = b * H.p.na_fwhm / (H.p.height * H.p.height);
+                    double sig = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0))) / pix_rad;
+                    double a = 2.0 * M_PI * M_PI * sig * sig / ((double)H.p.n_fft * H.p.n_fft);
+                    d.elong_a = (float)a;
+                    d.dir_x = (float)(cx / b);
+                    d.dir_y = (float)(cy / b);
+                }
+            }
+            H.subaps.push_back(d);
+        }
+        WfsDev D{};
+        D.type = H.p.type;
+        D.n_sub = H.p.n_sub; D.n_px = npx; D.n_fft = H.p.n_fft; D.n_bin = H.p.n_bin; D.n_det = H.n_det;
+        D.N = H.N;
+        D.n_valid = H.n_valid; D.slope0 = H.slope0; D.frame0 = H.frame0; D.wfs_index = w;
+        D.dx = H.dx; D.theta_x = H.p.theta_x; D.theta_y = H.p.theta_y; D.height = H.p.height;
+        D.scale = (float)(cfg->lambda_ref / H.p.lambda);
+        D.n_photons = (float)H.p.n_photons;
+        D.read_noise = (float)H.p.read_noise;
+        for (int u = -(npx - 1); u <= npx - 1 && npx <= kMaxNpx; ++u) {
+            double re = 0, im = 0;
+            for (int t = 0; t < H.p.n_bin; ++t) {
+                double a = 2.0 * M_PI * (double)u * t / (double)H.p.n_fft;
+                re += std::cos(a);
+                im += std::sin(a);
+            }
+            double sgn = (((u % 2) + 2) % 2) ? -1.0 : 1.0;
+            D.h[u + npx - 1] = make_float2((float)(sgn * re), (float)(sgn * im));
+        }
+        for (int k = 0; k < H.n_det && k < kMaxNd; ++k) {
+            double a = 2.0 * M_PI * (double)k / (double)H.n_det;
+            D.tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        amp_off.push_back(amp_all.size());
+        amp_all.insert(amp_all.end(), H.amp.begin(), H.amp.end());
+        wdev.push_back(D);
+        S->wfs.push_back(std::move(H));
+    }
+    S->n_slopes = ns;
+    S->n_frame_px = nframe;
+    CKC(dalloc(&S->d_amp_all, amp_all.size()));
+    CKC(cudaMemcpy(S->d_amp_all, amp_all.data(), sizeof(float) * amp_all.size(), cudaMemcpyHostToDevice));
+    for (size_t w = 0; w < wdev.size(); ++w) wdev[w].amp = S->d_amp_all + amp_off[w];
+    CKC(dalloc(&S->d_wfs, wdev.size()));
+    CKC(cudaMemcpy(S->d_wfs, wdev.data(), sizeof(WfsDev) * wdev.size(), cudaMemcpyHostToDevice));
+    CKC(dalloc(&S->d_slopes, ns));
+    CKC(cudaMemset(S->d_slopes, 0, sizeof(float) * std::max(ns, 1)));
+    CKC(dalloc(&S->d_sref, ns));
+    CKC(cudaMemset(S->d_sref, 0, sizeof(float) * std::max(ns, 1)));
+    if (cfg->keep_frames) {
+        CKC(dalloc(&S->d_lam, nframe));
+        CKC(dalloc(&S->d_frames, nframe));
+        CKC(cudaMemset(S->d_lam, 0, sizeof(float) * std::max(nframe, 1)));
+        CKC(cudaMemset(S->d_frames, 0, sizeof(int) * std::max(nframe, 1)));
+    }
+
+    // ---- kernel groups: the group with the most subapertures runs on the main stream
+    for (int w = 0; w < cfg->n_wfs; ++w) {
+        const mcao_wfs& p = cfg->wfs[w];
+        Group* g = nullptr;
+        for (auto& x : S->groups)
+            if (x.n_px == p.n_px && x.n_fft == p.n_fft && x.n_bin == p.n_bin) g = &x;
+        if (!g) {
+            S->groups.push_back(Group{p.n_px, p.n_fft, p.n_bin, {}, nullptr, 0});
+            g = &S->groups.back();
+        }
+        g->wfs.push_back(w);
+    }
+    for (auto& g : S->groups) {
+        std::vector<SubapDev> all;
+        for (int w : g.wfs) all.insert(all.end(), S->wfs[w].subaps.begin(), S->wfs[w].subaps.end());
+        g.n_subaps = (int)all.size();
+        CKC(dalloc(&g.d_subaps, all.size()));
+        if (!all.empty())
+            CKC(cudaMemcpy(g.d_subaps, all.data(), sizeof(SubapDev) * all.size(), cudaMemcpyHostToDevice));
+    }
+    std::stable_sort(S->groups.begin(), S->groups.end(),
+                     [](const Group& a, const Group& b) { return a.n_subaps > b.n_subaps; });
+
+    // ---- science directions
+    int maxM = 0;
+    for (int q = 0; q < cfg->n_sci; ++q) {
+        Science C;
+        C.p = cfg->sci[q];
+        C.N = C.p.n_px;
+        C.M = C.p.n_px * C.p.pad;
+        C.dx = cfg->D / (double)C.N;
+        std::vector<float> A = pupil(cfg->D, cfg->obstruction, C.N);
+        C.sum_amp = 0.0;
+        for (float a : A) C.sum_amp += a;
+        C.n_tiles = (C.N / 8) * (C.N / 8);
+        C.radices = factor_fft(C.M);
+        CKC(dalloc(&C.d_amp, A.size()));
+        CKC(cudaMemcpy(C.d_amp, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice));
+        CKC(dalloc(&C.d_field, (size_t)C.N * C.N));
+        CKC(dalloc(&C.d_ft, (size_t)C.M * C.N));
+        CKC(dalloc(&C.d_psf_t, (size_t)C.M * C.M));
+        CKC(cudaMemset(C.d_psf_t, 0, sizeof(double) * (size_t)C.M * C.M));
+        CKC(dalloc(&C.d_sr_part, C.n_tiles));
+        std::vector<float2> W(C.M);
+        for (int m = 0; m < C.M; ++m) {
+            double a = -2.0 * M_PI * (double)m / (double)C.M;
+            W[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        CKC(dalloc(&C.d_w, C.M));
+        CKC(cudaMemcpy(C.d_w, W.data(), sizeof(float2) * C.M, cudaMemcpyHostToDevice));
+        maxM = std::max(maxM, C.M);
+        S->sci.push_back(C);
+    }
+    if (maxM > 0) {
+        int dev_smem = 0;
+        CKC(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device));
+        if (sci_smem_bytes(maxM) > (size_t)dev_smem) {
+            fail(S, MCAO_E_UNSUPPORTED, "science FFT of %d points needs %zu B of shared memory", maxM,
+                 sci_smem_bytes(maxM));
+            return bail(MCAO_E_UNSUPPORTED);
+        }
+        CKC(sci_prepare(maxM));
+    }
+    CKC(dalloc(&S->d_acc, std::max(cfg->n_sci, 1)));
+    CKC(cudaMemset(S->d_acc, 0, sizeof(SciAcc) * std::max(cfg->n_sci, 1)));
+    CKC(dalloc(&S->d_st, 1));
+    CKC(cudaMemset(S->d_st, 0, sizeof(StepState)));
+    *out = S;
+    return MCAO_OK;
+#undef CKC
+}
+
+mcao_status mcao_sim_destroy(mcao_sim* sim) {
+    destroy_all(sim);
+    return MCAO_OK;
+}
+
+mcao_status mcao_set_stream(mcao_sim* S, void* stream) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    S->user = (cudaStream_t)stream;
+    S->user_set = true;
+    return MCAO_OK;
+}
+
+mcao_status mcao_load_atmosphere(mcao_sim* S, int n_layers, const mcao_layer* layers) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (n_layers < 0 || (n_layers > 0 && !layers)) return fail(S, MCAO_E_INVALID_ARG, "bad layer list");
+    CK(cudaSetDevice(S->device));
+    for (int l = 0; l < n_layers; ++l) {
+        const mcao_layer& L = layers[l];
+        if (L.n < 2 || !(is_fin(L.pixel_m) && L.pixel_m > 0) || !L.phase)
+            return fail(S, MCAO_E_INVALID_ARG, "layer %d: n >= 2, pixel > 0 and phase required", l);
+        if (!is_fin(L.alt_m) || L.alt_m < 0 || !is_fin(L.vx) || !is_fin(L.vy))
+            return fail(S, MCAO_E_INVALID_ARG, "layer %d: altitude and wind must be finite, altitude >= 0", l);
+        for (const auto& w : S->wfs)
+            if (w.p.type == MCAO_WFS_LGS && L.alt_m >= w.p.height)
+                return fail(S, MCAO_E_INVALID_ARG, "layer %d lies above a laser guide star", l);
+    }
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    for (auto p : S->d_layer_owned) cudaFree(p);
+    S->d_layer_owned.clear();
+    S->d_layer_ptr.clear();
+    S->layers.assign(layers, layers + n_layers);
+    S->atm_loaded = false;
+    for (int l = 0; l < n_layers; ++l) {
+        const mcao_layer& L = layers[l];
+        if (L.on_device) {
+            S->d_layer_ptr.push_back(L.phase);
+        } else {
+            float* d = nullptr;
+            CK(dalloc(&d, (size_t)L.n * L.n));
+            S->d_layer_owned.push_back(d);
+            CK(cudaMemcpy(d, L.phase, sizeof(float) * (size_t)L.n * L.n, cudaMemcpyHostToDevice));
+            S->d_layer_ptr.push_back(d);
+        }
+        S->layers[l].phase = nullptr;
+    }
+    S->n_layers = n_layers;
+    mcao_status r = rebuild_grids(S);
+    if (r != MCAO_OK) return r;
+    S->atm_loaded = true;
+    return MCAO_OK;
+}
+
+mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (n_dms < 0 || n_dms > kMaxDms || (n_dms > 0 && !dms))
+        return fail(S, MCAO_E_INVALID_ARG, "n_dms must be in [0, %d]", kMaxDms);
+    for (int m = 0; m < n_dms; ++m) {
+        const mcao_dm& d = dms[m];
+        if (d.nx < 1 || d.ny < 1 || !d.valid || d.surf_n < 2 || !(is_fin(d.surf_dx) && d.surf_dx > 0) ||
+            !(is_fin(d.pitch_m) && d.pitch_m > 0) || !(is_fin(d.coupling) && d.coupling > 0 && d.coupling < 1) ||
+            !is_fin(d.alt_m) || d.alt_m < 0)
+            return fail(S, MCAO_E_INVALID_ARG, "dm %d: invalid geometry", m);
+        for (const auto& w : S->wfs)
+            if (w.p.type == MCAO_WFS_LGS && d.alt_m >= w.p.height)
+                return fail(S, MCAO_E_INVALID_ARG, "dm %d lies above a laser guide star", m);
+    }
+    CK(cudaSetDevice(S->device));
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map); dfree(S->d_dm_tmp);
+    dfree(S->d_dm_surf); dfree(S->d_c); dfree(S->d_partial);
+    S->dms_loaded = false;
+    S->recon_loaded = false;  // command count may change
+    S->dms.assign(dms, dms + n_dms);
+    S->n_dms = n_dms;
+    S->dm_desc.clear();
+    S->dm_ncmd.clear();
+    std::vector<float> g;
+    std::vector<int2> band;
+    std::vector<int> map;
+    long long tmp_total = 0, surf_total = 0;
+    int ncmd = 0;
+    for (int m = 0; m < n_dms; ++m) {
+        const mcao_dm& d = dms[m];
+        DmDesc D{};
+        D.nx = d.nx; D.ny = d.ny; D.surf_n = d.surf_n;
+        double sig = d.pitch_m / std::sqrt(2.0 * std::log(1.0 / d.coupling));
+        const double thr = 1e-10;
+        auto table = [&](int na) {
+            long long off = (long long)g.size();
+            for (int i = 0; i < d.surf_n; ++i) {
+                double x = ((double)i - 0.5 * (double)(d.surf_n - 1)) * d.surf_dx;
+                int lo = na, hi = 0;
+                for (int a = 0; a < na; ++a) {
+                    double xa = ((double)a - 0.5 * (double)(na - 1)) * d.pitch_m;
+                    double v = std::exp(-(x - xa) * (x - xa) / (2.0 * sig * sig));
+                    g.push_back((float)v);
+                    if (v >= thr) { lo = std::min(lo, a); hi = std::max(hi, a + 1); }
+                }
+                if (lo >= hi) { lo = 0; hi = 0; }
+                band.push_back(make_int2(lo, hi));
+            }
+            return off;
+        };
+        D.band_off = (long long)band.size();
+        D.gx_off = table(d.nx);
+        D.gy_off = table(d.ny);
+        D.map_off = (long long)map.size();
+        int cnt = 0;
+        for (int a = 0; a < d.nx * d.ny; ++a) {
+            if (d.valid[a]) { map.push_back(ncmd + cnt); ++cnt; }
+            else map.push_back(-1);
+        }
+        S->dm_ncmd.push_back(cnt);
+        ncmd += cnt;
+        D.tmp_off = tmp_total;
+        D.surf_off = surf_total;
+        S->dm_tmp_start[m] = tmp_total;
+        S->dm_surf_start[m] = surf_total;
+        tmp_total += (long long)d.ny * d.surf_n;
+        surf_total += (long long)d.surf_n * d.surf_n;
+        S->dm_desc.push_back(D);
+    }
+    S->n_cmd = ncmd;
+    S->dm_tmp_total = tmp_total;
+    S->dm_surf_total = surf_total;
+    CK(dalloc(&S->d_dm_desc, S->dm_desc.size()));
+    if (n_dms) CK(cudaMemcpy(S->d_dm_desc, S->dm_desc.data(), sizeof(DmDesc) * n_dms, cudaMemcpyHostToDevice));
+    CK(dalloc(&S->d_dm_g, g.size()));
+    if (!g.empty()) CK(cudaMemcpy(S->d_dm_g, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice));
+    CK(dalloc(&S->d_dm_band, band.size()));
+    if (!band.empty()) CK(cudaMemcpy(S->d_dm_band, band.data(), sizeof(int2) * band.size(), cudaMemcpyHostToDevice));
+    CK(dalloc(&S->d_dm_map, map.size()));
+    if (!map.empty()) CK(cudaMemcpy(S->d_dm_map, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice));
+    CK(dalloc(&S->d_dm_tmp, (size_t)tmp_total));
+    CK(dalloc(&S->d_dm_surf, (size_t)surf_total));
+    CK(cudaMemset(S->d_dm_surf, 0, sizeof(float) * std::max<long long>(surf_total, 1)));
+    CK(dalloc(&S->d_c, ncmd));
+    CK(cudaMemset(S->d_c, 0, sizeof(float) * std::max(ncmd, 1)));
+    mcao_status r = rebuild_grids(S);
+    if (r != MCAO_OK) return r;
+    S->dms_loaded = true;
+    return MCAO_OK;
+}
+
+mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const float* R, const float* s_ref,
+                                    int dtype, int on_device) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "load the DMs before the reconstructor");
+    if (dtype != MCAO_DTYPE_F32) return fail(S, MCAO_E_UNSUPPORTED, "only MCAO_DTYPE_F32 reconstructors");
+    if (n_cmd != S->n_cmd || n_slopes != S->n_slopes)
+        return fail(S, MCAO_E_SHAPE, "reconstructor is %d x %d, configuration needs %d x %d", n_cmd, n_slopes,
+                    S->n_cmd, S->n_slopes);
+    if (!R && n_cmd > 0) return fail(S, MCAO_E_INVALID_ARG, "R is NULL");
+    if (n_slopes < 1) return fail(S, MCAO_E_SHAPE, "no valid subapertures");
+    CK(cudaSetDevice(S->device));
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    dfree(S->d_R);
+    dfree(S->d_partial);
+    S->recon_loaded = false;
+    S->ld = (n_slopes + 3) / 4 * 4;
+    S->rows_pad = std::max(1, (n_cmd + kReconRowBlock - 1) / kReconRowBlock) * kReconRowBlock;
+    size_t elems = (size_t)S->rows_pad * S->ld;
+    CK(dalloc(&S->d_R, elems));
+    CK(cudaMemset(S->d_R, 0, sizeof(float) * elems));
+    if (n_cmd > 0)
+        CK(cudaMemcpy2D(S->d_R, sizeof(float) * S->ld, R, sizeof(float) * n_slopes, sizeof(float) * n_slopes, n_cmd,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    CK(dalloc(&S->d_partial, (size_t)recon_chunks(n_slopes) * std::max(n_cmd, 1)));
+    if (s_ref)
+        CK(cudaMemcpy(S->d_sref, s_ref, sizeof(float) * n_slopes,
+                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    else
+        CK(cudaMemset(S->d_sref, 0, sizeof(float) * n_slopes));
+    release_graph(S);
+    S->recon_loaded = true;
+    return MCAO_OK;
+}
+
+mcao_status mcao_step(mcao_sim* S, int n_steps) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (n_steps < 0) return fail(S, MCAO_E_INVALID_ARG, "n_steps must be >= 0");
+    if (!S->atm_loaded || !S->dms_loaded || !S->recon_loaded)
+        return fail(S, MCAO_E_STATE, "load the atmosphere, the DMs and the reconstructor before stepping");
+    if (n_steps == 0) return MCAO_OK;
+    CK(cudaSetDevice(S->device));
+    if (S->graph_dirty) {
+        mcao_status r = build_graph(S);
+        if (r != MCAO_OK) return r;
+    }
+    mcao_status r = order_after_user(S);
+    if (r != MCAO_OK) return r;
+    for (int i = 0; i < n_steps; ++i) {
+        if (S->profiling) {
+            for (int stg = 0; stg < ST_COUNT; ++stg) {
+                cudaGraphNode_t na = S->prof_node[2 * stg], nb = S->prof_node[2 * stg + 1];
+                if (!na || !nb) continue;
+                if (S->prof_used + 2 > S->prof_pool.size()) {
+                    cudaEvent_t a, b;
+                    CK(cudaEventCreate(&a));
+                    CK(cudaEventCreate(&b));
+                    S->prof_pool.push_back(a);
+                    S->prof_pool.push_back(b);
+                }
+                cudaEvent_t ea = S->prof_pool[S->prof_used], eb = S->prof_pool[S->prof_used + 1];
+                S->prof_used += 2;
+                CK(cudaGraphExecEventRecordNodeSetEvent(S->exec, na, ea));
+                CK(cudaGraphExecEventRecordNodeSetEvent(S->exec, nb, eb));
+                S->prof_records.push_back({stg, {ea, eb}});
+            }
+        }
+        CK(cudaGraphLaunch(S->exec, S->s0));
+    }
+    return signal_user(S);
+}
+
+mcao_status mcao_sync(mcao_sim* S) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    CK(cudaSetDevice(S->device));
+    return sync_all(S);
+}
+
+mcao_status mcao_query(const mcao_sim* S, int kind, int index, size_t* n) {
+    if (!S || !n) return MCAO_E_INVALID_ARG;
+    mcao_sim* Sm = const_cast<mcao_sim*>(S);
+    switch (kind) {
+        case MCAO_Q_SLOPES: *n = (size_t)S->n_slopes; return MCAO_OK;
+        case MCAO_Q_COMMANDS:
+            if (!S->dms_loaded) return fail(Sm, MCAO_E_STATE, "DMs not loaded");
+            *n = (size_t)S->n_cmd;
+            return MCAO_OK;
+        case MCAO_Q_VALID:
+        case MCAO_Q_FRAME:
+        case MCAO_Q_WFS_PHASE:
+            if (index < 0 || index >= (int)S->wfs.size()) return fail(Sm, MCAO_E_INVALID_ARG, "bad WFS index");
+            if (kind == MCAO_Q_VALID) *n = (size_t)S->wfs[index].n_valid;
+            else if (kind == MCAO_Q_FRAME) *n = (size_t)S->wfs[index].n_valid * S->wfs[index].n_det * S->wfs[index].n_det;
+            else *n = (size_t)S->wfs[index].N * S->wfs[index].N;
+            return MCAO_OK;
+        case MCAO_Q_DM_SURFACE:
+            if (index < 0 || index >= S->n_dms) return fail(Sm, MCAO_E_INVALID_ARG, "bad DM index");
+            *n = (size_t)S->dms[index].surf_n * S->dms[index].surf_n;
+            return MCAO_OK;
+        case MCAO_Q_PSF:
+            if (index < 0 || index >= (int)S->sci.size()) return fail(Sm, MCAO_E_INVALID_ARG, "bad science index");
+            *n = (size_t)S->sci[index].M * S->sci[index].M;
+            return MCAO_OK;
+        case MCAO_Q_STATE: {
+            size_t b = 4 * sizeof(int64_t) + sizeof(float) * ((size_t)S->n_cmd + S->n_slopes);
+            for (const auto& c : S->sci) b += sizeof(SciAcc) + sizeof(double) * (size_t)c.M * c.M;
+            *n = b;
+            return MCAO_OK;
+        }
+        default: return fail(Sm, MCAO_E_INVALID_ARG, "unknown query kind %d", kind);
+    }
+}
+
+mcao_status mcao_get_step_index(mcao_sim* S, int64_t* k) {
+    if (!S || !k) return MCAO_E_INVALID_ARG;
+    CK(cudaSetDevice(S->device));
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    StepState st;
+    CK(cudaMemcpy(&st, S->d_st, sizeof(st), cudaMemcpyDeviceToHost));
+    *k = st.k_next;
+    return MCAO_OK;
+}
+
+static mcao_status d2h(mcao_sim* S, void* dst, const void* src, size_t bytes) {
+    CK(cudaSetDevice(S->device));
+    mcao_status r = sync_all(S);
+    if (r != MCAO_OK) return r;
+    if (bytes) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    return MCAO_OK;
+}
+
+mcao_status mcao_get_slopes(mcao_sim* S, float* out, size_t n) {
+    if (!S || !out) return MCAO_E_INVALID_ARG;
+    if (n < (size_t)S->n_slopes) return fail(S, MCAO_E_SHAPE, "need %d slopes", S->n_slopes);
+    return d2h(S, out, S->d_slopes, sizeof(float) * S->n_slopes);
+}
+
+mcao_status mcao_get_commands(mcao_sim* S, float* out, size_t n) {
+    if (!S || !out) return MCAO_E_INVALID_ARG;
+    if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");
+    if (n < (size_t)S->n_cmd) return fail(S, MCAO_E_SHAPE, "need %d commands", S->n_cmd);
+    return d2h(S, out, S->d_c, sizeof(float) * S->n_cmd);
+}
+
+mcao_status mcao_set_commands(mcao_sim* S, const float* in, size_t n) {
+    if (!S || !in) return MCAO_E_INVALID_ARG;
+    if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");
+    if (n != (size_t)S->n_cmd) return fail(S, MCAO_E_SHAPE, "need exactly %d commands", S->n_cmd);
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(in[i])) return fail(S, MCAO_E_INVALID_ARG, "command %zu is not finite", i);
+    CK(cudaSetDevice(S->device));
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    if (n) CK(cudaMemcpy(S->d_c, in, sizeof(float) * n, cudaMemcpyHostToDevice));
+    return MCAO_OK;
+}
+
+mcao_status mcao_get_valid(mcao_sim* S, int wfs, int32_t* out, size_t n) {
+    if (!S || !out) return MCAO_E_INVALID_ARG;
+    if (wfs < 0 || wfs >= (int)S->wfs.size()) return fail(S, MCAO_E_INVALID_ARG, "bad WFS index");
+    const auto& v = S->wfs[wfs].valid;
+    if (n < v.size()) return fail(S, MCAO_E_SHAPE, "need %zu entries", v.size());
+    for (size_t i = 0; i < v.size(); ++i) out[i] = v[i];
+    return MCAO_OK;
+}
+
+mcao_status mcao_get_wfs_phase(mcao_sim* S, int wfs, float* out, size_t n) {
+    if (!S || !out) return MCAO_E_INVALID_ARG;
+    if (wfs < 0 || wfs >= (int)S->wfs.size()) return fail(S, MCAO_E_INVALID_ARG, "bad WFS index");
+    if (!S->atm_loaded || !S->dms_loaded) return fail(S, MCAO_E_STATE, "atmosphere and DMs must be loaded");
+    const int N = S->wfs[wfs].N;
+    if (n < (size_t)N * N) return fail(S, MCAO_E_SHAPE, "need %d samples", N * N);
+    CK(cudaSetDevice(S->device));
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    float* d = nullptr;
+    CK(dalloc(&d, (size_t)N * N));
+    cudaError_t e = launch_dm_surfaces(make_dm_launch(S), S->s0);
+    if (e == cudaSuccess) e = launch_wfs_phase(make_ctx(S), wfs, N, d, S->s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d, sizeof(float) * (size_t)N * N, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    CK(e);
+    return MCAO_OK;
+}
+
+mcao_status mcao_get_dm_surface(mcao_sim* S, int dm, float* out, size_t n) {
+    if (!S || !out) return MCAO_E_INVALID_ARG;
+    if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");
+    if (dm < 0 || dm >= S->n_dms) return fail(S, MCAO_E_INVALID_ARG, "bad DM index");
+    size_t cnt = (size_t)S->dms[dm].surf_n * S->dms[dm].surf_n;
+    if (n < cnt) return fail(S, MCAO_E_SHAPE, "need %zu samples", cnt);
+    CK(cudaSetDevice(S->device));
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    CK(launch_dm_surfaces(make_dm_launch(S), S->s0));
+    CK(cudaStreamSynchronize(S->s0));
+    CK(cudaMemcpy(out, S->d_dm_surf + S->dm_desc[dm].surf_off, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
+    return MCAO_OK;
+}
+
+mcao_status mcao_get_frames(mcao_sim* S, int wfs, float* lambda, int32_t* frames, size_t n) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (!S->cfg.keep_frames) return fail(S, MCAO_E_STATE, "create the simulation with keep_frames = 1");
+    if (wfs < 0 || wfs >= (int)S->wfs.size()) return fail(S, MCAO_E_INVALID_ARG, "bad WFS index");
+    const WfsHost& W = S->wfs[wfs];
+    size_t cnt = (size_t)W.n_valid * W.n_det * W.n_det;
+    if (n < cnt) return fail(S, MCAO_E_SHAPE, "need %zu pixels", cnt);
+    mcao_status r = MCAO_OK;
+    if (lambda) r = d2h(S, lambda, S->d_lam + W.frame0, sizeof(float) * cnt);
+    if (r == MCAO_OK && frames) r = d2h(S, frames, S->d_frames + W.frame0, sizeof(int32_t) * cnt);
+    return r;
+}
+
+mcao_status mcao_get_psf(mcao_sim* S, int sci, double* out, size_t n, double* sr_long, double* sr_last) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (sci < 0 || sci >= (int)S->sci.size()) return fail(S, MCAO_E_INVALID_ARG, "bad science index");
+    const Science& C = S->sci[sci];
+    const size_t M = (size_t)C.M;
+    if (out && n < M * M) return fail(S, MCAO_E_SHAPE, "need %zu pixels", M * M);
+    SciAcc acc;
+    mcao_status r = d2h(S, &acc, S->d_acc + sci, sizeof(acc));
+    if (r != MCAO_OK) return r;
+    if (sr_long) *sr_long = acc.n_sr ? acc.sr_sum / (double)acc.n_sr : 0.0;
+    if (sr_last) *sr_last = acc.sr_last;
+    if (out) {
+        std::vector<double> t(M * M);
+        r = d2h(S, t.data(), C.d_psf_t, sizeof(double) * M * M);
+        if (r != MCAO_OK) return r;
+        double norm = acc.n_psf ? 1.0 / ((double)acc.n_psf * C.sum_amp * C.sum_amp) : 0.0;
+        for (size_t j = 0; j < M; ++j)
+            for (size_t i = 0; i < M; ++i)
+                out[j * M + i] = t[((i + M / 2) % M) * M + (j + M / 2) % M] * norm;
+    }
+    return MCAO_OK;
+}
+
+mcao_status mcao_reset_psf(mcao_sim* S) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    CK(cudaSetDevice(S->device));
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    for (auto& c : S->sci) CK(cudaMemset(c.d_psf_t, 0, sizeof(double) * (size_t)c.M * c.M));
+    CK(cudaMemset(S->d_acc, 0, sizeof(SciAcc) * std::max<size_t>(S->sci.size(), 1)));
+    return MCAO_OK;
+}
+
+mcao_status mcao_get_state(mcao_sim* S, void* buf, size_t n) {
+    if (!S || !buf) return MCAO_E_INVALID_ARG;
+    if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");
+    size_t need = 0;
+    mcao_status r = mcao_query(S, MCAO_Q_STATE, 0, &need);
+    if (r != MCAO_OK) return r;
+    if (n < need) return fail(S, MCAO_E_SHAPE, "need %zu bytes", need);
+    char* p = (char*)buf;
+    StepState st;
+    r = d2h(S, &st, S->d_st, sizeof(st));
+    if (r != MCAO_OK) return r;
+    int64_t hdr[4] = {0x4d43414f53544154LL, (int64_t)st.k_next, S->n_cmd, S->n_slopes};
+    memcpy(p, hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    if ((r = d2h(S, p, S->d_c, sizeof(float) * S->n_cmd)) != MCAO_OK) return r;
+    p += sizeof(float) * S->n_cmd;
+    if ((r = d2h(S, p, S->d_slopes, sizeof(float) * S->n_slopes)) != MCAO_OK) return r;
+    p += sizeof(float) * S->n_slopes;
+    for (size_t q = 0; q < S->sci.size(); ++q) {
+        if ((r = d2h(S, p, S->d_acc + q, sizeof(SciAcc))) != MCAO_OK) return r;
+        p += sizeof(SciAcc);
+        size_t b = sizeof(double) * (size_t)S->sci[q].M * S->sci[q].M;
+        if ((r = d2h(S, p, S->sci[q].d_psf_t, b)) != MCAO_OK) return r;
+        p += b;
+    }
+    return MCAO_OK;
+}
+
+mcao_status mcao_set_state(mcao_sim* S, const void* buf, size_t n) {
+    if (!S || !buf) return MCAO_E_INVALID_ARG;
+    if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");
+    size_t need = 0;
+    mcao_status r = mcao_query(S, MCAO_Q_STATE, 0, &need);
+    if (r != MCAO_OK) return r;
+    if (n != need) return fail(S, MCAO_E_SHAPE, "checkpoint has %zu bytes, expected %zu", n, need);
+    const char* p = (const char*)buf;
+    int64_t hdr[4];
+    memcpy(hdr, p, sizeof(hdr));
+    if (hdr[0] != 0x4d43414f53544154LL || hdr[2] != S->n_cmd || hdr[3] != S->n_slopes || hdr[1] < 0)
+        return fail(S, MCAO_E_SHAPE, "checkpoint does not match this configuration");
+    p += sizeof(hdr);
+    CK(cudaSetDevice(S->device));
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    StepState st;
+    st.k = hdr[1];
+    st.k_next = hdr[1];
+    CK(cudaMemcpy(S->d_st, &st, sizeof(st), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S->d_c, p, sizeof(float) * S->n_cmd, cudaMemcpyHostToDevice));
+    p += sizeof(float) * S->n_cmd;
+    CK(cudaMemcpy(S->d_slopes, p, sizeof(float) * S->n_slopes, cudaMemcpyHostToDevice));
+    p += sizeof(float) * S->n_slopes;
+    for (size_t q = 0; q < S->sci.size(); ++q) {
+        CK(cudaMemcpy(S->d_acc + q, p, sizeof(SciAcc), cudaMemcpyHostToDevice));
+        p += sizeof(SciAcc);
+        size_t b = sizeof(double) * (size_t)S->sci[q].M * S->sci[q].M;
+        CK(cudaMemcpy(S->sci[q].d_psf_t, p, b, cudaMemcpyHostToDevice));
+        p += b;
+    }
+    return MCAO_OK;
+}
+
+mcao_status mcao_set_profiling(mcao_sim* S, int on) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    S->profiling = on != 0;
+    S->prof_used = 0;
+    S->prof_records.clear();
+    return MCAO_OK;
+}
+
+mcao_status mcao_get_profile(mcao_sim* S, double* ms, int64_t* counts, int n_stages, int64_t* launches_per_step) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    CK(cudaSetDevice(S->device));
+    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    std::vector<double> tot(ST_COUNT, 0.0);
+    std::vector<int64_t> cnt(ST_COUNT, 0);
+    for (auto& rec : S->prof_records) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, rec.second.first, rec.second.second));
+        tot[rec.first] += t;
+        cnt[rec.first] += 1;
+    }
+    for (int i = 0; i < n_stages && i < ST_COUNT; ++i) {
+        if (ms) ms[i] = tot[i];
+        if (counts) counts[i] = cnt[i];
+    }
+    if (launches_per_step) *launches_per_step = S->launches_per_step;
+    S->prof_used = 0;
+    S->prof_records.clear();
+    return MCAO_OK;
+}
+
+}  // extern "C"

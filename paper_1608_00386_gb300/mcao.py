@@ -1,0 +1,315 @@
+"""Thin ctypes binding of libmcao.so (include/mcao.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  Arrays may be numpy arrays (host) or
+CUDA torch tensors (device, passed by address with ``on_device = 1`` where the ABI allows it).
+If the library has not been built, or no CUDA device is available, the calls raise: there is
+no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+STATUS = {0: "MCAO_OK", 1: "MCAO_E_INVALID_ARG", 2: "MCAO_E_SHAPE", 3: "MCAO_E_STATE", 4: "MCAO_E_CUDA",
+          5: "MCAO_E_OOM", 6: "MCAO_E_TIMEOUT", 7: "MCAO_E_UNSUPPORTED"}
+Q_SLOPES, Q_COMMANDS, Q_VALID, Q_FRAME, Q_WFS_PHASE, Q_DM_SURFACE, Q_PSF, Q_STATE = range(8)
+STAGES = ["dm", "wfs_main", "wfs_aux", "recon", "recon_reduce", "science"]
+
+# exported names of include/mcao.h (checked by the tests against the built library)
+EXPORTS = [
+    "mcao_sim_create", "mcao_sim_destroy", "mcao_last_error", "mcao_create_error", "mcao_set_stream",
+    "mcao_load_atmosphere", "mcao_load_dms", "mcao_load_reconstructor", "mcao_step", "mcao_sync",
+    "mcao_query", "mcao_get_step_index", "mcao_get_slopes", "mcao_get_commands", "mcao_set_commands",
+    "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
+    "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
+]
+
+
+class McaoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Wfs(C.Structure):
+    _fields_ = [("type", C.c_int), ("n_sub", C.c_int), ("n_px", C.c_int), ("n_fft", C.c_int), ("n_bin", C.c_int),
+                ("theta_x", C.c_double), ("theta_y", C.c_double), ("height", C.c_double), ("lambda_", C.c_double),
+                ("n_photons", C.c_double), ("read_noise", C.c_double), ("valid_thr", C.c_double),
+                ("na_fwhm", C.c_double), ("launch_x", C.c_double), ("launch_y", C.c_double)]
+
+
+class _Science(C.Structure):
+    _fields_ = [("n_px", C.c_int), ("pad", C.c_int), ("theta_x", C.c_double), ("theta_y", C.c_double),
+                ("lambda_", C.c_double)]
+
+
+class _Config(C.Structure):
+    _fields_ = [("struct_size", C.c_size_t), ("D", C.c_double), ("obstruction", C.c_double),
+                ("lambda_ref", C.c_double), ("dt", C.c_double), ("gain", C.c_double), ("seed", C.c_uint64),
+                ("noise", C.c_int), ("psf_every", C.c_int), ("keep_frames", C.c_int), ("n_wfs", C.c_int),
+                ("wfs", C.POINTER(_Wfs)), ("n_sci", C.c_int), ("sci", C.POINTER(_Science))]
+
+
+class _Layer(C.Structure):
+    _fields_ = [("n", C.c_int), ("pixel_m", C.c_double), ("alt_m", C.c_double), ("vx", C.c_double),
+                ("vy", C.c_double), ("phase", C.c_void_p), ("on_device", C.c_int)]
+
+
+class _Dm(C.Structure):
+    _fields_ = [("alt_m", C.c_double), ("pitch_m", C.c_double), ("coupling", C.c_double), ("nx", C.c_int),
+                ("ny", C.c_int), ("valid", C.POINTER(C.c_uint8)), ("surf_n", C.c_int), ("surf_dx", C.c_double)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libmcao.so (built in-tree by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (paper_1608_00386_gb300.build.build())")
+    L = C.CDLL(path)
+    vp, st = C.c_void_p, C.c_int
+    sig = {
+        "mcao_sim_create": [C.POINTER(_Config), C.POINTER(vp)],
+        "mcao_sim_destroy": [vp],
+        "mcao_set_stream": [vp, vp],
+        "mcao_load_atmosphere": [vp, C.c_int, C.POINTER(_Layer)],
+        "mcao_load_dms": [vp, C.c_int, C.POINTER(_Dm)],
+        "mcao_load_reconstructor": [vp, C.c_int, C.c_int, vp, vp, C.c_int, C.c_int],
+        "mcao_step": [vp, C.c_int],
+        "mcao_sync": [vp],
+        "mcao_query": [vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)],
+        "mcao_get_step_index": [vp, C.POINTER(C.c_int64)],
+        "mcao_get_slopes": [vp, vp, C.c_size_t],
+        "mcao_get_commands": [vp, vp, C.c_size_t],
+        "mcao_set_commands": [vp, vp, C.c_size_t],
+        "mcao_get_valid": [vp, C.c_int, vp, C.c_size_t],
+        "mcao_get_wfs_phase": [vp, C.c_int, vp, C.c_size_t],
+        "mcao_get_dm_surface": [vp, C.c_int, vp, C.c_size_t],
+        "mcao_get_frames": [vp, C.c_int, vp, vp, C.c_size_t],
+        "mcao_get_psf": [vp, C.c_int, vp, C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "mcao_reset_psf": [vp],
+        "mcao_get_state": [vp, vp, C.c_size_t],
+        "mcao_set_state": [vp, vp, C.c_size_t],
+        "mcao_set_profiling": [vp, C.c_int],
+        "mcao_get_profile": [vp, vp, vp, C.c_int, C.POINTER(C.c_int64)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = st
+    L.mcao_last_error.argtypes = [vp]
+    L.mcao_last_error.restype = C.c_char_p
+    L.mcao_create_error.argtypes = []
+    L.mcao_create_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _addr(a):
+    """(address, keepalive, on_device) of a numpy array or a torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), a, int(a.is_cuda)
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data, a, 0
+
+
+class Sim:
+    """One closed-loop simulation handle (mcao_sim)."""
+
+    def __init__(self, cfg: dict, keep_frames: bool = False, stream=None):
+        L = lib()
+        self.cfg = cfg
+        nw, nsci = len(cfg["wfs"]), len(cfg["science"])
+        self._wfs = (_Wfs * nw)()
+        for i, w in enumerate(cfg["wfs"]):
+            self._wfs[i] = _Wfs(1 if w["type"] == "lgs" else 0, w["n_sub"], w["n_px"], w["n_fft"], w["n_bin"],
+                                w["theta"][0], w["theta"][1], w["height"], w["lambda"], w["n_photons"],
+                                w["read_noise"], w["valid_thr"], w["na_fwhm"], w["launch"][0], w["launch"][1])
+        self._sci = (_Science * max(nsci, 1))()
+        for i, s in enumerate(cfg["science"]):
+            self._sci[i] = _Science(s["n_px"], s["pad"], s["theta"][0], s["theta"][1], s["lambda"])
+        c = _Config()
+        c.struct_size = C.sizeof(_Config)
+        c.D, c.obstruction, c.lambda_ref = cfg["D"], cfg["obstruction"], cfg["lambda_ref"]
+        c.dt, c.gain, c.seed = cfg["dt"], cfg["gain"], cfg["seed"]
+        c.noise, c.psf_every, c.keep_frames = int(cfg["noise"]), int(cfg.get("psf_every", 1)), int(keep_frames)
+        c.n_wfs, c.wfs, c.n_sci, c.sci = nw, self._wfs, nsci, self._sci
+        h = C.c_void_p()
+        st = L.mcao_sim_create(C.byref(c), C.byref(h))
+        if st != 0:
+            raise McaoError(st, L.mcao_create_error().decode())
+        self.h = h
+        self._keep = []
+        if stream is not None:
+            self.set_stream(stream)
+
+    # ---------------------------------------------------------------- plumbing
+    def _ck(self, st):
+        if st != 0:
+            raise McaoError(st, lib().mcao_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mcao_sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, kind: int, index: int = 0) -> int:
+        n = C.c_size_t()
+        self._ck(lib().mcao_query(self.h, kind, index, C.byref(n)))
+        return n.value
+
+    def set_stream(self, stream):
+        ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+        self._ck(lib().mcao_set_stream(self.h, C.c_void_p(ptr)))
+
+    # ---------------------------------------------------------------- loads
+    def load_atmosphere(self, screens):
+        layers = (_Layer * len(screens))()
+        keep = []
+        for i, (lay, scr) in enumerate(zip(self.cfg["layers"], screens)):
+            if not hasattr(scr, "data_ptr"):
+                scr = np.ascontiguousarray(scr, dtype=np.float32)
+            addr, k, dev = _addr(scr)
+            keep.append(k)
+            layers[i] = _Layer(lay["n"], lay["pixel"], lay["alt"], lay["vx"], lay["vy"], addr, dev)
+        self._ck(lib().mcao_load_atmosphere(self.h, len(screens), layers))
+        self._keep.append(keep)  # device tensors are adopted: keep them alive
+
+    def load_dms(self):
+        dms = self.cfg["dms"]
+        arr = (_Dm * max(len(dms), 1))()
+        keep = []
+        for i, d in enumerate(dms):
+            v = np.ascontiguousarray(d["valid"], dtype=np.uint8)
+            keep.append(v)
+            arr[i] = _Dm(d["alt"], d["pitch"], d["coupling"], d["nx"], d["ny"],
+                         v.ctypes.data_as(C.POINTER(C.c_uint8)), d["surf_n"], d["surf_dx"])
+        self._ck(lib().mcao_load_dms(self.h, len(dms), arr))
+
+    def load_reconstructor(self, R, s_ref=None):
+        if not hasattr(R, "data_ptr"):
+            R = np.ascontiguousarray(R, dtype=np.float32)
+        addr, k, dev = _addr(R)
+        sp = None
+        if s_ref is not None:
+            if not hasattr(s_ref, "data_ptr"):
+                s_ref = np.ascontiguousarray(s_ref, dtype=np.float32)
+            sp, ks, sdev = _addr(s_ref)
+            if sdev != dev:
+                raise ValueError("R and s_ref must both be on the host or both on the device")
+        self._ck(lib().mcao_load_reconstructor(self.h, R.shape[0], R.shape[1], addr, sp, 0, dev))
+
+    # ---------------------------------------------------------------- loop
+    def step(self, n: int = 1):
+        self._ck(lib().mcao_step(self.h, int(n)))
+
+    def sync(self):
+        self._ck(lib().mcao_sync(self.h))
+
+    @property
+    def step_index(self) -> int:
+        k = C.c_int64()
+        self._ck(lib().mcao_get_step_index(self.h, C.byref(k)))
+        return k.value
+
+    # ---------------------------------------------------------------- outputs
+    def slopes(self, out=None) -> np.ndarray:
+        n = self.query(Q_SLOPES)
+        out = np.empty(n, np.float32) if out is None else out
+        self._ck(lib().mcao_get_slopes(self.h, out.ctypes.data, out.size))
+        return out
+
+    def commands(self, out=None) -> np.ndarray:
+        n = self.query(Q_COMMANDS)
+        out = np.empty(n, np.float32) if out is None else out
+        self._ck(lib().mcao_get_commands(self.h, out.ctypes.data, out.size))
+        return out
+
+    def set_commands(self, c):
+        c = np.ascontiguousarray(c, dtype=np.float32)
+        self._ck(lib().mcao_set_commands(self.h, c.ctypes.data, c.size))
+
+    def valid(self, w: int) -> np.ndarray:
+        out = np.empty(self.query(Q_VALID, w), np.int32)
+        self._ck(lib().mcao_get_valid(self.h, w, out.ctypes.data, out.size))
+        return out
+
+    def wfs_phase(self, w: int) -> np.ndarray:
+        ww = self.cfg["wfs"][w]
+        n = ww["n_sub"] * ww["n_px"]
+        out = np.empty((n, n), np.float32)
+        self._ck(lib().mcao_get_wfs_phase(self.h, w, out.ctypes.data, out.size))
+        return out
+
+    def dm_surface(self, m: int) -> np.ndarray:
+        n = self.cfg["dms"][m]["surf_n"]
+        out = np.empty((n, n), np.float32)
+        self._ck(lib().mcao_get_dm_surface(self.h, m, out.ctypes.data, out.size))
+        return out
+
+    def frames(self, w: int):
+        ww = self.cfg["wfs"][w]
+        nd = ww["n_fft"] // ww["n_bin"]
+        nv = self.query(Q_VALID, w)
+        lam = np.empty((nv, nd, nd), np.float32)
+        fr = np.empty((nv, nd, nd), np.int32)
+        self._ck(lib().mcao_get_frames(self.h, w, lam.ctypes.data, fr.ctypes.data, lam.size))
+        return lam, fr
+
+    def psf(self, q: int = 0, with_image: bool = True):
+        M = self.cfg["science"][q]["n_px"] * self.cfg["science"][q]["pad"]
+        out = np.empty((M, M), np.float64) if with_image else None
+        a, b = C.c_double(), C.c_double()
+        self._ck(lib().mcao_get_psf(self.h, q, out.ctypes.data if with_image else None, M * M if with_image else 0,
+                                    C.byref(a), C.byref(b)))
+        return out, a.value, b.value
+
+    def reset_psf(self):
+        self._ck(lib().mcao_reset_psf(self.h))
+
+    def get_state(self) -> bytes:
+        n = self.query(Q_STATE)
+        buf = (C.c_char * n)()
+        self._ck(lib().mcao_get_state(self.h, buf, n))
+        return bytes(buf)
+
+    def set_state(self, blob: bytes):
+        buf = (C.c_char * len(blob)).from_buffer_copy(blob)
+        self._ck(lib().mcao_set_state(self.h, buf, len(blob)))
+
+    def set_profiling(self, on: bool):
+        self._ck(lib().mcao_set_profiling(self.h, int(on)))
+
+    def get_profile(self):
+        ms = (C.c_double * len(STAGES))()
+        cnt = (C.c_int64 * len(STAGES))()
+        lps = C.c_int64()
+        self._ck(lib().mcao_get_profile(self.h, ms, cnt, len(STAGES), C.byref(lps)))
+        return ({s: ms[i] for i, s in enumerate(STAGES)}, {s: cnt[i] for i, s in enumerate(STAGES)}, lps.value)
+
+
+def make_sim(cfg: dict, screens, R, s_ref=None, keep_frames: bool = False, stream=None) -> Sim:
+    """Create a simulation and load the atmosphere, the DMs and the reconstructor."""
+    s = Sim(cfg, keep_frames=keep_frames, stream=stream)
+    s.load_atmosphere(screens)
+    s.load_dms()
+    s.load_reconstructor(R, s_ref)
+    return s

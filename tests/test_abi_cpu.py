@@ -1,0 +1,68 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and exports every
+function include/mcao.h declares; configuration validation rejects bad inputs before any CUDA
+call; the product path does not reach the oracle."""
+import os
+import re
+
+import pytest
+
+from paper_1608_00386_gb300 import build, inputs, mcao
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mcao.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mcao_[a-z_]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    build.build()
+    L = mcao.lib()
+    names = _declared()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(L, n)]
+    assert missing == []
+    assert sorted(mcao.EXPORTS) == names
+
+
+def _expect(status, cfg):
+    with pytest.raises(mcao.McaoError) as ei:
+        mcao.Sim(cfg)
+    assert ei.value.status == status, str(ei.value)
+
+
+@pytest.mark.parametrize("mutate,status", [
+    (lambda c: c.update(D=-1.0), 1),
+    (lambda c: c.update(obstruction=1.0), 1),
+    (lambda c: c.update(lambda_ref=0.0), 1),
+    (lambda c: c.update(gain=float("nan")), 1),
+    (lambda c: c.update(psf_every=-1), 1),
+    (lambda c: c.update(wfs=[]), 1),
+    (lambda c: c["wfs"][0].update(n_fft=8), 7),            # pad < 2
+    (lambda c: c["wfs"][0].update(n_bin=3), 1),            # bin must divide n_fft
+    (lambda c: c["wfs"][0].update(n_px=6, n_fft=12), 7),   # no kernel variant
+    (lambda c: c["wfs"][0].update(valid_thr=1.5), 1),
+    (lambda c: c["wfs"][0].update(type="lgs", height=-1.0), 1),
+    (lambda c: c["science"][0].update(n_px=100), 7),       # not a multiple of 8
+    (lambda c: c["science"][0].update(pad=7), 7),          # FFT size 896 = 2^7 * 7
+])
+def test_config_validation_rejects(mutate, status):
+    build.build()
+    cfg = inputs.scao_tiny()
+    mutate(cfg)
+    _expect(status, cfg)
+
+
+def test_product_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1608_00386_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "mcao_oracle" not in text and "liboracle" not in text, f
+    for f in ("mcao_oracle.c", "__init__.py"):
+        text = open(os.path.join(ROOT, "oracle", f)).read()
+        assert "paper_1608_00386_gb300" not in text and "mcao.h" not in text

@@ -1,0 +1,281 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (written per test) follow the targets for the FP32 step: slopes within 1e-4 pixel
+RMS, commands within 1e-5 relative (norm-wise), long-exposure Strehl within 1e-3 absolute.
+Stage tolerances derive from float32 arithmetic: phases of tens of radians carry ~1e-6 rad of
+rounding, grid coordinates ~1e-6 sample (origin in double, in-tile offset in float).
+Sizes: the 8 m case spans 208 subapertures (26 warps-blocks of 8 with a ragged tail), a
+249 x 416 reconstructor (ragged against the 32-row and 4096-column tiles); the 39 m case is
+the full 6-LGS + 3-NGS workload.
+"""
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_00386_gb300 import build, inputs, mcao
+
+from _helpers import eelt_inputs, scao_tiny_inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    build.build()
+    oracle.build()
+
+
+def _set_k(sim, k):
+    """Set the step index of a library simulation through its checkpoint."""
+    blob = bytearray(sim.get_state())
+    blob[8:16] = int(k).to_bytes(8, "little", signed=True)
+    sim.set_state(bytes(blob))
+
+
+def _rms(a):
+    return float(np.sqrt(np.mean(np.square(a))))
+
+
+# ------------------------------------------------------------------------------------------ DM
+@pytest.mark.parametrize("case", ["scao", "eelt"])
+def test_dm_surface_parity(case):
+    if case == "scao":
+        cfg, screens, R = scao_tiny_inputs()
+    else:
+        cfg, screens, n_cmd = eelt_inputs(2)
+        R = np.zeros((n_cmd, 1), np.float32)
+    rng = np.random.default_rng(21)
+    g = mcao.Sim(cfg)
+    g.load_atmosphere(screens)
+    g.load_dms()
+    c = rng.standard_normal(g.query(mcao.Q_COMMANDS)).astype(np.float32)
+    g.set_commands(c)
+    o = oracle.Sim(cfg, screens)
+    o.set_commands(c.astype(np.float64))
+    for m in range(len(cfg["dms"])):
+        sg = g.dm_surface(m)
+        so = o.dm_surface(m)
+        assert np.max(np.abs(sg - so)) <= 2e-6 * np.max(np.abs(so)) + 1e-6
+
+
+# ------------------------------------------------------------------------------------------ propagation
+@pytest.mark.parametrize("case,wfs", [("scao", 0), ("eelt", 0), ("eelt", 3), ("eelt", 6)])
+def test_wfs_phase_parity(case, wfs):
+    if case == "scao":
+        cfg, screens, R = scao_tiny_inputs()
+    else:
+        cfg, screens, _ = eelt_inputs(10)
+    rng = np.random.default_rng(5)
+    g = mcao.Sim(cfg)
+    g.load_atmosphere(screens)
+    g.load_dms()
+    c = (0.3 * rng.standard_normal(g.query(mcao.Q_COMMANDS))).astype(np.float32)
+    g.set_commands(c)
+    o = oracle.Sim(cfg, screens)
+    o.set_commands(c.astype(np.float64))
+    k = 437
+    _set_k(g, k)
+    o.k = k
+    pg = g.wfs_phase(wfs)
+    po = o.wfs_phase(wfs)
+    scale = max(1.0, float(np.max(np.abs(po))))
+    assert np.max(np.abs(pg - po)) <= 2e-5 * scale
+    assert _rms(pg - po) <= 2e-6 * scale
+
+
+# ------------------------------------------------------------------------------------------ slopes
+@pytest.mark.parametrize("case", ["scao", "eelt"])
+def test_slopes_one_step_noise_free(case):
+    if case == "scao":
+        cfg, screens, R = scao_tiny_inputs()
+    else:
+        cfg, screens, n_cmd = eelt_inputs(10)
+        R = np.zeros((n_cmd, 55608), np.float32)
+    rng = np.random.default_rng(9)
+    g = mcao.make_sim(cfg, screens, R)
+    c = (0.2 * rng.standard_normal(g.query(mcao.Q_COMMANDS))).astype(np.float32)
+    g.set_commands(c)
+    _set_k(g, 12)
+    o = oracle.Sim(cfg, screens, R)
+    o.set_commands(c.astype(np.float64))
+    o.k = 12
+    g.step(1)
+    o.step(1)
+    sg, so = g.slopes(), o.slopes()
+    assert sg.shape == so.shape
+    assert _rms(sg - so) <= 1e-4
+    assert np.max(np.abs(sg - so)) <= 2e-3
+    # slopes are not trivially zero
+    assert _rms(so) > 0.05
+
+
+def test_closed_loop_scao_100_steps():
+    cfg, screens, R = scao_tiny_inputs()
+    g = mcao.make_sim(cfg, screens, R)
+    o = oracle.Sim(cfg, screens, R)
+    worst_s = 0.0
+    for _ in range(10):
+        g.step(10)
+        o.step(10)
+        worst_s = max(worst_s, _rms(g.slopes() - o.slopes()))
+    assert g.step_index == 100
+    assert worst_s <= 1e-4
+    cg, co = g.commands(), o.commands()
+    assert np.linalg.norm(cg - co) / np.linalg.norm(co) <= 1e-5
+    pg, srg, lastg = g.psf()
+    po, sro, lasto = o.psf()
+    assert abs(srg - sro) <= 1e-3 and abs(lastg - lasto) <= 1e-3
+    assert 0.75 < sro < 0.95          # K-band Strehl of the corrected 8 m loop
+    assert np.max(np.abs(pg - po)) <= 1e-4
+
+
+def test_eelt_full_size_steps():
+    cfg, screens, n_cmd = eelt_inputs(10)
+    R = inputs.random_reconstructor(n_cmd, 55608, 1e-4, 3)
+    g = mcao.make_sim(cfg, screens, R)
+    o = oracle.Sim(cfg, screens, R)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        assert _rms(g.slopes() - o.slopes()) <= 1e-4
+    cg, co = g.commands(), o.commands()
+    assert np.linalg.norm(cg - co) / np.linalg.norm(co) <= 1e-5
+    pg, srg, _ = g.psf()
+    po, sro, _ = o.psf()
+    assert abs(srg - sro) <= 1e-3
+    assert np.max(np.abs(pg - po)) <= 1e-4 * max(1.0, po.max())
+
+
+def test_reconstructor_product_full_size():
+    """Delta c = g R s at the 39 m size (8k x 55.6k) against a float64 product of the same s."""
+    cfg, screens, n_cmd = eelt_inputs(10)
+    R = inputs.random_reconstructor(n_cmd, 55608, 1.0, 11)
+    g = mcao.make_sim(cfg, screens, R)
+    c0 = g.commands().astype(np.float64)
+    g.step(1)
+    s = g.slopes().astype(np.float64)
+    dc = (g.commands().astype(np.float64) - c0) / cfg["gain"]
+    ref = R.astype(np.float64) @ s
+    bound = 1e-5 * np.sqrt((R.astype(np.float64) ** 2).sum(axis=1)) * np.linalg.norm(s) + 1e-3
+    assert np.all(np.abs(dc - ref) <= bound)
+
+
+# ------------------------------------------------------------------------------------------ noise
+def test_philox_matches_curand():
+    nvcc = build.nvcc()
+    src = os.path.join(os.path.dirname(__file__), "philox_curand.cu")
+    rng = np.random.default_rng(1)
+    cases = [[0, 0, 0, 0, 0, 0], [0xFFFFFFFF] * 6] + [list(map(int, rng.integers(0, 2 ** 32, 6))) for _ in range(30)]
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "ph")
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-o", exe, src], check=True)
+        out = subprocess.run([exe] + [str(v) for cse in cases for v in cse], check=True, capture_output=True,
+                             text=True).stdout.split("\n")
+    for cse, line in zip(cases, out):
+        ref = [int(w, 16) for w in line.split()]
+        assert list(oracle.philox(cse[:4], cse[4:])) == ref
+
+
+@pytest.mark.parametrize("case,wfs", [("scao", 0), ("eelt", 0), ("eelt", 7)])
+def test_noise_frames_bit_exact_given_lambda(case, wfs):
+    if case == "scao":
+        cfg, screens, R = scao_tiny_inputs()
+        cfg = dict(cfg, noise=True)
+    else:
+        cfg, screens, n_cmd = eelt_inputs(3)
+        cfg = dict(cfg, noise=True)
+        R = inputs.random_reconstructor(n_cmd, 55608, 1e-5, 2)
+    g = mcao.make_sim(cfg, screens, R, keep_frames=True)
+    g.step(3)
+    lam, fr = g.frames(wfs)
+    k = 2
+    w = cfg["wfs"][wfs]
+    ref = oracle.noise_frame(lam.ravel(), w["read_noise"], 0, k, wfs, cfg["seed"])
+    assert np.array_equal(fr.ravel(), ref)
+    assert fr.min() < 0 or w["read_noise"] == 0 or fr.size < 1000  # read noise reaches negative counts
+
+
+def test_noisy_loop_flip_count_and_tolerance():
+    """Noisy 8 m loop: the GPU intensities are float, the oracle's double, so a few counts flip
+    at CDF boundaries; slopes then agree within 3x the noise-free tolerance."""
+    cfg, screens, R = scao_tiny_inputs()
+    cfg = dict(cfg, noise=True)
+    g = mcao.make_sim(cfg, screens, R, keep_frames=True)
+    o = oracle.Sim(cfg, screens, R)
+    g.step(1)
+    o.step(1)
+    _, fg = g.frames(0)
+    _, fo = o.frames(0)
+    flips = int(np.sum(fg != fo))
+    assert flips <= max(3, fg.size // 2000)
+    assert _rms(g.slopes() - o.slopes()) <= 3e-4 * max(1, flips)
+
+
+# ------------------------------------------------------------------------------------------ state
+def test_checkpoint_resume_is_bit_identical():
+    cfg, screens, R = scao_tiny_inputs()
+    cfg = dict(cfg, noise=True)
+    g = mcao.make_sim(cfg, screens, R)
+    g.step(5)
+    blob = g.get_state()
+    g.step(5)
+    a = g.slopes().copy()
+    ca = g.commands().copy()
+    g.set_state(blob)
+    assert g.step_index == 5
+    g.step(5)
+    assert np.array_equal(a, g.slopes()) and np.array_equal(ca, g.commands())
+
+
+def test_device_resident_inputs_and_torch_stream():
+    import torch
+    cfg, screens, R = scao_tiny_inputs()
+    dev = [torch.from_numpy(s).cuda() for s in screens]
+    Rd = torch.from_numpy(R).cuda()
+    st = torch.cuda.Stream()
+    g = mcao.make_sim(cfg, dev, Rd, stream=st)
+    h = mcao.make_sim(cfg, screens, R)
+    g.step(4)
+    h.step(4)
+    assert np.array_equal(g.slopes(), h.slopes())
+
+
+def test_errors_and_degenerate_calls():
+    cfg, screens, R = scao_tiny_inputs()
+    g = mcao.Sim(cfg)
+    with pytest.raises(mcao.McaoError) as e:
+        g.step(1)
+    assert e.value.status == 3
+    g.load_atmosphere(screens)
+    g.load_dms()
+    with pytest.raises(mcao.McaoError) as e:
+        g.load_reconstructor(R[:, :-1])
+    assert e.value.status == 2
+    g.load_reconstructor(R)
+    g.step(0)
+    assert g.step_index == 0
+    with pytest.raises(mcao.McaoError) as e:
+        g.set_commands(np.zeros(3, np.float32))
+    assert e.value.status == 2
+    bad = np.zeros(R.shape[0], np.float32)
+    bad[3] = np.nan
+    with pytest.raises(mcao.McaoError) as e:
+        g.set_commands(bad)
+    assert e.value.status == 1
+    with pytest.raises(mcao.McaoError) as e:
+        g.frames(0)
+    assert e.value.status == 3
+    with pytest.raises(mcao.McaoError) as e:
+        g.step(-1)
+    assert e.value.status == 1
+    # zero reconstructor: commands stay at zero, the loop is open
+    z = mcao.make_sim(cfg, screens, np.zeros_like(R))
+    z.step(3)
+    assert np.all(z.commands() == 0)
