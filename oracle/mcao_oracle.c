@@ -484,8 +484,9 @@ static float box_muller(float u0, float u1) {
 }
 
 /* One noisy detector pixel: photon count ~ Poisson(lambda) plus rint(read_noise * z').
- * lambda < 16: inversion with p_0 = exp(-lambda), p_{k+1} = p_k lambda / (k+1), smallest k with
- * u <= F_k, k capped at 64, u from word 0.  lambda >= 16: max(0, rint(lambda + sqrt(lambda) z)),
+ * lambda < 16: inversion with p_0 = exp(-lambda), p_{k+1} = (p_k lambda) r_{k+1} where
+ * r_j = fl(1/j) is the correctly rounded float reciprocal, smallest k with u <= F_k, k capped
+ * at 64, u from word 0.  lambda >= 16: max(0, rint(lambda + sqrt(lambda) z)),
  * z Box-Muller of words 0 and 1.  Read noise z' is Box-Muller of words 2 and 3.
  * Counter = (c0, c1, c2, 0), key = (seed low word, seed high word). */
 int orc_noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1, uint32_t c2, uint64_t seed) {
@@ -498,7 +499,7 @@ int orc_noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1, uint
         int k = 0;
         while (F < u && k < 64) {
             k += 1;
-            p = (p * lam) / (float)k;
+            p = (p * lam) * (1.0f / (float)k);
             F = F + p;
         }
         n = k;
