@@ -12,71 +12,75 @@ namespace mcao {
 // Geometric propagation ("The open loop wave-front measurements" of arXiv:1608.00386: geometric
 // projection of each layer, laser guide star at finite distance).  A pupil point x seen along
 // direction theta from a source at height H crosses altitude h at x (1 - h/H) + h theta
-// (H infinite for natural stars); layers move by (k dt) v.  For a tile of pupil samples with
-// origin (i0, j0) the grid index of sample (i0 + x, j0 + y) is base + frac + x * step, where the
-// origin part is evaluated in double once per tile and the in-tile offset in float.
+// (H infinite for natural stars); layers move by (k dt) v.  The host turns that map into Q32.32
+// fixed-point grid coordinates (GridView); the kernels evaluate, for a T x T tile of pupil
+// samples, one axis entry per grid and per tile column / row (bilinear sampling is separable in
+// x and y), then every sample of the tile reads its two entries per grid.
 // ---------------------------------------------------------------------------------------------
-struct Coef {
-    const float* data;
-    int n, periodic;
-    int bx, by;          // integer part of the origin's grid index (wrapped for layers)
-    float fx, fy;        // fractional part, in [0, 1)
-    float step;          // grid samples per pupil sample
-    float sign;          // +1 layer, -1 DM
+struct AxisEnt {
+    int idx;     // i0 | (i1 << 16): the two neighbouring grid indices
+    float t;     // weight of i1
 };
 
-__device__ __forceinline__ Coef make_coef(const GridDev& g, double N, double dxp, double thx,
-                                          double thy, double H, double t, int i0, int j0) {
-    Coef c;
-    double f = (H > 0.0) ? 1.0 - g.alt / H : 1.0;
-    double u0 = ((double)i0 - 0.5 * (N - 1.0)) * dxp * f + g.alt * thx + t * g.vx;
-    double v0 = ((double)j0 - 0.5 * (N - 1.0)) * dxp * f + g.alt * thy + t * g.vy;
-    double gx = u0 / g.pixel + 0.5 * (double)(g.n - 1);
-    double gy = v0 / g.pixel + 0.5 * (double)(g.n - 1);
-    double flx = floor(gx), fly = floor(gy);
-    long long ix = (long long)flx, iy = (long long)fly;
-    if (g.periodic) {
-        ix %= g.n; if (ix < 0) ix += g.n;
-        iy %= g.n; if (iy < 0) iy += g.n;
+__device__ __forceinline__ AxisEnt axis_entry(long long X, int n, int periodic) {
+    int i = (int)(X >> 32);
+    float t = __uint2float_rn((unsigned)(X & 0xffffffffull)) * 2.3283064365386963e-10f;  // 2^-32
+    int i1;
+    if (periodic) {
+        i %= n;
+        if (i < 0) i += n;
+        i1 = (i + 1 == n) ? 0 : i + 1;
+    } else {
+        if (i < 0) {
+            i = 0;
+            t = 0.0f;
+        } else if (i >= n - 1) {
+            i = n - 2;
+            t = 1.0f;
+        }
+        i1 = i + 1;
     }
-    c.data = g.data;
-    c.n = g.n;
-    c.periodic = g.periodic;
-    c.bx = (int)ix;
-    c.by = (int)iy;
-    c.fx = (float)(gx - flx);
-    c.fy = (float)(gy - fly);
-    c.step = (float)(dxp * f / g.pixel);
-    c.sign = g.sign;
-    return c;
+    AxisEnt e;
+    e.idx = i | (i1 << 16);
+    e.t = t;
+    return e;
 }
 
-// bilinear sample of one grid at in-tile offset (x, y); periodic wrap for layers, index clamp
-// into [0, n-1] for DM surfaces
-__device__ __forceinline__ float sample_coef(const Coef& c, float x, float y) {
-    float px = fmaf(x, c.step, c.fx), py = fmaf(y, c.step, c.fy);
-    float flx = floorf(px), fly = floorf(py);
-    float tx = px - flx, ty = py - fly;
-    int ix = c.bx + (int)flx, iy = c.by + (int)fly;
-    int n = c.n;
-    int ix1, iy1;
-    if (c.periodic) {
-        while (ix >= n) ix -= n;
-        while (iy >= n) iy -= n;
-        ix1 = (ix + 1 == n) ? 0 : ix + 1;
-        iy1 = (iy + 1 == n) ? 0 : iy + 1;
-    } else {
-        if (ix < 0) { ix = 0; tx = 0.0f; } else if (ix >= n - 1) { ix = n - 2; tx = 1.0f; }
-        if (iy < 0) { iy = 0; ty = 0.0f; } else if (iy >= n - 1) { iy = n - 2; ty = 1.0f; }
-        ix1 = ix + 1;
-        iy1 = iy + 1;
+// entries of every grid for the T x T tile with origin (i0, j0): ex[g T + x], ey[g T + y]
+__device__ __forceinline__ void tile_entries(const GridView* V, int n_grids, long long k, int i0, int j0,
+                                             int T, AxisEnt* ex, AxisEnt* ey, int tid, int nthr) {
+    for (int e = tid; e < n_grids * 2 * T; e += nthr) {
+        int g = e / (2 * T), r = e - g * 2 * T;
+        const GridView& v = V[g];
+        if (r < T) {
+            ex[g * T + r] = axis_entry(v.ax + (long long)(i0 + r) * v.bp + k * v.vx, v.n, v.periodic);
+        } else {
+            int y = r - T;
+            ey[g * T + y] = axis_entry(v.ay + (long long)(j0 + y) * v.bp + k * v.vy, v.n, v.periodic);
+        }
     }
-    const float* r0 = c.data + (long long)iy * n;
-    const float* r1 = c.data + (long long)iy1 * n;
-    float a = __ldg(r0 + ix), b = __ldg(r0 + ix1), d = __ldg(r1 + ix), e = __ldg(r1 + ix1);
-    float top = fmaf(tx, b - a, a);
-    float bot = fmaf(tx, e - d, d);
-    return c.sign * fmaf(ty, bot - top, top);
+}
+
+__device__ __forceinline__ float bilinear(const float* data, int n, AxisEnt ex, AxisEnt ey) {
+    const int x0 = ex.idx & 0xffff, x1 = ex.idx >> 16;
+    const float* r0 = data + (ey.idx & 0xffff) * n;
+    const float* r1 = data + (ey.idx >> 16) * n;
+    float a = __ldg(r0 + x0), b = __ldg(r0 + x1), c = __ldg(r1 + x0), d = __ldg(r1 + x1);
+    float top = fmaf(ex.t, b - a, a);
+    float bot = fmaf(ex.t, d - c, c);
+    return fmaf(ey.t, bot - top, top);
+}
+
+// residual phase (layers - DMs) at tile sample (x, y)
+__device__ __forceinline__ float tile_phase(const GridView* V, int n_grids, const AxisEnt* ex,
+                                            const AxisEnt* ey, int T, int x, int y) {
+    float phi = 0.0f;
+#pragma unroll 4
+    for (int g = 0; g < n_grids; ++g) {
+        float v = bilinear(V[g].data, V[g].n, ex[g * T + x], ey[g * T + y]);
+        phi = fmaf(V[g].sign, v, phi);
+    }
+    return phi;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -199,8 +203,8 @@ __device__ __forceinline__ float2* stockham_fft(float2* a, float2* b, int N, con
 // Detector noise.  Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by the
 // seed, counter (pixel, step, WFS, 0); float sampler with a fixed operation order written with
 // round-to-nearest intrinsics (never contracted), so one float intensity maps to one integer:
-//   lambda < 16: Poisson by inversion, p0 = exp(-lambda), p_{k+1} = p_k lambda / (k+1), smallest
-//                k with u <= F_k (k <= 64), u from word 0;
+//   lambda < 16: Poisson by inversion, p0 = exp(-lambda), p_{k+1} = (p_k lambda) fl(1/(k+1)),
+//                smallest k with u <= F_k (k <= 64), u from word 0;
 //   lambda >= 16: max(0, rint(lambda + sqrt(lambda) z)), z = Box-Muller(words 0, 1);
 //   read noise rint(sigma z'), z' = Box-Muller(words 2, 3).
 // exp: Cody-Waite reduction by ln 2 (two-part constant) and a degree-7 Taylor polynomial; log:
@@ -210,13 +214,13 @@ __device__ __forceinline__ float2* stockham_fft(float2* a, float2* b, int N, con
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
-        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
-        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        unsigned long long p0 = 0xD2511F53ull * (unsigned long long)c[0];
+        unsigned long long p1 = 0xCD9E8D57ull * (unsigned long long)c[2];
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
         c[0] = n0;
-        c[1] = lo1;
+        c[1] = (uint32_t)p1;
         c[2] = n2;
-        c[3] = lo0;
+        c[3] = (uint32_t)p0;
         if (r < 9) {
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
@@ -296,8 +300,13 @@ __device__ __forceinline__ float nz_box_muller(float u0, float u1) {
     return __fmul_rn(rad, nz_cos2pi(u1));
 }
 
+// recip[j] = fl(1/j), j = 0..64 (entry 0 unused), filled with correctly rounded divisions
+__device__ __forceinline__ void fill_recip(float* recip, int tid, int nthr) {
+    for (int j = tid; j <= 64; j += nthr) recip[j] = (j > 0) ? __fdiv_rn(1.0f, (float)j) : 0.0f;
+}
+
 __device__ __forceinline__ int noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1,
-                                            uint32_t c2, unsigned long long seed) {
+                                            uint32_t c2, unsigned long long seed, const float* recip) {
     uint32_t w[4] = {c0, c1, c2, 0u};
     philox4x32_10(w, (uint32_t)seed, (uint32_t)(seed >> 32));
     int n;
@@ -307,7 +316,7 @@ __device__ __forceinline__ int noise_sample(float lam, float read_noise, uint32_
         int k = 0;
         while (F < u && k < 64) {
             k += 1;
-            p = __fdiv_rn(__fmul_rn(p, lam), (float)k);
+            p = __fmul_rn(__fmul_rn(p, lam), recip[k]);
             F = __fadd_rn(F, p);
         }
         n = k;

@@ -2,10 +2,12 @@
 // control matrix give differential coefficients added to the mirror commands; pure integrator):
 //   Delta c = R s,   c <- c + g Delta c.
 // R is float32 [n_cmd][n_slopes], far larger than L2, and is read exactly once per step, so the
-// product is bound by HBM bandwidth.  Split-K: block (rb, kc) multiplies 32 rows by one
-// 4096-column chunk of s held in shared memory; each warp streams four rows at a time with
-// 16-byte evict-first loads and writes its row sums to a partial buffer [n_chunks][n_cmd];
-// a second kernel adds the partials in a fixed order (deterministic) and applies the gain.
+// product is bound by HBM bandwidth.  The product is issued per slice of columns (one slice per
+// wavefront sensor, so a slice can start as soon as its sensor's slopes exist) and split-K
+// inside a slice: block (rb, kc) multiplies 32 rows by one column chunk of s held in shared
+// memory; each warp streams four rows at a time with 16-byte evict-first loads and writes its
+// row sums to a partial buffer [n_chunks][n_cmd].  A second kernel adds the partials in a fixed
+// order (deterministic) and applies the gain.
 #include "mcao_internal.h"
 
 namespace mcao {
@@ -28,17 +30,17 @@ __device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
 __global__ void __launch_bounds__(256) recon_gemv_kernel(ReconLaunch L) {
     __shared__ float4 s_sh[kKC / 4];
     const int kc = blockIdx.y;
-    const int col0 = kc * kKC;
-    int ncols = L.ld - col0;
-    if (ncols > kKC) ncols = kKC;
-    const int n4 = ncols / 4;
+    const int c_begin = kc * L.kc;                 // column offset inside the slice
+    int ncols = L.len - c_begin;
+    if (ncols > L.kc) ncols = L.kc;
+    const int n4 = (ncols + 3) / 4;                // R rows are zero-padded to a multiple of 4
     for (int i = threadIdx.x; i < n4; i += blockDim.x) {
-        int c = col0 + 4 * i;
+        int c = c_begin + 4 * i;
         float4 v;
-        v.x = (c + 0 < L.n_slopes) ? L.s[c + 0] : 0.0f;
-        v.y = (c + 1 < L.n_slopes) ? L.s[c + 1] : 0.0f;
-        v.z = (c + 2 < L.n_slopes) ? L.s[c + 2] : 0.0f;
-        v.w = (c + 3 < L.n_slopes) ? L.s[c + 3] : 0.0f;
+        v.x = (c + 0 < L.len) ? L.s[L.s0 + c + 0] : 0.0f;
+        v.y = (c + 1 < L.len) ? L.s[L.s0 + c + 1] : 0.0f;
+        v.z = (c + 2 < L.len) ? L.s[L.s0 + c + 2] : 0.0f;
+        v.w = (c + 3 < L.len) ? L.s[L.s0 + c + 3] : 0.0f;
         s_sh[i] = v;
     }
     __syncthreads();
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(256) recon_gemv_kernel(ReconLaunch L) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.x * kRB + warp * kRowsPerWarp;
     const size_t ld4 = (size_t)L.ld / 4;
-    const float4* r0 = reinterpret_cast<const float4*>(L.R) + (size_t)row0 * ld4 + col0 / 4;
+    const float4* r0 = reinterpret_cast<const float4*>(L.R) + (size_t)row0 * ld4 + (L.col0 + c_begin) / 4;
     const float4* r1 = r0 + ld4;
     const float4* r2 = r1 + ld4;
     const float4* r3 = r2 + ld4;
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(256) recon_gemv_kernel(ReconLaunch L) {
         a3 += __shfl_xor_sync(0xffffffffu, a3, o);
     }
     if (lane == 0) {
-        float* p = L.partial + (size_t)kc * L.n_cmd;
+        float* p = L.partial + (size_t)(L.chunk0 + kc) * L.n_cmd;
         if (row0 + 0 < L.n_cmd) p[row0 + 0] = a0;
         if (row0 + 1 < L.n_cmd) p[row0 + 1] = a1;
         if (row0 + 2 < L.n_cmd) p[row0 + 2] = a2;
@@ -87,29 +89,27 @@ __global__ void __launch_bounds__(256) recon_gemv_kernel(ReconLaunch L) {
     }
 }
 
-__global__ void recon_reduce_kernel(ReconLaunch L, int n_chunks) {
+__global__ void recon_reduce_kernel(ReduceLaunch L) {
     int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row == 0 && L.st) L.st->k_next = L.st->k + 1;
     if (row >= L.n_cmd) return;
     float acc = 0.0f;
-    for (int kc = 0; kc < n_chunks; ++kc) acc += L.partial[(size_t)kc * L.n_cmd + row];
+    for (int kc = 0; kc < L.n_chunks; ++kc) acc += L.partial[(size_t)kc * L.n_cmd + row];
     L.c[row] = fmaf(L.gain, acc, L.c[row]);
 }
 
 }  // namespace
 
-int recon_chunks(int n_slopes) { return (n_slopes + kKC - 1) / kKC; }
-
 cudaError_t launch_recon(const ReconLaunch& L, cudaStream_t s) {
-    if (L.n_cmd <= 0) return cudaSuccess;
-    dim3 grid((unsigned)(L.rows_pad / kRB), (unsigned)recon_chunks(L.n_slopes));
+    if (L.n_cmd <= 0 || L.len <= 0) return cudaSuccess;
+    dim3 grid((unsigned)(L.rows_pad / kRB), (unsigned)((L.len + L.kc - 1) / L.kc));
     recon_gemv_kernel<<<grid, 256, 0, s>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_recon_reduce(const ReconLaunch& L, cudaStream_t s) {
+cudaError_t launch_recon_reduce(const ReduceLaunch& L, cudaStream_t s) {
     int n = L.n_cmd > 0 ? L.n_cmd : 1;
-    recon_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, recon_chunks(L.n_slopes));
+    recon_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -16,23 +16,23 @@ namespace {
 constexpr int kRowsPerBlock = 4;
 
 __global__ void __launch_bounds__(256) sci_field_kernel(SciLaunch L) {
-    __shared__ Coef s_cf[8][kMaxEntries];
+    __shared__ AxisEnt s_ex[8][kMaxEntries * 8];
+    __shared__ AxisEnt s_ey[8][kMaxEntries * 8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_x = L.N / 8;
     const int tile = blockIdx.x * 8 + warp;
     if (tile >= tiles_x * tiles_x) return;
     const int i0 = (tile % tiles_x) * 8, j0 = (tile / tiles_x) * 8;
-    Coef* cf = s_cf[warp];
-    if (lane < L.ctx.n_grids) {
-        double t = (double)L.ctx.st->k * L.ctx.dt;
-        cf[lane] = make_coef(L.ctx.grids[lane], (double)L.N, L.dx, L.theta_x, L.theta_y, 0.0, t, i0, j0);
-    }
+    const int n_grids = L.ctx.n_grids;
+    const GridView* V = L.ctx.views + (long long)L.view * n_grids;
+    tile_entries(V, n_grids, L.ctx.st->k, i0, j0, 8, s_ex[warp], s_ey[warp], lane, 32);
     __syncwarp();
     float sr = 0.0f, si = 0.0f;
-    for (int q = lane; q < 64; q += 32) {
-        int x = q % 8, y = q / 8;
-        float phi = 0.0f;
-        for (int g = 0; g < L.ctx.n_grids; ++g) phi += sample_coef(cf[g], (float)x, (float)y);
+    const int x = lane & 7;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        const int y = (lane >> 3) + 4 * hh;
+        float phi = tile_phase(V, n_grids, s_ex[warp], s_ey[warp], 8, x, y);
         float a = __ldg(L.amp + (long long)(j0 + y) * L.N + i0 + x);
         float sn, cs;
         sincosf(L.scale * phi, &sn, &cs);
@@ -121,8 +121,8 @@ __global__ void __launch_bounds__(256) sci_cols_kernel(SciLaunch L) {
     for (int q = tid; q < kRowsPerBlock * L.M; q += nthr) {
         int r = q / L.M, j = q - r * L.M;
         float2 v = R[q];
-        double p = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-        L.psf_t[(long long)(c0 + r) * L.M + j] += p;
+        float p = fmaf(v.x, v.x, v.y * v.y);   // frame intensity in float, accumulated in double
+        L.psf_t[(long long)(c0 + r) * L.M + j] += (double)p;
     }
     if (blockIdx.x == 0 && tid == 0) L.acc->n_psf += 1;
 }

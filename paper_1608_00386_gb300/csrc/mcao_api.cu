@@ -1,9 +1,12 @@
 // Host side of libmcao: the C ABI declared in include/mcao.h.  Validates the configuration,
-// derives geometry (pupils, valid subapertures, elongation, influence-function tables), owns the
-// device state, and issues one closed-loop step as a CUDA graph with three branches:
-//   s0: DM surfaces -> main WFS kernel -> reconstructor product -> reduction/integrator
-//   s1: other WFS kernels (joined before the reconstructor)
-//   s2: science field, row FFT (+ Strehl), column FFT (+ PSF accumulation)
+// derives geometry (pupils, valid subapertures, elongation, fixed-point projection maps,
+// influence-function tables), owns the device state, and issues one closed-loop step as a CUDA
+// graph whose branches overlap the ALU-bound sensing with the HBM-bound reconstructor product:
+//   s0 (high priority): DM surfaces -> WFS kernel of sensor 0 -> sensor 1 -> ...
+//   s1: block-per-subaperture WFS kernels (low-order sensors)
+//   s3: reconstructor slice of sensor w as soon as sensor w's slopes exist, ..., reduction and
+//       integrator
+//   s2 (low priority): science field, row FFT (+ Strehl), column FFT (+ PSF accumulation)
 // Every stage is a kernel of this library (k_dm.cu, k_wfs.cu, k_recon.cu, k_science.cu).
 #include <cuda_runtime.h>
 
@@ -24,13 +27,6 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct Group {                 // WFSs sharing one kernel variant
-    int n_px, n_fft, n_bin;
-    std::vector<int> wfs;
-    SubapDev* d_subaps = nullptr;
-    int n_subaps = 0;
-};
-
 struct Science {
     mcao_science p;
     int N, M;
@@ -48,15 +44,32 @@ struct Science {
 struct WfsHost {
     mcao_wfs p;
     int N, n_det, n_valid, slope0, frame0;
+    int rcol0 = 0;                 // first column of this sensor's block in the padded R
     double dx;
+    bool fft_route = false;
     std::vector<float> amp;
     std::vector<int> valid;        // subaperture index sy*n_sub+sx
     std::vector<double> frac;
     std::vector<SubapDev> subaps;
+    SubapDev* d_subaps = nullptr;
 };
 
-// profiling stages
-enum { ST_DM = 0, ST_WFS_MAIN, ST_WFS_AUX, ST_RECON, ST_REDUCE, ST_SCIENCE, ST_COUNT };
+struct FftGroup {                  // block-per-subaperture sensors sharing one kernel variant
+    int n_px, n_fft, n_bin;
+    std::vector<int> wfs;
+    SubapDev* d_subaps = nullptr;
+    int n_subaps = 0;
+};
+
+struct ProfSlot {                  // event-record nodes around one launch of one stage
+    int stage;
+    cudaEvent_t tpl_a = nullptr, tpl_b = nullptr;
+    cudaGraphNode_t na = nullptr, nb = nullptr;
+};
+
+enum { ST_DM = MCAO_STAGE_DM, ST_WFS_MAIN = MCAO_STAGE_WFS_MAIN, ST_WFS_AUX = MCAO_STAGE_WFS_AUX,
+       ST_RECON = MCAO_STAGE_RECON, ST_REDUCE = MCAO_STAGE_RECON_REDUCE, ST_SCIENCE = MCAO_STAGE_SCIENCE,
+       ST_COUNT = MCAO_N_STAGES };
 
 }  // namespace
 
@@ -64,15 +77,16 @@ struct mcao_sim {
     mcao_config cfg{};
     std::vector<WfsHost> wfs;
     std::vector<Science> sci;
-    std::vector<Group> groups;
+    std::vector<FftGroup> fft_groups;
     std::string err;
     int device = 0;
-    int n_slopes = 0, n_frame_px = 0;
+    int n_slopes = 0, n_frame_px = 0, ld = 0;
 
-    cudaStream_t s0 = nullptr, s1 = nullptr, s2 = nullptr;
+    cudaStream_t s0 = nullptr, s1 = nullptr, s2 = nullptr, s3 = nullptr;
     cudaStream_t user = nullptr;
     bool user_set = false;
-    cudaEvent_t ev_fork = nullptr, ev_join1 = nullptr, ev_join2 = nullptr, ev_user = nullptr, ev_done = nullptr;
+    std::vector<cudaEvent_t> ev_pool;     // dependency events used while capturing
+    cudaEvent_t ev_user = nullptr, ev_done = nullptr;
 
     // wfs
     WfsDev* d_wfs = nullptr;
@@ -93,27 +107,29 @@ struct mcao_sim {
     int n_dms = 0;
     std::vector<mcao_dm> dms;
     std::vector<DmDesc> dm_desc;
-    std::vector<int> dm_ncmd;
     DmDesc* d_dm_desc = nullptr;
     float* d_dm_g = nullptr;
     int2* d_dm_band = nullptr;
     int* d_dm_map = nullptr;
     float* d_dm_tmp = nullptr;
     float* d_dm_surf = nullptr;
-    long long dm_tmp_total = 0, dm_surf_total = 0;
-    long long dm_tmp_start[kMaxDms] = {0}, dm_surf_start[kMaxDms] = {0};
+    int dm_pass1_blocks = 0;
+    int dm_tile_start[kMaxDms + 1] = {0};
     int n_cmd = 0;
     bool dms_loaded = false;
 
-    // grids = layers then DMs
-    GridDev* d_grids = nullptr;
+    // grid views (layers then DMs) for every WFS and science direction
+    GridView* d_views = nullptr;
     int n_grids = 0;
 
     // reconstructor
     float* d_R = nullptr;
-    int ld = 0, rows_pad = 0;
+    int rows_pad = 0;
     float* d_c = nullptr;
     float* d_partial = nullptr;
+    std::vector<ReconLaunch> slices;      // one per sensor with slopes
+    std::vector<int> slice_wfs;
+    int n_chunks = 0;
     bool recon_loaded = false;
 
     StepState* d_st = nullptr;
@@ -123,8 +139,7 @@ struct mcao_sim {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_dirty = true;
-    cudaGraphNode_t prof_node[2 * ST_COUNT] = {nullptr};  // event-record node of each slot
-    cudaEvent_t prof_tpl[2 * ST_COUNT] = {nullptr};
+    std::vector<ProfSlot> prof_slots;
     bool profiling = false;
     std::vector<cudaEvent_t> prof_pool;
     size_t prof_used = 0;
@@ -169,6 +184,8 @@ void dfree(T*& p) {
 
 bool is_fin(double x) { return std::isfinite(x); }
 
+long long to_q32(double v) { return std::llround(std::ldexp(v, 32)); }
+
 // pupil amplitude on an n x n grid across D (sample i at (i - (n-1)/2) D/n), annulus rule
 std::vector<float> pupil(double D, double obs, int n) {
     std::vector<float> A((size_t)n * n);
@@ -200,16 +217,19 @@ void release_graph(mcao_sim* S) {
     S->exec = nullptr;
     S->graph = nullptr;
     S->graph_dirty = true;
-    for (auto& n : S->prof_node) n = nullptr;
+    for (auto& p : S->prof_slots) {
+        if (p.tpl_a) cudaEventDestroy(p.tpl_a);
+        if (p.tpl_b) cudaEventDestroy(p.tpl_b);
+    }
+    S->prof_slots.clear();
 }
 
 Ctx make_ctx(mcao_sim* S) {
     Ctx c;
-    c.grids = S->d_grids;
+    c.views = S->d_views;
     c.n_grids = S->n_grids;
     c.wfs = S->d_wfs;
     c.st = S->d_st;
-    c.dt = S->cfg.dt;
     c.seed = S->cfg.seed;
     c.noise = S->cfg.noise;
     return c;
@@ -225,27 +245,8 @@ DmLaunch make_dm_launch(mcao_sim* S) {
     L.c = S->d_c;
     L.tmp = S->d_dm_tmp;
     L.surf = S->d_dm_surf;
-    L.tmp_total = S->dm_tmp_total;
-    L.surf_total = S->dm_surf_total;
-    for (int m = 0; m < kMaxDms; ++m) {
-        L.tmp_start[m] = S->dm_tmp_start[m];
-        L.surf_start[m] = S->dm_surf_start[m];
-    }
-    L.st = S->d_st;
-    return L;
-}
-
-ReconLaunch make_recon_launch(mcao_sim* S) {
-    ReconLaunch L{};
-    L.R = S->d_R;
-    L.n_cmd = S->n_cmd;
-    L.n_slopes = S->n_slopes;
-    L.ld = S->ld;
-    L.rows_pad = S->rows_pad;
-    L.s = S->d_slopes;
-    L.partial = S->d_partial;
-    L.c = S->d_c;
-    L.gain = (float)S->cfg.gain;
+    L.pass1_blocks = S->dm_pass1_blocks;
+    for (int m = 0; m <= kMaxDms; ++m) L.tile_start[m] = S->dm_tile_start[m];
     L.st = S->d_st;
     return L;
 }
@@ -254,11 +255,9 @@ SciLaunch make_sci_launch(mcao_sim* S, int q) {
     Science& C = S->sci[q];
     SciLaunch L{};
     L.ctx = make_ctx(S);
+    L.view = (int)S->wfs.size() + q;
     L.N = C.N;
     L.M = C.M;
-    L.dx = C.dx;
-    L.theta_x = C.p.theta_x;
-    L.theta_y = C.p.theta_y;
     L.scale = (float)(S->cfg.lambda_ref / C.p.lambda);
     L.amp = C.d_amp;
     L.field = C.d_field;
@@ -276,11 +275,11 @@ SciLaunch make_sci_launch(mcao_sim* S, int q) {
     return L;
 }
 
-WfsLaunch make_wfs_launch(mcao_sim* S, const Group& g) {
+WfsLaunch make_wfs_launch(mcao_sim* S, const SubapDev* subaps, int n) {
     WfsLaunch L{};
     L.ctx = make_ctx(S);
-    L.subaps = g.d_subaps;
-    L.n_subaps = g.n_subaps;
+    L.subaps = subaps;
+    L.n_subaps = n;
     L.s_ref = S->d_sref;
     L.slopes = S->d_slopes;
     L.lam_out = S->cfg.keep_frames ? S->d_lam : nullptr;
@@ -288,39 +287,51 @@ WfsLaunch make_wfs_launch(mcao_sim* S, const Group& g) {
     return L;
 }
 
-// Rebuild the grid table (layers, then DM surfaces) after either set changes.
-mcao_status rebuild_grids(mcao_sim* S) {
-    std::vector<GridDev> g;
+// Fixed-point projection maps of every grid (layers, then DMs) for every view (WFSs, then
+// science directions): a pupil sample x of a view with N samples across D at height H maps to
+// the grid index (x (1 - h/H) + h theta + (k dt) v) / pixel + (n - 1)/2.
+mcao_status rebuild_views(mcao_sim* S) {
+    struct G { const float* data; int n, periodic; double pixel, alt, vx, vy; float sign; };
+    std::vector<G> grids;
     for (int l = 0; l < S->n_layers; ++l) {
-        GridDev d{};
-        d.data = S->d_layer_ptr[l];
-        d.n = S->layers[l].n;
-        d.periodic = 1;
-        d.pixel = S->layers[l].pixel_m;
-        d.alt = S->layers[l].alt_m;
-        d.vx = S->layers[l].vx;
-        d.vy = S->layers[l].vy;
-        d.sign = 1.0f;
-        g.push_back(d);
+        const mcao_layer& L = S->layers[l];
+        grids.push_back({S->d_layer_ptr[l], L.n, 1, L.pixel_m, L.alt_m, L.vx, L.vy, 1.0f});
     }
     for (int m = 0; m < S->n_dms; ++m) {
-        GridDev d{};
-        d.data = S->d_dm_surf + S->dm_desc[m].surf_off;
-        d.n = S->dms[m].surf_n;
-        d.periodic = 0;
-        d.pixel = S->dms[m].surf_dx;
-        d.alt = S->dms[m].alt_m;
-        d.vx = 0.0;
-        d.vy = 0.0;
-        d.sign = -1.0f;
-        g.push_back(d);
+        const mcao_dm& d = S->dms[m];
+        grids.push_back({S->d_dm_surf + S->dm_desc[m].surf_off, d.surf_n, 0, d.surf_dx, d.alt_m, 0.0, 0.0, -1.0f});
     }
-    if ((int)g.size() > kMaxEntries)
-        return fail(S, MCAO_E_UNSUPPORTED, "layers + DMs = %d exceeds %d", (int)g.size(), kMaxEntries);
-    dfree(S->d_grids);
-    S->n_grids = (int)g.size();
-    CK(dalloc(&S->d_grids, g.size()));
-    if (!g.empty()) CK(cudaMemcpy(S->d_grids, g.data(), sizeof(GridDev) * g.size(), cudaMemcpyHostToDevice));
+    if ((int)grids.size() > kMaxEntries)
+        return fail(S, MCAO_E_UNSUPPORTED, "layers + DMs = %d exceeds %d", (int)grids.size(), kMaxEntries);
+    struct View { int N; double thx, thy, H; };
+    std::vector<View> views;
+    for (const auto& w : S->wfs)
+        views.push_back({w.N, w.p.theta_x, w.p.theta_y, w.p.type == MCAO_WFS_LGS ? w.p.height : 0.0});
+    for (const auto& c : S->sci) views.push_back({c.N, c.p.theta_x, c.p.theta_y, 0.0});
+    std::vector<GridView> out;
+    const double D = S->cfg.D, dt = S->cfg.dt;
+    for (const auto& v : views) {
+        const double dxp = D / (double)v.N;
+        for (const auto& g : grids) {
+            double f = (v.H > 0.0) ? 1.0 - g.alt / v.H : 1.0;
+            double x0 = (0.0 - 0.5 * (double)(v.N - 1)) * dxp * f;
+            GridView gv{};
+            gv.data = g.data;
+            gv.n = g.n;
+            gv.periodic = g.periodic;
+            gv.ax = to_q32((x0 + g.alt * v.thx) / g.pixel + 0.5 * (double)(g.n - 1));
+            gv.ay = to_q32((x0 + g.alt * v.thy) / g.pixel + 0.5 * (double)(g.n - 1));
+            gv.bp = to_q32(dxp * f / g.pixel);
+            gv.vx = to_q32(dt * g.vx / g.pixel);
+            gv.vy = to_q32(dt * g.vy / g.pixel);
+            gv.sign = g.sign;
+            out.push_back(gv);
+        }
+    }
+    dfree(S->d_views);
+    S->n_grids = (int)grids.size();
+    CK(dalloc(&S->d_views, out.size()));
+    if (!out.empty()) CK(cudaMemcpy(S->d_views, out.data(), sizeof(GridView) * out.size(), cudaMemcpyHostToDevice));
     release_graph(S);
     return MCAO_OK;
 }
@@ -328,64 +339,108 @@ mcao_status rebuild_grids(mcao_sim* S) {
 // ---------------------------------------------------------------------------------------------
 // step issue
 // ---------------------------------------------------------------------------------------------
-void prof_mark(mcao_sim* S, int slot, cudaStream_t st) {
-    cudaEventRecordWithFlags(S->prof_tpl[slot], st, cudaEventRecordExternal);
+cudaEvent_t dep_event(mcao_sim* S, size_t& used) {
+    if (used >= S->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        S->ev_pool.push_back(e);
+    }
+    return S->ev_pool[used++];
 }
 
-// Queue one step on s0/s1/s2 (captured into the graph).  Returns the first launch error.
+// profiling: an event-record node before and after a launch (recorded into per-step events
+// only while profiling is on)
+int prof_begin(mcao_sim* S, int stage, cudaStream_t st) {
+    ProfSlot p;
+    p.stage = stage;
+    cudaEventCreate(&p.tpl_a);
+    cudaEventCreate(&p.tpl_b);
+    cudaEventRecordWithFlags(p.tpl_a, st, cudaEventRecordExternal);
+    S->prof_slots.push_back(p);
+    return (int)S->prof_slots.size() - 1;
+}
+
+void prof_end(mcao_sim* S, int slot, cudaStream_t st) {
+    cudaEventRecordWithFlags(S->prof_slots[slot].tpl_b, st, cudaEventRecordExternal);
+}
+
+// Queue one step (captured into the graph).  Returns the first launch error.
 cudaError_t enqueue_step(mcao_sim* S, int* launches) {
     cudaError_t e;
     int nl = 0;
-    prof_mark(S, 2 * ST_DM, S->s0);
-    DmLaunch dl = make_dm_launch(S);
-    if ((e = launch_dm_surfaces(dl, S->s0)) != cudaSuccess) return e;
+    size_t used = 0;
+    int slot = prof_begin(S, ST_DM, S->s0);
+    if ((e = launch_dm_surfaces(make_dm_launch(S), S->s0)) != cudaSuccess) return e;
     nl += S->n_dms > 0 ? 2 : 1;
-    prof_mark(S, 2 * ST_DM + 1, S->s0);
-    if ((e = cudaEventRecord(S->ev_fork, S->s0)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(S->s1, S->ev_fork, 0)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(S->s2, S->ev_fork, 0)) != cudaSuccess) return e;
+    prof_end(S, slot, S->s0);
+    cudaEvent_t ev_fork = dep_event(S, used);
+    if ((e = cudaEventRecord(ev_fork, S->s0)) != cudaSuccess) return e;
+    for (cudaStream_t st : {S->s1, S->s2, S->s3})
+        if ((e = cudaStreamWaitEvent(st, ev_fork, 0)) != cudaSuccess) return e;
 
-    // auxiliary WFS groups on s1
-    prof_mark(S, 2 * ST_WFS_AUX, S->s1);
-    for (size_t gi = 1; gi < S->groups.size(); ++gi) {
-        const Group& g = S->groups[gi];
-        if ((e = launch_wfs(make_wfs_launch(S, g), g.n_px, g.n_fft, g.n_bin, S->s1)) != cudaSuccess) return e;
-        ++nl;
-    }
-    prof_mark(S, 2 * ST_WFS_AUX + 1, S->s1);
-    if ((e = cudaEventRecord(S->ev_join1, S->s1)) != cudaSuccess) return e;
-
-    // science on s2
-    prof_mark(S, 2 * ST_SCIENCE, S->s2);
+    // science on s2 (low priority, fills idle SMs)
     for (size_t q = 0; q < S->sci.size(); ++q) {
         SciLaunch L = make_sci_launch(S, (int)q);
+        slot = prof_begin(S, ST_SCIENCE, S->s2);
         if ((e = launch_sci_field(L, S->s2)) != cudaSuccess) return e;
         if ((e = launch_sci_rows(L, S->s2)) != cudaSuccess) return e;
         if ((e = launch_sci_cols(L, S->s2)) != cudaSuccess) return e;
+        prof_end(S, slot, S->s2);
         nl += 3;
     }
-    prof_mark(S, 2 * ST_SCIENCE + 1, S->s2);
-    if ((e = cudaEventRecord(S->ev_join2, S->s2)) != cudaSuccess) return e;
+    cudaEvent_t ev_sci = dep_event(S, used);
+    if ((e = cudaEventRecord(ev_sci, S->s2)) != cudaSuccess) return e;
 
-    // main WFS group on s0
-    prof_mark(S, 2 * ST_WFS_MAIN, S->s0);
-    if (!S->groups.empty()) {
-        const Group& g = S->groups[0];
-        if ((e = launch_wfs(make_wfs_launch(S, g), g.n_px, g.n_fft, g.n_bin, S->s0)) != cudaSuccess) return e;
+    // block-per-subaperture sensors on s1
+    std::vector<cudaEvent_t> ready(S->wfs.size(), nullptr);
+    for (const auto& g : S->fft_groups) {
+        slot = prof_begin(S, ST_WFS_AUX, S->s1);
+        if ((e = launch_wfs(make_wfs_launch(S, g.d_subaps, g.n_subaps), g.n_px, g.n_fft, g.n_bin, S->s1)) != cudaSuccess)
+            return e;
+        prof_end(S, slot, S->s1);
+        ++nl;
+        cudaEvent_t ev = dep_event(S, used);
+        if ((e = cudaEventRecord(ev, S->s1)) != cudaSuccess) return e;
+        for (int w : g.wfs) ready[w] = ev;
+    }
+
+    // warp-per-subaperture sensors, one launch each, on s0
+    for (size_t w = 0; w < S->wfs.size(); ++w) {
+        const WfsHost& W = S->wfs[w];
+        if (W.fft_route || W.n_valid == 0) continue;
+        slot = prof_begin(S, ST_WFS_MAIN, S->s0);
+        if ((e = launch_wfs(make_wfs_launch(S, W.d_subaps, W.n_valid), W.p.n_px, W.p.n_fft, W.p.n_bin, S->s0)) !=
+            cudaSuccess)
+            return e;
+        prof_end(S, slot, S->s0);
+        ++nl;
+        cudaEvent_t ev = dep_event(S, used);
+        if ((e = cudaEventRecord(ev, S->s0)) != cudaSuccess) return e;
+        ready[w] = ev;
+    }
+
+    // reconstructor slices on s3, each after its sensor, then the reduction
+    for (size_t i = 0; i < S->slices.size(); ++i) {
+        cudaEvent_t ev = ready[S->slice_wfs[i]];
+        if (ev && (e = cudaStreamWaitEvent(S->s3, ev, 0)) != cudaSuccess) return e;
+        slot = prof_begin(S, ST_RECON, S->s3);
+        if ((e = launch_recon(S->slices[i], S->s3)) != cudaSuccess) return e;
+        prof_end(S, slot, S->s3);
         ++nl;
     }
-    prof_mark(S, 2 * ST_WFS_MAIN + 1, S->s0);
-    if ((e = cudaStreamWaitEvent(S->s0, S->ev_join1, 0)) != cudaSuccess) return e;
+    ReduceLaunch rl{S->n_cmd, S->n_chunks, S->d_partial, S->d_c, (float)S->cfg.gain, S->d_st};
+    slot = prof_begin(S, ST_REDUCE, S->s3);
+    if ((e = launch_recon_reduce(rl, S->s3)) != cudaSuccess) return e;
+    prof_end(S, slot, S->s3);
+    ++nl;
 
-    ReconLaunch rl = make_recon_launch(S);
-    prof_mark(S, 2 * ST_RECON, S->s0);
-    if ((e = launch_recon(rl, S->s0)) != cudaSuccess) return e;
-    prof_mark(S, 2 * ST_RECON + 1, S->s0);
-    prof_mark(S, 2 * ST_REDUCE, S->s0);
-    if ((e = launch_recon_reduce(rl, S->s0)) != cudaSuccess) return e;
-    prof_mark(S, 2 * ST_REDUCE + 1, S->s0);
-    nl += (S->n_cmd > 0 ? 2 : 1);
-    if ((e = cudaStreamWaitEvent(S->s0, S->ev_join2, 0)) != cudaSuccess) return e;
+    // join every branch back into s0
+    cudaEvent_t ev_gemv = dep_event(S, used);
+    if ((e = cudaEventRecord(ev_gemv, S->s3)) != cudaSuccess) return e;
+    cudaEvent_t ev_s1 = dep_event(S, used);
+    if ((e = cudaEventRecord(ev_s1, S->s1)) != cudaSuccess) return e;
+    for (cudaEvent_t ev : {ev_gemv, ev_sci, ev_s1})
+        if ((e = cudaStreamWaitEvent(S->s0, ev, 0)) != cudaSuccess) return e;
     if (launches) *launches = nl;
     return cudaSuccess;
 }
@@ -403,7 +458,7 @@ mcao_status build_graph(mcao_sim* S) {
     }
     if (e2 != cudaSuccess) return fail(S, MCAO_E_CUDA, "end capture: %s", cudaGetErrorString(e2));
     S->graph = g;
-    CK(cudaGraphInstantiate(&S->exec, S->graph, 0));
+    CK(cudaGraphInstantiate(&S->exec, S->graph, cudaGraphInstantiateFlagUseNodePriority));
     // locate the profiling event-record nodes
     size_t n = 0;
     CK(cudaGraphGetNodes(S->graph, nullptr, &n));
@@ -415,8 +470,10 @@ mcao_status build_graph(mcao_sim* S) {
         if (t != cudaGraphNodeTypeEventRecord) continue;
         cudaEvent_t ev;
         CK(cudaGraphEventRecordNodeGetEvent(nodes[i], &ev));
-        for (int slot = 0; slot < 2 * ST_COUNT; ++slot)
-            if (S->prof_tpl[slot] == ev) S->prof_node[slot] = nodes[i];
+        for (auto& p : S->prof_slots) {
+            if (p.tpl_a == ev) p.na = nodes[i];
+            if (p.tpl_b == ev) p.nb = nodes[i];
+        }
     }
     S->launches_per_step = nl;
     S->graph_dirty = false;
@@ -438,20 +495,18 @@ mcao_status signal_user(mcao_sim* S) {
 }
 
 mcao_status sync_all(mcao_sim* S) {
-    CK(cudaStreamSynchronize(S->s0));
-    CK(cudaStreamSynchronize(S->s1));
-    CK(cudaStreamSynchronize(S->s2));
+    for (cudaStream_t st : {S->s0, S->s1, S->s2, S->s3}) CK(cudaStreamSynchronize(st));
     return MCAO_OK;
 }
 
 void destroy_all(mcao_sim* S) {
     if (!S) return;
     cudaSetDevice(S->device);
-    if (S->s0) cudaStreamSynchronize(S->s0);
-    if (S->s1) cudaStreamSynchronize(S->s1);
-    if (S->s2) cudaStreamSynchronize(S->s2);
+    for (cudaStream_t st : {S->s0, S->s1, S->s2, S->s3})
+        if (st) cudaStreamSynchronize(st);
     release_graph(S);
-    for (auto& g : S->groups) dfree(g.d_subaps);
+    for (auto& w : S->wfs) dfree(w.d_subaps);
+    for (auto& g : S->fft_groups) dfree(g.d_subaps);
     for (auto& c : S->sci) {
         dfree(c.d_amp); dfree(c.d_field); dfree(c.d_ft); dfree(c.d_psf_t); dfree(c.d_sr_part); dfree(c.d_w);
     }
@@ -460,15 +515,14 @@ void destroy_all(mcao_sim* S) {
     for (auto p : S->d_layer_owned) cudaFree(p);
     S->d_layer_owned.clear();
     dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map); dfree(S->d_dm_tmp);
-    dfree(S->d_dm_surf); dfree(S->d_grids); dfree(S->d_R); dfree(S->d_c); dfree(S->d_partial);
+    dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_c); dfree(S->d_partial);
     dfree(S->d_st); dfree(S->d_acc);
-    for (auto& e : S->prof_tpl) if (e) cudaEventDestroy(e);
     for (auto e : S->prof_pool) cudaEventDestroy(e);
-    cudaEvent_t evs[] = {S->ev_fork, S->ev_join1, S->ev_join2, S->ev_user, S->ev_done};
-    for (auto e : evs) if (e) cudaEventDestroy(e);
-    if (S->s0) cudaStreamDestroy(S->s0);
-    if (S->s1) cudaStreamDestroy(S->s1);
-    if (S->s2) cudaStreamDestroy(S->s2);
+    for (auto e : S->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : {S->ev_user, S->ev_done})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : {S->s0, S->s1, S->s2, S->s3})
+        if (st) cudaStreamDestroy(st);
     delete S;
 }
 
@@ -493,6 +547,7 @@ mcao_status validate_config(const mcao_config* c) {
             return fail(S, MCAO_E_INVALID_ARG, "wfs %d: sizes must be positive", w);
         if (p.n_fft < 2 * p.n_px) return fail(S, MCAO_E_UNSUPPORTED, "wfs %d: n_fft must be >= 2 n_px", w);
         if (p.n_fft % p.n_bin) return fail(S, MCAO_E_INVALID_ARG, "wfs %d: n_bin must divide n_fft", w);
+        if ((long long)p.n_sub * p.n_px > 16384) return fail(S, MCAO_E_UNSUPPORTED, "wfs %d: pupil grid too large", w);
         if (!(is_fin(p.lambda) && p.lambda > 0)) return fail(S, MCAO_E_INVALID_ARG, "wfs %d: lambda must be > 0", w);
         if (!(is_fin(p.n_photons) && p.n_photons >= 0) || !(is_fin(p.read_noise) && p.read_noise >= 0))
             return fail(S, MCAO_E_INVALID_ARG, "wfs %d: flux and read noise must be >= 0", w);
@@ -513,10 +568,20 @@ mcao_status validate_config(const mcao_config* c) {
         if (p.n_px < 8 || p.n_px % 8 || p.pad < 1)
             return fail(S, MCAO_E_UNSUPPORTED, "science %d: n_px must be a multiple of 8, pad >= 1", q);
         if (!(is_fin(p.lambda) && p.lambda > 0)) return fail(S, MCAO_E_INVALID_ARG, "science %d: lambda must be > 0", q);
+        if (!is_fin(p.theta_x) || !is_fin(p.theta_y))
+            return fail(S, MCAO_E_INVALID_ARG, "science %d: non-finite direction", q);
         int M = p.n_px * p.pad;
         if (factor_fft(M).empty() || M > 4096)
             return fail(S, MCAO_E_UNSUPPORTED, "science %d: FFT size %d must factor into 2,3,5 and be <= 4096", q, M);
     }
+    return MCAO_OK;
+}
+
+mcao_status d2h(mcao_sim* S, void* dst, const void* src, size_t bytes) {
+    CK(cudaSetDevice(S->device));
+    mcao_status r = sync_all(S);
+    if (r != MCAO_OK) return r;
+    if (bytes) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
     return MCAO_OK;
 }
 
@@ -539,6 +604,8 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     if (vs != MCAO_OK) return vs;
     mcao_sim* S = new mcao_sim();
     S->cfg = *cfg;
+    S->cfg.wfs = nullptr;
+    S->cfg.sci = nullptr;
     auto bail = [&](mcao_status s) {
         g_create_error = S->err;
         destroy_all(S);
@@ -554,16 +621,18 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         }                                                                                        \
     } while (0)
     CKC(cudaGetDevice(&S->device));
-    CKC(cudaStreamCreateWithFlags(&S->s0, cudaStreamNonBlocking));
-    CKC(cudaStreamCreateWithFlags(&S->s1, cudaStreamNonBlocking));
-    CKC(cudaStreamCreateWithFlags(&S->s2, cudaStreamNonBlocking));
-    cudaEvent_t* evs[] = {&S->ev_fork, &S->ev_join1, &S->ev_join2, &S->ev_user, &S->ev_done};
-    for (auto e : evs) CKC(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-    for (auto& e : S->prof_tpl) CKC(cudaEventCreate(&e));
+    int prio_lo = 0, prio_hi = 0;
+    CKC(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    CKC(cudaStreamCreateWithPriority(&S->s0, cudaStreamNonBlocking, prio_hi));
+    CKC(cudaStreamCreateWithPriority(&S->s1, cudaStreamNonBlocking, prio_hi));
+    CKC(cudaStreamCreateWithPriority(&S->s3, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
+    CKC(cudaStreamCreateWithPriority(&S->s2, cudaStreamNonBlocking, prio_lo));
+    CKC(cudaEventCreateWithFlags(&S->ev_user, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&S->ev_done, cudaEventDisableTiming));
     CKC(wfs_prepare());
 
     // ---- wavefront sensors
-    int ns = 0, nframe = 0;
+    int ns = 0, nframe = 0, ld = 0;
     std::vector<WfsDev> wdev;
     std::vector<float> amp_all;
     std::vector<size_t> amp_off;
@@ -573,6 +642,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         H.N = H.p.n_sub * H.p.n_px;
         H.dx = cfg->D / (double)H.N;
         H.n_det = H.p.n_fft / H.p.n_bin;
+        H.fft_route = wfs_variant_is_fft(H.p.n_px, H.p.n_fft, H.p.n_bin);
         H.amp = pupil(cfg->D, cfg->obstruction, H.N);
         const int npx = H.p.n_px;
         for (int sy = 0; sy < H.p.n_sub; ++sy)
@@ -589,6 +659,8 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         H.n_valid = (int)H.valid.size();
         H.slope0 = ns;
         ns += 2 * H.n_valid;
+        H.rcol0 = ld;
+        ld += (2 * H.n_valid + 3) / 4 * 4;
         H.frame0 = nframe;
         nframe += H.n_valid * H.n_det * H.n_det;
         bool el = H.p.type == MCAO_WFS_LGS && H.p.na_fwhm > 0;
@@ -601,6 +673,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
             d.rank = v;
             d.frac = (float)H.frac[v];
             if (el) {
+                // elongation: FWHM b dh / H^2 rad along the launch-to-subaperture direction
                 double cx = ((double)d.sx - 0.5 * (double)(H.p.n_sub - 1)) * npx * H.dx - H.p.launch_x;
                 double cy = ((double)d.sy - 0.5 * (double)(H.p.n_sub - 1)) * npx * H.dx - H.p.launch_y;
                 double b = std::sqrt(cx * cx + cy * cy);
@@ -615,12 +688,14 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
             }
             H.subaps.push_back(d);
         }
+        CKC(dalloc(&H.d_subaps, H.subaps.size()));
+        if (!H.subaps.empty())
+            CKC(cudaMemcpy(H.d_subaps, H.subaps.data(), sizeof(SubapDev) * H.subaps.size(), cudaMemcpyHostToDevice));
         WfsDev D{};
         D.type = H.p.type;
         D.n_sub = H.p.n_sub; D.n_px = npx; D.n_fft = H.p.n_fft; D.n_bin = H.p.n_bin; D.n_det = H.n_det;
         D.N = H.N;
         D.n_valid = H.n_valid; D.slope0 = H.slope0; D.frame0 = H.frame0; D.wfs_index = w;
-        D.dx = H.dx; D.theta_x = H.p.theta_x; D.theta_y = H.p.theta_y; D.height = H.p.height;
         D.scale = (float)(cfg->lambda_ref / H.p.lambda);
         D.n_photons = (float)H.p.n_photons;
         D.read_noise = (float)H.p.read_noise;
@@ -645,6 +720,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     }
     S->n_slopes = ns;
     S->n_frame_px = nframe;
+    S->ld = std::max(ld, 4);
     CKC(dalloc(&S->d_amp_all, amp_all.size()));
     CKC(cudaMemcpy(S->d_amp_all, amp_all.data(), sizeof(float) * amp_all.size(), cudaMemcpyHostToDevice));
     for (size_t w = 0; w < wdev.size(); ++w) wdev[w].amp = S->d_amp_all + amp_off[w];
@@ -661,19 +737,20 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         CKC(cudaMemset(S->d_frames, 0, sizeof(int) * std::max(nframe, 1)));
     }
 
-    // ---- kernel groups: the group with the most subapertures runs on the main stream
+    // ---- block-per-subaperture sensors: one launch per kernel variant
     for (int w = 0; w < cfg->n_wfs; ++w) {
+        if (!S->wfs[w].fft_route) continue;
         const mcao_wfs& p = cfg->wfs[w];
-        Group* g = nullptr;
-        for (auto& x : S->groups)
+        FftGroup* g = nullptr;
+        for (auto& x : S->fft_groups)
             if (x.n_px == p.n_px && x.n_fft == p.n_fft && x.n_bin == p.n_bin) g = &x;
         if (!g) {
-            S->groups.push_back(Group{p.n_px, p.n_fft, p.n_bin, {}, nullptr, 0});
-            g = &S->groups.back();
+            S->fft_groups.push_back(FftGroup{p.n_px, p.n_fft, p.n_bin, {}, nullptr, 0});
+            g = &S->fft_groups.back();
         }
         g->wfs.push_back(w);
     }
-    for (auto& g : S->groups) {
+    for (auto& g : S->fft_groups) {
         std::vector<SubapDev> all;
         for (int w : g.wfs) all.insert(all.end(), S->wfs[w].subaps.begin(), S->wfs[w].subaps.end());
         g.n_subaps = (int)all.size();
@@ -681,8 +758,6 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         if (!all.empty())
             CKC(cudaMemcpy(g.d_subaps, all.data(), sizeof(SubapDev) * all.size(), cudaMemcpyHostToDevice));
     }
-    std::stable_sort(S->groups.begin(), S->groups.end(),
-                     [](const Group& a, const Group& b) { return a.n_subaps > b.n_subaps; });
 
     // ---- science directions
     int maxM = 0;
@@ -751,8 +826,8 @@ mcao_status mcao_load_atmosphere(mcao_sim* S, int n_layers, const mcao_layer* la
     CK(cudaSetDevice(S->device));
     for (int l = 0; l < n_layers; ++l) {
         const mcao_layer& L = layers[l];
-        if (L.n < 2 || !(is_fin(L.pixel_m) && L.pixel_m > 0) || !L.phase)
-            return fail(S, MCAO_E_INVALID_ARG, "layer %d: n >= 2, pixel > 0 and phase required", l);
+        if (L.n < 2 || L.n > kMaxGridN || !(is_fin(L.pixel_m) && L.pixel_m > 0) || !L.phase)
+            return fail(S, MCAO_E_INVALID_ARG, "layer %d: 2 <= n <= %d, pixel > 0 and phase required", l, kMaxGridN);
         if (!is_fin(L.alt_m) || L.alt_m < 0 || !is_fin(L.vx) || !is_fin(L.vy))
             return fail(S, MCAO_E_INVALID_ARG, "layer %d: altitude and wind must be finite, altitude >= 0", l);
         for (const auto& w : S->wfs)
@@ -779,7 +854,7 @@ mcao_status mcao_load_atmosphere(mcao_sim* S, int n_layers, const mcao_layer* la
         S->layers[l].phase = nullptr;
     }
     S->n_layers = n_layers;
-    mcao_status r = rebuild_grids(S);
+    mcao_status r = rebuild_views(S);
     if (r != MCAO_OK) return r;
     S->atm_loaded = true;
     return MCAO_OK;
@@ -795,6 +870,9 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
             !(is_fin(d.pitch_m) && d.pitch_m > 0) || !(is_fin(d.coupling) && d.coupling > 0 && d.coupling < 1) ||
             !is_fin(d.alt_m) || d.alt_m < 0)
             return fail(S, MCAO_E_INVALID_ARG, "dm %d: invalid geometry", m);
+        if (d.nx > kDmMaxAct || d.surf_n > kMaxGridN)
+            return fail(S, MCAO_E_UNSUPPORTED, "dm %d: at most %d actuators per row and %d surface samples", m,
+                        kDmMaxAct, kMaxGridN);
         for (const auto& w : S->wfs)
             if (w.p.type == MCAO_WFS_LGS && d.alt_m >= w.p.height)
                 return fail(S, MCAO_E_INVALID_ARG, "dm %d lies above a laser guide star", m);
@@ -808,19 +886,20 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     S->dms.assign(dms, dms + n_dms);
     S->n_dms = n_dms;
     S->dm_desc.clear();
-    S->dm_ncmd.clear();
     std::vector<float> g;
     std::vector<int2> band;
     std::vector<int> map;
     long long tmp_total = 0, surf_total = 0;
-    int ncmd = 0;
+    int ncmd = 0, pass1 = 0, tiles = 0;
     for (int m = 0; m < n_dms; ++m) {
         const mcao_dm& d = dms[m];
         DmDesc D{};
         D.nx = d.nx; D.ny = d.ny; D.surf_n = d.surf_n;
+        D.tiles_x = (d.surf_n + 31) / 32;
         double sig = d.pitch_m / std::sqrt(2.0 * std::log(1.0 / d.coupling));
         const double thr = 1e-10;
-        auto table = [&](int na) {
+        // table [surf_n][na] and per-row band of weights >= thr
+        auto table = [&](int na, std::vector<int2>& bands) {
             long long off = (long long)g.size();
             for (int i = 0; i < d.surf_n; ++i) {
                 double x = ((double)i - 0.5 * (double)(d.surf_n - 1)) * d.surf_dx;
@@ -832,32 +911,42 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
                     if (v >= thr) { lo = std::min(lo, a); hi = std::max(hi, a + 1); }
                 }
                 if (lo >= hi) { lo = 0; hi = 0; }
-                band.push_back(make_int2(lo, hi));
+                bands.push_back(make_int2(lo, hi));
             }
             return off;
         };
+        std::vector<int2> bands_x, bands_y;
+        D.gx_off = table(d.nx, bands_x);
+        D.gy_off = table(d.ny, bands_y);
         D.band_off = (long long)band.size();
-        D.gx_off = table(d.nx);
-        D.gy_off = table(d.ny);
+        band.insert(band.end(), bands_x.begin(), bands_x.end());
+        D.tband_off = (long long)band.size();
+        for (int t = 0; t < D.tiles_x; ++t) {
+            int lo = d.ny, hi = 0;
+            for (int j = t * 32; j < std::min(d.surf_n, t * 32 + 32); ++j)
+                if (bands_y[j].y > bands_y[j].x) { lo = std::min(lo, bands_y[j].x); hi = std::max(hi, bands_y[j].y); }
+            if (lo >= hi) { lo = 0; hi = 0; }
+            band.push_back(make_int2(lo, hi));
+        }
         D.map_off = (long long)map.size();
         int cnt = 0;
         for (int a = 0; a < d.nx * d.ny; ++a) {
             if (d.valid[a]) { map.push_back(ncmd + cnt); ++cnt; }
             else map.push_back(-1);
         }
-        S->dm_ncmd.push_back(cnt);
         ncmd += cnt;
         D.tmp_off = tmp_total;
         D.surf_off = surf_total;
-        S->dm_tmp_start[m] = tmp_total;
-        S->dm_surf_start[m] = surf_total;
         tmp_total += (long long)d.ny * d.surf_n;
         surf_total += (long long)d.surf_n * d.surf_n;
+        S->dm_tile_start[m] = tiles;
+        tiles += D.tiles_x * D.tiles_x;
+        pass1 += d.ny * ((d.surf_n + 255) / 256);
         S->dm_desc.push_back(D);
     }
+    for (int m = n_dms; m <= kMaxDms; ++m) S->dm_tile_start[m] = tiles;
+    S->dm_pass1_blocks = pass1;
     S->n_cmd = ncmd;
-    S->dm_tmp_total = tmp_total;
-    S->dm_surf_total = surf_total;
     CK(dalloc(&S->d_dm_desc, S->dm_desc.size()));
     if (n_dms) CK(cudaMemcpy(S->d_dm_desc, S->dm_desc.data(), sizeof(DmDesc) * n_dms, cudaMemcpyHostToDevice));
     CK(dalloc(&S->d_dm_g, g.size()));
@@ -871,7 +960,7 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     CK(cudaMemset(S->d_dm_surf, 0, sizeof(float) * std::max<long long>(surf_total, 1)));
     CK(dalloc(&S->d_c, ncmd));
     CK(cudaMemset(S->d_c, 0, sizeof(float) * std::max(ncmd, 1)));
-    mcao_status r = rebuild_grids(S);
+    mcao_status r = rebuild_views(S);
     if (r != MCAO_OK) return r;
     S->dms_loaded = true;
     return MCAO_OK;
@@ -892,18 +981,51 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     dfree(S->d_R);
     dfree(S->d_partial);
     S->recon_loaded = false;
-    S->ld = (n_slopes + 3) / 4 * 4;
     S->rows_pad = std::max(1, (n_cmd + kReconRowBlock - 1) / kReconRowBlock) * kReconRowBlock;
     size_t elems = (size_t)S->rows_pad * S->ld;
     CK(dalloc(&S->d_R, elems));
     CK(cudaMemset(S->d_R, 0, sizeof(float) * elems));
-    if (n_cmd > 0)
-        CK(cudaMemcpy2D(S->d_R, sizeof(float) * S->ld, R, sizeof(float) * n_slopes, sizeof(float) * n_slopes, n_cmd,
-                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
-    CK(dalloc(&S->d_partial, (size_t)recon_chunks(n_slopes) * std::max(n_cmd, 1)));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // padded layout: each sensor's slope block starts on a 16-byte boundary of a row; slices
+    // run warp-per-subaperture sensors first, block-per-subaperture sensors last
+    S->slices.clear();
+    S->slice_wfs.clear();
+    int chunks = 0;
+    std::vector<int> order;
+    for (size_t w = 0; w < S->wfs.size(); ++w)
+        if (!S->wfs[w].fft_route) order.push_back((int)w);
+    for (size_t w = 0; w < S->wfs.size(); ++w)
+        if (S->wfs[w].fft_route) order.push_back((int)w);
+    for (int w : order) {
+        const WfsHost& W = S->wfs[w];
+        const int len = 2 * W.n_valid;
+        if (len == 0) continue;
+        if (n_cmd > 0)
+            CK(cudaMemcpy2D(S->d_R + W.rcol0, sizeof(float) * S->ld, R + W.slope0, sizeof(float) * n_slopes,
+                            sizeof(float) * len, n_cmd, kind));
+        ReconLaunch L{};
+        L.R = S->d_R;
+        L.n_cmd = n_cmd;
+        L.ld = S->ld;
+        L.rows_pad = S->rows_pad;
+        L.col0 = W.rcol0;
+        L.s0 = W.slope0;
+        L.len = len;
+        int nch = (len + kReconChunk - 1) / kReconChunk;
+        int kc = (len + nch - 1) / nch;
+        L.kc = (kc + 3) / 4 * 4;
+        nch = (len + L.kc - 1) / L.kc;
+        L.chunk0 = chunks;
+        L.s = S->d_slopes;
+        chunks += nch;
+        S->slices.push_back(L);
+        S->slice_wfs.push_back(w);
+    }
+    S->n_chunks = chunks;
+    CK(dalloc(&S->d_partial, (size_t)std::max(chunks, 1) * std::max(n_cmd, 1)));
+    for (auto& L : S->slices) L.partial = S->d_partial;
     if (s_ref)
-        CK(cudaMemcpy(S->d_sref, s_ref, sizeof(float) * n_slopes,
-                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(S->d_sref, s_ref, sizeof(float) * n_slopes, kind));
     else
         CK(cudaMemset(S->d_sref, 0, sizeof(float) * n_slopes));
     release_graph(S);
@@ -926,9 +1048,8 @@ mcao_status mcao_step(mcao_sim* S, int n_steps) {
     if (r != MCAO_OK) return r;
     for (int i = 0; i < n_steps; ++i) {
         if (S->profiling) {
-            for (int stg = 0; stg < ST_COUNT; ++stg) {
-                cudaGraphNode_t na = S->prof_node[2 * stg], nb = S->prof_node[2 * stg + 1];
-                if (!na || !nb) continue;
+            for (const auto& p : S->prof_slots) {
+                if (!p.na || !p.nb) continue;
                 if (S->prof_used + 2 > S->prof_pool.size()) {
                     cudaEvent_t a, b;
                     CK(cudaEventCreate(&a));
@@ -938,9 +1059,9 @@ mcao_status mcao_step(mcao_sim* S, int n_steps) {
                 }
                 cudaEvent_t ea = S->prof_pool[S->prof_used], eb = S->prof_pool[S->prof_used + 1];
                 S->prof_used += 2;
-                CK(cudaGraphExecEventRecordNodeSetEvent(S->exec, na, ea));
-                CK(cudaGraphExecEventRecordNodeSetEvent(S->exec, nb, eb));
-                S->prof_records.push_back({stg, {ea, eb}});
+                CK(cudaGraphExecEventRecordNodeSetEvent(S->exec, p.na, ea));
+                CK(cudaGraphExecEventRecordNodeSetEvent(S->exec, p.nb, eb));
+                S->prof_records.push_back({p.stage, {ea, eb}});
             }
         }
         CK(cudaGraphLaunch(S->exec, S->s0));
@@ -991,19 +1112,10 @@ mcao_status mcao_query(const mcao_sim* S, int kind, int index, size_t* n) {
 
 mcao_status mcao_get_step_index(mcao_sim* S, int64_t* k) {
     if (!S || !k) return MCAO_E_INVALID_ARG;
-    CK(cudaSetDevice(S->device));
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
     StepState st;
-    CK(cudaMemcpy(&st, S->d_st, sizeof(st), cudaMemcpyDeviceToHost));
-    *k = st.k_next;
-    return MCAO_OK;
-}
-
-static mcao_status d2h(mcao_sim* S, void* dst, const void* src, size_t bytes) {
-    CK(cudaSetDevice(S->device));
-    mcao_status r = sync_all(S);
+    mcao_status r = d2h(S, &st, S->d_st, sizeof(st));
     if (r != MCAO_OK) return r;
-    if (bytes) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    *k = st.k_next;
     return MCAO_OK;
 }
 

@@ -9,16 +9,24 @@ namespace mcao {
 constexpr int kMaxEntries = 16;   // layers + DMs sampled along one direction
 constexpr int kMaxNpx = 32;       // pupil samples per subaperture side
 constexpr int kMaxNd = 32;        // detector pixels per subaperture side
+constexpr int kMaxDms = 4;
+constexpr int kMaxGridN = 65535;  // grid side (indices are packed in 16 bits)
 
-// A phase grid sampled along a direction: a periodic turbulence layer or a bounded DM surface.
-struct GridDev {
+// A phase grid (periodic turbulence layer or bounded DM surface) seen from one direction
+// (a wavefront sensor or a science direction).  Grid coordinates are Q32.32 fixed point in
+// grid samples: pupil sample (i, j) at step k sits at
+//   x = ax + i bp + k vx,  y = ay + j bp + k vy,
+// which is the cone-beam projection x_p (1 - h/H) + h theta plus the frozen-flow offset
+// (k dt) v, converted to grid index units on the host in double precision.
+struct GridView {
     const float* data;   // [n][n]
     int n;
-    int periodic;        // 1: layer (wrap), 0: DM (clamp)
-    double pixel;        // m
-    double alt;          // m
-    double vx, vy;       // m/s (0 for DMs)
+    int periodic;        // 1: layer (wrap), 0: DM (index clamp into [0, n-1])
+    long long ax, ay;    // grid index of pupil sample (0, 0) at step 0
+    long long bp;        // grid samples per pupil sample
+    long long vx, vy;    // grid samples per step (0 for DMs)
     float sign;          // +1 layers, -1 DMs (residual = layers - DMs)
+    float pad_;
 };
 
 // One wavefront sensor.
@@ -27,8 +35,6 @@ struct WfsDev {
     int n_sub, n_px, n_fft, n_bin, n_det, N;  // N pupil samples across D
     int n_valid, slope0, frame0;              // frame0: first detector pixel in frame buffers
     int wfs_index;
-    double dx;           // pupil sample pitch, m
-    double theta_x, theta_y, height;
     float scale;         // lambda_ref / lambda
     float n_photons, read_noise;
     const float* amp;    // [N][N] pupil amplitude
@@ -60,30 +66,30 @@ struct SciAcc {
 };
 
 struct Ctx {
-    const GridDev* grids;   // [n_grids]
+    const GridView* views;  // [n_views][n_grids]: WFSs first, then science directions
     int n_grids;
     const WfsDev* wfs;      // [n_wfs]
     const StepState* st;
-    double dt;
     unsigned long long seed;
     int noise;
 };
 
 // ---------------------------------------------------------------------------------------------
-// launchers (return cudaGetLastError() of the launch)
+// DM surfaces
 // ---------------------------------------------------------------------------------------------
-
 // One DM in the concatenated DM buffers.  T = C Gx^T restricted to the nonzero band of each
 // Gaussian row, then S = Gy T (the Gaussian influence function factorises in x and y).
 struct DmDesc {
-    int nx, ny, surf_n, pad_;
+    int nx, ny, surf_n, tiles_x;   // tiles_x: 32-sample tiles per side of the surface
     long long gx_off;    // Gx [surf_n][nx] in the table buffer
     long long gy_off;    // Gy [surf_n][ny]
-    long long band_off;  // band_x [surf_n], band_y [surf_n] (lo, hi exclusive) in the band buffer
+    long long band_off;  // band_x [surf_n] (lo, hi exclusive) in the band buffer
+    long long tband_off; // per 32-row tile: union of the Gy bands of its rows
     long long map_off;   // act_map [ny][nx]: command index or -1
     long long tmp_off;   // T [ny][surf_n]
     long long surf_off;  // S [surf_n][surf_n]
 };
+constexpr int kDmMaxAct = 256;   // actuators per row of a DM
 
 struct DmLaunch {
     int n_dm;
@@ -94,16 +100,19 @@ struct DmLaunch {
     const float* c;          // commands
     float* tmp;              // T buffers
     float* surf;             // surfaces
-    long long tmp_total, surf_total;
-    long long tmp_start[4], surf_start[4];   // per-DM prefix offsets (host copy, kernel args)
-    StepState* st;           // begin of step: k = k_next (block 0)
+    int pass1_blocks;        // sum over DMs of ny * ceil(surf_n / 256)
+    int tile_start[kMaxDms + 1];    // per-DM prefix of 32 x 32 surface tiles
+    StepState* st;           // begin of step: k = k_next
 };
-constexpr int kMaxDms = 4;
 cudaError_t launch_dm_surfaces(const DmLaunch& L, cudaStream_t s);
+cudaError_t launch_begin_step(StepState* st, cudaStream_t s);
 
+// ---------------------------------------------------------------------------------------------
+// wavefront sensors
+// ---------------------------------------------------------------------------------------------
 struct WfsLaunch {
     Ctx ctx;
-    const SubapDev* subaps;  // [n_subaps] of the WFSs handled by this launch
+    const SubapDev* subaps;  // [n_subaps] handled by this launch
     int n_subaps;
     const float* s_ref;
     float* slopes;
@@ -111,33 +120,50 @@ struct WfsLaunch {
     int* frame_out;
 };
 
-// variant = (n_px, n_fft, n_bin); returns cudaErrorInvalidValue when no kernel exists
 bool wfs_variant_supported(int n_px, int n_fft, int n_bin, bool elongated);
+bool wfs_variant_is_fft(int n_px, int n_fft, int n_bin);   // block-per-subaperture FFT route
 cudaError_t wfs_prepare();   // kernel attributes (call once per device, outside stream capture)
 cudaError_t launch_wfs(const WfsLaunch& L, int n_px, int n_fft, int n_bin, cudaStream_t s);
 
 // residual phase of one WFS on its full pupil grid (tests)
 cudaError_t launch_wfs_phase(const Ctx& ctx, int wfs, int N, float* out, cudaStream_t s);
 
+// ---------------------------------------------------------------------------------------------
+// reconstructor
+// ---------------------------------------------------------------------------------------------
+constexpr int kReconRowBlock = 32;   // rows per block of the reconstructor product
+constexpr int kReconChunk = 4096;    // maximum slope columns per block
+
+// One slice of the reconstructor product: the columns of one WFS's slope block.
 struct ReconLaunch {
     const float* R;     // [rows_pad][ld]
-    int n_cmd, n_slopes, ld, rows_pad;
-    const float* s;     // [n_slopes]
+    int n_cmd, ld, rows_pad;
+    int col0;           // first column of the slice in R (multiple of 4)
+    int s0;             // first slope of the slice in the slope vector
+    int len;            // columns in the slice
+    int kc;             // columns per block (multiple of 4)
+    int chunk0;         // first partial-sum slot of the slice
+    const float* s;     // slope vector
     float* partial;     // [n_chunks][n_cmd]
-    float* c;           // [n_cmd]
-    float gain;
-    StepState* st;      // k_next = k + 1 written by the reduce kernel (may be null)
 };
-constexpr int kReconRowBlock = 32;   // rows per block of the reconstructor product
-constexpr int kReconChunk = 4096;    // slope columns per block
-int recon_chunks(int n_slopes);
 cudaError_t launch_recon(const ReconLaunch& L, cudaStream_t s);
-cudaError_t launch_recon_reduce(const ReconLaunch& L, cudaStream_t s);
 
+struct ReduceLaunch {
+    int n_cmd, n_chunks;
+    const float* partial;
+    float* c;
+    float gain;
+    StepState* st;      // k_next = k + 1 (may be null)
+};
+cudaError_t launch_recon_reduce(const ReduceLaunch& L, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------
+// science
+// ---------------------------------------------------------------------------------------------
 struct SciLaunch {
     Ctx ctx;
+    int view;                 // index of this direction's grid views
     int N, M;                 // pupil samples, FFT size
-    double dx, theta_x, theta_y;
     float scale;              // lambda_ref / lambda_sci
     const float* amp;         // [N][N]
     float2* field;            // [N][N]
@@ -158,7 +184,5 @@ size_t sci_smem_bytes(int M);
 cudaError_t launch_sci_field(const SciLaunch& L, cudaStream_t s);
 cudaError_t launch_sci_rows(const SciLaunch& L, cudaStream_t s);
 cudaError_t launch_sci_cols(const SciLaunch& L, cudaStream_t s);
-
-cudaError_t launch_begin_step(StepState* st, cudaStream_t s);
 
 }  // namespace mcao
