@@ -234,6 +234,31 @@ mcao_status mcao_reset_psf(mcao_sim* sim);
 mcao_status mcao_get_state(mcao_sim* sim, void* buf, size_t n);
 mcao_status mcao_set_state(mcao_sim* sim, const void* buf, size_t n);
 
+/* Reconstructor update without device allocation: c <- c + gain * R s on the current device,
+ * queued on `stream` (a cudaStream_t; NULL = legacy default stream).  The paper has no
+ * counterpart: it is a service for callers that cannot allocate device memory -- for example a
+ * real-time controller that reserves all of its memory at start-up and must never block on the
+ * allocator inside its loop, or code that runs under another framework's memory pool where a
+ * stray cudaMalloc would fragment or oversubscribe that pool.  It needs no mcao_sim handle and
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *   R      device pointer, row-major [n_cmd][ld] float32, 16-byte aligned; ld >= n_slopes and
+ *          ld a multiple of 4; columns n_slopes..ld-1 are read and multiplied by zero, so they
+ *          must hold finite values.
+ *   s      device pointer, [n_slopes] float32.     c  device pointer, [n_cmd] float32, updated.
+ *   err    optional host buffer of err_len bytes that receives a message on failure.
+ * Split-K partial sums live in one fixed device array of 524288 floats (2 MiB) inside the
+ * library, created on every device that loads the library and kept until the process exits;
+ * n_cmd times ceil(n_slopes / 4096) must not exceed that size (else MCAO_E_SHAPE, nothing is
+ * launched).  Each partial sum is written before it is read, so nothing needs clearing between
+ * calls.  The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * under a lock); make that first call before any stream capture.  All calls share the array:
+ * calls whose kernels overlap on the GPU (different streams, or concurrent host threads on
+ * different streams) race on it -- order them on one stream.  Asynchronous: returns once the two
+ * kernels are queued.  Errors: MCAO_E_INVALID_ARG, MCAO_E_SHAPE, MCAO_E_UNSUPPORTED (device
+ * index >= 64), MCAO_E_CUDA. */
+mcao_status mcao_reconstruct_noalloc(const float* R, int n_cmd, int n_slopes, int ld, const float* s,
+                                     float* c, float gain, void* stream, char* err, size_t err_len);
+
 /* Stages timed by the profiler. */
 enum {
     MCAO_STAGE_DM = 0,          /* DM surfaces                                                  */

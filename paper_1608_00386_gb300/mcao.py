@@ -28,6 +28,7 @@ EXPORTS = [
     "mcao_query", "mcao_get_step_index", "mcao_get_slopes", "mcao_get_commands", "mcao_set_commands",
     "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
+    "mcao_reconstruct_noalloc",
 ]
 
 
@@ -104,6 +105,7 @@ def lib():
         "mcao_set_state": [vp, vp, C.c_size_t],
         "mcao_set_profiling": [vp, C.c_int],
         "mcao_get_profile": [vp, vp, vp, C.c_int, C.POINTER(C.c_int64)],
+        "mcao_reconstruct_noalloc": [vp, C.c_int, C.c_int, C.c_int, vp, vp, C.c_float, vp, C.c_char_p, C.c_size_t],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -304,6 +306,22 @@ class Sim:
         lps = C.c_int64()
         self._ck(lib().mcao_get_profile(self.h, ms, cnt, len(STAGES), C.byref(lps)))
         return ({s: ms[i] for i, s in enumerate(STAGES)}, {s: cnt[i] for i, s in enumerate(STAGES)}, lps.value)
+
+
+def reconstruct_noalloc(R, s, c, gain: float, stream=None) -> None:
+    """c <- c + gain R s with the allocation-free entry point; R [n_cmd][ld], s and c are CUDA
+    tensors (float32).  Queued on ``stream`` (torch stream or raw handle; default: the current
+    torch stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    n_cmd, ld = R.shape
+    buf = C.create_string_buffer(256)
+    st = lib().mcao_reconstruct_noalloc(R.data_ptr(), n_cmd, s.numel(), ld, s.data_ptr(), c.data_ptr(),
+                                        float(gain), C.c_void_p(ptr), buf, 256)
+    if st != 0:
+        raise McaoError(st, buf.value.decode())
 
 
 def make_sim(cfg: dict, screens, R, s_ref=None, keep_frames: bool = False, stream=None) -> Sim:
