@@ -170,9 +170,10 @@ mcao_status mcao_load_dms(mcao_sim* sim, int n_dms, const mcao_dm* dms);
 /* Load the control matrix R [n_cmd][n_slopes] (row-major float32) and the reference slopes
  * s_ref [n_slopes] (NULL = zeros) ("Control Matrix"; "The calibration of the interaction
  * matrices": reference slope vector).  The library keeps its own copy in a padded layout.
- * on_device = 1: R and s_ref are device addresses.  Errors: MCAO_E_STATE (DMs not loaded),
- * MCAO_E_SHAPE (n_cmd or n_slopes differ from the configuration), MCAO_E_UNSUPPORTED
- * (dtype other than MCAO_DTYPE_F32), MCAO_E_OOM, MCAO_E_CUDA. */
+ * on_device = 1: R and s_ref are device addresses; the call first waits for all work queued
+ * on the device, so the kernel producing R may still be running when it is made.  Errors:
+ * MCAO_E_STATE (DMs not loaded), MCAO_E_SHAPE (n_cmd or n_slopes differ from the
+ * configuration), MCAO_E_UNSUPPORTED (dtype other than MCAO_DTYPE_F32), MCAO_E_OOM, MCAO_E_CUDA. */
 mcao_status mcao_load_reconstructor(mcao_sim* sim, int n_cmd, int n_slopes, const float* R,
                                     const float* s_ref, int dtype, int on_device);
 

@@ -199,6 +199,49 @@ __device__ __forceinline__ float2* stockham_fft(float2* a, float2* b, int N, con
     return src;
 }
 
+// Compile-time Stockham: the same stages with N, the sub-transform length and the radix known
+// at compile time (index arithmetic by constants, no twiddle modulo).  Radices are taken as
+// 4 while possible, then 2, 5, 3, matching the host's factorisation.
+__host__ __device__ constexpr int ct_radix(int m) {
+    return (m % 4 == 0) ? 4 : (m % 2 == 0) ? 2 : (m % 5 == 0) ? 5 : 3;
+}
+
+template <int N, int NS, int R>
+__device__ __forceinline__ void stockham_stage_ct(const float2* src, float2* dst, int batch, int fstride,
+                                                  const float2* W, int tid, int nthr) {
+    constexpr int NR = N / R;
+    constexpr int TW = N / (NS * R);
+    for (int idx = tid; idx < batch * NR; idx += nthr) {
+        const int f = idx / NR, j = idx - f * NR;
+        const float2* s = src + (long long)f * fstride;
+        float2* d = dst + (long long)f * fstride;
+        const int k = j % NS;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[j + r * NR];
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], W[r * k * TW]);
+        small_dft<R>(v);
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[base + r * NS] = v[r];
+    }
+}
+
+// returns the buffer holding the result; a block-wide barrier follows every stage
+template <int N, int NS = 1>
+__device__ __forceinline__ float2* stockham_fft_ct(float2* a, float2* b, int batch, int fstride, const float2* W,
+                                                   int tid, int nthr) {
+    if constexpr (NS >= N) {
+        return a;
+    } else {
+        constexpr int R = ct_radix(N / NS);
+        stockham_stage_ct<N, NS, R>(a, b, batch, fstride, W, tid, nthr);
+        __syncthreads();
+        return stockham_fft_ct<N, NS * R>(b, a, batch, fstride, W, tid, nthr);
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Detector noise.  Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by the
 // seed, counter (pixel, step, WFS, 0); float sampler with a fixed operation order written with

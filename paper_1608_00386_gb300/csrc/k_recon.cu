@@ -4,10 +4,20 @@
 // R is float32 [n_cmd][n_slopes], far larger than L2, and is read exactly once per step, so the
 // product is bound by HBM bandwidth.  The product is issued per slice of columns (one slice per
 // wavefront sensor, so a slice can start as soon as its sensor's slopes exist) and split-K
-// inside a slice: block (rb, kc) multiplies 32 rows by one column chunk of s held in shared
-// memory; each warp streams four rows at a time with 16-byte evict-first loads and writes its
-// row sums to a partial buffer [n_chunks][n_cmd].  A second kernel adds the partials in a fixed
-// order (deterministic) and applies the gain.
+// inside a slice: a work item is 4 rows times one column chunk; row sums go to a partial buffer
+// [n_chunks][n_cmd], and a second kernel adds the partials in a fixed order (deterministic) and
+// applies the gain.  The slopes are read (L1-cached) from a copy the sensing kernels write in
+// R's padded column layout, so every 16-byte load of s is aligned.
+//
+// Streaming.  One persistent block per SM (3 warps).  Each warp owns a four-stage ring in
+// shared memory and keeps it filled with TMA bulk copies (cp.async.bulk, completion counted on a
+// per-stage mbarrier, L2 evict-first policy).  R is held stage-tiled (see ReconLaunch), so each
+// stage -- four row segments of up to 2 KB -- is one contiguous copy of up to 8 KB (bulk copies
+// that small lose bandwidth), and up to 96 KB per SM are in flight.  The block needs
+// few registers and warps, which leaves each SM room for three wavefront-sensor blocks that run
+// concurrently, hiding their ALU work under the HBM stream.  Every mbarrier wait is bounded
+// (about one second of clock); on expiry the warp records kErrReconTimeout, waits (bounded)
+// for its copies in flight and exits.
 #include "mcao_internal.h"
 
 namespace mcao {
@@ -15,10 +25,6 @@ namespace mcao {
 namespace {
 
 constexpr int kKC = kReconChunk;
-constexpr int kRowsPerWarp = 4;
-constexpr int kWarps = 8;
-constexpr int kRB = kRowsPerWarp * kWarps;
-static_assert(kRB == kReconRowBlock, "row block");
 
 __device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
     acc = fmaf(a.x, b.x, acc);
@@ -27,65 +33,232 @@ __device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
     return fmaf(a.w, b.w, acc);
 }
 
-__global__ void __launch_bounds__(256) recon_gemv_kernel(ReconLaunch L) {
-    __shared__ float4 s_sh[kKC / 4];
-    const int kc = blockIdx.y;
-    const int c_begin = kc * L.kc;                 // column offset inside the slice
-    int ncols = L.len - c_begin;
-    if (ncols > L.kc) ncols = L.kc;
-    const int n4 = (ncols + 3) / 4;                // R rows are zero-padded to a multiple of 4
-    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
-        int c = c_begin + 4 * i;
-        float4 v;
-        v.x = (c + 0 < L.len) ? L.s[L.s0 + c + 0] : 0.0f;
-        v.y = (c + 1 < L.len) ? L.s[L.s0 + c + 1] : 0.0f;
-        v.z = (c + 2 < L.len) ? L.s[L.s0 + c + 2] : 0.0f;
-        v.w = (c + 3 < L.len) ? L.s[L.s0 + c + 3] : 0.0f;
-        s_sh[i] = v;
-    }
-    __syncthreads();
+// ------------------------------------------------------------------------------------------
+// TMA bulk-copy streaming
+// ------------------------------------------------------------------------------------------
+constexpr int kTmaWarps = 3;
+constexpr int kTmaRows = kReconRows;               // rows per item
+constexpr int kTmaSeg = kReconSeg;                 // float4 per row segment (2 KB)
+constexpr int kTmaStages = 4;
+constexpr long long kWaitCycles = 2000000000ll;    // ~1 s at 2 GHz
 
+struct TmaSmem {
+    float4 ring[kTmaWarps][kTmaStages][kTmaRows * kTmaSeg];
+    unsigned long long bar[kTmaWarps][kTmaStages];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// wait for the given phase parity, giving up after kWaitCycles
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar,
+                                         uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+// stage geometry of chunk kc of a slice: n4 float4 per row, nst stages of seg float4
+__device__ __forceinline__ void chunk_geom(const ReconLaunch& L, int kc, int& n4, int& nst, int& seg) {
+    const int ncols = min(L.len - kc * L.kc, L.kc);
+    n4 = (ncols + 3) / 4;
+    nst = (n4 + kTmaSeg - 1) / kTmaSeg;
+    seg = (n4 + nst - 1) / nst;
+}
+
+// Chunk geometry {n4, nst, seg} of a full chunk and of the slice's last (possibly shorter) one,
+// computed once per thread so that the per-stage path needs no division.
+struct SliceGeom {
+    int n_chunks;
+    int full[3], last[3];
+};
+
+__device__ __forceinline__ SliceGeom slice_geom(const ReconLaunch& L) {
+    SliceGeom g;
+    g.n_chunks = (L.len + L.kc - 1) / L.kc;
+    chunk_geom(L, 0, g.full[0], g.full[1], g.full[2]);
+    chunk_geom(L, g.n_chunks - 1, g.last[0], g.last[1], g.last[2]);
+    return g;
+}
+
+// Item cursor: item i = (row quad rq, chunk kc) with i = kc * n_rq + rq; a warp visits items
+// gwarp, gwarp + nwarps, ... in that order.
+struct ItemCursor {
+    int rq, kc;
+    __device__ __forceinline__ void start(int gwarp, int n_rq) {
+        rq = gwarp;
+        kc = 0;
+        while (rq >= n_rq) { rq -= n_rq; ++kc; }
+    }
+    __device__ __forceinline__ void advance(int nwarps, int n_rq) {
+        rq += nwarps;
+        while (rq >= n_rq) { rq -= n_rq; ++kc; }
+    }
+};
+
+// Each warp streams its items as one continuous sequence of stages.  Per stage: wait for the
+// slot's copy, pull the stage into registers, let lane 0 refill the slot with the next stage of
+// the sequence, then do the multiply-adds -- a slot is held only for its shared-memory loads,
+// which keeps four copies per warp in flight.
+__global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L) {
+    extern __shared__ __align__(128) unsigned char tma_raw[];
+    TmaSmem& sm = *reinterpret_cast<TmaSmem*>(tma_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = blockIdx.x * kRB + warp * kRowsPerWarp;
-    const size_t ld4 = (size_t)L.ld / 4;
-    const float4* r0 = reinterpret_cast<const float4*>(L.R) + (size_t)row0 * ld4 + (L.col0 + c_begin) / 4;
-    const float4* r1 = r0 + ld4;
-    const float4* r2 = r1 + ld4;
-    const float4* r3 = r2 + ld4;
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    int i = lane;
-    // four float4 per row in flight per lane
-    for (; i + 96 < n4; i += 128) {
-        float4 x00 = __ldcs(r0 + i), x01 = __ldcs(r0 + i + 32), x02 = __ldcs(r0 + i + 64), x03 = __ldcs(r0 + i + 96);
-        float4 x10 = __ldcs(r1 + i), x11 = __ldcs(r1 + i + 32), x12 = __ldcs(r1 + i + 64), x13 = __ldcs(r1 + i + 96);
-        float4 x20 = __ldcs(r2 + i), x21 = __ldcs(r2 + i + 32), x22 = __ldcs(r2 + i + 64), x23 = __ldcs(r2 + i + 96);
-        float4 x30 = __ldcs(r3 + i), x31 = __ldcs(r3 + i + 32), x32 = __ldcs(r3 + i + 64), x33 = __ldcs(r3 + i + 96);
-        float4 s0 = s_sh[i], s1 = s_sh[i + 32], s2 = s_sh[i + 64], s3 = s_sh[i + 96];
-        a0 = dot4(x00, s0, a0); a0 = dot4(x01, s1, a0); a0 = dot4(x02, s2, a0); a0 = dot4(x03, s3, a0);
-        a1 = dot4(x10, s0, a1); a1 = dot4(x11, s1, a1); a1 = dot4(x12, s2, a1); a1 = dot4(x13, s3, a1);
-        a2 = dot4(x20, s0, a2); a2 = dot4(x21, s1, a2); a2 = dot4(x22, s2, a2); a2 = dot4(x23, s3, a2);
-        a3 = dot4(x30, s0, a3); a3 = dot4(x31, s1, a3); a3 = dot4(x32, s2, a3); a3 = dot4(x33, s3, a3);
-    }
-    for (; i < n4; i += 32) {
-        float4 s0 = s_sh[i];
-        a0 = dot4(__ldcs(r0 + i), s0, a0);
-        a1 = dot4(__ldcs(r1 + i), s0, a1);
-        a2 = dot4(__ldcs(r2 + i), s0, a2);
-        a3 = dot4(__ldcs(r3 + i), s0, a3);
-    }
+    if (lane == 0)
+        for (int st = 0; st < kTmaStages; ++st) mbar_init(&sm.bar[warp][st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    const uint64_t pol = evict_first_policy();
+    const int gwarp = blockIdx.x * kTmaWarps + warp, nwarps = gridDim.x * kTmaWarps;
+    const int n_rq = L.n_rq;
+    const SliceGeom g = slice_geom(L);
+    const float4* R4 = reinterpret_cast<const float4*>(L.R + L.base);
+    const long long blk4 = (long long)L.kc;   // float4 per item block: 4 rows x kc floats / 4
+
+    // producer state (used by lane 0 only)
+    ItemCursor p;
+    p.start(gwarp, n_rq);
+    int p_t = 0;
+    const int* pg = p.kc == g.n_chunks - 1 ? g.last : g.full;
+    int p_n4 = pg[0], p_nst = pg[1], p_seg = pg[2];
+    const float4* p_src = R4 + ((long long)p.kc * n_rq + p.rq) * blk4;
+    int issued = 0;
+    auto issue_next = [&](int st) {
+        const int cnt = min(p_seg, p_n4 - p_t * p_seg);
+        const uint32_t bytes = (uint32_t)(kTmaRows * cnt) * 16u;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&sm.bar[warp][st], bytes);
+        bulk_g2s(sm.ring[warp][st], p_src + (long long)kTmaRows * p_seg * p_t, bytes, &sm.bar[warp][st], pol);
+        ++issued;
+        if (++p_t == p_nst) {
+            p_t = 0;
+            p.advance(nwarps, n_rq);
+            const int* q = p.kc == g.n_chunks - 1 ? g.last : g.full;
+            p_n4 = q[0];
+            p_nst = q[1];
+            p_seg = q[2];
+            p_src = R4 + ((long long)p.kc * n_rq + p.rq) * blk4;
+        }
+    };
+    if (lane == 0)
+        for (int st = 0; st < kTmaStages && p.kc < g.n_chunks; ++st) issue_next(st);
+
+    uint32_t parity = 0;  // bit st: parity of the next completion of slot st
+    int consumed = 0;
+    ItemCursor c;
+    for (c.start(gwarp, n_rq); c.kc < g.n_chunks; c.advance(nwarps, n_rq)) {
+        const int* cg = c.kc == g.n_chunks - 1 ? g.last : g.full;
+        const int n4 = cg[0], nst = cg[1], seg = cg[2];
+        const float4* s4 = reinterpret_cast<const float4*>(L.s + L.col0 + c.kc * L.kc);
+        float acc[kTmaRows] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int t = 0; t < nst; ++t, ++consumed) {
+            const int st = consumed % kTmaStages;
+            const int e0 = t * seg, cnt = min(seg, n4 - e0);
+            float4 sv[kTmaSeg / 32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-        a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+            for (int j = 0; j < kTmaSeg / 32; ++j) {
+                const int e = lane + 32 * j;
+                sv[j] = e < cnt ? __ldg(s4 + e0 + e) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            if (!mbar_wait_bounded(&sm.bar[warp][st], (parity >> st) & 1u)) {
+                // record the failure, let the copies still in flight land (bounded), stop the warp
+                if (lane == 0) {
+                    atomicExch(L.err, kErrReconTimeout);
+                    for (int k = consumed + 1; k < issued; ++k) {
+                        const int s2 = k % kTmaStages;
+                        mbar_wait_bounded(&sm.bar[warp][s2], (parity >> s2) & 1u);
+                    }
+                }
+                __syncwarp();
+                return;
+            }
+            parity ^= 1u << st;
+            const float4* ring = sm.ring[warp][st];
+            float4 rv[kTmaSeg / 32][kTmaRows];
+#pragma unroll
+            for (int j = 0; j < kTmaSeg / 32; ++j) {
+                const int e = lane + 32 * j;
+#pragma unroll
+                for (int q = 0; q < kTmaRows; ++q)
+                    rv[j][q] = e < cnt ? ring[q * cnt + e] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            __syncwarp();  // every lane has read the slot before it is refilled
+            if (lane == 0 && p.kc < g.n_chunks) issue_next(st);
+#pragma unroll
+            for (int j = 0; j < kTmaSeg / 32; ++j)
+#pragma unroll
+                for (int q = 0; q < kTmaRows; ++q) acc[q] = dot4(rv[j][q], sv[j], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kTmaRows; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        }
+        if (lane == 0) {
+            float* out = L.partial + (size_t)(L.chunk0 + c.kc) * L.n_cmd;
+            const int row0 = c.rq * kTmaRows;
+#pragma unroll
+            for (int q = 0; q < kTmaRows; ++q)
+                if (row0 + q < L.n_cmd) out[row0 + q] = acc[q];
+        }
     }
-    if (lane == 0) {
-        float* p = L.partial + (size_t)(L.chunk0 + kc) * L.n_cmd;
-        if (row0 + 0 < L.n_cmd) p[row0 + 0] = a0;
-        if (row0 + 1 < L.n_cmd) p[row0 + 1] = a1;
-        if (row0 + 2 < L.n_cmd) p[row0 + 2] = a2;
-        if (row0 + 3 < L.n_cmd) p[row0 + 3] = a3;
+}
+
+// Re-tiling: one thread per float4 of the slice in the source layout (rows x chunk columns).
+__global__ void recon_tile_kernel(const float4* __restrict__ src, long long ld4, ReconLaunch L) {
+    const long long n4_slice = (long long)(L.kc / 4) * ((L.len + L.kc - 1) / L.kc);
+    const long long total = (long long)L.n_rq * kTmaRows * n4_slice;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / n4_slice;
+        const int c4 = (int)(i - r * n4_slice);           // float4 column inside the slice
+        const int kc = c4 / (L.kc / 4), e4 = c4 - kc * (L.kc / 4);
+        int n4, nst, seg;
+        chunk_geom(L, kc, n4, nst, seg);
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (e4 < n4) v = src[r * ld4 + L.col0 / 4 + c4];
+        else continue;                                     // padding of a short last chunk
+        const int t = e4 / seg, e = e4 - t * seg;
+        const int cnt = min(seg, n4 - t * seg);
+        const int rq = (int)(r / kTmaRows), q = (int)(r % kTmaRows);
+        float4* dst = reinterpret_cast<float4*>(const_cast<float*>(L.R) + L.base) +
+                      ((long long)kc * L.n_rq + rq) * (long long)L.kc + (long long)kTmaRows * seg * t + q * cnt + e;
+        *dst = v;
     }
 }
 
@@ -100,10 +273,27 @@ __global__ void recon_reduce_kernel(ReduceLaunch L) {
 
 }  // namespace
 
+long long recon_slice_floats(int n_rq, int len, int kc) {
+    const long long chunks = (len + kc - 1) / kc;
+    return chunks * n_rq * (long long)kTmaRows * kc;
+}
+
+cudaError_t recon_prepare() {
+    return cudaFuncSetAttribute(recon_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TmaSmem));
+}
+
 cudaError_t launch_recon(const ReconLaunch& L, cudaStream_t s) {
     if (L.n_cmd <= 0 || L.len <= 0) return cudaSuccess;
-    dim3 grid((unsigned)(L.rows_pad / kRB), (unsigned)((L.len + L.kc - 1) / L.kc));
-    recon_gemv_kernel<<<grid, 256, 0, s>>>(L);
+    const int n_items = L.n_rq * ((L.len + L.kc - 1) / L.kc);
+    const int need = (n_items + kTmaWarps - 1) / kTmaWarps;
+    int ctas = (L.max_ctas > 0 && L.max_ctas < need) ? L.max_ctas : need;
+    recon_tma_kernel<<<(unsigned)ctas, kTmaWarps * 32, sizeof(TmaSmem), s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recon_tile(const float* src, int ld, const ReconLaunch& L, cudaStream_t s) {
+    if (L.len <= 0) return cudaSuccess;
+    recon_tile_kernel<<<2048, 256, 0, s>>>(reinterpret_cast<const float4*>(src), ld / 4, L);
     return cudaGetLastError();
 }
 

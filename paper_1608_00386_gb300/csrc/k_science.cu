@@ -127,6 +127,113 @@ __global__ void __launch_bounds__(256) sci_cols_kernel(SciLaunch L) {
     if (blockIdx.x == 0 && tid == 0) L.acc->n_psf += 1;
 }
 
+// Compile-time-size versions of the two FFT passes (2 rows / columns per block).
+constexpr int kCtRows = 2;
+
+template <int M>
+__global__ void __launch_bounds__(256) sci_rows_ct(SciLaunch L) {
+    extern __shared__ float4 smem_raw[];
+    float2* A = reinterpret_cast<float2*>(smem_raw);
+    float2* B = A + kCtRows * M;
+    float2* W = B + kCtRows * M;
+    double* red = reinterpret_cast<double*>(W + M);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (blockIdx.x == 0) {
+        double sr = 0.0, si = 0.0;
+        for (int q = tid; q < L.n_tiles; q += nthr) {
+            float2 p = L.sr_part[q];
+            sr += p.x;
+            si += p.y;
+        }
+        red[tid] = sr;
+        red[nthr + tid] = si;
+        __syncthreads();
+        for (int o = nthr / 2; o > 0; o >>= 1) {
+            if (tid < o) {
+                red[tid] += red[tid + o];
+                red[nthr + tid] += red[nthr + tid + o];
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            double s = (red[0] * red[0] + red[nthr] * red[nthr]) / (L.sum_amp * L.sum_amp);
+            L.acc->sr_sum += s;
+            L.acc->sr_last = s;
+            L.acc->n_sr += 1;
+        }
+        __syncthreads();
+    }
+    if (!psf_step(L)) return;
+    const int row0 = blockIdx.x * kCtRows;
+    for (int q = tid; q < M; q += nthr) W[q] = L.w[q];
+    for (int q = tid; q < kCtRows * M; q += nthr) {
+        int r = q / M, c = q - r * M;
+        int row = row0 + r;
+        A[q] = (row < L.N && c < L.N) ? L.field[(long long)row * L.N + c] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    float2* R = stockham_fft_ct<M>(A, B, kCtRows, M, W, tid, nthr);
+    for (int q = tid; q < kCtRows * M; q += nthr) {
+        int c = q / kCtRows, r = q - c * kCtRows;
+        int row = row0 + r;
+        if (row < L.N) L.ft[(long long)c * L.N + row] = R[r * M + c];
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) sci_cols_ct(SciLaunch L) {
+    if (!psf_step(L)) return;
+    extern __shared__ float4 smem_raw[];
+    float2* A = reinterpret_cast<float2*>(smem_raw);
+    float2* B = A + kCtRows * M;
+    float2* W = B + kCtRows * M;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int c0 = blockIdx.x * kCtRows;
+    for (int q = tid; q < M; q += nthr) W[q] = L.w[q];
+    for (int q = tid; q < kCtRows * M; q += nthr) {
+        int r = q / M, j = q - r * M;
+        A[q] = (j < L.N) ? L.ft[(long long)(c0 + r) * L.N + j] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    float2* R = stockham_fft_ct<M>(A, B, kCtRows, M, W, tid, nthr);
+    for (int q = tid; q < kCtRows * M; q += nthr) {
+        int r = q / M, j = q - r * M;
+        float2 v = R[q];
+        float p = fmaf(v.x, v.x, v.y * v.y);   // frame intensity in float, accumulated in double
+        L.psf_t[(long long)(c0 + r) * M + j] += (double)p;
+    }
+    if (blockIdx.x == 0 && tid == 0) L.acc->n_psf += 1;
+}
+
+template <int M>
+size_t ct_smem() {
+    return sizeof(float2) * (2 * kCtRows * (size_t)M + M) + sizeof(double) * 2 * 256;
+}
+
+template <int M>
+cudaError_t ct_prepare() {
+    cudaError_t e = cudaFuncSetAttribute((const void*)sci_rows_ct<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ct_smem<M>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)sci_cols_ct<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ct_smem<M>());
+}
+
+template <int M>
+cudaError_t ct_rows(const SciLaunch& L, cudaStream_t s) {
+    sci_rows_ct<M><<<(unsigned)((L.N + kCtRows - 1) / kCtRows), 256, ct_smem<M>(), s>>>(L);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t ct_cols(const SciLaunch& L, cudaStream_t s) {
+    sci_cols_ct<M><<<(unsigned)(M / kCtRows), 256, ct_smem<M>(), s>>>(L);
+    return cudaGetLastError();
+}
+
+// sizes with a compile-time kernel; other sizes use the generic one
+#define MCAO_SCI_CT_SIZES(X) X(128) X(256) X(512) X(640) X(1024) X(1280) X(2048)
+
 size_t fft_smem_bytes(int M) {
     return sizeof(float2) * (2 * kRowsPerBlock * (size_t)M + M) + sizeof(double) * 2 * 256;
 }
@@ -147,18 +254,35 @@ cudaError_t sci_prepare(int M) {
     size_t sm = fft_smem_bytes(M);
     cudaError_t e = set_smem((const void*)sci_rows_kernel, sm);
     if (e != cudaSuccess) return e;
-    return set_smem((const void*)sci_cols_kernel, sm);
+    e = set_smem((const void*)sci_cols_kernel, sm);
+    if (e != cudaSuccess) return e;
+#define MCAO_CT_PREP(n) \
+    if (M >= n) {       \
+        e = ct_prepare<n>(); \
+        if (e != cudaSuccess) return e; \
+    }
+    MCAO_SCI_CT_SIZES(MCAO_CT_PREP)
+#undef MCAO_CT_PREP
+    return cudaSuccess;
 }
 
 size_t sci_smem_bytes(int M) { return fft_smem_bytes(M); }
 
 cudaError_t launch_sci_rows(const SciLaunch& L, cudaStream_t s) {
+#define MCAO_CT_ROWS(n) \
+    if (L.M == n) return ct_rows<n>(L, s);
+    MCAO_SCI_CT_SIZES(MCAO_CT_ROWS)
+#undef MCAO_CT_ROWS
     size_t sm = fft_smem_bytes(L.M);
     sci_rows_kernel<<<(unsigned)((L.N + kRowsPerBlock - 1) / kRowsPerBlock), 256, sm, s>>>(L);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sci_cols(const SciLaunch& L, cudaStream_t s) {
+#define MCAO_CT_COLS(n) \
+    if (L.M == n) return ct_cols<n>(L, s);
+    MCAO_SCI_CT_SIZES(MCAO_CT_COLS)
+#undef MCAO_CT_COLS
     size_t sm = fft_smem_bytes(L.M);
     sci_cols_kernel<<<(unsigned)(L.M / kRowsPerBlock), 256, sm, s>>>(L);
     return cudaGetLastError();

@@ -31,173 +31,258 @@ namespace {
 constexpr float kPi = 3.14159265358979323846f;
 
 // ------------------------------------------------------------------------------------------
+// small inverse DFTs in registers: out[k] = sum_j in[j] exp(+2 pi i j k / M), M = 1, 2, 4, 8
+// ------------------------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void idft_small(float2* v);
+
+template <>
+__device__ __forceinline__ void idft_small<1>(float2*) {}
+
+template <>
+__device__ __forceinline__ void idft_small<2>(float2* v) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void idft_small<4>(float2* v) {
+    float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+    float2 a2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+    float2 a3 = make_float2(-d.y, d.x);  // +i (v1 - v3)
+    v[0] = cadd(a0, a2);
+    v[2] = csub(a0, a2);
+    v[1] = cadd(a1, a3);
+    v[3] = csub(a1, a3);
+}
+
+template <>
+__device__ __forceinline__ void idft_small<8>(float2* v) {
+    // radix-2 split: even / odd 4-point transforms, twiddles exp(+2 pi i k / 8)
+    float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    idft_small<4>(e);
+    idft_small<4>(o);
+    const float r = 0.707106781186547524f;
+    float2 t1 = make_float2(r * (o[1].x - o[1].y), r * (o[1].x + o[1].y));    // o1 (1 + i)/sqrt2
+    float2 t2 = make_float2(-o[2].y, o[2].x);                                 // o2 i
+    float2 t3 = make_float2(-r * (o[3].x + o[3].y), r * (o[3].x - o[3].y));   // o3 (-1 + i)/sqrt2
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], t1);
+    v[5] = csub(e[1], t1);
+    v[2] = cadd(e[2], t2);
+    v[6] = csub(e[2], t2);
+    v[3] = cadd(e[3], t3);
+    v[7] = csub(e[3], t3);
+}
+
+// ------------------------------------------------------------------------------------------
 // autocorrelation route: one warp per 8 x 8 subaperture, 8 warps per block
 // ------------------------------------------------------------------------------------------
+struct GridMeta {
+    const float* data;
+    int n;
+    float sign;
+};
+
 template <int NFFT, int NBIN>
-__global__ void __launch_bounds__(256) wfs_acf_kernel(WfsLaunch L) {
+__global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
     constexpr int NPX = 8;
     constexpr int ND = NFFT / NBIN;
     constexpr int NL = 2 * NPX - 1;
-    constexpr int PIX_PER_LANE = (ND * ND + 31) / 32;
-    constexpr int Y_PER_LANE = (NPX * ND + 31) / 32;
-    __shared__ AxisEnt s_ex[8][kMaxEntries * NPX];
-    __shared__ AxisEnt s_ey[8][kMaxEntries * NPX];
-    __shared__ float2 s_E[8][NPX * NPX];
-    __shared__ float2 s_M[8][NPX * NPX];
+    constexpr int PIX_PER_LANE = ND * ND / 32;
+    constexpr int QY = ND / 4;        // outputs per lane of the row transform (4 lanes per row)
+    constexpr int LPC = 32 / ND;      // lanes per column of the column transform
+    constexpr int QB = ND / LPC;      // outputs per lane of the column transform
+    static_assert(ND == 8 || ND == 16, "detector of 8 or 16 pixels per side");
+    // per warp: axis entries (dead after the field, then reused for the row transform),
+    // grid metadata, the field (reused for M_uy), the lag products; per block: twiddles and
+    // reciprocals.  About 30 KB per block, so three blocks fit beside a reconstructor block.
+    union Scratch {
+        AxisEnt e[2][kMaxEntries * NPX];
+        float2 y[NPX * ND];
+    };
+    __shared__ Scratch s_u[8];
+    __shared__ GridMeta s_gm[8][kMaxEntries];
+    __shared__ float2 s_EM[8][NPX * NPX];
     __shared__ float2 s_P[8][NPX * NL];
-    __shared__ float2 s_Y[8][NPX * ND];
-    __shared__ float2 s_tw[8][ND];
-    __shared__ float s_recip[8][65];
+    __shared__ float2 s_tw[ND];
+    __shared__ float s_recip[65];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < ND) {
+        float sn, cs;
+        sincospif(2.0f * (float)threadIdx.x / (float)ND, &sn, &cs);  // exp(2 pi i k / ND)
+        s_tw[threadIdx.x] = make_float2(cs, sn);
+    }
+    if (L.ctx.noise) fill_recip(s_recip, threadIdx.x, blockDim.x);
+    __syncthreads();  // the only block-wide barrier
     const int sub = blockIdx.x * 8 + warp;
-    if (sub >= L.n_subaps) return;  // warp-uniform; the kernel uses warp-level sync only
+    if (sub >= L.n_subaps) return;  // warp-uniform; warp-level sync only from here on
     const SubapDev sd = L.subaps[sub];
     const WfsDev& w = L.ctx.wfs[sd.wfs];
     const int i0 = sd.sx * NPX, j0 = sd.sy * NPX;
     const int n_grids = L.ctx.n_grids;
     const GridView* V = L.ctx.views + (long long)sd.wfs * n_grids;
     const long long k = L.ctx.st->k;
+    AxisEnt* s_ex = s_u[warp].e[0];
+    AxisEnt* s_ey = s_u[warp].e[1];
 
-    tile_entries(V, n_grids, k, i0, j0, NPX, s_ex[warp], s_ey[warp], lane, 32);
-    if (lane < ND) s_tw[warp][lane] = w.tw[lane];
-    if (L.ctx.noise) fill_recip(s_recip[warp], lane, 32);
+    tile_entries(V, n_grids, k, i0, j0, NPX, s_ex, s_ey, lane, 32);
+    if (lane < n_grids) {
+        GridMeta gm;
+        gm.data = V[lane].data;
+        gm.n = V[lane].n;
+        gm.sign = V[lane].sign;
+        s_gm[warp][lane] = gm;
+    }
     __syncwarp();
 
-    // field E = A exp(i (scale phi - pi (x + y) / N)): lane -> column x, rows y and y + 4
-    const float scale = w.scale;
+    // field E = A exp(i (scale phi - pi (x + y) / N)): lane -> column x, rows y0 and y0 + 4
     {
-        const int x = lane & 7;
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int y = (lane >> 3) + 4 * hh;
-            float phi = tile_phase(V, n_grids, s_ex[warp], s_ey[warp], NPX, x, y);
-            float a = __ldg(w.amp + (long long)(j0 + y) * w.N + i0 + x);
-            float arg = scale * phi - kPi * (float)(x + y) / (float)NFFT;
-            float sn, cs;
-            sincosf(arg, &sn, &cs);
-            s_E[warp][y * NPX + x] = make_float2(a * cs, a * sn);
+        const int x = lane & 7, y0 = lane >> 3, y1 = y0 + 4;
+        float phi0 = 0.0f, phi1 = 0.0f;
+#pragma unroll 2
+        for (int g = 0; g < n_grids; ++g) {
+            const GridMeta gm = s_gm[warp][g];
+            const AxisEnt ex = s_ex[g * NPX + x];
+            phi0 = fmaf(gm.sign, bilinear(gm.data, gm.n, ex, s_ey[g * NPX + y0]), phi0);
+            phi1 = fmaf(gm.sign, bilinear(gm.data, gm.n, ex, s_ey[g * NPX + y1]), phi1);
         }
+        const float scale = w.scale;
+        const float* arow = w.amp + (long long)j0 * w.N + i0 + x;
+        float a0 = __ldg(arow + (long long)y0 * w.N), a1 = __ldg(arow + (long long)y1 * w.N);
+        float sn, cs;
+        sincosf(scale * phi0 - kPi * (float)(x + y0) / (float)NFFT, &sn, &cs);
+        s_EM[warp][y0 * NPX + x] = make_float2(a0 * cs, a0 * sn);
+        sincosf(scale * phi1 - kPi * (float)(x + y1) / (float)NFFT, &sn, &cs);
+        s_EM[warp][y1 * NPX + x] = make_float2(a1 * cs, a1 * sn);
     }
     __syncwarp();
 
-    // columns a, b0, b1 of E in registers
-    const int ca_i = lane >> 2, cb_i = lane & 3;
-    float2 ca[NPX], cb0[NPX], cb1[NPX];
+    // ACF(ux, uy) = sum_a M_uy[a][a + ux], M_uy[a][b] = sum_r E[r][a] conj(E[r + uy][b]);
+    // lane holds columns a, b0, b1 of E
+    {
+        const int ca_i = lane >> 2, cb_i = lane & 3;
+        float2 ca[NPX], cb0[NPX], cb1[NPX];
 #pragma unroll
-    for (int r = 0; r < NPX; ++r) {
-        ca[r] = s_E[warp][r * NPX + ca_i];
-        cb0[r] = s_E[warp][r * NPX + cb_i];
-        cb1[r] = s_E[warp][r * NPX + cb_i + 4];
-    }
-    float2 hx = make_float2(0.0f, 0.0f);
-    if (lane < NL) hx = w.h[lane];  // h(ux), ux = lane - 7
-    const int ux = lane - (NPX - 1);
-
-#pragma unroll
-    for (int uy = 0; uy < NPX; ++uy) {
-        float m0r = 0.0f, m0i = 0.0f, m1r = 0.0f, m1i = 0.0f;
-#pragma unroll
-        for (int r = 0; r + uy < NPX; ++r) {
-            // ca[r] conj(cb[r + uy])
-            float2 a = ca[r], b0 = cb0[r + uy], b1 = cb1[r + uy];
-            m0r = fmaf(a.x, b0.x, fmaf(a.y, b0.y, m0r));
-            m0i = fmaf(a.y, b0.x, fmaf(-a.x, b0.y, m0i));
-            m1r = fmaf(a.x, b1.x, fmaf(a.y, b1.y, m1r));
-            m1i = fmaf(a.y, b1.x, fmaf(-a.x, b1.y, m1i));
+        for (int r = 0; r < NPX; ++r) {
+            ca[r] = s_EM[warp][r * NPX + ca_i];
+            cb0[r] = s_EM[warp][r * NPX + cb_i];
+            cb1[r] = s_EM[warp][r * NPX + cb_i + 4];
         }
-        s_M[warp][ca_i * NPX + cb_i] = make_float2(m0r, m0i);
-        s_M[warp][ca_i * NPX + cb_i + 4] = make_float2(m1r, m1i);
-        __syncwarp();
-        if (lane < NL) {
-            // ACF(ux, uy) = sum_a M[a][a + ux]
-            float ar = 0.0f, ai = 0.0f;
+        __syncwarp();  // every lane holds its columns: the buffer now receives M_uy
+        float2 hx = make_float2(0.0f, 0.0f);
+        if (lane < NL) hx = w.h[lane];  // h(ux), ux = lane - 7
+        const int ux = lane - (NPX - 1);
 #pragma unroll
-            for (int a = 0; a < NPX; ++a) {
-                int b = a + ux;
-                if (b >= 0 && b < NPX) {
-                    float2 m = s_M[warp][a * NPX + b];
-                    ar += m.x;
-                    ai += m.y;
+        for (int uy = 0; uy < NPX; ++uy) {
+            float m0r = 0.0f, m0i = 0.0f, m1r = 0.0f, m1i = 0.0f;
+#pragma unroll
+            for (int r = 0; r + uy < NPX; ++r) {
+                float2 a = ca[r], b0 = cb0[r + uy], b1 = cb1[r + uy];
+                m0r = fmaf(a.x, b0.x, fmaf(a.y, b0.y, m0r));
+                m0i = fmaf(a.y, b0.x, fmaf(-a.x, b0.y, m0i));
+                m1r = fmaf(a.x, b1.x, fmaf(a.y, b1.y, m1r));
+                m1i = fmaf(a.y, b1.x, fmaf(-a.x, b1.y, m1i));
+            }
+            s_EM[warp][ca_i * NPX + cb_i] = make_float2(m0r, m0i);
+            s_EM[warp][ca_i * NPX + cb_i + 4] = make_float2(m1r, m1i);
+            __syncwarp();
+            if (lane < NL) {
+                float ar = 0.0f, ai = 0.0f;
+#pragma unroll
+                for (int a = 0; a < NPX; ++a) {
+                    int b = a + ux;
+                    if (b >= 0 && b < NPX) {
+                        float2 m = s_EM[warp][a * NPX + b];
+                        ar += m.x;
+                        ai += m.y;
+                    }
                 }
+                float otf = 1.0f;
+                if (sd.elong_a > 0.0f) {
+                    float d = (float)ux * sd.dir_x + (float)uy * sd.dir_y;
+                    otf = expf(-sd.elong_a * d * d);
+                }
+                float2 hh = cmul(hx, w.h[uy + NPX - 1]);
+                s_P[warp][uy * NL + lane] = cmul(make_float2(ar * otf, ai * otf), hh);
             }
-            float otf = 1.0f;
-            if (sd.elong_a > 0.0f) {
-                float d = (float)ux * sd.dir_x + (float)uy * sd.dir_y;
-                otf = expf(-sd.elong_a * d * d);
-            }
-            float2 hh = cmul(hx, w.h[uy + NPX - 1]);
-            float2 p = cmul(make_float2(ar * otf, ai * otf), hh);
-            s_P[warp][uy * NL + lane] = p;
+            __syncwarp();
         }
-        __syncwarp();
     }
 
-    // Y[uy][mx] = sum_ux P(ux, uy) e^{2 pi i ux mx / ND}, uy >= 0
+    // rows: Y[uy][q + 4 j] = sum_ux P[uy][ux] w^{ux q} (w^4)^{ux j}, w = e^{2 pi i / ND};
+    // lane -> (uy, q), fold ux mod ND/4, then an ND/4-point inverse DFT
+    {
+        const int uy = lane >> 2, q = lane & 3;
+        float2 S[QY];
 #pragma unroll
-    for (int j = 0; j < Y_PER_LANE; ++j) {
-        int o = lane + 32 * j;
-        if (o < NPX * ND) {
-            int uy = o / ND, mx = o % ND;
-            const float2* prow = s_P[warp] + uy * NL;
-            float yr = 0.0f, yi = 0.0f;
+        for (int r = 0; r < QY; ++r) S[r] = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int q = 0; q < NL; ++q) {
-                int m = (((q - (NPX - 1)) % ND + ND) * mx) % ND;
-                float2 t = s_tw[warp][m], p = prow[q];
-                yr = fmaf(p.x, t.x, fmaf(-p.y, t.y, yr));
-                yi = fmaf(p.x, t.y, fmaf(p.y, t.x, yi));
-            }
-            s_Y[warp][o] = make_float2(yr, yi);
+        for (int c = 0; c < NL; ++c) {
+            const int ux = c - (NPX - 1);
+            const float2 p = s_P[warp][uy * NL + c];
+            const float2 t = s_tw[((ux + 2 * ND) * q) % ND];
+            const int r = (ux + 2 * ND) % QY;
+            S[r] = cadd(S[r], cmul(p, t));
         }
+        idft_small<QY>(S);
+#pragma unroll
+        for (int j = 0; j < QY; ++j) s_u[warp].y[uy * ND + q + 4 * j] = S[j];
     }
     __syncwarp();
 
-    // B[my][mx] = Re(Y[0][mx]) + 2 Re sum_{uy>0} Y[uy][mx] e^{2 pi i uy my / ND}
+    // columns: B[h + LPC j][mx] = Re sum_uy z[uy] w^{uy h} (w^LPC)^{uy j}, z = Y[0], 2 Y[uy > 0];
+    // lane -> (mx, h); fold uy mod QB, then a QB-point inverse DFT (real part).  Output j of
+    // lane l is detector pixel o = l + 32 j.
     float B[PIX_PER_LANE];
     float bsum = 0.0f;
+    {
+        const int mx = lane & (ND - 1), h = lane / ND;
+        static_assert(PIX_PER_LANE == QB, "pixel mapping");
+        float2 Z[QB];
 #pragma unroll
-    for (int j = 0; j < PIX_PER_LANE; ++j) {
-        int o = lane + 32 * j;
-        float b = 0.0f;
-        if (o < ND * ND) {
-            int my = o / ND, mx = o % ND;
-            float acc = 0.0f;
+        for (int r = 0; r < QB; ++r) Z[r] = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int uy = 1; uy < NPX; ++uy) {
-                float2 t = s_tw[warp][(uy * my) % ND], yv = s_Y[warp][uy * ND + mx];
-                acc = fmaf(yv.x, t.x, fmaf(-yv.y, t.y, acc));
-            }
-            b = fmaf(2.0f, acc, s_Y[warp][mx].x);
+        for (int uy = 0; uy < NPX; ++uy) {
+            float2 y = s_u[warp].y[uy * ND + mx];
+            if (uy > 0) y = make_float2(2.0f * y.x, 2.0f * y.y);
+            const float2 t = s_tw[(uy * h) % ND];
+            Z[uy % QB] = cadd(Z[uy % QB], cmul(y, t));
         }
-        B[j] = b;
-        bsum += b;
+        idft_small<QB>(Z);
+#pragma unroll
+        for (int j = 0; j < QB; ++j) {
+            B[j] = Z[j].x;
+            bsum += Z[j].x;
+        }
     }
     bsum = warp_sum(bsum);
     const float norm = (bsum > 0.0f) ? w.n_photons * sd.frac / bsum : 0.0f;
 
-    // detector pixels: expected photo-electrons, optional noise, centre of gravity
+    // detector pixels o = lane + 32 j = my ND + mx: expected photo-electrons, optional noise,
+    // centre of gravity
     const float c0 = 0.5f * (float)(ND - 1);
     float sv = 0.0f, sx = 0.0f, sy = 0.0f;
     const long long pix0 = (long long)sd.rank * ND * ND;
 #pragma unroll
     for (int j = 0; j < PIX_PER_LANE; ++j) {
         int o = lane + 32 * j;
-        if (o < ND * ND) {
-            float lam = B[j] * norm;
-            float v = lam;
-            if (L.ctx.noise) {
-                int n = noise_sample(lam, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
-                                     L.ctx.seed, s_recip[warp]);
-                v = (float)n;
-                if (L.frame_out) L.frame_out[w.frame0 + pix0 + o] = n;
-            }
-            if (L.lam_out) L.lam_out[w.frame0 + pix0 + o] = lam;
-            int my = o / ND, mx = o % ND;
-            sv += v;
-            sx = fmaf((float)mx - c0, v, sx);
-            sy = fmaf((float)my - c0, v, sy);
+        float lam = B[j] * norm;
+        float v = lam;
+        if (L.ctx.noise) {
+            int n = noise_sample(lam, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
+                                 L.ctx.seed, s_recip);
+            v = (float)n;
+            if (L.frame_out) L.frame_out[w.frame0 + pix0 + o] = n;
         }
+        if (L.lam_out) L.lam_out[w.frame0 + pix0 + o] = lam;
+        int my = o / ND, mx = o % ND;
+        sv += v;
+        sx = fmaf((float)mx - c0, v, sx);
+        sy = fmaf((float)my - c0, v, sy);
     }
     sv = warp_sum(sv);
     sx = warp_sum(sx);
@@ -209,8 +294,13 @@ __global__ void __launch_bounds__(256) wfs_acf_kernel(WfsLaunch L) {
             gy = sy / sv;
         }
         int ix = w.slope0 + sd.rank, iy = w.slope0 + w.n_valid + sd.rank;
-        L.slopes[ix] = gx - (L.s_ref ? L.s_ref[ix] : 0.0f);
-        L.slopes[iy] = gy - (L.s_ref ? L.s_ref[iy] : 0.0f);
+        const float vx = gx - (L.s_ref ? L.s_ref[ix] : 0.0f), vy = gy - (L.s_ref ? L.s_ref[iy] : 0.0f);
+        L.slopes[ix] = vx;
+        L.slopes[iy] = vy;
+        if (L.slopes_pad) {
+            L.slopes_pad[w.rcol0 + sd.rank] = vx;
+            L.slopes_pad[w.rcol0 + w.n_valid + sd.rank] = vy;
+        }
     }
 }
 
@@ -335,8 +425,13 @@ __global__ void __launch_bounds__(kFftThreads) wfs_fft_kernel(WfsLaunch L) {
             gy = ty / tv;
         }
         int ix = w.slope0 + sd.rank, iy = w.slope0 + w.n_valid + sd.rank;
-        L.slopes[ix] = gx - (L.s_ref ? L.s_ref[ix] : 0.0f);
-        L.slopes[iy] = gy - (L.s_ref ? L.s_ref[iy] : 0.0f);
+        const float vx = gx - (L.s_ref ? L.s_ref[ix] : 0.0f), vy = gy - (L.s_ref ? L.s_ref[iy] : 0.0f);
+        L.slopes[ix] = vx;
+        L.slopes[iy] = vy;
+        if (L.slopes_pad) {
+            L.slopes_pad[w.rcol0 + sd.rank] = vx;
+            L.slopes_pad[w.rcol0 + w.n_valid + sd.rank] = vy;
+        }
     }
 }
 

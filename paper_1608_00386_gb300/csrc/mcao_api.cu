@@ -79,7 +79,7 @@ struct mcao_sim {
     std::vector<Science> sci;
     std::vector<FftGroup> fft_groups;
     std::string err;
-    int device = 0;
+    int device = 0, sm_count = 0;
     int n_slopes = 0, n_frame_px = 0, ld = 0;
 
     cudaStream_t s0 = nullptr, s1 = nullptr, s2 = nullptr, s3 = nullptr;
@@ -92,6 +92,7 @@ struct mcao_sim {
     WfsDev* d_wfs = nullptr;
     float* d_amp_all = nullptr;
     float* d_slopes = nullptr;
+    float* d_slopes_pad = nullptr;        // slopes in R's padded column layout
     float* d_sref = nullptr;
     float* d_lam = nullptr;
     int* d_frames = nullptr;
@@ -111,9 +112,7 @@ struct mcao_sim {
     float* d_dm_g = nullptr;
     int2* d_dm_band = nullptr;
     int* d_dm_map = nullptr;
-    float* d_dm_tmp = nullptr;
     float* d_dm_surf = nullptr;
-    int dm_pass1_blocks = 0;
     int dm_tile_start[kMaxDms + 1] = {0};
     int n_cmd = 0;
     bool dms_loaded = false;
@@ -134,6 +133,7 @@ struct mcao_sim {
 
     StepState* d_st = nullptr;
     SciAcc* d_acc = nullptr;
+    int* d_err = nullptr;                 // device-side error code (bounded waits)
 
     // graph
     cudaGraph_t graph = nullptr;
@@ -243,9 +243,7 @@ DmLaunch make_dm_launch(mcao_sim* S) {
     L.band = S->d_dm_band;
     L.act_map = S->d_dm_map;
     L.c = S->d_c;
-    L.tmp = S->d_dm_tmp;
     L.surf = S->d_dm_surf;
-    L.pass1_blocks = S->dm_pass1_blocks;
     for (int m = 0; m <= kMaxDms; ++m) L.tile_start[m] = S->dm_tile_start[m];
     L.st = S->d_st;
     return L;
@@ -282,6 +280,7 @@ WfsLaunch make_wfs_launch(mcao_sim* S, const SubapDev* subaps, int n) {
     L.n_subaps = n;
     L.s_ref = S->d_sref;
     L.slopes = S->d_slopes;
+    L.slopes_pad = S->d_slopes_pad;
     L.lam_out = S->cfg.keep_frames ? S->d_lam : nullptr;
     L.frame_out = (S->cfg.keep_frames && S->cfg.noise) ? S->d_frames : nullptr;
     return L;
@@ -331,8 +330,9 @@ mcao_status rebuild_views(mcao_sim* S) {
     dfree(S->d_views);
     S->n_grids = (int)grids.size();
     CK(dalloc(&S->d_views, out.size()));
-    if (!out.empty()) CK(cudaMemcpy(S->d_views, out.data(), sizeof(GridView) * out.size(), cudaMemcpyHostToDevice));
+    if (!out.empty()) CK(cudaMemcpyAsync(S->d_views, out.data(), sizeof(GridView) * out.size(), cudaMemcpyHostToDevice, S->s0));
     release_graph(S);
+    CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
 
@@ -371,7 +371,7 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
     size_t used = 0;
     int slot = prof_begin(S, ST_DM, S->s0);
     if ((e = launch_dm_surfaces(make_dm_launch(S), S->s0)) != cudaSuccess) return e;
-    nl += S->n_dms > 0 ? 2 : 1;
+    nl += 1;
     prof_end(S, slot, S->s0);
     cudaEvent_t ev_fork = dep_event(S, used);
     if ((e = cudaEventRecord(ev_fork, S->s0)) != cudaSuccess) return e;
@@ -496,6 +496,15 @@ mcao_status signal_user(mcao_sim* S) {
 
 mcao_status sync_all(mcao_sim* S) {
     for (cudaStream_t st : {S->s0, S->s1, S->s2, S->s3}) CK(cudaStreamSynchronize(st));
+    if (S->d_err) {
+        int e = 0;
+        CK(cudaMemcpy(&e, S->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e != 0) {
+            CK(cudaMemsetAsync(S->d_err, 0, sizeof(int), S->s0));
+            return fail(S, MCAO_E_TIMEOUT, "a bounded device wait gave up (code %d): results of the last steps are invalid",
+                        e);
+        }
+    }
     return MCAO_OK;
 }
 
@@ -510,13 +519,14 @@ void destroy_all(mcao_sim* S) {
     for (auto& c : S->sci) {
         dfree(c.d_amp); dfree(c.d_field); dfree(c.d_ft); dfree(c.d_psf_t); dfree(c.d_sr_part); dfree(c.d_w);
     }
-    dfree(S->d_wfs); dfree(S->d_amp_all); dfree(S->d_slopes); dfree(S->d_sref); dfree(S->d_lam);
+    dfree(S->d_wfs); dfree(S->d_amp_all); dfree(S->d_slopes); dfree(S->d_slopes_pad); dfree(S->d_sref);
+    dfree(S->d_lam);
     dfree(S->d_frames);
     for (auto p : S->d_layer_owned) cudaFree(p);
     S->d_layer_owned.clear();
-    dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map); dfree(S->d_dm_tmp);
+    dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
     dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_c); dfree(S->d_partial);
-    dfree(S->d_st); dfree(S->d_acc);
+    dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err);
     for (auto e : S->prof_pool) cudaEventDestroy(e);
     for (auto e : S->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : {S->ev_user, S->ev_done})
@@ -621,15 +631,21 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         }                                                                                        \
     } while (0)
     CKC(cudaGetDevice(&S->device));
+    CKC(cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, S->device));
     int prio_lo = 0, prio_hi = 0;
     CKC(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-    CKC(cudaStreamCreateWithPriority(&S->s0, cudaStreamNonBlocking, prio_hi));
-    CKC(cudaStreamCreateWithPriority(&S->s1, cudaStreamNonBlocking, prio_hi));
-    CKC(cudaStreamCreateWithPriority(&S->s3, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
+    // the reconstructor stream is served first so that its few resident blocks keep HBM busy
+    // while the sensing kernels fill the remaining slots; science runs last
+    CKC(cudaStreamCreateWithPriority(&S->s3, cudaStreamNonBlocking, prio_hi));
+    CKC(cudaStreamCreateWithPriority(&S->s0, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
+    CKC(cudaStreamCreateWithPriority(&S->s1, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
     CKC(cudaStreamCreateWithPriority(&S->s2, cudaStreamNonBlocking, prio_lo));
     CKC(cudaEventCreateWithFlags(&S->ev_user, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&S->ev_done, cudaEventDisableTiming));
     CKC(wfs_prepare());
+    CKC(recon_prepare());
+    CKC(dalloc(&S->d_err, 1));
+    CKC(cudaMemsetAsync(S->d_err, 0, sizeof(int), S->s0));
 
     // ---- wavefront sensors
     int ns = 0, nframe = 0, ld = 0;
@@ -690,12 +706,12 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         }
         CKC(dalloc(&H.d_subaps, H.subaps.size()));
         if (!H.subaps.empty())
-            CKC(cudaMemcpy(H.d_subaps, H.subaps.data(), sizeof(SubapDev) * H.subaps.size(), cudaMemcpyHostToDevice));
+            CKC(cudaMemcpyAsync(H.d_subaps, H.subaps.data(), sizeof(SubapDev) * H.subaps.size(), cudaMemcpyHostToDevice, S->s0));
         WfsDev D{};
         D.type = H.p.type;
         D.n_sub = H.p.n_sub; D.n_px = npx; D.n_fft = H.p.n_fft; D.n_bin = H.p.n_bin; D.n_det = H.n_det;
         D.N = H.N;
-        D.n_valid = H.n_valid; D.slope0 = H.slope0; D.frame0 = H.frame0; D.wfs_index = w;
+        D.n_valid = H.n_valid; D.slope0 = H.slope0; D.frame0 = H.frame0; D.rcol0 = H.rcol0; D.wfs_index = w;
         D.scale = (float)(cfg->lambda_ref / H.p.lambda);
         D.n_photons = (float)H.p.n_photons;
         D.read_noise = (float)H.p.read_noise;
@@ -722,19 +738,21 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     S->n_frame_px = nframe;
     S->ld = std::max(ld, 4);
     CKC(dalloc(&S->d_amp_all, amp_all.size()));
-    CKC(cudaMemcpy(S->d_amp_all, amp_all.data(), sizeof(float) * amp_all.size(), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpyAsync(S->d_amp_all, amp_all.data(), sizeof(float) * amp_all.size(), cudaMemcpyHostToDevice, S->s0));
     for (size_t w = 0; w < wdev.size(); ++w) wdev[w].amp = S->d_amp_all + amp_off[w];
     CKC(dalloc(&S->d_wfs, wdev.size()));
-    CKC(cudaMemcpy(S->d_wfs, wdev.data(), sizeof(WfsDev) * wdev.size(), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpyAsync(S->d_wfs, wdev.data(), sizeof(WfsDev) * wdev.size(), cudaMemcpyHostToDevice, S->s0));
     CKC(dalloc(&S->d_slopes, ns));
-    CKC(cudaMemset(S->d_slopes, 0, sizeof(float) * std::max(ns, 1)));
+    CKC(cudaMemsetAsync(S->d_slopes, 0, sizeof(float) * std::max(ns, 1), S->s0));
+    CKC(dalloc(&S->d_slopes_pad, S->ld));
+    CKC(cudaMemsetAsync(S->d_slopes_pad, 0, sizeof(float) * S->ld, S->s0));
     CKC(dalloc(&S->d_sref, ns));
-    CKC(cudaMemset(S->d_sref, 0, sizeof(float) * std::max(ns, 1)));
+    CKC(cudaMemsetAsync(S->d_sref, 0, sizeof(float) * std::max(ns, 1), S->s0));
     if (cfg->keep_frames) {
         CKC(dalloc(&S->d_lam, nframe));
         CKC(dalloc(&S->d_frames, nframe));
-        CKC(cudaMemset(S->d_lam, 0, sizeof(float) * std::max(nframe, 1)));
-        CKC(cudaMemset(S->d_frames, 0, sizeof(int) * std::max(nframe, 1)));
+        CKC(cudaMemsetAsync(S->d_lam, 0, sizeof(float) * std::max(nframe, 1), S->s0));
+        CKC(cudaMemsetAsync(S->d_frames, 0, sizeof(int) * std::max(nframe, 1), S->s0));
     }
 
     // ---- block-per-subaperture sensors: one launch per kernel variant
@@ -756,7 +774,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         g.n_subaps = (int)all.size();
         CKC(dalloc(&g.d_subaps, all.size()));
         if (!all.empty())
-            CKC(cudaMemcpy(g.d_subaps, all.data(), sizeof(SubapDev) * all.size(), cudaMemcpyHostToDevice));
+            CKC(cudaMemcpyAsync(g.d_subaps, all.data(), sizeof(SubapDev) * all.size(), cudaMemcpyHostToDevice, S->s0));
     }
 
     // ---- science directions
@@ -773,11 +791,11 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         C.n_tiles = (C.N / 8) * (C.N / 8);
         C.radices = factor_fft(C.M);
         CKC(dalloc(&C.d_amp, A.size()));
-        CKC(cudaMemcpy(C.d_amp, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpyAsync(C.d_amp, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice, S->s0));
         CKC(dalloc(&C.d_field, (size_t)C.N * C.N));
         CKC(dalloc(&C.d_ft, (size_t)C.M * C.N));
         CKC(dalloc(&C.d_psf_t, (size_t)C.M * C.M));
-        CKC(cudaMemset(C.d_psf_t, 0, sizeof(double) * (size_t)C.M * C.M));
+        CKC(cudaMemsetAsync(C.d_psf_t, 0, sizeof(double) * (size_t)C.M * C.M, S->s0));
         CKC(dalloc(&C.d_sr_part, C.n_tiles));
         std::vector<float2> W(C.M);
         for (int m = 0; m < C.M; ++m) {
@@ -785,7 +803,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
             W[m] = make_float2((float)std::cos(a), (float)std::sin(a));
         }
         CKC(dalloc(&C.d_w, C.M));
-        CKC(cudaMemcpy(C.d_w, W.data(), sizeof(float2) * C.M, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpyAsync(C.d_w, W.data(), sizeof(float2) * C.M, cudaMemcpyHostToDevice, S->s0));
         maxM = std::max(maxM, C.M);
         S->sci.push_back(C);
     }
@@ -800,9 +818,10 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         CKC(sci_prepare(maxM));
     }
     CKC(dalloc(&S->d_acc, std::max(cfg->n_sci, 1)));
-    CKC(cudaMemset(S->d_acc, 0, sizeof(SciAcc) * std::max(cfg->n_sci, 1)));
+    CKC(cudaMemsetAsync(S->d_acc, 0, sizeof(SciAcc) * std::max(cfg->n_sci, 1), S->s0));
     CKC(dalloc(&S->d_st, 1));
-    CKC(cudaMemset(S->d_st, 0, sizeof(StepState)));
+    CKC(cudaMemsetAsync(S->d_st, 0, sizeof(StepState), S->s0));
+    CKC(cudaStreamSynchronize(S->s0));
     *out = S;
     return MCAO_OK;
 #undef CKC
@@ -834,7 +853,7 @@ mcao_status mcao_load_atmosphere(mcao_sim* S, int n_layers, const mcao_layer* la
             if (w.p.type == MCAO_WFS_LGS && L.alt_m >= w.p.height)
                 return fail(S, MCAO_E_INVALID_ARG, "layer %d lies above a laser guide star", l);
     }
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     for (auto p : S->d_layer_owned) cudaFree(p);
     S->d_layer_owned.clear();
     S->d_layer_ptr.clear();
@@ -848,7 +867,7 @@ mcao_status mcao_load_atmosphere(mcao_sim* S, int n_layers, const mcao_layer* la
             float* d = nullptr;
             CK(dalloc(&d, (size_t)L.n * L.n));
             S->d_layer_owned.push_back(d);
-            CK(cudaMemcpy(d, L.phase, sizeof(float) * (size_t)L.n * L.n, cudaMemcpyHostToDevice));
+            CK(cudaMemcpyAsync(d, L.phase, sizeof(float) * (size_t)L.n * L.n, cudaMemcpyHostToDevice, S->s0));
             S->d_layer_ptr.push_back(d);
         }
         S->layers[l].phase = nullptr;
@@ -857,6 +876,7 @@ mcao_status mcao_load_atmosphere(mcao_sim* S, int n_layers, const mcao_layer* la
     mcao_status r = rebuild_views(S);
     if (r != MCAO_OK) return r;
     S->atm_loaded = true;
+    CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
 
@@ -870,16 +890,15 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
             !(is_fin(d.pitch_m) && d.pitch_m > 0) || !(is_fin(d.coupling) && d.coupling > 0 && d.coupling < 1) ||
             !is_fin(d.alt_m) || d.alt_m < 0)
             return fail(S, MCAO_E_INVALID_ARG, "dm %d: invalid geometry", m);
-        if (d.nx > kDmMaxAct || d.surf_n > kMaxGridN)
-            return fail(S, MCAO_E_UNSUPPORTED, "dm %d: at most %d actuators per row and %d surface samples", m,
-                        kDmMaxAct, kMaxGridN);
+        if (d.surf_n > kMaxGridN)
+            return fail(S, MCAO_E_UNSUPPORTED, "dm %d: at most %d surface samples per side", m, kMaxGridN);
         for (const auto& w : S->wfs)
             if (w.p.type == MCAO_WFS_LGS && d.alt_m >= w.p.height)
                 return fail(S, MCAO_E_INVALID_ARG, "dm %d lies above a laser guide star", m);
     }
     CK(cudaSetDevice(S->device));
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
-    dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map); dfree(S->d_dm_tmp);
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
     dfree(S->d_dm_surf); dfree(S->d_c); dfree(S->d_partial);
     S->dms_loaded = false;
     S->recon_loaded = false;  // command count may change
@@ -889,18 +908,19 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     std::vector<float> g;
     std::vector<int2> band;
     std::vector<int> map;
-    long long tmp_total = 0, surf_total = 0;
-    int ncmd = 0, pass1 = 0, tiles = 0;
+    long long surf_total = 0;
+    int ncmd = 0, tiles = 0;
     for (int m = 0; m < n_dms; ++m) {
         const mcao_dm& d = dms[m];
         DmDesc D{};
         D.nx = d.nx; D.ny = d.ny; D.surf_n = d.surf_n;
-        D.tiles_x = (d.surf_n + 31) / 32;
+        D.tiles_x = (d.surf_n + kDmTile - 1) / kDmTile;
         double sig = d.pitch_m / std::sqrt(2.0 * std::log(1.0 / d.coupling));
         const double thr = 1e-10;
-        // table [surf_n][na] and per-row band of weights >= thr
-        auto table = [&](int na, std::vector<int2>& bands) {
+        // table [surf_n][na]; per 32-sample tile, the actuator range with weight >= thr on it
+        auto table = [&](int na, long long& tband) {
             long long off = (long long)g.size();
+            std::vector<int2> rows;
             for (int i = 0; i < d.surf_n; ++i) {
                 double x = ((double)i - 0.5 * (double)(d.surf_n - 1)) * d.surf_dx;
                 int lo = na, hi = 0;
@@ -910,23 +930,25 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
                     g.push_back((float)v);
                     if (v >= thr) { lo = std::min(lo, a); hi = std::max(hi, a + 1); }
                 }
+                rows.push_back(make_int2(lo, hi));
+            }
+            tband = (long long)band.size();
+            for (int t = 0; t < D.tiles_x; ++t) {
+                int lo = na, hi = 0;
+                for (int i = t * kDmTile; i < std::min(d.surf_n, (t + 1) * kDmTile); ++i)
+                    if (rows[i].y > rows[i].x) { lo = std::min(lo, rows[i].x); hi = std::max(hi, rows[i].y); }
                 if (lo >= hi) { lo = 0; hi = 0; }
-                bands.push_back(make_int2(lo, hi));
+                band.push_back(make_int2(lo, hi));
             }
             return off;
         };
-        std::vector<int2> bands_x, bands_y;
-        D.gx_off = table(d.nx, bands_x);
-        D.gy_off = table(d.ny, bands_y);
-        D.band_off = (long long)band.size();
-        band.insert(band.end(), bands_x.begin(), bands_x.end());
-        D.tband_off = (long long)band.size();
-        for (int t = 0; t < D.tiles_x; ++t) {
-            int lo = d.ny, hi = 0;
-            for (int j = t * 32; j < std::min(d.surf_n, t * 32 + 32); ++j)
-                if (bands_y[j].y > bands_y[j].x) { lo = std::min(lo, bands_y[j].x); hi = std::max(hi, bands_y[j].y); }
-            if (lo >= hi) { lo = 0; hi = 0; }
-            band.push_back(make_int2(lo, hi));
+        D.gx_off = table(d.nx, D.tband_x);
+        D.gy_off = table(d.ny, D.tband_y);
+        for (int t = 0; t < 2 * D.tiles_x; ++t) {
+            int2 b = band[(t < D.tiles_x ? D.tband_x : D.tband_y) + t % D.tiles_x];
+            if (b.y - b.x > kDmMaxBand)
+                return fail(S, MCAO_E_UNSUPPORTED, "dm %d: more than %d actuators per axis act on a %d-sample tile",
+                            m, kDmMaxBand, kDmTile);
         }
         D.map_off = (long long)map.size();
         int cnt = 0;
@@ -935,34 +957,30 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
             else map.push_back(-1);
         }
         ncmd += cnt;
-        D.tmp_off = tmp_total;
         D.surf_off = surf_total;
-        tmp_total += (long long)d.ny * d.surf_n;
         surf_total += (long long)d.surf_n * d.surf_n;
         S->dm_tile_start[m] = tiles;
         tiles += D.tiles_x * D.tiles_x;
-        pass1 += d.ny * ((d.surf_n + 255) / 256);
         S->dm_desc.push_back(D);
     }
     for (int m = n_dms; m <= kMaxDms; ++m) S->dm_tile_start[m] = tiles;
-    S->dm_pass1_blocks = pass1;
     S->n_cmd = ncmd;
     CK(dalloc(&S->d_dm_desc, S->dm_desc.size()));
-    if (n_dms) CK(cudaMemcpy(S->d_dm_desc, S->dm_desc.data(), sizeof(DmDesc) * n_dms, cudaMemcpyHostToDevice));
+    if (n_dms) CK(cudaMemcpyAsync(S->d_dm_desc, S->dm_desc.data(), sizeof(DmDesc) * n_dms, cudaMemcpyHostToDevice, S->s0));
     CK(dalloc(&S->d_dm_g, g.size()));
-    if (!g.empty()) CK(cudaMemcpy(S->d_dm_g, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice));
+    if (!g.empty()) CK(cudaMemcpyAsync(S->d_dm_g, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice, S->s0));
     CK(dalloc(&S->d_dm_band, band.size()));
-    if (!band.empty()) CK(cudaMemcpy(S->d_dm_band, band.data(), sizeof(int2) * band.size(), cudaMemcpyHostToDevice));
+    if (!band.empty()) CK(cudaMemcpyAsync(S->d_dm_band, band.data(), sizeof(int2) * band.size(), cudaMemcpyHostToDevice, S->s0));
     CK(dalloc(&S->d_dm_map, map.size()));
-    if (!map.empty()) CK(cudaMemcpy(S->d_dm_map, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice));
-    CK(dalloc(&S->d_dm_tmp, (size_t)tmp_total));
+    if (!map.empty()) CK(cudaMemcpyAsync(S->d_dm_map, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, S->s0));
     CK(dalloc(&S->d_dm_surf, (size_t)surf_total));
-    CK(cudaMemset(S->d_dm_surf, 0, sizeof(float) * std::max<long long>(surf_total, 1)));
+    CK(cudaMemsetAsync(S->d_dm_surf, 0, sizeof(float) * std::max<long long>(surf_total, 1), S->s0));
     CK(dalloc(&S->d_c, ncmd));
-    CK(cudaMemset(S->d_c, 0, sizeof(float) * std::max(ncmd, 1)));
+    CK(cudaMemsetAsync(S->d_c, 0, sizeof(float) * std::max(ncmd, 1), S->s0));
     mcao_status r = rebuild_views(S);
     if (r != MCAO_OK) return r;
     S->dms_loaded = true;
+    CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
 
@@ -977,20 +995,25 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     if (!R && n_cmd > 0) return fail(S, MCAO_E_INVALID_ARG, "R is NULL");
     if (n_slopes < 1) return fail(S, MCAO_E_SHAPE, "no valid subapertures");
     CK(cudaSetDevice(S->device));
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     dfree(S->d_R);
     dfree(S->d_partial);
     S->recon_loaded = false;
     S->rows_pad = std::max(1, (n_cmd + kReconRowBlock - 1) / kReconRowBlock) * kReconRowBlock;
-    size_t elems = (size_t)S->rows_pad * S->ld;
-    CK(dalloc(&S->d_R, elems));
-    CK(cudaMemset(S->d_R, 0, sizeof(float) * elems));
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    // padded layout: each sensor's slope block starts on a 16-byte boundary of a row; slices
-    // run warp-per-subaperture sensors first, block-per-subaperture sensors last
+    // device inputs may come from any stream of the caller: wait for all of them
+    if (on_device) CK(cudaDeviceSynchronize());
+    // 1) row-major staging copy in the padded column layout (each sensor's slope block starts on
+    //    a 16-byte boundary of a row, rows padded with zeros)
+    float* tmp = nullptr;
+    size_t elems = (size_t)S->rows_pad * S->ld;
+    CK(dalloc(&tmp, elems));
+    cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(float) * elems, S->s0);
+    // 2) slices: warp-per-subaperture sensors first, block-per-subaperture sensors last
     S->slices.clear();
     S->slice_wfs.clear();
     int chunks = 0;
+    long long tiled = 0;
     std::vector<int> order;
     for (size_t w = 0; w < S->wfs.size(); ++w)
         if (!S->wfs[w].fft_route) order.push_back((int)w);
@@ -1000,34 +1023,45 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
         const WfsHost& W = S->wfs[w];
         const int len = 2 * W.n_valid;
         if (len == 0) continue;
-        if (n_cmd > 0)
-            CK(cudaMemcpy2D(S->d_R + W.rcol0, sizeof(float) * S->ld, R + W.slope0, sizeof(float) * n_slopes,
-                            sizeof(float) * len, n_cmd, kind));
+        if (e == cudaSuccess && n_cmd > 0)
+            e = cudaMemcpy2DAsync(tmp + W.rcol0, sizeof(float) * S->ld, R + W.slope0, sizeof(float) * n_slopes,
+                                  sizeof(float) * len, n_cmd, kind, S->s0);
         ReconLaunch L{};
-        L.R = S->d_R;
         L.n_cmd = n_cmd;
-        L.ld = S->ld;
-        L.rows_pad = S->rows_pad;
+        L.n_rq = S->rows_pad / kReconRows;
         L.col0 = W.rcol0;
-        L.s0 = W.slope0;
         L.len = len;
         int nch = (len + kReconChunk - 1) / kReconChunk;
         int kc = (len + nch - 1) / nch;
         L.kc = (kc + 3) / 4 * 4;
         nch = (len + L.kc - 1) / L.kc;
         L.chunk0 = chunks;
-        L.s = S->d_slopes;
+        L.base = tiled;
+        L.s = S->d_slopes_pad;
+        L.max_ctas = S->sm_count;  // one resident block per SM beside the sensing kernels
+        L.err = S->d_err;
         chunks += nch;
+        tiled += recon_slice_floats(L.n_rq, L.len, L.kc);
         S->slices.push_back(L);
         S->slice_wfs.push_back(w);
     }
+    // 3) stage-tiled copy used by the product (see ReconLaunch)
+    if (e == cudaSuccess) e = dalloc(&S->d_R, (size_t)std::max<long long>(tiled, 4));
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_R, 0, sizeof(float) * (size_t)std::max<long long>(tiled, 4), S->s0);
+    for (auto& L : S->slices) {
+        L.R = S->d_R;
+        if (e == cudaSuccess) e = launch_recon_tile(tmp, S->ld, L, S->s0);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
+    cudaFree(tmp);
+    CK(e);
     S->n_chunks = chunks;
     CK(dalloc(&S->d_partial, (size_t)std::max(chunks, 1) * std::max(n_cmd, 1)));
     for (auto& L : S->slices) L.partial = S->d_partial;
     if (s_ref)
-        CK(cudaMemcpy(S->d_sref, s_ref, sizeof(float) * n_slopes, kind));
+        CK(cudaMemcpyAsync(S->d_sref, s_ref, sizeof(float) * n_slopes, kind, S->s0));
     else
-        CK(cudaMemset(S->d_sref, 0, sizeof(float) * n_slopes));
+        CK(cudaMemsetAsync(S->d_sref, 0, sizeof(float) * n_slopes, S->s0));
     release_graph(S);
     S->recon_loaded = true;
     return MCAO_OK;
@@ -1139,8 +1173,9 @@ mcao_status mcao_set_commands(mcao_sim* S, const float* in, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(in[i])) return fail(S, MCAO_E_INVALID_ARG, "command %zu is not finite", i);
     CK(cudaSetDevice(S->device));
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
-    if (n) CK(cudaMemcpy(S->d_c, in, sizeof(float) * n, cudaMemcpyHostToDevice));
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    if (n) CK(cudaMemcpyAsync(S->d_c, in, sizeof(float) * n, cudaMemcpyHostToDevice, S->s0));
+    CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
 
@@ -1160,7 +1195,7 @@ mcao_status mcao_get_wfs_phase(mcao_sim* S, int wfs, float* out, size_t n) {
     const int N = S->wfs[wfs].N;
     if (n < (size_t)N * N) return fail(S, MCAO_E_SHAPE, "need %d samples", N * N);
     CK(cudaSetDevice(S->device));
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     float* d = nullptr;
     CK(dalloc(&d, (size_t)N * N));
     cudaError_t e = launch_dm_surfaces(make_dm_launch(S), S->s0);
@@ -1179,7 +1214,7 @@ mcao_status mcao_get_dm_surface(mcao_sim* S, int dm, float* out, size_t n) {
     size_t cnt = (size_t)S->dms[dm].surf_n * S->dms[dm].surf_n;
     if (n < cnt) return fail(S, MCAO_E_SHAPE, "need %zu samples", cnt);
     CK(cudaSetDevice(S->device));
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     CK(launch_dm_surfaces(make_dm_launch(S), S->s0));
     CK(cudaStreamSynchronize(S->s0));
     CK(cudaMemcpy(out, S->d_dm_surf + S->dm_desc[dm].surf_off, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
@@ -1225,9 +1260,10 @@ mcao_status mcao_get_psf(mcao_sim* S, int sci, double* out, size_t n, double* sr
 mcao_status mcao_reset_psf(mcao_sim* S) {
     if (!S) return MCAO_E_INVALID_ARG;
     CK(cudaSetDevice(S->device));
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
-    for (auto& c : S->sci) CK(cudaMemset(c.d_psf_t, 0, sizeof(double) * (size_t)c.M * c.M));
-    CK(cudaMemset(S->d_acc, 0, sizeof(SciAcc) * std::max<size_t>(S->sci.size(), 1)));
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    for (auto& c : S->sci) CK(cudaMemsetAsync(c.d_psf_t, 0, sizeof(double) * (size_t)c.M * c.M, S->s0));
+    CK(cudaMemsetAsync(S->d_acc, 0, sizeof(SciAcc) * std::max<size_t>(S->sci.size(), 1), S->s0));
+    CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
 
@@ -1273,22 +1309,23 @@ mcao_status mcao_set_state(mcao_sim* S, const void* buf, size_t n) {
         return fail(S, MCAO_E_SHAPE, "checkpoint does not match this configuration");
     p += sizeof(hdr);
     CK(cudaSetDevice(S->device));
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     StepState st;
     st.k = hdr[1];
     st.k_next = hdr[1];
-    CK(cudaMemcpy(S->d_st, &st, sizeof(st), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(S->d_c, p, sizeof(float) * S->n_cmd, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(S->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, S->s0));
+    CK(cudaMemcpyAsync(S->d_c, p, sizeof(float) * S->n_cmd, cudaMemcpyHostToDevice, S->s0));
     p += sizeof(float) * S->n_cmd;
-    CK(cudaMemcpy(S->d_slopes, p, sizeof(float) * S->n_slopes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(S->d_slopes, p, sizeof(float) * S->n_slopes, cudaMemcpyHostToDevice, S->s0));
     p += sizeof(float) * S->n_slopes;
     for (size_t q = 0; q < S->sci.size(); ++q) {
-        CK(cudaMemcpy(S->d_acc + q, p, sizeof(SciAcc), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(S->d_acc + q, p, sizeof(SciAcc), cudaMemcpyHostToDevice, S->s0));
         p += sizeof(SciAcc);
         size_t b = sizeof(double) * (size_t)S->sci[q].M * S->sci[q].M;
-        CK(cudaMemcpy(S->sci[q].d_psf_t, p, b, cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(S->sci[q].d_psf_t, p, b, cudaMemcpyHostToDevice, S->s0));
         p += b;
     }
+    CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
 
@@ -1303,7 +1340,7 @@ mcao_status mcao_set_profiling(mcao_sim* S, int on) {
 mcao_status mcao_get_profile(mcao_sim* S, double* ms, int64_t* counts, int n_stages, int64_t* launches_per_step) {
     if (!S) return MCAO_E_INVALID_ARG;
     CK(cudaSetDevice(S->device));
-    if (sync_all(S) != MCAO_OK) return MCAO_E_CUDA;
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     std::vector<double> tot(ST_COUNT, 0.0);
     std::vector<int64_t> cnt(ST_COUNT, 0);
     for (auto& rec : S->prof_records) {

@@ -34,6 +34,7 @@ struct WfsDev {
     int type;            // 0 NGS, 1 LGS
     int n_sub, n_px, n_fft, n_bin, n_det, N;  // N pupil samples across D
     int n_valid, slope0, frame0;              // frame0: first detector pixel in frame buffers
+    int rcol0;           // first column of this sensor's block in the padded slope / R layout
     int wfs_index;
     float scale;         // lambda_ref / lambda
     float n_photons, read_noise;
@@ -77,30 +78,29 @@ struct Ctx {
 // ---------------------------------------------------------------------------------------------
 // DM surfaces
 // ---------------------------------------------------------------------------------------------
-// One DM in the concatenated DM buffers.  T = C Gx^T restricted to the nonzero band of each
-// Gaussian row, then S = Gy T (the Gaussian influence function factorises in x and y).
+// One DM in the concatenated DM buffers.  S = Gy C Gx^T (the Gaussian influence function
+// factorises in x and y), evaluated per 32 x 32 surface tile over the actuators whose weight on
+// the tile is at least 1e-10.
 struct DmDesc {
     int nx, ny, surf_n, tiles_x;   // tiles_x: 32-sample tiles per side of the surface
     long long gx_off;    // Gx [surf_n][nx] in the table buffer
     long long gy_off;    // Gy [surf_n][ny]
-    long long band_off;  // band_x [surf_n] (lo, hi exclusive) in the band buffer
-    long long tband_off; // per 32-row tile: union of the Gy bands of its rows
+    long long tband_x;   // per 32-column tile: actuator columns [lo, hi) in the band buffer
+    long long tband_y;   // per 32-row tile: actuator rows [lo, hi)
     long long map_off;   // act_map [ny][nx]: command index or -1
-    long long tmp_off;   // T [ny][surf_n]
     long long surf_off;  // S [surf_n][surf_n]
 };
-constexpr int kDmMaxAct = 256;   // actuators per row of a DM
+constexpr int kDmTile = 32;
+constexpr int kDmMaxBand = 64;   // actuators per tile and axis (checked on the host)
 
 struct DmLaunch {
     int n_dm;
     const DmDesc* desc;      // [n_dm] device
     const float* g;          // Gaussian tables
-    const int2* band;        // bands
+    const int2* band;        // tile bands
     const int* act_map;      // actuator maps
     const float* c;          // commands
-    float* tmp;              // T buffers
     float* surf;             // surfaces
-    int pass1_blocks;        // sum over DMs of ny * ceil(surf_n / 256)
     int tile_start[kMaxDms + 1];    // per-DM prefix of 32 x 32 surface tiles
     StepState* st;           // begin of step: k = k_next
 };
@@ -116,6 +116,7 @@ struct WfsLaunch {
     int n_subaps;
     const float* s_ref;
     float* slopes;
+    float* slopes_pad;       // slopes again in the padded column layout of R (16-byte blocks)
     float* lam_out;          // keep_frames: [total pixels] or null
     int* frame_out;
 };
@@ -131,22 +132,35 @@ cudaError_t launch_wfs_phase(const Ctx& ctx, int wfs, int N, float* out, cudaStr
 // ---------------------------------------------------------------------------------------------
 // reconstructor
 // ---------------------------------------------------------------------------------------------
-constexpr int kReconRowBlock = 32;   // rows per block of the reconstructor product
-constexpr int kReconChunk = 4096;    // maximum slope columns per block
+constexpr int kReconRowBlock = 32;   // rows of R are padded to a multiple of this
+constexpr int kReconChunk = 4096;    // maximum slope columns per chunk
 
 // One slice of the reconstructor product: the columns of one WFS's slope block.
+// R is held stage-tiled in HBM: for each slice, column chunk kc and row quad rq, a contiguous
+// block of 4 x kc floats; inside it, stage t (seg float4 per row, seg = ceil(n4 / nst),
+// nst = ceil(n4 / 128), n4 = the chunk's float4 count) holds its 4 row segments back to back,
+// so every stage is one contiguous bulk copy of up to 8 KB.
 struct ReconLaunch {
-    const float* R;     // [rows_pad][ld]
-    int n_cmd, ld, rows_pad;
-    int col0;           // first column of the slice in R (multiple of 4)
-    int s0;             // first slope of the slice in the slope vector
+    const float* R;     // stage-tiled reconstructor
+    long long base;     // first float of this slice in R
+    int n_cmd, n_rq;    // rows, row quads (rows padded to a multiple of 4)
+    int col0;           // first column of the slice in the padded slope layout (multiple of 4)
     int len;            // columns in the slice
-    int kc;             // columns per block (multiple of 4)
+    int kc;             // columns per chunk (multiple of 4)
     int chunk0;         // first partial-sum slot of the slice
-    const float* s;     // slope vector
+    const float* s;     // slopes in the padded layout (zeros in the padding)
     float* partial;     // [n_chunks][n_cmd]
+    int max_ctas;       // persistent grid size (0: enough blocks for every item)
+    int* err;           // set to a nonzero code if a bounded wait gives up
 };
+constexpr int kReconRows = 4;        // rows per work item (row quad)
+constexpr int kReconSeg = 128;       // float4 per row and stage (at most)
+long long recon_slice_floats(int n_rq, int len, int kc);   // floats of one slice in the tiled R
+cudaError_t recon_prepare();   // kernel attributes (outside stream capture)
 cudaError_t launch_recon(const ReconLaunch& L, cudaStream_t s);
+// Re-lay the row-major, column-padded R [rows][ld] (slice columns from col0) into the tiled slice.
+cudaError_t launch_recon_tile(const float* src, int ld, const ReconLaunch& L, cudaStream_t s);
+constexpr int kErrReconTimeout = 1;
 
 struct ReduceLaunch {
     int n_cmd, n_chunks;
