@@ -281,6 +281,14 @@ mcao_status mcao_set_profiling(mcao_sim* sim, int on);
 mcao_status mcao_get_profile(mcao_sim* sim, double* ms, int64_t* counts, int n_stages,
                              int64_t* launches_per_step);
 
+/* Synchronise and return the launch timeline of the profiled steps (call before
+ * mcao_get_profile, which clears the records): for each profiled launch, in issue order, its
+ * stage, its start and end in device milliseconds relative to the start of the first launch
+ * of the same step, and the index of that step among the profiled ones.  Fills at most n
+ * entries of each non-NULL array; *n_total (if not NULL) receives the number of records. */
+mcao_status mcao_get_timeline(mcao_sim* sim, int32_t* stage, double* start_ms, double* end_ms,
+                              int32_t* step, size_t n, size_t* n_total);
+
 #ifdef __cplusplus
 }
 #endif

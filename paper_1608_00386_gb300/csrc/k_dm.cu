@@ -18,7 +18,10 @@ __global__ void __launch_bounds__(256) dm_surface_kernel(DmLaunch L) {
     __shared__ float s_Gx[kT][kB + 1];
     __shared__ float s_Gy[kT][kB + 1];
     __shared__ float s_T[kB][kT];
-    if (blockIdx.x == 0 && threadIdx.x == 0 && L.st) L.st->k = L.st->k_next;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0 && L.st) L.st->k = L.st->k_next;
+        for (int i = threadIdx.x; i < L.n_work; i += blockDim.x) L.work[i] = 0u;
+    }
     int t = blockIdx.x;
     int m = 0;
     while (m + 1 < L.n_dm && t >= L.tile_start[m + 1]) ++m;
@@ -76,21 +79,22 @@ __global__ void __launch_bounds__(256) dm_surface_kernel(DmLaunch L) {
     }
 }
 
-__global__ void begin_step_kernel(StepState* st) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) st->k = st->k_next;
+__global__ void begin_step_kernel(StepState* st, unsigned int* work, int n_work) {
+    if (threadIdx.x == 0 && st) st->k = st->k_next;
+    for (int i = threadIdx.x; i < n_work; i += blockDim.x) work[i] = 0u;
 }
 
 }  // namespace
 
 cudaError_t launch_dm_surfaces(const DmLaunch& L, cudaStream_t s) {
-    if (L.n_dm <= 0) return launch_begin_step(L.st, s);
+    if (L.n_dm <= 0) return launch_begin_step(L.st, L.work, L.n_work, s);
     dm_surface_kernel<<<(unsigned)L.tile_start[L.n_dm], 256, 0, s>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_begin_step(StepState* st, cudaStream_t s) {
-    if (!st) return cudaSuccess;
-    begin_step_kernel<<<1, 32, 0, s>>>(st);
+cudaError_t launch_begin_step(StepState* st, unsigned int* work, int n_work, cudaStream_t s) {
+    if (!st && n_work <= 0) return cudaSuccess;
+    begin_step_kernel<<<1, 32, 0, s>>>(st, work, n_work);
     return cudaGetLastError();
 }
 

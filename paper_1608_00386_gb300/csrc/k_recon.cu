@@ -9,7 +9,7 @@
 // applies the gain.  The slopes are read (L1-cached) from a copy the sensing kernels write in
 // R's padded column layout, so every 16-byte load of s is aligned.
 //
-// Streaming.  One persistent block per SM (3 warps).  Each warp owns a four-stage ring in
+// Streaming.  At most one block per SM (3 warps).  Each warp owns a four-stage ring in
 // shared memory and keeps it filled with TMA bulk copies (cp.async.bulk, completion counted on a
 // per-stage mbarrier, L2 evict-first policy).  R is held stage-tiled (see ReconLaunch), so each
 // stage -- four row segments of up to 2 KB -- is one contiguous copy of up to 8 KB (bulk copies
@@ -45,6 +45,7 @@ constexpr long long kWaitCycles = 2000000000ll;    // ~1 s at 2 GHz
 struct TmaSmem {
     float4 ring[kTmaWarps][kTmaStages][kTmaRows * kTmaSeg];
     unsigned long long bar[kTmaWarps][kTmaStages];
+    int item[kTmaWarps][kTmaStages];  // item whose first stage the slot holds; -1: no more items
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -116,25 +117,14 @@ __device__ __forceinline__ SliceGeom slice_geom(const ReconLaunch& L) {
     return g;
 }
 
-// Item cursor: item i = (row quad rq, chunk kc) with i = kc * n_rq + rq; a warp visits items
-// gwarp, gwarp + nwarps, ... in that order.
-struct ItemCursor {
-    int rq, kc;
-    __device__ __forceinline__ void start(int gwarp, int n_rq) {
-        rq = gwarp;
-        kc = 0;
-        while (rq >= n_rq) { rq -= n_rq; ++kc; }
-    }
-    __device__ __forceinline__ void advance(int nwarps, int n_rq) {
-        rq += nwarps;
-        while (rq >= n_rq) { rq -= n_rq; ++kc; }
-    }
-};
-
-// Each warp streams its items as one continuous sequence of stages.  Per stage: wait for the
-// slot's copy, pull the stage into registers, let lane 0 refill the slot with the next stage of
-// the sequence, then do the multiply-adds -- a slot is held only for its shared-memory loads,
-// which keeps four copies per warp in flight.
+// Work items i = kc * n_rq + rq (row quad rq, chunk kc) are handed out one at a time by the
+// slice's counter (zero when the step starts), so blocks that become resident late -- the
+// sensing kernels share the SMs -- take only what is left.  Lane 0 of each warp is the producer:
+// it claims items (one claim ahead, hiding the atomic's latency), records in the slot that
+// receives an item's first stage which item it is (-1 once the counter is exhausted) and issues
+// the copies.  The other lanes follow the slots in order.  Per stage: wait for the slot's copy,
+// pull the stage into registers, let lane 0 refill the slot, then do the multiply-adds -- a slot
+// is held only for its shared-memory loads, which keeps four copies per warp in flight.
 __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L) {
     extern __shared__ __align__(128) unsigned char tma_raw[];
     TmaSmem& sm = *reinterpret_cast<TmaSmem*>(tma_raw);
@@ -144,47 +134,56 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
     const uint64_t pol = evict_first_policy();
-    const int gwarp = blockIdx.x * kTmaWarps + warp, nwarps = gridDim.x * kTmaWarps;
     const int n_rq = L.n_rq;
     const SliceGeom g = slice_geom(L);
+    const int n_items = n_rq * g.n_chunks;
     const float4* R4 = reinterpret_cast<const float4*>(L.R + L.base);
     const long long blk4 = (long long)L.kc;   // float4 per item block: 4 rows x kc floats / 4
 
     // producer state (used by lane 0 only)
-    ItemCursor p;
-    p.start(gwarp, n_rq);
-    int p_t = 0;
-    const int* pg = p.kc == g.n_chunks - 1 ? g.last : g.full;
-    int p_n4 = pg[0], p_nst = pg[1], p_seg = pg[2];
-    const float4* p_src = R4 + ((long long)p.kc * n_rq + p.rq) * blk4;
-    int issued = 0;
+    int p_next = 0, p_t = 0, p_n4 = 0, p_nst = 1, p_seg = 1, issued = 0;
+    bool p_done = false;
+    const float4* p_src = R4;
+    if (lane == 0) p_next = (int)atomicAdd(L.work, 1u);
     auto issue_next = [&](int st) {
+        if (p_t == 0) {
+            const int it = p_next;
+            if (it >= n_items) {
+                sm.item[warp][st] = -1;
+                p_done = true;
+                return;
+            }
+            p_next = (int)atomicAdd(L.work, 1u);
+            const int kc = it / n_rq, rq = it - kc * n_rq;
+            const int* q = kc == g.n_chunks - 1 ? g.last : g.full;
+            p_n4 = q[0];
+            p_nst = q[1];
+            p_seg = q[2];
+            p_src = R4 + ((long long)kc * n_rq + rq) * blk4;
+            sm.item[warp][st] = it;
+        }
         const int cnt = min(p_seg, p_n4 - p_t * p_seg);
         const uint32_t bytes = (uint32_t)(kTmaRows * cnt) * 16u;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&sm.bar[warp][st], bytes);
         bulk_g2s(sm.ring[warp][st], p_src + (long long)kTmaRows * p_seg * p_t, bytes, &sm.bar[warp][st], pol);
         ++issued;
-        if (++p_t == p_nst) {
-            p_t = 0;
-            p.advance(nwarps, n_rq);
-            const int* q = p.kc == g.n_chunks - 1 ? g.last : g.full;
-            p_n4 = q[0];
-            p_nst = q[1];
-            p_seg = q[2];
-            p_src = R4 + ((long long)p.kc * n_rq + p.rq) * blk4;
-        }
+        if (++p_t == p_nst) p_t = 0;
     };
     if (lane == 0)
-        for (int st = 0; st < kTmaStages && p.kc < g.n_chunks; ++st) issue_next(st);
+        for (int st = 0; st < kTmaStages && !p_done; ++st) issue_next(st);
 
     uint32_t parity = 0;  // bit st: parity of the next completion of slot st
     int consumed = 0;
-    ItemCursor c;
-    for (c.start(gwarp, n_rq); c.kc < g.n_chunks; c.advance(nwarps, n_rq)) {
-        const int* cg = c.kc == g.n_chunks - 1 ? g.last : g.full;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = sm.item[warp][consumed % kTmaStages];
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it < 0) break;
+        const int kc = it / n_rq, rq = it - kc * n_rq;
+        const int* cg = kc == g.n_chunks - 1 ? g.last : g.full;
         const int n4 = cg[0], nst = cg[1], seg = cg[2];
-        const float4* s4 = reinterpret_cast<const float4*>(L.s + L.col0 + c.kc * L.kc);
+        const float4* s4 = reinterpret_cast<const float4*>(L.s + L.col0 + kc * L.kc);
         float acc[kTmaRows] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int t = 0; t < nst; ++t, ++consumed) {
             const int st = consumed % kTmaStages;
@@ -218,7 +217,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
                     rv[j][q] = e < cnt ? ring[q * cnt + e] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
             __syncwarp();  // every lane has read the slot before it is refilled
-            if (lane == 0 && p.kc < g.n_chunks) issue_next(st);
+            if (lane == 0 && !p_done) issue_next(st);
 #pragma unroll
             for (int j = 0; j < kTmaSeg / 32; ++j)
 #pragma unroll
@@ -230,8 +229,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
             for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
         }
         if (lane == 0) {
-            float* out = L.partial + (size_t)(L.chunk0 + c.kc) * L.n_cmd;
-            const int row0 = c.rq * kTmaRows;
+            float* out = L.partial + (size_t)(L.chunk0 + kc) * L.n_cmd;
+            const int row0 = rq * kTmaRows;
 #pragma unroll
             for (int q = 0; q < kTmaRows; ++q)
                 if (row0 + q < L.n_cmd) out[row0 + q] = acc[q];
@@ -284,6 +283,7 @@ cudaError_t recon_prepare() {
 
 cudaError_t launch_recon(const ReconLaunch& L, cudaStream_t s) {
     if (L.n_cmd <= 0 || L.len <= 0) return cudaSuccess;
+    if (!L.work) return cudaErrorInvalidValue;
     const int n_items = L.n_rq * ((L.len + L.kc - 1) / L.kc);
     const int need = (n_items + kTmaWarps - 1) / kTmaWarps;
     int ctas = (L.max_ctas > 0 && L.max_ctas < need) ? L.max_ctas : need;

@@ -118,189 +118,201 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
     }
     if (L.ctx.noise) fill_recip(s_recip, threadIdx.x, blockDim.x);
     __syncthreads();  // the only block-wide barrier
-    const int sub = blockIdx.x * 8 + warp;
-    if (sub >= L.n_subaps) return;  // warp-uniform; warp-level sync only from here on
-    const SubapDev sd = L.subaps[sub];
-    const WfsDev& w = L.ctx.wfs[sd.wfs];
-    const int i0 = sd.sx * NPX, j0 = sd.sy * NPX;
-    const int n_grids = L.ctx.n_grids;
-    const GridView* V = L.ctx.views + (long long)sd.wfs * n_grids;
-    const long long k = L.ctx.st->k;
-    AxisEnt* s_ex = s_u[warp].e[0];
-    AxisEnt* s_ey = s_u[warp].e[1];
+    // subapertures: one per warp (no counter), or taken one at a time from the counter, so that
+    // warps of blocks that become resident late take only what is left
+    auto take = [&]() {
+        unsigned int v = 0;
+        if (lane == 0) v = atomicAdd(L.work, 1u);
+        return (int)__shfl_sync(0xffffffffu, v, 0);
+    };
+    int sub = L.work ? take() : blockIdx.x * 8 + warp;
+    for (;;) {
+        if (sub >= L.n_subaps) break;  // warp-uniform; warp-level sync only from here on
+        const SubapDev sd = L.subaps[sub];
+        const WfsDev& w = L.ctx.wfs[sd.wfs];
+        const int i0 = sd.sx * NPX, j0 = sd.sy * NPX;
+        const int n_grids = L.ctx.n_grids;
+        const GridView* V = L.ctx.views + (long long)sd.wfs * n_grids;
+        const long long k = L.ctx.st->k;
+        AxisEnt* s_ex = s_u[warp].e[0];
+        AxisEnt* s_ey = s_u[warp].e[1];
 
-    tile_entries(V, n_grids, k, i0, j0, NPX, s_ex, s_ey, lane, 32);
-    if (lane < n_grids) {
-        GridMeta gm;
-        gm.data = V[lane].data;
-        gm.n = V[lane].n;
-        gm.sign = V[lane].sign;
-        s_gm[warp][lane] = gm;
-    }
-    __syncwarp();
-
-    // field E = A exp(i (scale phi - pi (x + y) / N)): lane -> column x, rows y0 and y0 + 4
-    {
-        const int x = lane & 7, y0 = lane >> 3, y1 = y0 + 4;
-        float phi0 = 0.0f, phi1 = 0.0f;
-#pragma unroll 2
-        for (int g = 0; g < n_grids; ++g) {
-            const GridMeta gm = s_gm[warp][g];
-            const AxisEnt ex = s_ex[g * NPX + x];
-            phi0 = fmaf(gm.sign, bilinear(gm.data, gm.n, ex, s_ey[g * NPX + y0]), phi0);
-            phi1 = fmaf(gm.sign, bilinear(gm.data, gm.n, ex, s_ey[g * NPX + y1]), phi1);
+        tile_entries(V, n_grids, k, i0, j0, NPX, s_ex, s_ey, lane, 32);
+        if (lane < n_grids) {
+            GridMeta gm;
+            gm.data = V[lane].data;
+            gm.n = V[lane].n;
+            gm.sign = V[lane].sign;
+            s_gm[warp][lane] = gm;
         }
-        const float scale = w.scale;
-        const float* arow = w.amp + (long long)j0 * w.N + i0 + x;
-        float a0 = __ldg(arow + (long long)y0 * w.N), a1 = __ldg(arow + (long long)y1 * w.N);
-        float sn, cs;
-        sincosf(scale * phi0 - kPi * (float)(x + y0) / (float)NFFT, &sn, &cs);
-        s_EM[warp][y0 * NPX + x] = make_float2(a0 * cs, a0 * sn);
-        sincosf(scale * phi1 - kPi * (float)(x + y1) / (float)NFFT, &sn, &cs);
-        s_EM[warp][y1 * NPX + x] = make_float2(a1 * cs, a1 * sn);
-    }
-    __syncwarp();
+        __syncwarp();
 
-    // ACF(ux, uy) = sum_a M_uy[a][a + ux], M_uy[a][b] = sum_r E[r][a] conj(E[r + uy][b]);
-    // lane holds columns a, b0, b1 of E
-    {
-        const int ca_i = lane >> 2, cb_i = lane & 3;
-        float2 ca[NPX], cb0[NPX], cb1[NPX];
-#pragma unroll
-        for (int r = 0; r < NPX; ++r) {
-            ca[r] = s_EM[warp][r * NPX + ca_i];
-            cb0[r] = s_EM[warp][r * NPX + cb_i];
-            cb1[r] = s_EM[warp][r * NPX + cb_i + 4];
-        }
-        __syncwarp();  // every lane holds its columns: the buffer now receives M_uy
-        float2 hx = make_float2(0.0f, 0.0f);
-        if (lane < NL) hx = w.h[lane];  // h(ux), ux = lane - 7
-        const int ux = lane - (NPX - 1);
-#pragma unroll
-        for (int uy = 0; uy < NPX; ++uy) {
-            float m0r = 0.0f, m0i = 0.0f, m1r = 0.0f, m1i = 0.0f;
-#pragma unroll
-            for (int r = 0; r + uy < NPX; ++r) {
-                float2 a = ca[r], b0 = cb0[r + uy], b1 = cb1[r + uy];
-                m0r = fmaf(a.x, b0.x, fmaf(a.y, b0.y, m0r));
-                m0i = fmaf(a.y, b0.x, fmaf(-a.x, b0.y, m0i));
-                m1r = fmaf(a.x, b1.x, fmaf(a.y, b1.y, m1r));
-                m1i = fmaf(a.y, b1.x, fmaf(-a.x, b1.y, m1i));
+        // field E = A exp(i (scale phi - pi (x + y) / N)): lane -> column x, rows y0 and y0 + 4
+        {
+            const int x = lane & 7, y0 = lane >> 3, y1 = y0 + 4;
+            float phi0 = 0.0f, phi1 = 0.0f;
+    #pragma unroll 2
+            for (int g = 0; g < n_grids; ++g) {
+                const GridMeta gm = s_gm[warp][g];
+                const AxisEnt ex = s_ex[g * NPX + x];
+                phi0 = fmaf(gm.sign, bilinear(gm.data, gm.n, ex, s_ey[g * NPX + y0]), phi0);
+                phi1 = fmaf(gm.sign, bilinear(gm.data, gm.n, ex, s_ey[g * NPX + y1]), phi1);
             }
-            s_EM[warp][ca_i * NPX + cb_i] = make_float2(m0r, m0i);
-            s_EM[warp][ca_i * NPX + cb_i + 4] = make_float2(m1r, m1i);
-            __syncwarp();
-            if (lane < NL) {
-                float ar = 0.0f, ai = 0.0f;
-#pragma unroll
-                for (int a = 0; a < NPX; ++a) {
-                    int b = a + ux;
-                    if (b >= 0 && b < NPX) {
-                        float2 m = s_EM[warp][a * NPX + b];
-                        ar += m.x;
-                        ai += m.y;
+            const float scale = w.scale;
+            const float* arow = w.amp + (long long)j0 * w.N + i0 + x;
+            float a0 = __ldg(arow + (long long)y0 * w.N), a1 = __ldg(arow + (long long)y1 * w.N);
+            float sn, cs;
+            sincosf(scale * phi0 - kPi * (float)(x + y0) / (float)NFFT, &sn, &cs);
+            s_EM[warp][y0 * NPX + x] = make_float2(a0 * cs, a0 * sn);
+            sincosf(scale * phi1 - kPi * (float)(x + y1) / (float)NFFT, &sn, &cs);
+            s_EM[warp][y1 * NPX + x] = make_float2(a1 * cs, a1 * sn);
+        }
+        __syncwarp();
+
+        // ACF(ux, uy) = sum_a M_uy[a][a + ux], M_uy[a][b] = sum_r E[r][a] conj(E[r + uy][b]);
+        // lane holds columns a, b0, b1 of E
+        {
+            const int ca_i = lane >> 2, cb_i = lane & 3;
+            float2 ca[NPX], cb0[NPX], cb1[NPX];
+    #pragma unroll
+            for (int r = 0; r < NPX; ++r) {
+                ca[r] = s_EM[warp][r * NPX + ca_i];
+                cb0[r] = s_EM[warp][r * NPX + cb_i];
+                cb1[r] = s_EM[warp][r * NPX + cb_i + 4];
+            }
+            __syncwarp();  // every lane holds its columns: the buffer now receives M_uy
+            float2 hx = make_float2(0.0f, 0.0f);
+            if (lane < NL) hx = w.h[lane];  // h(ux), ux = lane - 7
+            const int ux = lane - (NPX - 1);
+    #pragma unroll
+            for (int uy = 0; uy < NPX; ++uy) {
+                float m0r = 0.0f, m0i = 0.0f, m1r = 0.0f, m1i = 0.0f;
+    #pragma unroll
+                for (int r = 0; r + uy < NPX; ++r) {
+                    float2 a = ca[r], b0 = cb0[r + uy], b1 = cb1[r + uy];
+                    m0r = fmaf(a.x, b0.x, fmaf(a.y, b0.y, m0r));
+                    m0i = fmaf(a.y, b0.x, fmaf(-a.x, b0.y, m0i));
+                    m1r = fmaf(a.x, b1.x, fmaf(a.y, b1.y, m1r));
+                    m1i = fmaf(a.y, b1.x, fmaf(-a.x, b1.y, m1i));
+                }
+                s_EM[warp][ca_i * NPX + cb_i] = make_float2(m0r, m0i);
+                s_EM[warp][ca_i * NPX + cb_i + 4] = make_float2(m1r, m1i);
+                __syncwarp();
+                if (lane < NL) {
+                    float ar = 0.0f, ai = 0.0f;
+    #pragma unroll
+                    for (int a = 0; a < NPX; ++a) {
+                        int b = a + ux;
+                        if (b >= 0 && b < NPX) {
+                            float2 m = s_EM[warp][a * NPX + b];
+                            ar += m.x;
+                            ai += m.y;
+                        }
                     }
+                    float otf = 1.0f;
+                    if (sd.elong_a > 0.0f) {
+                        float d = (float)ux * sd.dir_x + (float)uy * sd.dir_y;
+                        otf = expf(-sd.elong_a * d * d);
+                    }
+                    float2 hh = cmul(hx, w.h[uy + NPX - 1]);
+                    s_P[warp][uy * NL + lane] = cmul(make_float2(ar * otf, ai * otf), hh);
                 }
-                float otf = 1.0f;
-                if (sd.elong_a > 0.0f) {
-                    float d = (float)ux * sd.dir_x + (float)uy * sd.dir_y;
-                    otf = expf(-sd.elong_a * d * d);
-                }
-                float2 hh = cmul(hx, w.h[uy + NPX - 1]);
-                s_P[warp][uy * NL + lane] = cmul(make_float2(ar * otf, ai * otf), hh);
+                __syncwarp();
             }
-            __syncwarp();
         }
-    }
 
-    // rows: Y[uy][q + 4 j] = sum_ux P[uy][ux] w^{ux q} (w^4)^{ux j}, w = e^{2 pi i / ND};
-    // lane -> (uy, q), fold ux mod ND/4, then an ND/4-point inverse DFT
-    {
-        const int uy = lane >> 2, q = lane & 3;
-        float2 S[QY];
-#pragma unroll
-        for (int r = 0; r < QY; ++r) S[r] = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int c = 0; c < NL; ++c) {
-            const int ux = c - (NPX - 1);
-            const float2 p = s_P[warp][uy * NL + c];
-            const float2 t = s_tw[((ux + 2 * ND) * q) % ND];
-            const int r = (ux + 2 * ND) % QY;
-            S[r] = cadd(S[r], cmul(p, t));
+        // rows: Y[uy][q + 4 j] = sum_ux P[uy][ux] w^{ux q} (w^4)^{ux j}, w = e^{2 pi i / ND};
+        // lane -> (uy, q), fold ux mod ND/4, then an ND/4-point inverse DFT
+        {
+            const int uy = lane >> 2, q = lane & 3;
+            float2 S[QY];
+    #pragma unroll
+            for (int r = 0; r < QY; ++r) S[r] = make_float2(0.0f, 0.0f);
+    #pragma unroll
+            for (int c = 0; c < NL; ++c) {
+                const int ux = c - (NPX - 1);
+                const float2 p = s_P[warp][uy * NL + c];
+                const float2 t = s_tw[((ux + 2 * ND) * q) % ND];
+                const int r = (ux + 2 * ND) % QY;
+                S[r] = cadd(S[r], cmul(p, t));
+            }
+            idft_small<QY>(S);
+    #pragma unroll
+            for (int j = 0; j < QY; ++j) s_u[warp].y[uy * ND + q + 4 * j] = S[j];
         }
-        idft_small<QY>(S);
-#pragma unroll
-        for (int j = 0; j < QY; ++j) s_u[warp].y[uy * ND + q + 4 * j] = S[j];
-    }
-    __syncwarp();
+        __syncwarp();
 
-    // columns: B[h + LPC j][mx] = Re sum_uy z[uy] w^{uy h} (w^LPC)^{uy j}, z = Y[0], 2 Y[uy > 0];
-    // lane -> (mx, h); fold uy mod QB, then a QB-point inverse DFT (real part).  Output j of
-    // lane l is detector pixel o = l + 32 j.
-    float B[PIX_PER_LANE];
-    float bsum = 0.0f;
-    {
-        const int mx = lane & (ND - 1), h = lane / ND;
-        static_assert(PIX_PER_LANE == QB, "pixel mapping");
-        float2 Z[QB];
-#pragma unroll
-        for (int r = 0; r < QB; ++r) Z[r] = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int uy = 0; uy < NPX; ++uy) {
-            float2 y = s_u[warp].y[uy * ND + mx];
-            if (uy > 0) y = make_float2(2.0f * y.x, 2.0f * y.y);
-            const float2 t = s_tw[(uy * h) % ND];
-            Z[uy % QB] = cadd(Z[uy % QB], cmul(y, t));
+        // columns: B[h + LPC j][mx] = Re sum_uy z[uy] w^{uy h} (w^LPC)^{uy j}, z = Y[0], 2 Y[uy > 0];
+        // lane -> (mx, h); fold uy mod QB, then a QB-point inverse DFT (real part).  Output j of
+        // lane l is detector pixel o = l + 32 j.
+        float B[PIX_PER_LANE];
+        float bsum = 0.0f;
+        {
+            const int mx = lane & (ND - 1), h = lane / ND;
+            static_assert(PIX_PER_LANE == QB, "pixel mapping");
+            float2 Z[QB];
+    #pragma unroll
+            for (int r = 0; r < QB; ++r) Z[r] = make_float2(0.0f, 0.0f);
+    #pragma unroll
+            for (int uy = 0; uy < NPX; ++uy) {
+                float2 y = s_u[warp].y[uy * ND + mx];
+                if (uy > 0) y = make_float2(2.0f * y.x, 2.0f * y.y);
+                const float2 t = s_tw[(uy * h) % ND];
+                Z[uy % QB] = cadd(Z[uy % QB], cmul(y, t));
+            }
+            idft_small<QB>(Z);
+    #pragma unroll
+            for (int j = 0; j < QB; ++j) {
+                B[j] = Z[j].x;
+                bsum += Z[j].x;
+            }
         }
-        idft_small<QB>(Z);
-#pragma unroll
-        for (int j = 0; j < QB; ++j) {
-            B[j] = Z[j].x;
-            bsum += Z[j].x;
-        }
-    }
-    bsum = warp_sum(bsum);
-    const float norm = (bsum > 0.0f) ? w.n_photons * sd.frac / bsum : 0.0f;
+        bsum = warp_sum(bsum);
+        const float norm = (bsum > 0.0f) ? w.n_photons * sd.frac / bsum : 0.0f;
 
-    // detector pixels o = lane + 32 j = my ND + mx: expected photo-electrons, optional noise,
-    // centre of gravity
-    const float c0 = 0.5f * (float)(ND - 1);
-    float sv = 0.0f, sx = 0.0f, sy = 0.0f;
-    const long long pix0 = (long long)sd.rank * ND * ND;
-#pragma unroll
-    for (int j = 0; j < PIX_PER_LANE; ++j) {
-        int o = lane + 32 * j;
-        float lam = B[j] * norm;
-        float v = lam;
-        if (L.ctx.noise) {
-            int n = noise_sample(lam, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
-                                 L.ctx.seed, s_recip);
-            v = (float)n;
-            if (L.frame_out) L.frame_out[w.frame0 + pix0 + o] = n;
+        // detector pixels o = lane + 32 j = my ND + mx: expected photo-electrons, optional noise,
+        // centre of gravity
+        const float c0 = 0.5f * (float)(ND - 1);
+        float sv = 0.0f, sx = 0.0f, sy = 0.0f;
+        const long long pix0 = (long long)sd.rank * ND * ND;
+    #pragma unroll
+        for (int j = 0; j < PIX_PER_LANE; ++j) {
+            int o = lane + 32 * j;
+            float lam = B[j] * norm;
+            float v = lam;
+            if (L.ctx.noise) {
+                int n = noise_sample(lam, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
+                                     L.ctx.seed, s_recip);
+                v = (float)n;
+                if (L.frame_out) L.frame_out[w.frame0 + pix0 + o] = n;
+            }
+            if (L.lam_out) L.lam_out[w.frame0 + pix0 + o] = lam;
+            int my = o / ND, mx = o % ND;
+            sv += v;
+            sx = fmaf((float)mx - c0, v, sx);
+            sy = fmaf((float)my - c0, v, sy);
         }
-        if (L.lam_out) L.lam_out[w.frame0 + pix0 + o] = lam;
-        int my = o / ND, mx = o % ND;
-        sv += v;
-        sx = fmaf((float)mx - c0, v, sx);
-        sy = fmaf((float)my - c0, v, sy);
-    }
-    sv = warp_sum(sv);
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    if (lane == 0) {
-        float gx = 0.0f, gy = 0.0f;
-        if (sv > 0.0f) {
-            gx = sx / sv;
-            gy = sy / sv;
+        sv = warp_sum(sv);
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) {
+            float gx = 0.0f, gy = 0.0f;
+            if (sv > 0.0f) {
+                gx = sx / sv;
+                gy = sy / sv;
+            }
+            int ix = w.slope0 + sd.rank, iy = w.slope0 + w.n_valid + sd.rank;
+            const float vx = gx - (L.s_ref ? L.s_ref[ix] : 0.0f), vy = gy - (L.s_ref ? L.s_ref[iy] : 0.0f);
+            L.slopes[ix] = vx;
+            L.slopes[iy] = vy;
+            if (L.slopes_pad) {
+                L.slopes_pad[w.rcol0 + sd.rank] = vx;
+                L.slopes_pad[w.rcol0 + w.n_valid + sd.rank] = vy;
+            }
         }
-        int ix = w.slope0 + sd.rank, iy = w.slope0 + w.n_valid + sd.rank;
-        const float vx = gx - (L.s_ref ? L.s_ref[ix] : 0.0f), vy = gy - (L.s_ref ? L.s_ref[iy] : 0.0f);
-        L.slopes[ix] = vx;
-        L.slopes[iy] = vy;
-        if (L.slopes_pad) {
-            L.slopes_pad[w.rcol0 + sd.rank] = vx;
-            L.slopes_pad[w.rcol0 + w.n_valid + sd.rank] = vy;
-        }
+        if (!L.work) break;
+        sub = take();
+        __syncwarp();  // the scratch of this subaperture is read before the next one writes it
     }
 }
 
@@ -463,6 +475,7 @@ __global__ void __launch_bounds__(256) wfs_phase_kernel(Ctx ctx, int wi, int N, 
 template <int NFFT, int NBIN>
 cudaError_t launch_acf(const WfsLaunch& L, cudaStream_t s) {
     unsigned blocks = (unsigned)((L.n_subaps + 7) / 8);
+    if (L.work && L.max_blocks > 0 && blocks > (unsigned)L.max_blocks) blocks = (unsigned)L.max_blocks;
     if (blocks) wfs_acf_kernel<NFFT, NBIN><<<blocks, 256, 0, s>>>(L);
     return cudaGetLastError();
 }

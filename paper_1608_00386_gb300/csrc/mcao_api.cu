@@ -127,13 +127,14 @@ struct mcao_sim {
     float* d_c = nullptr;
     float* d_partial = nullptr;
     std::vector<ReconLaunch> slices;      // one per sensor with slopes
-    std::vector<int> slice_wfs;
+    std::vector<std::vector<int>> slice_wfs;  // sensors whose slopes each slice reads
     int n_chunks = 0;
     bool recon_loaded = false;
 
     StepState* d_st = nullptr;
     SciAcc* d_acc = nullptr;
     int* d_err = nullptr;                 // device-side error code (bounded waits)
+    unsigned int* d_work = nullptr;       // work counters: [n_wfs] sensing launches, [n_wfs + 1] slices
 
     // graph
     cudaGraph_t graph = nullptr;
@@ -144,6 +145,7 @@ struct mcao_sim {
     std::vector<cudaEvent_t> prof_pool;
     size_t prof_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_records;
+    std::vector<size_t> prof_step_begin;  // index of each profiled step's first record
     int launches_per_step = 0;
 };
 
@@ -246,6 +248,8 @@ DmLaunch make_dm_launch(mcao_sim* S) {
     L.surf = S->d_dm_surf;
     for (int m = 0; m <= kMaxDms; ++m) L.tile_start[m] = S->dm_tile_start[m];
     L.st = S->d_st;
+    L.work = S->d_work;
+    L.n_work = (int)(S->wfs.size() + S->slices.size());
     return L;
 }
 
@@ -273,8 +277,10 @@ SciLaunch make_sci_launch(mcao_sim* S, int q) {
     return L;
 }
 
-WfsLaunch make_wfs_launch(mcao_sim* S, const SubapDev* subaps, int n) {
+WfsLaunch make_wfs_launch(mcao_sim* S, const SubapDev* subaps, int n, unsigned int* work = nullptr) {
     WfsLaunch L{};
+    L.work = work;
+    L.max_blocks = 4 * S->sm_count;  // blocks of the warp-per-subaperture kernel resident per SM
     L.ctx = make_ctx(S);
     L.subaps = subaps;
     L.n_subaps = n;
@@ -409,8 +415,8 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         const WfsHost& W = S->wfs[w];
         if (W.fft_route || W.n_valid == 0) continue;
         slot = prof_begin(S, ST_WFS_MAIN, S->s0);
-        if ((e = launch_wfs(make_wfs_launch(S, W.d_subaps, W.n_valid), W.p.n_px, W.p.n_fft, W.p.n_bin, S->s0)) !=
-            cudaSuccess)
+        if ((e = launch_wfs(make_wfs_launch(S, W.d_subaps, W.n_valid, S->d_work + w), W.p.n_px, W.p.n_fft,
+                            W.p.n_bin, S->s0)) != cudaSuccess)
             return e;
         prof_end(S, slot, S->s0);
         ++nl;
@@ -421,8 +427,12 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
 
     // reconstructor slices on s3, each after its sensor, then the reduction
     for (size_t i = 0; i < S->slices.size(); ++i) {
-        cudaEvent_t ev = ready[S->slice_wfs[i]];
-        if (ev && (e = cudaStreamWaitEvent(S->s3, ev, 0)) != cudaSuccess) return e;
+        cudaEvent_t last = nullptr;
+        for (int w : S->slice_wfs[i]) {
+            cudaEvent_t ev = ready[w];
+            if (ev && ev != last && (e = cudaStreamWaitEvent(S->s3, ev, 0)) != cudaSuccess) return e;
+            last = ev;
+        }
         slot = prof_begin(S, ST_RECON, S->s3);
         if ((e = launch_recon(S->slices[i], S->s3)) != cudaSuccess) return e;
         prof_end(S, slot, S->s3);
@@ -526,7 +536,7 @@ void destroy_all(mcao_sim* S) {
     S->d_layer_owned.clear();
     dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
     dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_c); dfree(S->d_partial);
-    dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err);
+    dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err); dfree(S->d_work);
     for (auto e : S->prof_pool) cudaEventDestroy(e);
     for (auto e : S->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : {S->ev_user, S->ev_done})
@@ -646,6 +656,8 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     CKC(recon_prepare());
     CKC(dalloc(&S->d_err, 1));
     CKC(cudaMemsetAsync(S->d_err, 0, sizeof(int), S->s0));
+    CKC(dalloc(&S->d_work, (size_t)(2 * cfg->n_wfs + 1)));
+    CKC(cudaMemsetAsync(S->d_work, 0, sizeof(unsigned int) * (2 * cfg->n_wfs + 1), S->s0));
 
     // ---- wavefront sensors
     int ns = 0, nframe = 0, ld = 0;
@@ -1009,27 +1021,49 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     size_t elems = (size_t)S->rows_pad * S->ld;
     CK(dalloc(&tmp, elems));
     cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(float) * elems, S->s0);
-    // 2) slices: warp-per-subaperture sensors first, block-per-subaperture sensors last
+    // 2) slices.  Block-per-subaperture sensors first (their kernel runs beside the first
+    //    warp-per-subaperture sensor, so their slice can run before that sensor is done), and
+    //    runs of them adjacent in the padded layout merged into one slice; then one slice per
+    //    warp-per-subaperture sensor, in sensor order.
     S->slices.clear();
     S->slice_wfs.clear();
     int chunks = 0;
     long long tiled = 0;
-    std::vector<int> order;
-    for (size_t w = 0; w < S->wfs.size(); ++w)
-        if (!S->wfs[w].fft_route) order.push_back((int)w);
-    for (size_t w = 0; w < S->wfs.size(); ++w)
-        if (S->wfs[w].fft_route) order.push_back((int)w);
-    for (int w : order) {
+    for (size_t w = 0; w < S->wfs.size(); ++w) {
         const WfsHost& W = S->wfs[w];
         const int len = 2 * W.n_valid;
-        if (len == 0) continue;
-        if (e == cudaSuccess && n_cmd > 0)
+        if (len > 0 && e == cudaSuccess && n_cmd > 0)
             e = cudaMemcpy2DAsync(tmp + W.rcol0, sizeof(float) * S->ld, R + W.slope0, sizeof(float) * n_slopes,
                                   sizeof(float) * len, n_cmd, kind, S->s0);
+    }
+    std::vector<std::vector<int>> units;
+    for (const auto& g : S->fft_groups) {
+        std::vector<int> ws;
+        for (int w : g.wfs)
+            if (S->wfs[w].n_valid > 0) ws.push_back(w);
+        std::sort(ws.begin(), ws.end(), [&](int a, int b) { return S->wfs[a].rcol0 < S->wfs[b].rcol0; });
+        for (int w : ws) {
+            if (!units.empty()) {
+                const WfsHost& P = S->wfs[units.back().back()];
+                const bool same_group = std::find(g.wfs.begin(), g.wfs.end(), units.back().back()) != g.wfs.end();
+                if (same_group && S->wfs[w].rcol0 == P.rcol0 + (2 * P.n_valid + 3) / 4 * 4) {
+                    units.back().push_back(w);
+                    continue;
+                }
+            }
+            units.push_back({w});
+        }
+    }
+    for (size_t w = 0; w < S->wfs.size(); ++w)
+        if (!S->wfs[w].fft_route && S->wfs[w].n_valid > 0) units.push_back({(int)w});
+    for (const auto& u : units) {
+        const WfsHost& F = S->wfs[u.front()];
+        const WfsHost& B = S->wfs[u.back()];
+        const int len = B.rcol0 + 2 * B.n_valid - F.rcol0;
         ReconLaunch L{};
         L.n_cmd = n_cmd;
         L.n_rq = S->rows_pad / kReconRows;
-        L.col0 = W.rcol0;
+        L.col0 = F.rcol0;
         L.len = len;
         int nch = (len + kReconChunk - 1) / kReconChunk;
         int kc = (len + nch - 1) / nch;
@@ -1039,11 +1073,12 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
         L.base = tiled;
         L.s = S->d_slopes_pad;
         L.max_ctas = S->sm_count;  // one resident block per SM beside the sensing kernels
+        L.work = S->d_work + S->wfs.size() + S->slices.size();
         L.err = S->d_err;
         chunks += nch;
         tiled += recon_slice_floats(L.n_rq, L.len, L.kc);
         S->slices.push_back(L);
-        S->slice_wfs.push_back(w);
+        S->slice_wfs.push_back(u);
     }
     // 3) stage-tiled copy used by the product (see ReconLaunch)
     if (e == cudaSuccess) e = dalloc(&S->d_R, (size_t)std::max<long long>(tiled, 4));
@@ -1082,6 +1117,7 @@ mcao_status mcao_step(mcao_sim* S, int n_steps) {
     if (r != MCAO_OK) return r;
     for (int i = 0; i < n_steps; ++i) {
         if (S->profiling) {
+            S->prof_step_begin.push_back(S->prof_records.size());
             for (const auto& p : S->prof_slots) {
                 if (!p.na || !p.nb) continue;
                 if (S->prof_used + 2 > S->prof_pool.size()) {
@@ -1334,6 +1370,7 @@ mcao_status mcao_set_profiling(mcao_sim* S, int on) {
     S->profiling = on != 0;
     S->prof_used = 0;
     S->prof_records.clear();
+    S->prof_step_begin.clear();
     return MCAO_OK;
 }
 
@@ -1356,6 +1393,33 @@ mcao_status mcao_get_profile(mcao_sim* S, double* ms, int64_t* counts, int n_sta
     if (launches_per_step) *launches_per_step = S->launches_per_step;
     S->prof_used = 0;
     S->prof_records.clear();
+    S->prof_step_begin.clear();
+    return MCAO_OK;
+}
+
+mcao_status mcao_get_timeline(mcao_sim* S, int32_t* stage, double* start_ms, double* end_ms, int32_t* step,
+                              size_t n, size_t* n_total) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    CK(cudaSetDevice(S->device));
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    if (n_total) *n_total = S->prof_records.size();
+    size_t out = 0;
+    for (size_t q = 0; q < S->prof_step_begin.size(); ++q) {
+        const size_t b = S->prof_step_begin[q];
+        const size_t e = q + 1 < S->prof_step_begin.size() ? S->prof_step_begin[q + 1] : S->prof_records.size();
+        if (b >= e) continue;
+        cudaEvent_t origin = S->prof_records[b].second.first;
+        for (size_t r = b; r < e && out < n; ++r, ++out) {
+            const auto& rec = S->prof_records[r];
+            float t0 = 0.0f, t1 = 0.0f;
+            CK(cudaEventElapsedTime(&t0, origin, rec.second.first));
+            CK(cudaEventElapsedTime(&t1, origin, rec.second.second));
+            if (stage) stage[out] = rec.first;
+            if (start_ms) start_ms[out] = t0;
+            if (end_ms) end_ms[out] = t1;
+            if (step) step[out] = (int32_t)q;
+        }
+    }
     return MCAO_OK;
 }
 

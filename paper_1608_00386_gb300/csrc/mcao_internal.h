@@ -103,9 +103,11 @@ struct DmLaunch {
     float* surf;             // surfaces
     int tile_start[kMaxDms + 1];    // per-DM prefix of 32 x 32 surface tiles
     StepState* st;           // begin of step: k = k_next
+    unsigned int* work;      // begin of step: the sensing kernels' work counters are zeroed
+    int n_work;
 };
 cudaError_t launch_dm_surfaces(const DmLaunch& L, cudaStream_t s);
-cudaError_t launch_begin_step(StepState* st, cudaStream_t s);
+cudaError_t launch_begin_step(StepState* st, unsigned int* work, int n_work, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------
 // wavefront sensors
@@ -119,6 +121,11 @@ struct WfsLaunch {
     float* slopes_pad;       // slopes again in the padded column layout of R (16-byte blocks)
     float* lam_out;          // keep_frames: [total pixels] or null
     int* frame_out;
+    // warp-per-subaperture route: with a work counter (zero at launch) the grid is capped at
+    // max_blocks and warps take subapertures from the counter, so the launch adapts to the SM
+    // slots that the concurrent reconstructor stream leaves; without one, one warp per subaperture
+    unsigned int* work;
+    int max_blocks;
 };
 
 bool wfs_variant_supported(int n_px, int n_fft, int n_bin, bool elongated);
@@ -150,7 +157,8 @@ struct ReconLaunch {
     int chunk0;         // first partial-sum slot of the slice
     const float* s;     // slopes in the padded layout (zeros in the padding)
     float* partial;     // [n_chunks][n_cmd]
-    int max_ctas;       // persistent grid size (0: enough blocks for every item)
+    int max_ctas;       // grid size cap (0: enough blocks for every item)
+    unsigned int* work; // item counter, zero when the launch starts
     int* err;           // set to a nonzero code if a bounded wait gives up
 };
 constexpr int kReconRows = 4;        // rows per work item (row quad)

@@ -28,7 +28,7 @@ EXPORTS = [
     "mcao_query", "mcao_get_step_index", "mcao_get_slopes", "mcao_get_commands", "mcao_set_commands",
     "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
-    "mcao_reconstruct_noalloc",
+    "mcao_reconstruct_noalloc", "mcao_get_timeline",
 ]
 
 
@@ -106,6 +106,7 @@ def lib():
         "mcao_set_profiling": [vp, C.c_int],
         "mcao_get_profile": [vp, vp, vp, C.c_int, C.POINTER(C.c_int64)],
         "mcao_reconstruct_noalloc": [vp, C.c_int, C.c_int, C.c_int, vp, vp, C.c_float, vp, C.c_char_p, C.c_size_t],
+        "mcao_get_timeline": [vp, vp, vp, vp, vp, C.c_size_t, C.POINTER(C.c_size_t)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -306,6 +307,20 @@ class Sim:
         lps = C.c_int64()
         self._ck(lib().mcao_get_profile(self.h, ms, cnt, len(STAGES), C.byref(lps)))
         return ({s: ms[i] for i, s in enumerate(STAGES)}, {s: cnt[i] for i, s in enumerate(STAGES)}, lps.value)
+
+    def get_timeline(self):
+        """Launch timeline of the profiled steps (read before get_profile, which clears it):
+        a list of (step, stage name, start ms, end ms), times relative to each step's first
+        launch."""
+        tot = C.c_size_t()
+        self._ck(lib().mcao_get_timeline(self.h, None, None, None, None, 0, C.byref(tot)))
+        n = tot.value
+        stg = (C.c_int32 * max(n, 1))()
+        t0 = (C.c_double * max(n, 1))()
+        t1 = (C.c_double * max(n, 1))()
+        stp = (C.c_int32 * max(n, 1))()
+        self._ck(lib().mcao_get_timeline(self.h, stg, t0, t1, stp, n, C.byref(tot)))
+        return [(stp[i], STAGES[stg[i]], t0[i], t1[i]) for i in range(n)]
 
 
 def reconstruct_noalloc(R, s, c, gain: float, stream=None) -> None:
