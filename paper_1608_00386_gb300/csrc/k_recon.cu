@@ -26,11 +26,23 @@ namespace {
 
 constexpr int kKC = kReconChunk;
 
-__device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
-    acc = fmaf(a.x, b.x, acc);
-    acc = fmaf(a.y, b.y, acc);
-    acc = fmaf(a.z, b.z, acc);
-    return fmaf(a.w, b.w, acc);
+// packed FP32 multiply-add (two lanes of a 64-bit register pair per instruction):
+// (c.x, c.y) + (a.x b.x, a.y b.y), each rounded once
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\tmov.b64 ra, {%1, %2};\n\tmov.b64 rb, {%3, %4};\n\t"
+        "mov.b64 rc, {%5, %6};\n\tfma.rn.f32x2 %0, ra, rb, rc;\n\t}"
+        : "=l"(d)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
+
+// even and odd products of a float4 pair accumulated in the two halves of acc
+__device__ __forceinline__ float2 dot4x2(float4 a, float4 b, float2 acc) {
+    acc = ffma2(make_float2(a.x, a.y), make_float2(b.x, b.y), acc);
+    return ffma2(make_float2(a.z, a.w), make_float2(b.z, b.w), acc);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -184,7 +196,9 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
         const int* cg = kc == g.n_chunks - 1 ? g.last : g.full;
         const int n4 = cg[0], nst = cg[1], seg = cg[2];
         const float4* s4 = reinterpret_cast<const float4*>(L.s + L.col0 + kc * L.kc);
-        float acc[kTmaRows] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float2 acc2[kTmaRows];
+#pragma unroll
+        for (int q = 0; q < kTmaRows; ++q) acc2[q] = make_float2(0.0f, 0.0f);
         for (int t = 0; t < nst; ++t, ++consumed) {
             const int st = consumed % kTmaStages;
             const int e0 = t * seg, cnt = min(seg, n4 - e0);
@@ -221,8 +235,11 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
 #pragma unroll
             for (int j = 0; j < kTmaSeg / 32; ++j)
 #pragma unroll
-                for (int q = 0; q < kTmaRows; ++q) acc[q] = dot4(rv[j][q], sv[j], acc[q]);
+                for (int q = 0; q < kTmaRows; ++q) acc2[q] = dot4x2(rv[j][q], sv[j], acc2[q]);
         }
+        float acc[kTmaRows];
+#pragma unroll
+        for (int q = 0; q < kTmaRows; ++q) acc[q] = acc2[q].x + acc2[q].y;
 #pragma unroll
         for (int q = 0; q < kTmaRows; ++q) {
 #pragma unroll
