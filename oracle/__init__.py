@@ -102,7 +102,9 @@ def lib():
         L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.orc_uniform_f32.argtypes = [C.c_uint32]
         L.orc_uniform_f32.restype = C.c_float
-        for nm in ("orc_exp_f32", "orc_log_f32", "orc_cos2pi_f32"):
+        L.orc_sincos2pi_f32.argtypes = [C.c_float, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+        L.orc_sincos2pi_f32.restype = None
+        for nm in ("orc_exp_f32", "orc_log_f32"):
             getattr(L, nm).argtypes = [C.c_float]
             getattr(L, nm).restype = C.c_float
         L.orc_noise_sample.argtypes = [C.c_float, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64]
@@ -233,8 +235,11 @@ def log_f32(x: float) -> float:
     return lib().orc_log_f32(x)
 
 
-def cos2pi_f32(x: float) -> float:
-    return lib().orc_cos2pi_f32(x)
+def sincos2pi_f32(x: float):
+    """(cos 2 pi x, sin 2 pi x) of the sampler's float polynomials."""
+    c, s = C.c_float(), C.c_float()
+    lib().orc_sincos2pi_f32(x, C.byref(c), C.byref(s))
+    return c.value, s.value
 
 
 def noise_sample(lam: float, read_noise: float, c0: int, c1: int, c2: int, seed: int) -> int:

@@ -430,13 +430,15 @@ float orc_exp_f32(float x) {
 }
 
 /* log(u) in float for normal u > 0: u = m 2^e with m in [sqrt(1/2), sqrt(2)), then
- * log m = 2 atanh(s), s = (m - 1)/(m + 1), by its odd series to s^9. */
+ * log m = 2 atanh(s), s = (m - 1) fl(1/(m + 1)) (a correctly rounded reciprocal, then a
+ * product), by its odd series to s^9. */
 float orc_log_f32(float u) {
     uint32_t b = bits_from_f32(u);
     int e = (int)((b >> 23) & 0xffu) - 127;
     float m = f32_from_bits((b & 0x007fffffu) | 0x3f800000u);
     if (m > 1.41421356f) { m = m * 0.5f; e += 1; }
-    float s = (m - 1.0f) / (m + 1.0f);
+    float rcp = 1.0f / (m + 1.0f);
+    float s = (m - 1.0f) * rcp;
     float s2 = s * s;
     float p = 1.0f / 9.0f;
     p = fmaf(p, s2, 1.0f / 7.0f);
@@ -467,31 +469,43 @@ static float cos_poly(float y) {
     return fmaf(p, y2, 1.0f);
 }
 
-/* cos(2 pi u): t = |u - rint(u)| in [0, 1/2]; octant selection maps the argument into
- * [-pi/4, pi/4] through cos(2 pi t) = sin(2 pi (1/4 - t)) = -cos(2 pi (1/2 - t)). */
-float orc_cos2pi_f32(float u) {
+/* cos(2 pi u) and sin(2 pi u) for u in [0, 1]: quadrant q = rint(4u), y = 2 pi (u - q/4) in
+ * [-pi/4, pi/4] (u - q/4 is exact: for q > 0, q/4 and u are within a factor 2 of each other),
+ * then cos(y + q pi/2) and sin(y + q pi/2) from the two polynomials by quadrant. */
+void orc_sincos2pi_f32(float u, float* c, float* s) {
     const float twopi = 6.28318548f;
-    float t = fabsf(u - rintf(u));
-    if (t <= 0.125f) return cos_poly(t * twopi);
-    if (t <= 0.375f) return sin_poly((0.25f - t) * twopi);
-    return -cos_poly((0.5f - t) * twopi);
+    float qf = rintf(4.0f * u);
+    float y = (u - 0.25f * qf) * twopi;
+    float sp = sin_poly(y), cp = cos_poly(y);
+    switch (((int)qf) & 3) {
+        case 0: *c = cp; *s = sp; break;
+        case 1: *c = -sp; *s = cp; break;
+        case 2: *c = -cp; *s = -sp; break;
+        default: *c = sp; *s = -cp; break;
+    }
 }
 
-/* Standard normal by Box-Muller from two uniforms. */
-static float box_muller(float u0, float u1) {
+/* Two independent standard normals by Box-Muller from two uniforms:
+ * r = sqrt(-2 log u0), (r cos 2 pi u1, r sin 2 pi u1). */
+static void box_muller2(float u0, float u1, float* zc, float* zs) {
     float rad = sqrtf(-2.0f * orc_log_f32(u0));
-    return rad * orc_cos2pi_f32(u1);
+    float c, s;
+    orc_sincos2pi_f32(u1, &c, &s);
+    *zc = rad * c;
+    *zs = rad * s;
 }
 
-/* One noisy detector pixel: photon count ~ Poisson(lambda) plus rint(read_noise * z').
- * lambda < 16: inversion with p_0 = exp(-lambda), p_{k+1} = (p_k lambda) r_{k+1} where
- * r_j = fl(1/j) is the correctly rounded float reciprocal, smallest k with u <= F_k, k capped
- * at 64, u from word 0.  lambda >= 16: max(0, rint(lambda + sqrt(lambda) z)),
- * z Box-Muller of words 0 and 1.  Read noise z' is Box-Muller of words 2 and 3.
+/* One noisy detector pixel: photon count ~ Poisson(lambda) plus rint(read_noise * z_c).
+ * Words 2 and 3 give one Box-Muller pair (z_c, z_s), computed when read_noise > 0 or
+ * lambda >= 16.  lambda < 16: inversion with p_0 = exp(-lambda), p_{k+1} = p_k q_{k+1},
+ * q_j = fl(lambda fl(1/j)) (the ratio formed first, then the product), smallest k with
+ * u <= F_k, k capped at 64, u from word 0.  lambda >= 16: max(0, rint(lambda + sqrt(lambda) z_s)).
  * Counter = (c0, c1, c2, 0), key = (seed low word, seed high word). */
 int orc_noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1, uint32_t c2, uint64_t seed) {
     uint32_t ctr[4] = {c0, c1, c2, 0u}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, w[4];
     orc_philox4x32_10(ctr, key, w);
+    float zc = 0.0f, zs = 0.0f;
+    if (read_noise > 0.0f || !(lam < 16.0f)) box_muller2(orc_uniform_f32(w[2]), orc_uniform_f32(w[3]), &zc, &zs);
     int n;
     if (lam < 16.0f) {
         float u = orc_uniform_f32(w[0]);
@@ -499,20 +513,17 @@ int orc_noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1, uint
         int k = 0;
         while (F < u && k < 64) {
             k += 1;
-            p = (p * lam) * (1.0f / (float)k);
+            float q = lam * (1.0f / (float)k);
+            p = p * q;
             F = F + p;
         }
         n = k;
     } else {
-        float z = box_muller(orc_uniform_f32(w[0]), orc_uniform_f32(w[1]));
-        float v = fmaf(sqrtf(lam), z, lam);
+        float v = fmaf(sqrtf(lam), zs, lam);
         n = (int)lrintf(v);
         if (n < 0) n = 0;
     }
-    if (read_noise > 0.0f) {
-        float z2 = box_muller(orc_uniform_f32(w[2]), orc_uniform_f32(w[3]));
-        n += (int)lrintf(read_noise * z2);
-    }
+    if (read_noise > 0.0f) n += (int)lrintf(read_noise * zc);
     return n;
 }
 

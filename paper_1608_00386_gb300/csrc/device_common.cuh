@@ -246,13 +246,14 @@ __device__ __forceinline__ float2* stockham_fft_ct(float2* a, float2* b, int bat
 // Detector noise.  Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by the
 // seed, counter (pixel, step, WFS, 0); float sampler with a fixed operation order written with
 // round-to-nearest intrinsics (never contracted), so one float intensity maps to one integer:
-//   lambda < 16: Poisson by inversion, p0 = exp(-lambda), p_{k+1} = (p_k lambda) fl(1/(k+1)),
+//   words 2, 3: one Box-Muller pair (z_c, z_s), formed when read noise is on or lambda >= 16;
+//   lambda < 16: Poisson by inversion, p0 = exp(-lambda), p_{k+1} = p_k fl(lambda fl(1/(k+1))),
 //                smallest k with u <= F_k (k <= 64), u from word 0;
-//   lambda >= 16: max(0, rint(lambda + sqrt(lambda) z)), z = Box-Muller(words 0, 1);
-//   read noise rint(sigma z'), z' = Box-Muller(words 2, 3).
+//   lambda >= 16: max(0, rint(lambda + sqrt(lambda) z_s));
+//   read noise rint(sigma z_c).
 // exp: Cody-Waite reduction by ln 2 (two-part constant) and a degree-7 Taylor polynomial; log:
-// mantissa in [sqrt(1/2), sqrt(2)) and the atanh series to s^9; cos(2 pi u): octant reduction
-// and Taylor polynomials of sin / cos on [-pi/4, pi/4].
+// mantissa in [sqrt(1/2), sqrt(2)) and the atanh series to s^9, s = (m - 1) fl(1/(m + 1));
+// cos and sin of 2 pi u: quadrant reduction and Taylor polynomials of sin / cos on [-pi/4, pi/4].
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -300,7 +301,7 @@ __device__ __forceinline__ float nz_log(float u) {
         m = __fmul_rn(m, 0.5f);
         e += 1;
     }
-    float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    float s = __fmul_rn(__fsub_rn(m, 1.0f), __frcp_rn(__fadd_rn(m, 1.0f)));
     float s2 = __fmul_rn(s, s);
     float p = 1.11111112e-01f;              // 1/9
     p = __fmaf_rn(p, s2, 1.42857149e-01f);  // 1/7
@@ -330,49 +331,65 @@ __device__ __forceinline__ float nz_cos_poly(float y) {
     return __fmaf_rn(p, y2, 1.0f);
 }
 
-__device__ __forceinline__ float nz_cos2pi(float u) {
+// (cos 2 pi u, sin 2 pi u) for u in [0, 1]: quadrant q = rint(4u), y = 2 pi (u - q/4) (exact
+// subtraction), both polynomials, then the quadrant's signs and swap
+__device__ __forceinline__ void nz_sincos2pi(float u, float& c, float& s) {
     const float twopi = 6.28318548f;
-    float t = fabsf(__fsub_rn(u, rintf(u)));
-    if (t <= 0.125f) return nz_cos_poly(__fmul_rn(t, twopi));
-    if (t <= 0.375f) return nz_sin_poly(__fmul_rn(__fsub_rn(0.25f, t), twopi));
-    return -nz_cos_poly(__fmul_rn(__fsub_rn(0.5f, t), twopi));
+    const float qf = rintf(__fmul_rn(4.0f, u));
+    const float y = __fmul_rn(__fsub_rn(u, __fmul_rn(0.25f, qf)), twopi);
+    const float sp = nz_sin_poly(y), cp = nz_cos_poly(y);
+    const int q = ((int)qf) & 3;
+    const float a = (q & 1) ? sp : cp, b = (q & 1) ? cp : sp;   // cos, sin of y + (q & 1) pi / 2 up to sign
+    c = (q == 1 || q == 2) ? -a : a;
+    s = (q >= 2) ? -b : b;
 }
 
-__device__ __forceinline__ float nz_box_muller(float u0, float u1) {
-    float rad = __fsqrt_rn(__fmul_rn(-2.0f, nz_log(u0)));
-    return __fmul_rn(rad, nz_cos2pi(u1));
+// two independent standard normals: r = sqrt(-2 log u0), (r cos 2 pi u1, r sin 2 pi u1)
+__device__ __forceinline__ void nz_box_muller2(float u0, float u1, float& zc, float& zs) {
+    const float rad = __fsqrt_rn(__fmul_rn(-2.0f, nz_log(u0)));
+    float c, s;
+    nz_sincos2pi(u1, c, s);
+    zc = __fmul_rn(rad, c);
+    zs = __fmul_rn(rad, s);
 }
 
-// recip[j] = fl(1/j), j = 0..64 (entry 0 unused), filled with correctly rounded divisions
+// recip[j] = fl(1/j), j = 0..65 (entry 0 unused), filled with correctly rounded divisions
+constexpr int kRecipEntries = 66;
 __device__ __forceinline__ void fill_recip(float* recip, int tid, int nthr) {
-    for (int j = tid; j <= 64; j += nthr) recip[j] = (j > 0) ? __fdiv_rn(1.0f, (float)j) : 0.0f;
+    for (int j = tid; j < kRecipEntries; j += nthr) recip[j] = (j > 0) ? __fdiv_rn(1.0f, (float)j) : 0.0f;
 }
 
 __device__ __forceinline__ int noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1,
                                             uint32_t c2, unsigned long long seed, const float* recip) {
     uint32_t w[4] = {c0, c1, c2, 0u};
     philox4x32_10(w, (uint32_t)seed, (uint32_t)(seed >> 32));
+    float zc = 0.0f, zs = 0.0f;
+    if (read_noise > 0.0f || !(lam < 16.0f)) nz_box_muller2(nz_uniform(w[2]), nz_uniform(w[3]), zc, zs);
     int n;
     if (lam < 16.0f) {
-        float u = nz_uniform(w[0]);
+        // sequential search, two terms per pass: the terms are formed in the same order as one
+        // at a time and the pass stops at the same k
+        const float u = nz_uniform(w[0]);
         float p = nz_exp(-lam), F = p;
         int k = 0;
         while (F < u && k < 64) {
-            k += 1;
-            p = __fmul_rn(__fmul_rn(p, lam), recip[k]);
-            F = __fadd_rn(F, p);
+            const float qa = __fmul_rn(lam, recip[k + 1]), qb = __fmul_rn(lam, recip[k + 2]);
+            const float pa = __fmul_rn(p, qa), Fa = __fadd_rn(F, pa);
+            if (!(Fa < u) || k + 1 >= 64) {
+                k += 1;
+                break;
+            }
+            p = __fmul_rn(pa, qb);
+            F = __fadd_rn(Fa, p);
+            k += 2;
         }
         n = k;
     } else {
-        float z = nz_box_muller(nz_uniform(w[0]), nz_uniform(w[1]));
-        float v = __fmaf_rn(__fsqrt_rn(lam), z, lam);
+        const float v = __fmaf_rn(__fsqrt_rn(lam), zs, lam);
         n = __float2int_rn(v);
         if (n < 0) n = 0;
     }
-    if (read_noise > 0.0f) {
-        float z2 = nz_box_muller(nz_uniform(w[2]), nz_uniform(w[3]));
-        n += __float2int_rn(__fmul_rn(read_noise, z2));
-    }
+    if (read_noise > 0.0f) n += __float2int_rn(__fmul_rn(read_noise, zc));
     return n;
 }
 

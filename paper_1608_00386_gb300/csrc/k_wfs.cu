@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
     __shared__ float2 s_EM[8][NPX * NPX];
     __shared__ float2 s_P[8][NPX * NL];
     __shared__ float2 s_tw[ND];
-    __shared__ float s_recip[65];
+    __shared__ float s_recip[kRecipEntries];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < ND) {
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kFftThreads) wfs_fft_kernel(WfsLaunch L) {
     float2* W = Z + NFFT * NFFT;                                   // [NFFT]
     AxisEnt* ex = reinterpret_cast<AxisEnt*>(W + NFFT);            // [kMaxEntries * NPX]
     AxisEnt* ey = ex + kMaxEntries * NPX;                          // [kMaxEntries * NPX]
-    float* recip = reinterpret_cast<float*>(ey + kMaxEntries * NPX);  // [65]
+    float* recip = reinterpret_cast<float*>(ey + kMaxEntries * NPX);  // [kRecipEntries]
     float* red = recip + 68;                                       // [3 * NW]
 
     const int tid = threadIdx.x;

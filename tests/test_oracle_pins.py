@@ -347,12 +347,24 @@ def test_exp_f32_accuracy(x):
     assert oracle.exp_f32(x) == pytest.approx(math.exp(np.float32(x)), rel=4e-7)
 
 
-def test_log_cos_f32_accuracy():
+def test_log_sincos_f32_accuracy():
     rng = np.random.default_rng(1)
-    for u in list(rng.random(300)) + [2 ** -25, 0.5, 0.7071, 0.99999994]:
+    for u in list(rng.random(300)) + [2 ** -25, 0.125, 0.375, 0.5, 0.625, 0.7071, 0.875, 0.99999994, 1.0]:
         u = float(np.float32(u))
         assert oracle.log_f32(u) == pytest.approx(math.log(u), rel=4e-7, abs=4e-7)
-        assert oracle.cos2pi_f32(u) == pytest.approx(math.cos(2 * math.pi * u), abs=6e-7)
+        c, s = oracle.sincos2pi_f32(u)
+        assert c == pytest.approx(math.cos(2 * math.pi * u), abs=6e-7)
+        assert s == pytest.approx(math.sin(2 * math.pi * u), abs=6e-7)
+
+
+def test_photon_and_read_noise_independent():
+    # the photon normal (lambda >= 16) and the read noise come from the two outputs of one
+    # Box-Muller pair: independent, so the variances add
+    lam, sig, n = 40.0, 3.0, 200_000
+    x = np.array([oracle.noise_sample(lam, sig, i, 5, 2, 11) for i in range(n)], dtype=np.float64)
+    var = lam + sig * sig + 2.0 / 12.0   # two roundings to integers
+    assert x.mean() == pytest.approx(lam, abs=4 * math.sqrt(var / n))
+    assert x.var() == pytest.approx(var, rel=4 * math.sqrt(2.0 / n) + 0.01)
 
 
 @pytest.mark.parametrize("lam", [0.0, 0.7, 5.0, 15.9, 16.0, 40.0, 250.0])
