@@ -76,7 +76,9 @@ class _Config(C.Structure):
                 ("n_wfs", C.c_int), ("n_sci", C.c_int), ("n_layers", C.c_int), ("n_dms", C.c_int),
                 ("wfs", C.POINTER(_Wfs)), ("sci", C.POINTER(_Sci)), ("layers", C.POINTER(_Layer)),
                 ("dms", C.POINTER(_Dm)), ("n_cmd", C.c_int), ("n_slopes", C.c_int),
-                ("R", _fp), ("s_ref", _fp)]
+                ("R", _fp), ("s_ref", _fp), ("r_dtype", C.c_int)]
+
+DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
 
 
 def lib():
@@ -107,6 +109,15 @@ def lib():
         for nm in ("orc_exp_f32", "orc_log_f32"):
             getattr(L, nm).argtypes = [C.c_float]
             getattr(L, nm).restype = C.c_float
+        L.orc_bf16_rn.argtypes = [C.c_float]
+        L.orc_bf16_rn.restype = C.c_uint16
+        L.orc_bf16_to_f32.argtypes = [C.c_uint16]
+        L.orc_bf16_to_f32.restype = C.c_float
+        L.orc_e4m3_rn_sat.argtypes = [C.c_float]
+        L.orc_e4m3_rn_sat.restype = C.c_uint8
+        L.orc_e4m3_to_f32.argtypes = [C.c_uint8]
+        L.orc_e4m3_to_f32.restype = C.c_float
+        L.orc_quantize_rows.argtypes = [_fp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, _fp]
         L.orc_noise_sample.argtypes = [C.c_float, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64]
         L.orc_noise_sample.restype = C.c_int
         L.orc_noise_frame.argtypes = [_fp, C.c_int, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -242,6 +253,41 @@ def sincos2pi_f32(x: float):
     return c.value, s.value
 
 
+def bf16_rn(x: float) -> int:
+    return lib().orc_bf16_rn(x)
+
+
+def bf16_to_f32(h: int) -> float:
+    return lib().orc_bf16_to_f32(h)
+
+
+def e4m3_rn_sat(x: float) -> int:
+    return lib().orc_e4m3_rn_sat(x)
+
+
+def e4m3_to_f32(b: int) -> float:
+    return lib().orc_e4m3_to_f32(b)
+
+
+def quantize_rows(R: np.ndarray, dtype: int):
+    """(codes, scales) of the rows of R: bfloat16 codes (uint16) with scale 1, or FP8 E4M3 codes
+    (uint8) with one float scale per row."""
+    R = np.ascontiguousarray(R, dtype=np.float32)
+    rows, cols = R.shape
+    out = np.empty((rows, cols), np.uint16 if dtype == DTYPE_BF16 else np.uint8)
+    sc = np.empty(rows, np.float32)
+    lib().orc_quantize_rows(_ptr(R, C.c_float), rows, cols, cols, dtype, out.ctypes.data, _ptr(sc, C.c_float))
+    return out, sc
+
+
+def dequantize_rows(codes: np.ndarray, scales: np.ndarray, dtype: int) -> np.ndarray:
+    """float64 values represented by the codes (the definition the reduced-precision product uses)."""
+    if dtype == DTYPE_BF16:
+        return (codes.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    table = np.array([e4m3_to_f32(b) for b in range(256)], dtype=np.float64)
+    return table[codes] * scales.astype(np.float64)[:, None]
+
+
 def noise_sample(lam: float, read_noise: float, c0: int, c1: int, c2: int, seed: int) -> int:
     return lib().orc_noise_sample(lam, read_noise, c0, c1, c2, seed)
 
@@ -265,7 +311,8 @@ def num_threads() -> int:
 class Sim:
     """Closed-loop simulation state of the oracle for one configuration dictionary."""
 
-    def __init__(self, cfg: dict, screens, R: np.ndarray | None = None, s_ref: np.ndarray | None = None):
+    def __init__(self, cfg: dict, screens, R: np.ndarray | None = None, s_ref: np.ndarray | None = None,
+                 r_dtype: int = DTYPE_F32):
         L = lib()
         self._keep = []
         nw, ns, nl, nd = len(cfg["wfs"]), len(cfg["science"]), len(cfg["layers"]), len(cfg["dms"])
@@ -303,6 +350,7 @@ class Sim:
             s_ref = np.ascontiguousarray(s_ref, dtype=np.float32)
             self._keep.append(s_ref)
             c.s_ref = _ptr(s_ref, C.c_float)
+        c.r_dtype = int(r_dtype)
         self._cfg_struct = (c, wfs, sci, lay, dms)
         self.h = L.orc_create(C.byref(c))
         if not self.h:

@@ -24,7 +24,9 @@
  *   a9  centre-of-gravity slopes minus the reference slopes ("The calibration of the interaction
  *       matrices": reference slope vector)
  *   a10-a11 Delta c = R s (plain double loop), c <- c + g Delta c ("The closed loop": slopes times
- *       control matrix give differential coefficients added to the mirror; pure integrator)
+ *       control matrix give differential coefficients added to the mirror; pure integrator).
+ *       Reduced-precision variants replace each R_ij by its bfloat16 or FP8-E4M3 (per-row scale)
+ *       value, defined by the quantizers below; the product itself stays in double.
  *   a12 science residual along each science direction: instantaneous on-axis Strehl
  *       |sum A e^{i phi}|^2 / (sum A)^2 and the long-exposure PSF |FFT(pad(A e^{i phi}))|^2
  *       accumulated in double                                           ("The Point Spread
@@ -98,6 +100,8 @@ typedef struct {
     int n_cmd, n_slopes;
     const float* R;           /* [n_cmd][n_slopes] row-major, kept by reference                 */
     const float* s_ref;       /* [n_slopes]                                                       */
+    int r_dtype;              /* 0: R as given; 1: R rounded to bfloat16; 2: FP8 E4M3 with a
+                                 float scale per row (the reduced-precision product variants)    */
 } orc_config;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -527,6 +531,69 @@ int orc_noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1, uint
     return n;
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* Reduced-precision reconstructor (NEXT variant f1): the number formats, written from their     */
+/* definitions                                                                                  */
+/* ------------------------------------------------------------------------------------------ */
+
+/* bfloat16 = the upper 16 bits of an IEEE binary32 (1 sign, 8 exponent, 7 fraction bits); from
+ * float by round to nearest, ties to even.  Inputs are finite. */
+uint16_t orc_bf16_rn(float x) {
+    uint32_t u = bits_from_f32(x);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float orc_bf16_to_f32(uint16_t h) { return f32_from_bits((uint32_t)h << 16); }
+
+/* FP8 E4M3 in the OCP 8-bit floating-point format ("E4M3FN"): 1 sign, 4 exponent (bias 7) and 3
+ * fraction bits, subnormals below 2^-6 with step 2^-9, no infinities, S.1111.111 is NaN, so the
+ * largest finite magnitude is 1.75 * 2^8 = 448.  From float by round to nearest, ties to even,
+ * saturating to +-448. */
+uint8_t orc_e4m3_rn_sat(float x) {
+    if (x != x) return 0x7f;
+    uint8_t sgn = signbit(x) ? 0x80 : 0x00;
+    double a = fabs((double)x);
+    if (a >= 448.0) return sgn | 0x7e;
+    if (a < ldexp(1.0, -6)) return sgn | (uint8_t)nearbyint(a * 512.0);   /* m * 2^-9, m <= 8 */
+    int e;
+    double f = frexp(a, &e);             /* a = f 2^e, f in [1/2, 1) */
+    int E = e - 1;
+    double m = nearbyint((2.0 * f - 1.0) * 8.0);
+    if (m == 8.0) { m = 0.0; E += 1; }
+    int code = ((E + 7) << 3) | (int)m;
+    if (code > 0x7e) code = 0x7e;
+    return sgn | (uint8_t)code;
+}
+float orc_e4m3_to_f32(uint8_t b) {
+    int e = (b >> 3) & 15, m = b & 7;
+    double v;
+    if (e == 15 && m == 7) v = NAN;
+    else if (e == 0) v = ldexp((double)m, -9);
+    else v = ldexp(1.0 + m / 8.0, e - 7);
+    return (float)((b & 0x80) ? -v : v);
+}
+
+/* Quantize rows of R [rows][cols] (row stride ld).  dtype 1: bfloat16 codes, scale 1.
+ * dtype 2: scale_r = fl(max_j |R_rj| / 448) (1 for an all-zero row), codes e4m3(fl(R_rj / scale_r)).
+ * The represented value is code value * scale_r. */
+void orc_quantize_rows(const float* R, int rows, int cols, int ld, int dtype, void* out, float* scales) {
+    for (int r = 0; r < rows; ++r) {
+        const float* row = R + (size_t)r * ld;
+        if (dtype == 1) {
+            uint16_t* o = (uint16_t*)out + (size_t)r * cols;
+            for (int j = 0; j < cols; ++j) o[j] = orc_bf16_rn(row[j]);
+            if (scales) scales[r] = 1.0f;
+        } else {
+            uint8_t* o = (uint8_t*)out + (size_t)r * cols;
+            float amax = 0.0f;
+            for (int j = 0; j < cols; ++j) amax = fmaxf(amax, fabsf(row[j]));
+            float sc = amax > 0.0f ? amax / 448.0f : 1.0f;
+            for (int j = 0; j < cols; ++j) o[j] = orc_e4m3_rn_sat(row[j] / sc);
+            if (scales) scales[r] = sc;
+        }
+    }
+}
+
 /* Noisy frame of n pixels for counters (pixel0 + i, step, wfs). */
 void orc_noise_frame(const float* lam, int n, float read_noise, uint32_t pixel0, uint32_t step,
                      uint32_t wfs, uint64_t seed, int32_t* out) {
@@ -575,6 +642,10 @@ typedef struct {
     int* dm_nvalid; int* dm_cmd0;
     int n_cmd, n_slopes;
     const float* R; double* s_ref;
+    int r_dtype;
+    uint16_t* Rb;             /* bfloat16 codes of R (r_dtype 1)                                 */
+    uint8_t* Rq;              /* E4M3 codes of R (r_dtype 2)                                     */
+    float* r_scale;           /* per-row scales (r_dtype 2)                                      */
     double* c;                /* commands                                                        */
     double* s;                /* last slopes                                                     */
     long k;                   /* step counter                                                    */
@@ -705,6 +776,15 @@ orc_sim* orc_create(const orc_config* cfg) {
     S->n_slopes = ns;
     if ((cfg->R && (cfg->n_cmd != S->n_cmd || cfg->n_slopes != S->n_slopes))) { sim_free(S); return NULL; }
     S->R = cfg->R;
+    S->r_dtype = cfg->r_dtype;
+    if (S->R && S->r_dtype == 1) {
+        S->Rb = (uint16_t*)malloc(sizeof(uint16_t) * (size_t)S->n_cmd * ns);
+        orc_quantize_rows(S->R, S->n_cmd, ns, ns, 1, S->Rb, NULL);
+    } else if (S->R && S->r_dtype == 2) {
+        S->Rq = (uint8_t*)malloc((size_t)S->n_cmd * ns);
+        S->r_scale = (float*)malloc(sizeof(float) * (S->n_cmd ? S->n_cmd : 1));
+        orc_quantize_rows(S->R, S->n_cmd, ns, ns, 2, S->Rq, S->r_scale);
+    }
     S->s_ref = (double*)calloc(ns ? ns : 1, sizeof(double));
     if (cfg->s_ref) for (int i = 0; i < ns; ++i) S->s_ref[i] = (double)cfg->s_ref[i];
     S->c = (double*)calloc(S->n_cmd ? S->n_cmd : 1, sizeof(double));
@@ -740,6 +820,7 @@ static void sim_free(orc_sim* S) {
     free(S->screen); free(S->surf); free(S->dm_nvalid); free(S->dm_cmd0);
     free(S->wfs); free(S->sci); free(S->wfs_p); free(S->sci_p); free(S->lay_p); free(S->dm_p);
     free(S->s_ref); free(S->c); free(S->s);
+    free(S->Rb); free(S->Rq); free(S->r_scale);
     free(S);
 }
 void orc_destroy(orc_sim* S) { sim_free(S); }
@@ -870,9 +951,18 @@ int orc_step(orc_sim* S, int n_steps) {
         double* dc = (double*)malloc(sizeof(double) * (S->n_cmd ? S->n_cmd : 1));
         #pragma omp parallel for schedule(static)
         for (int i = 0; i < S->n_cmd; ++i) {
-            const float* row = S->R + (size_t)i * S->n_slopes;
             double acc = 0.0;
-            for (int j = 0; j < S->n_slopes; ++j) acc += (double)row[j] * S->s[j];
+            if (S->r_dtype == 1) {
+                const uint16_t* row = S->Rb + (size_t)i * S->n_slopes;
+                for (int j = 0; j < S->n_slopes; ++j) acc += (double)orc_bf16_to_f32(row[j]) * S->s[j];
+            } else if (S->r_dtype == 2) {
+                const uint8_t* row = S->Rq + (size_t)i * S->n_slopes;
+                const double sc = (double)S->r_scale[i];
+                for (int j = 0; j < S->n_slopes; ++j) acc += (double)orc_e4m3_to_f32(row[j]) * sc * S->s[j];
+            } else {
+                const float* row = S->R + (size_t)i * S->n_slopes;
+                for (int j = 0; j < S->n_slopes; ++j) acc += (double)row[j] * S->s[j];
+            }
             dc[i] = acc;
         }
         for (int i = 0; i < S->n_cmd; ++i) S->c[i] += S->cfg.gain * dc[i];

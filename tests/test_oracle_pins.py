@@ -439,3 +439,73 @@ def test_screen_structure_function_matches_von_karman_quadrature():
         if r / L0 < 0.02:
             # Kolmogorov limit 6.88 (r/r0)^(5/3) with the leading outer-scale correction
             assert th == pytest.approx(6.88 * (r / r0) ** (5 / 3), rel=0.35)
+
+
+# ------------------------------------------------------------------ reduced-precision reconstructor
+def _torch():
+    return pytest.importorskip("torch")
+
+
+def test_bf16_rounding_matches_torch():
+    torch = _torch()
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.normal(0, 1e-3, 4000), rng.normal(0, 30, 4000),
+                        [1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), 0.0, -0.0, 1e-40, 3.3e38]]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    got = np.array([oracle.bf16_rn(float(v)) for v in x], dtype=np.uint16)
+    assert np.array_equal(got, ref)
+    assert all(oracle.bf16_to_f32(int(h)) == float(torch.tensor([int(h)], dtype=torch.int32).to(torch.int16)
+                                                  .view(torch.bfloat16).float()) for h in got[:200])
+
+
+def test_e4m3_codes_match_torch_and_saturate():
+    torch = _torch()
+    table = torch.arange(256, dtype=torch.uint8).view(torch.float8_e4m3fn).float().numpy()
+    for b in range(256):
+        v = oracle.e4m3_to_f32(b)
+        assert (math.isnan(v) and math.isnan(table[b])) or v == table[b]
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.uniform(-460, 460, 3000), rng.normal(0, 1e-2, 3000),
+                        [2 ** -9, 1.5 * 2 ** -9, 2 ** -10, 2.5 * 2 ** -9, 448.0, 447.0, 440.0, 2 ** -6,
+                         0.9375 * 2 ** -6]]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    got = np.array([oracle.e4m3_rn_sat(float(v)) for v in x], dtype=np.uint8)
+    assert np.array_equal(got, ref)
+    # saturation to the largest finite magnitude (torch gives NaN above 464)
+    for v in (464.0, 500.0, 1e6, 3e38):
+        assert oracle.e4m3_rn_sat(v) == 0x7E and oracle.e4m3_rn_sat(-v) == 0xFE
+
+
+def test_quantize_rows_scales_and_error_bound():
+    rng = np.random.default_rng(5)
+    R = (rng.normal(0, 1e-2, (37, 301)) * rng.uniform(0.1, 10, (37, 1))).astype(np.float32)
+    R[5] = 0.0
+    codes, sc = oracle.quantize_rows(R, oracle.DTYPE_FP8_E4M3)
+    amax = np.abs(R).max(axis=1)
+    assert sc[5] == 1.0 and not codes[5].any()
+    nz = amax > 0
+    assert np.array_equal(sc[nz], (amax[nz] / np.float32(448.0)).astype(np.float32))
+    deq = oracle.dequantize_rows(codes, sc, oracle.DTYPE_FP8_E4M3)
+    # half a unit in the last place: 2^-4 relative for normals, 2^-10 scale below 2^-6 scale
+    bound = np.maximum(np.abs(R) * 2.0 ** -4, sc[:, None] * 2.0 ** -10) * (1 + 1e-6)
+    assert np.all(np.abs(deq - R) <= bound)
+    # the largest element of each row maps to +-448 exactly
+    i = np.abs(R).argmax(axis=1)
+    assert np.all(np.abs(deq[nz, i[nz]]) == pytest.approx(amax[nz], rel=1e-6))
+    cb, _ = oracle.quantize_rows(R, oracle.DTYPE_BF16)
+    d16 = oracle.dequantize_rows(cb, None, oracle.DTYPE_BF16)
+    assert np.all(np.abs(d16 - R) <= np.abs(R) * 2.0 ** -8 * (1 + 1e-6))
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_reduced_precision_product_is_dequantized_matmul(dtype):
+    # one closed-loop step of the 8 m case: the command update equals g * deq(R) @ s
+    from tests._helpers import scao_tiny_inputs
+    cfg, screens, R = scao_tiny_inputs()
+    sim = oracle.Sim(dict(cfg, noise=False), screens, R, r_dtype=dtype)
+    sim.step(1)
+    s = sim.slopes()
+    codes, sc = oracle.quantize_rows(R, dtype)
+    deq = oracle.dequantize_rows(codes, sc, dtype)
+    np.testing.assert_allclose(sim.commands(), cfg["gain"] * (deq @ s), rtol=1e-12, atol=1e-15)
+    sim.close()
