@@ -70,6 +70,41 @@ def step_algorithmic_bytes(cfg, recon_bytes):
     return recon_bytes + dm + layers + psf
 
 
+def recon_alg_bytes(n_cmd, n_slopes, esize):
+    """Bytes one product must move: R once in its stored format, s read, c read and written."""
+    return float(esize) * n_cmd * n_slopes + 4.0 * (n_slopes + 2 * n_cmd)
+
+
+def timed_steps(sim, stream, steps, warmup, dist, clocks):
+    """W >= 3 warm-up steps, then K steps bracketed by CUDA events on the launching stream (after
+    a barrier and a synchronize); returns (seconds, stage ms, stage counts, launches per step,
+    clock record), the seconds being the maximum over ranks."""
+    import torch
+    sim.step(max(3, warmup))
+    sim.sync()
+    sim.set_profiling(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    sim.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) * 1e-3
+    ck = clocks.stop()
+    ms, cnt, lps = sim.get_profile()
+    sim.set_profiling(False)
+    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item()), ms, cnt, lps, ck
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -165,10 +200,10 @@ def run_reference(args):
         sim.step(1)
     t0 = time.perf_counter()
     steps = 0
-    while steps < max(1, min(args.steps, 3)):
+    while steps < max(1, args.steps):
         sim.step(1)
         steps += 1
-        if time.perf_counter() - t0 > 30.0:
+        if time.perf_counter() - t0 > 60.0:     # bounded sample: about a minute of CPU work
             break
     dt = time.perf_counter() - t0
     v = steps / dt
@@ -183,7 +218,9 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(cfg, screens, R, budget_s=20.0):
+def cpu_baseline(cfg, screens, R, budget_s=15.0):
+    """The oracle as it stands on the host cores: whole steps of the same workload until about
+    budget_s seconds of CPU work (at most 64 steps)."""
     import oracle
     oracle.build()
     sim = oracle.Sim(cfg, screens, R)
@@ -192,7 +229,7 @@ def cpu_baseline(cfg, screens, R, budget_s=20.0):
     while True:
         sim.step(1)
         steps += 1
-        if time.perf_counter() - t0 > budget_s or steps >= 4:
+        if time.perf_counter() - t0 > budget_s or steps >= 64:
             break
     dt = time.perf_counter() - t0
     return {"value": steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
@@ -207,6 +244,7 @@ def main():
     ap.add_argument("--impl", default="mcao", choices=["mcao", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -232,38 +270,14 @@ def main():
     stream = torch.cuda.current_stream()
     sim = mcao.make_sim(cfg, d_screens, d_R, stream=stream)
     n_slopes = sim.query(mcao.Q_SLOPES)
-    sim.step(max(3, args.warmup))
-    sim.sync()
-
-    clocks = Clocks(local)
-    sim.set_profiling(True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ev0.record(stream)
-    sim.step(args.steps)
-    ev1.record(stream)
-    ev1.synchronize()
-    torch.cuda.synchronize()
-    elapsed = ev0.elapsed_time(ev1) * 1e-3
-    ck = clocks.stop()
-    ms, cnt, lps = sim.get_profile()
-    sim.set_profiling(False)
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
+    elapsed, ms, cnt, lps, ck = timed_steps(sim, stream, args.steps, args.warmup, dist, Clocks(local))
     value = ws * args.steps / elapsed
 
     # dominant kernel roofline (reconstructor product): one step issues it as one launch per
     # sensor slice; per-step bytes over the summed device time of those launches
     recon_launches = cnt["recon"] / max(1, args.steps)
     recon_ms = ms["recon"] / max(1, args.steps)
-    alg_bytes = 4.0 * (n_cmd * n_slopes + n_slopes + 2 * n_cmd)
+    alg_bytes = recon_alg_bytes(n_cmd, n_slopes, 4)
     peak, peak_kind = peaks()
     achieved = alg_bytes / (recon_ms * 1e-3) / 1e9
     step_bytes = step_algorithmic_bytes(cfg, alg_bytes)
@@ -275,6 +289,27 @@ def main():
                      "sensing and science kernels)")}
     step_ms = 1e3 * elapsed / args.steps
     stage_ms = {k: v / max(1, args.steps) for k, v in ms.items()}
+    sim.close()
+
+    # reduced-precision reconstructor variants (bfloat16; FP8 E4M3 with per-row scales): same
+    # workload and timing, R streamed in the narrower format
+    variants = {}
+    if not args.no_variants:
+        for name, dt in (("bf16", mcao.DTYPE_BF16), ("fp8_e4m3", mcao.DTYPE_FP8_E4M3)):
+            vs = mcao.make_sim(cfg, d_screens, d_R, stream=stream, r_dtype=dt)
+            el, vms, vcnt, _, vck = timed_steps(vs, stream, args.steps, args.warmup, dist, Clocks(local))
+            vs.close()
+            rb = recon_alg_bytes(n_cmd, n_slopes, 2 if dt == mcao.DTYPE_BF16 else 1)
+            if dt == mcao.DTYPE_FP8_E4M3:
+                rb += 4.0 * n_cmd                      # the row scales
+            r_ms = vms["recon"] / max(1, args.steps)
+            variants[name] = {
+                "value": ws * args.steps / el, "unit": UNIT, "ms_per_step": 1e3 * el / args.steps,
+                "recon_ms_per_step": r_ms, "recon_alg_bytes_per_step": rb,
+                "recon_frac": rb / (r_ms * 1e-3) / 1e9 / peak,
+                "step_frac": step_algorithmic_bytes(cfg, rb) / (el / args.steps) / 1e9 / peak,
+                "clocks": vck,
+                "accuracy": "long-exposure Strehl within 1% of the float32 loop (tests/test_gpu_precision.py)"}
 
     e2e = None
     if not args.no_e2e:
@@ -288,12 +323,12 @@ def main():
             "roofline": roof,
             "step_roofline": {"alg_bytes_per_step": step_bytes,
                               "frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak},
-            "stage_ms": stage_ms, "gpu_launches": int(lps * args.steps), "clocks": ck, "e2e": e2e}
+            "stage_ms": stage_ms, "gpu_launches": int(lps * args.steps), "clocks": ck, "e2e": e2e,
+            "variants": variants}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, screens, R)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    sim.close()
     if dist:
         dist.destroy_process_group()
 

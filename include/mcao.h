@@ -56,7 +56,11 @@ typedef enum {
 } mcao_status;
 
 enum { MCAO_WFS_NGS = 0, MCAO_WFS_LGS = 1 };
-enum { MCAO_DTYPE_F32 = 0 };
+/* Element format of the stored control matrix (mcao_load_reconstructor, mcao_quantize_rows):
+ * float32; bfloat16 (round to nearest even); FP8 E4M3 in the OCP 8-bit format (round to nearest
+ * even, saturating to +-448) with one float32 scale per row, scale = max|row| / 448 (1 for an
+ * all-zero row).  The product always accumulates in float32 against float32 slopes. */
+enum { MCAO_DTYPE_F32 = 0, MCAO_DTYPE_BF16 = 1, MCAO_DTYPE_FP8_E4M3 = 2 };
 
 /* One Shack-Hartmann wavefront sensor.  Its pupil grid has n_sub * n_px samples across D.
  * Each valid subaperture (illuminated fraction >= valid_thr) forms an n_fft x n_fft spot
@@ -172,8 +176,10 @@ mcao_status mcao_load_dms(mcao_sim* sim, int n_dms, const mcao_dm* dms);
  * matrices": reference slope vector).  The library keeps its own copy in a padded layout.
  * on_device = 1: R and s_ref are device addresses; the call first waits for all work queued
  * on the device, so the kernel producing R may still be running when it is made.  Errors:
- * MCAO_E_STATE (DMs not loaded), MCAO_E_SHAPE (n_cmd or n_slopes differ from the
- * configuration), MCAO_E_UNSUPPORTED (dtype other than MCAO_DTYPE_F32), MCAO_E_OOM, MCAO_E_CUDA. */
+ * R is always given in float32; dtype selects the format the library stores and streams
+ * (MCAO_DTYPE_F32, MCAO_DTYPE_BF16 or MCAO_DTYPE_FP8_E4M3, converted once here).
+ * Errors: MCAO_E_STATE (DMs not loaded), MCAO_E_SHAPE (n_cmd or n_slopes differ from the
+ * configuration), MCAO_E_UNSUPPORTED (unknown dtype), MCAO_E_OOM, MCAO_E_CUDA. */
 mcao_status mcao_load_reconstructor(mcao_sim* sim, int n_cmd, int n_slopes, const float* R,
                                     const float* s_ref, int dtype, int on_device);
 
@@ -259,6 +265,21 @@ mcao_status mcao_set_state(mcao_sim* sim, const void* buf, size_t n);
  * index >= 64), MCAO_E_CUDA. */
 mcao_status mcao_reconstruct_noalloc(const float* R, int n_cmd, int n_slopes, int ld, const float* s,
                                      float* c, float gain, void* stream, char* err, size_t err_len);
+
+/* Convert a float32 matrix to the stored reduced formats, as mcao_load_reconstructor does (no
+ * counterpart in the paper; exposed so that callers and tests can inspect the codes).
+ *   R      device pointer, row-major [rows][ld] float32, ld >= cols.
+ *   dtype  MCAO_DTYPE_BF16 (codes: uint16 per element) or MCAO_DTYPE_FP8_E4M3 (uint8 per element).
+ *   codes  device pointer, row-major [rows][cols] codes, 16-byte aligned; cols must be a multiple
+ *          of 8 (BF16) or 16 (FP8 E4M3).
+ *   scales device pointer [rows] float32: written for FP8 E4M3 (max|row| / 448, 1 for a zero row);
+ *          may be NULL for BF16.
+ *   stream CUDA stream (cudaStream_t) or NULL for the legacy stream; the call only queues work.
+ * err receives a message on failure (err_len bytes, may be NULL).  Errors: MCAO_E_INVALID_ARG
+ * (null pointers, rows < 0, ld < cols), MCAO_E_SHAPE (cols not a multiple of the vector width,
+ * codes not 16-byte aligned), MCAO_E_UNSUPPORTED (dtype), MCAO_E_CUDA. */
+mcao_status mcao_quantize_rows(const float* R, int rows, int cols, int ld, int dtype, void* codes,
+                               float* scales, void* stream, char* err, size_t err_len);
 
 /* Stages timed by the profiler. */
 enum {

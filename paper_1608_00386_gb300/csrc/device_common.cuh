@@ -22,13 +22,17 @@ struct AxisEnt {
     float t;     // weight of i1
 };
 
-__device__ __forceinline__ AxisEnt axis_entry(long long X, int n, int periodic) {
+__device__ __forceinline__ AxisEnt axis_entry(long long X, int n, int periodic, float inv_n) {
     int i = (int)(X >> 32);
     float t = __uint2float_rn((unsigned)(X & 0xffffffffull)) * 2.3283064365386963e-10f;  // 2^-32
     int i1;
     if (periodic) {
-        i %= n;
-        if (i < 0) i += n;
+        // i mod n: quotient from the float reciprocal (off by at most a few for |i| < 2^31),
+        // then exact integer corrections
+        const int q = __float2int_rd(__int2float_rn(i) * inv_n);
+        i -= q * n;
+        while (i < 0) i += n;
+        while (i >= n) i -= n;
         i1 = (i + 1 == n) ? 0 : i + 1;
     } else {
         if (i < 0) {
@@ -47,16 +51,17 @@ __device__ __forceinline__ AxisEnt axis_entry(long long X, int n, int periodic) 
 }
 
 // entries of every grid for the T x T tile with origin (i0, j0): ex[g T + x], ey[g T + y]
+template <int T>
 __device__ __forceinline__ void tile_entries(const GridView* V, int n_grids, long long k, int i0, int j0,
-                                             int T, AxisEnt* ex, AxisEnt* ey, int tid, int nthr) {
+                                             AxisEnt* ex, AxisEnt* ey, int tid, int nthr) {
     for (int e = tid; e < n_grids * 2 * T; e += nthr) {
-        int g = e / (2 * T), r = e - g * 2 * T;
+        const int g = e / (2 * T), r = e - g * 2 * T;
         const GridView& v = V[g];
         if (r < T) {
-            ex[g * T + r] = axis_entry(v.ax + (long long)(i0 + r) * v.bp + k * v.vx, v.n, v.periodic);
+            ex[g * T + r] = axis_entry(v.ax + (long long)(i0 + r) * v.bp + k * v.vx, v.n, v.periodic, v.inv_n);
         } else {
-            int y = r - T;
-            ey[g * T + y] = axis_entry(v.ay + (long long)(j0 + y) * v.bp + k * v.vy, v.n, v.periodic);
+            const int y = r - T;
+            ey[g * T + y] = axis_entry(v.ay + (long long)(j0 + y) * v.bp + k * v.vy, v.n, v.periodic, v.inv_n);
         }
     }
 }

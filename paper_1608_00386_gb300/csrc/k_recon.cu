@@ -9,6 +9,11 @@
 // applies the gain.  The slopes are read (L1-cached) from a copy the sensing kernels write in
 // R's padded column layout, so every 16-byte load of s is aligned.
 //
+// Formats.  R is stored as float32, bfloat16 or FP8 E4M3 with one float scale per row (the
+// reduced-precision variants); elements move in 16-byte vectors and are widened to float32 in
+// registers, the slopes stay float32, accumulation is float32 and an E4M3 row sum is multiplied
+// by its row's scale before it is written.
+//
 // Streaming.  At most one block per SM (3 warps).  Each warp owns a four-stage ring in
 // shared memory and keeps it filled with TMA bulk copies (cp.async.bulk, completion counted on a
 // per-stage mbarrier, L2 evict-first policy).  R is held stage-tiled (see ReconLaunch), so each
@@ -50,12 +55,12 @@ __device__ __forceinline__ float2 dot4x2(float4 a, float4 b, float2 acc) {
 // ------------------------------------------------------------------------------------------
 constexpr int kTmaWarps = 3;
 constexpr int kTmaRows = kReconRows;               // rows per item
-constexpr int kTmaSeg = kReconSeg;                 // float4 per row segment (2 KB)
+constexpr int kTmaSeg = kReconSeg;                 // 16-byte vectors per row segment (2 KB)
 constexpr int kTmaStages = 4;
 constexpr long long kWaitCycles = 2000000000ll;    // ~1 s at 2 GHz
 
 struct TmaSmem {
-    float4 ring[kTmaWarps][kTmaStages][kTmaRows * kTmaSeg];
+    uint4 ring[kTmaWarps][kTmaStages][kTmaRows * kTmaSeg];
     unsigned long long bar[kTmaWarps][kTmaStages];
     int item[kTmaWarps][kTmaStages];  // item whose first stage the slot holds; -1: no more items
 };
@@ -106,27 +111,123 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-// stage geometry of chunk kc of a slice: n4 float4 per row, nst stages of seg float4
-__device__ __forceinline__ void chunk_geom(const ReconLaunch& L, int kc, int& n4, int& nst, int& seg) {
+// stage geometry of chunk kc of a slice: n4 16-byte vectors per row, nst stages of kTmaSeg
+// vectors (the last one shorter)
+__device__ __forceinline__ void chunk_geom(const ReconLaunch& L, int kc, int& n4, int& nst) {
+    const int epv = 16 / recon_esize(L.dtype);
     const int ncols = min(L.len - kc * L.kc, L.kc);
-    n4 = (ncols + 3) / 4;
+    n4 = (ncols + epv - 1) / epv;
     nst = (n4 + kTmaSeg - 1) / kTmaSeg;
-    seg = (n4 + nst - 1) / nst;
 }
 
-// Chunk geometry {n4, nst, seg} of a full chunk and of the slice's last (possibly shorter) one,
+// widening of packed elements: bfloat16 pairs are the upper halves of float32 words; an E4M3
+// pair goes through an f16x2 conversion (exact), then each half to float32 (exact)
+__device__ __forceinline__ float2 bf16x2_to_f32x2(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+__device__ __forceinline__ float4 e4m3x4_to_f32x4(uint32_t w) {
+    float4 r;
+    asm("{\n\t.reg .b16 lo, hi;\n\t.reg .b32 h01, h23;\n\t.reg .f16 a, b, c, d;\n\t"
+        "mov.b32 {lo, hi}, %4;\n\t"
+        "cvt.rn.f16x2.e4m3x2 h01, lo;\n\t"
+        "cvt.rn.f16x2.e4m3x2 h23, hi;\n\t"
+        "mov.b32 {a, b}, h01;\n\t"
+        "mov.b32 {c, d}, h23;\n\t"
+        "cvt.f32.f16 %0, a;\n\t"
+        "cvt.f32.f16 %1, b;\n\t"
+        "cvt.f32.f16 %2, c;\n\t"
+        "cvt.f32.f16 %3, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "r"(w));
+    return r;
+}
+// narrowing with round to nearest even (E4M3 saturating to +-448); element 0 in the low bits
+__device__ __forceinline__ uint32_t f32x2_to_bf16x2(float x0, float x1) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(x1), "f"(x0));
+    return d;
+}
+__device__ __forceinline__ uint32_t f32x4_to_e4m3x4(float x0, float x1, float x2, float x3) {
+    uint32_t d;
+    asm("{\n\t.reg .b16 lo, hi;\n\t"
+        "cvt.rn.satfinite.e4m3x2.f32 lo, %2, %1;\n\t"
+        "cvt.rn.satfinite.e4m3x2.f32 hi, %4, %3;\n\t"
+        "mov.b32 %0, {lo, hi};\n\t}"
+        : "=r"(d)
+        : "f"(x0), "f"(x1), "f"(x2), "f"(x3));
+    return d;
+}
+
+// one 16-byte vector of R times the matching slopes, into the two halves of acc
+template <int DT>
+__device__ __forceinline__ float2 vec_dot(uint4 r, const float4* sv, float2 acc) {
+    if constexpr (DT == kReconF32) {
+        return dot4x2(make_float4(__uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z),
+                                  __uint_as_float(r.w)),
+                      sv[0], acc);
+    } else if constexpr (DT == kReconBF16) {
+        acc = ffma2(bf16x2_to_f32x2(r.x), make_float2(sv[0].x, sv[0].y), acc);
+        acc = ffma2(bf16x2_to_f32x2(r.y), make_float2(sv[0].z, sv[0].w), acc);
+        acc = ffma2(bf16x2_to_f32x2(r.z), make_float2(sv[1].x, sv[1].y), acc);
+        return ffma2(bf16x2_to_f32x2(r.w), make_float2(sv[1].z, sv[1].w), acc);
+    } else {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc = dot4x2(e4m3x4_to_f32x4(w[i]), sv[i], acc);
+        return acc;
+    }
+}
+
+// Chunk geometry {n4, nst} of a full chunk and of the slice's last (possibly shorter) one,
 // computed once per thread so that the per-stage path needs no division.
 struct SliceGeom {
     int n_chunks;
-    int full[3], last[3];
+    int full[2], last[2];
 };
 
 __device__ __forceinline__ SliceGeom slice_geom(const ReconLaunch& L) {
     SliceGeom g;
     g.n_chunks = (L.len + L.kc - 1) / L.kc;
-    chunk_geom(L, 0, g.full[0], g.full[1], g.full[2]);
-    chunk_geom(L, g.n_chunks - 1, g.last[0], g.last[1], g.last[2]);
+    chunk_geom(L, 0, g.full[0], g.full[1]);
+    chunk_geom(L, g.n_chunks - 1, g.last[0], g.last[1]);
     return g;
+}
+
+// One stage: the vectors e = lane + 32 j (j < 4) of the four rows.  A full stage (kTmaSeg
+// vectors) needs no predicate; a short one guards loads and multiply-adds alike (registers of
+// lanes past the end are never read).
+template <bool FULL>
+__device__ __forceinline__ void stage_load(const uint4* ring, int lane, int cnt, uint4 (&rv)[kTmaSeg / 32][kTmaRows]) {
+    const int stride = FULL ? kTmaSeg : cnt;
+#pragma unroll
+    for (int j = 0; j < kTmaSeg / 32; ++j) {
+        const int e = lane + 32 * j;
+        if (FULL || e < cnt) {
+#pragma unroll
+            for (int q = 0; q < kTmaRows; ++q) rv[j][q] = ring[q * stride + e];
+        }
+    }
+}
+
+template <int DT, bool FULL>
+__device__ __forceinline__ void stage_fma(const uint4 (&rv)[kTmaSeg / 32][kTmaRows], const float4 (&sv)[kTmaSeg / 32],
+                                          const float4* s4, int e0, int lane, int cnt, float2 (&acc)[kTmaRows]) {
+    constexpr int SPV = 4 / recon_esize(DT);
+#pragma unroll
+    for (int j = 0; j < kTmaSeg / 32; ++j) {
+        const int e = lane + 32 * j;
+        if (FULL || e < cnt) {
+            float4 sj[SPV];
+            if constexpr (DT == kReconF32) {
+                sj[0] = sv[j];
+            } else {
+#pragma unroll
+                for (int i = 0; i < SPV; ++i) sj[i] = __ldg(s4 + (e0 + e) * SPV + i);
+            }
+#pragma unroll
+            for (int q = 0; q < kTmaRows; ++q) acc[q] = vec_dot<DT>(rv[j][q], sj, acc[q]);
+        }
+    }
 }
 
 // Work items i = kc * n_rq + rq (row quad rq, chunk kc) are handed out one at a time by the
@@ -137,7 +238,9 @@ __device__ __forceinline__ SliceGeom slice_geom(const ReconLaunch& L) {
 // the copies.  The other lanes follow the slots in order.  Per stage: wait for the slot's copy,
 // pull the stage into registers, let lane 0 refill the slot, then do the multiply-adds -- a slot
 // is held only for its shared-memory loads, which keeps four copies per warp in flight.
+template <int DT>
 __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L) {
+    constexpr int SPV = 4 / recon_esize(DT);   // float4 of slopes per 16-byte vector of R
     extern __shared__ __align__(128) unsigned char tma_raw[];
     TmaSmem& sm = *reinterpret_cast<TmaSmem*>(tma_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -149,13 +252,13 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
     const int n_rq = L.n_rq;
     const SliceGeom g = slice_geom(L);
     const int n_items = n_rq * g.n_chunks;
-    const float4* R4 = reinterpret_cast<const float4*>(L.R + L.base);
-    const long long blk4 = (long long)L.kc;   // float4 per item block: 4 rows x kc floats / 4
+    const uint4* R4 = reinterpret_cast<const uint4*>(L.R + L.base);
+    const long long blk4 = (long long)kTmaRows * L.kc / (16 / recon_esize(DT));   // vectors per item block
 
     // producer state (used by lane 0 only)
-    int p_next = 0, p_t = 0, p_n4 = 0, p_nst = 1, p_seg = 1, issued = 0;
+    int p_next = 0, p_t = 0, p_n4 = 0, p_nst = 1, issued = 0;
     bool p_done = false;
-    const float4* p_src = R4;
+    const uint4* p_src = R4;
     if (lane == 0) p_next = (int)atomicAdd(L.work, 1u);
     auto issue_next = [&](int st) {
         if (p_t == 0) {
@@ -170,15 +273,14 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
             const int* q = kc == g.n_chunks - 1 ? g.last : g.full;
             p_n4 = q[0];
             p_nst = q[1];
-            p_seg = q[2];
             p_src = R4 + ((long long)kc * n_rq + rq) * blk4;
             sm.item[warp][st] = it;
         }
-        const int cnt = min(p_seg, p_n4 - p_t * p_seg);
+        const int cnt = min(kTmaSeg, p_n4 - p_t * kTmaSeg);
         const uint32_t bytes = (uint32_t)(kTmaRows * cnt) * 16u;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&sm.bar[warp][st], bytes);
-        bulk_g2s(sm.ring[warp][st], p_src + (long long)kTmaRows * p_seg * p_t, bytes, &sm.bar[warp][st], pol);
+        bulk_g2s(sm.ring[warp][st], p_src + (long long)kTmaRows * kTmaSeg * p_t, bytes, &sm.bar[warp][st], pol);
         ++issued;
         if (++p_t == p_nst) p_t = 0;
     };
@@ -194,19 +296,23 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
         if (it < 0) break;
         const int kc = it / n_rq, rq = it - kc * n_rq;
         const int* cg = kc == g.n_chunks - 1 ? g.last : g.full;
-        const int n4 = cg[0], nst = cg[1], seg = cg[2];
+        const int n4 = cg[0], nst = cg[1];
         const float4* s4 = reinterpret_cast<const float4*>(L.s + L.col0 + kc * L.kc);
         float2 acc2[kTmaRows];
 #pragma unroll
         for (int q = 0; q < kTmaRows; ++q) acc2[q] = make_float2(0.0f, 0.0f);
         for (int t = 0; t < nst; ++t, ++consumed) {
             const int st = consumed % kTmaStages;
-            const int e0 = t * seg, cnt = min(seg, n4 - e0);
+            const int e0 = t * kTmaSeg, cnt = min(kTmaSeg, n4 - e0);
+            const bool full = cnt == kTmaSeg;
             float4 sv[kTmaSeg / 32];
+            if constexpr (DT == kReconF32) {
+                // float32: the slopes of all four vectors are loaded before the wait
 #pragma unroll
-            for (int j = 0; j < kTmaSeg / 32; ++j) {
-                const int e = lane + 32 * j;
-                sv[j] = e < cnt ? __ldg(s4 + e0 + e) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                for (int j = 0; j < kTmaSeg / 32; ++j) {
+                    const int e = lane + 32 * j;
+                    if (full || e < cnt) sv[j] = __ldg(s4 + e0 + e);
+                }
             }
             if (!mbar_wait_bounded(&sm.bar[warp][st], (parity >> st) & 1u)) {
                 // record the failure, let the copies still in flight land (bounded), stop the warp
@@ -221,21 +327,14 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
                 return;
             }
             parity ^= 1u << st;
-            const float4* ring = sm.ring[warp][st];
-            float4 rv[kTmaSeg / 32][kTmaRows];
-#pragma unroll
-            for (int j = 0; j < kTmaSeg / 32; ++j) {
-                const int e = lane + 32 * j;
-#pragma unroll
-                for (int q = 0; q < kTmaRows; ++q)
-                    rv[j][q] = e < cnt ? ring[q * cnt + e] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            }
+            const uint4* ring = sm.ring[warp][st];
+            uint4 rv[kTmaSeg / 32][kTmaRows];
+            if (full) stage_load<true>(ring, lane, cnt, rv);
+            else stage_load<false>(ring, lane, cnt, rv);
             __syncwarp();  // every lane has read the slot before it is refilled
             if (lane == 0 && !p_done) issue_next(st);
-#pragma unroll
-            for (int j = 0; j < kTmaSeg / 32; ++j)
-#pragma unroll
-                for (int q = 0; q < kTmaRows; ++q) acc2[q] = dot4x2(rv[j][q], sv[j], acc2[q]);
+            if (full) stage_fma<DT, true>(rv, sv, s4, e0, lane, cnt, acc2);
+            else stage_fma<DT, false>(rv, sv, s4, e0, lane, cnt, acc2);
         }
         float acc[kTmaRows];
 #pragma unroll
@@ -250,52 +349,131 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
             const int row0 = rq * kTmaRows;
 #pragma unroll
             for (int q = 0; q < kTmaRows; ++q)
-                if (row0 + q < L.n_cmd) out[row0 + q] = acc[q];
+                if (row0 + q < L.n_cmd) out[row0 + q] = DT == kReconE4M3 ? acc[q] * L.scale[row0 + q] : acc[q];
         }
     }
 }
 
-// Re-tiling: one thread per float4 of the slice in the source layout (rows x chunk columns).
-__global__ void recon_tile_kernel(const float4* __restrict__ src, long long ld4, ReconLaunch L) {
-    const long long n4_slice = (long long)(L.kc / 4) * ((L.len + L.kc - 1) / L.kc);
-    const long long total = (long long)L.n_rq * kTmaRows * n4_slice;
+// 16 consecutive float32 elements of row r from column c (zero at and beyond column c_end)
+__device__ __forceinline__ void load16(const float* row, int c, int c_end, float* x, int n) {
+    for (int i = 0; i < n; ++i) x[i] = (c + i < c_end) ? row[c + i] : 0.0f;
+}
+
+// one 16-byte vector of codes from n = 16 / esize float32 elements
+__device__ __forceinline__ uint4 encode_vec(int dtype, const float* x, float scale) {
+    uint4 v;
+    if (dtype == kReconF32) {
+        v = make_uint4(__float_as_uint(x[0]), __float_as_uint(x[1]), __float_as_uint(x[2]), __float_as_uint(x[3]));
+    } else if (dtype == kReconBF16) {
+        v = make_uint4(f32x2_to_bf16x2(x[0], x[1]), f32x2_to_bf16x2(x[2], x[3]), f32x2_to_bf16x2(x[4], x[5]),
+                       f32x2_to_bf16x2(x[6], x[7]));
+    } else {
+        float y[16];
+        for (int i = 0; i < 16; ++i) y[i] = __fdiv_rn(x[i], scale);
+        v = make_uint4(f32x4_to_e4m3x4(y[0], y[1], y[2], y[3]), f32x4_to_e4m3x4(y[4], y[5], y[6], y[7]),
+                       f32x4_to_e4m3x4(y[8], y[9], y[10], y[11]), f32x4_to_e4m3x4(y[12], y[13], y[14], y[15]));
+    }
+    return v;
+}
+
+// Re-tiling: one thread per 16-byte vector of the slice (rows x chunk vectors); columns at or
+// beyond the slice's end are stored as zeros.
+__global__ void recon_tile_kernel(const float* __restrict__ src, long long ld, ReconLaunch L) {
+    const int epv = 16 / recon_esize(L.dtype);
+    const int kcv = L.kc / epv;
+    const int n_chunks = (L.len + L.kc - 1) / L.kc;
+    const long long nv_slice = (long long)kcv * n_chunks;
+    const long long total = (long long)L.n_rq * kTmaRows * nv_slice;
+    float x[16];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long r = i / n4_slice;
-        const int c4 = (int)(i - r * n4_slice);           // float4 column inside the slice
-        const int kc = c4 / (L.kc / 4), e4 = c4 - kc * (L.kc / 4);
-        int n4, nst, seg;
-        chunk_geom(L, kc, n4, nst, seg);
-        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (e4 < n4) v = src[r * ld4 + L.col0 / 4 + c4];
-        else continue;                                     // padding of a short last chunk
-        const int t = e4 / seg, e = e4 - t * seg;
-        const int cnt = min(seg, n4 - t * seg);
+        const long long r = i / nv_slice;
+        const int cv = (int)(i - r * nv_slice);           // vector column inside the slice
+        const int kc = cv / kcv, e4 = cv - kc * kcv;
+        int n4, nst;
+        chunk_geom(L, kc, n4, nst);
+        if (e4 >= n4) continue;                            // padding of a short last chunk
+        const float* row = src + r * ld + L.col0;
+        load16(row, kc * L.kc + e4 * epv, L.len, x, epv);
+        const float sc = (L.dtype == kReconE4M3) ? L.scale[r] : 1.0f;
+        const int t = e4 / kTmaSeg, e = e4 - t * kTmaSeg;
+        const int cnt = min(kTmaSeg, n4 - t * kTmaSeg);
         const int rq = (int)(r / kTmaRows), q = (int)(r % kTmaRows);
-        float4* dst = reinterpret_cast<float4*>(const_cast<float*>(L.R) + L.base) +
-                      ((long long)kc * L.n_rq + rq) * (long long)L.kc + (long long)kTmaRows * seg * t + q * cnt + e;
-        *dst = v;
+        uint4* dst = reinterpret_cast<uint4*>(const_cast<unsigned char*>(L.R) + L.base) +
+                     ((long long)kc * L.n_rq + rq) * (long long)kTmaRows * kcv + (long long)kTmaRows * kTmaSeg * t +
+                     q * cnt + e;
+        *dst = encode_vec(L.dtype, x, sc);
     }
 }
 
+// per-row scale for E4M3: fl(max |R_r.| / 448), 1 for an all-zero row
+__global__ void recon_scale_kernel(const float* __restrict__ src, int cols, int ld, float* scale) {
+    const long long r = blockIdx.x;
+    float m = 0.0f;
+    for (int j = threadIdx.x; j < cols; j += blockDim.x) m = fmaxf(m, fabsf(src[r * ld + j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmaxf(a, red[w]);
+        scale[r] = a > 0.0f ? __fdiv_rn(a, 448.0f) : 1.0f;
+    }
+}
+
+// row-major codes [rows][cols]: one thread per 16-byte vector of codes (cols a multiple of the
+// vector's element count, checked by the caller) 
+__global__ void quantize_rows_kernel(const float* __restrict__ src, int rows, int cols, int ld, int dtype,
+                                     uint4* out, const float* scale) {
+    const int epv = 16 / recon_esize(dtype);
+    const int vpr = cols / epv;
+    const long long total = (long long)rows * vpr;
+    float x[16];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / vpr;
+        const int v = (int)(i - r * vpr);
+        load16(src + r * ld, v * epv, cols, x, epv);
+        out[i] = encode_vec(dtype, x, dtype == kReconE4M3 ? scale[r] : 1.0f);
+    }
+}
+
+// c += g sum_k partial[k][row]: eight lanes per row, lane m adds slots m, m + 8, ... (all its
+// loads in flight at once), then a fixed shuffle tree; deterministic
 __global__ void recon_reduce_kernel(ReduceLaunch L) {
-    int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row == 0 && L.st) L.st->k_next = L.st->k + 1;
-    if (row >= L.n_cmd) return;
-    float acc = 0.0f;
-    for (int kc = 0; kc < L.n_chunks; ++kc) acc += L.partial[(size_t)kc * L.n_cmd + row];
-    L.c[row] = fmaf(L.gain, acc, L.c[row]);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0 && L.st) L.st->k_next = L.st->k + 1;
+    const int row = t >> 3, m = t & 7;
+    float a = 0.0f;
+    if (row < L.n_cmd) {
+#pragma unroll 4
+        for (int k = m; k < L.n_chunks; k += 8) a += L.partial[(size_t)k * L.n_cmd + row];
+    }
+    a += __shfl_xor_sync(0xffffffffu, a, 4);
+    a += __shfl_xor_sync(0xffffffffu, a, 2);
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    if (m == 0 && row < L.n_cmd) L.c[row] = fmaf(L.gain, a, L.c[row]);
 }
 
 }  // namespace
 
-long long recon_slice_floats(int n_rq, int len, int kc) {
+long long recon_slice_bytes(int n_rq, int len, int kc, int dtype) {
     const long long chunks = (len + kc - 1) / kc;
-    return chunks * n_rq * (long long)kTmaRows * kc;
+    return chunks * n_rq * (long long)kTmaRows * kc * recon_esize(dtype);
 }
 
 cudaError_t recon_prepare() {
-    return cudaFuncSetAttribute(recon_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TmaSmem));
+    cudaError_t e = cudaFuncSetAttribute(recon_tma_kernel<kReconF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(TmaSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(recon_tma_kernel<kReconBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(TmaSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(recon_tma_kernel<kReconE4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(TmaSmem));
+    return e;
 }
 
 cudaError_t launch_recon(const ReconLaunch& L, cudaStream_t s) {
@@ -304,18 +482,34 @@ cudaError_t launch_recon(const ReconLaunch& L, cudaStream_t s) {
     const int n_items = L.n_rq * ((L.len + L.kc - 1) / L.kc);
     const int need = (n_items + kTmaWarps - 1) / kTmaWarps;
     int ctas = (L.max_ctas > 0 && L.max_ctas < need) ? L.max_ctas : need;
-    recon_tma_kernel<<<(unsigned)ctas, kTmaWarps * 32, sizeof(TmaSmem), s>>>(L);
+    if (L.dtype == kReconF32) recon_tma_kernel<kReconF32><<<(unsigned)ctas, kTmaWarps * 32, sizeof(TmaSmem), s>>>(L);
+    else if (L.dtype == kReconBF16) recon_tma_kernel<kReconBF16><<<(unsigned)ctas, kTmaWarps * 32, sizeof(TmaSmem), s>>>(L);
+    else if (L.dtype == kReconE4M3) recon_tma_kernel<kReconE4M3><<<(unsigned)ctas, kTmaWarps * 32, sizeof(TmaSmem), s>>>(L);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recon_scales(const float* src, int rows, int cols, int ld, float* scale, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    recon_scale_kernel<<<(unsigned)rows, 256, 0, s>>>(src, cols, ld, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_rows(const float* src, int rows, int cols, int ld, int dtype, void* out,
+                                 const float* scale, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    quantize_rows_kernel<<<2048, 256, 0, s>>>(src, rows, cols, ld, dtype, reinterpret_cast<uint4*>(out), scale);
     return cudaGetLastError();
 }
 
 cudaError_t launch_recon_tile(const float* src, int ld, const ReconLaunch& L, cudaStream_t s) {
     if (L.len <= 0) return cudaSuccess;
-    recon_tile_kernel<<<2048, 256, 0, s>>>(reinterpret_cast<const float4*>(src), ld / 4, L);
+    recon_tile_kernel<<<2048, 256, 0, s>>>(src, ld, L);
     return cudaGetLastError();
 }
 
 cudaError_t launch_recon_reduce(const ReduceLaunch& L, cudaStream_t s) {
-    int n = L.n_cmd > 0 ? L.n_cmd : 1;
+    const long long n = 8LL * (L.n_cmd > 0 ? L.n_cmd : 1);
     recon_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L);
     return cudaGetLastError();
 }

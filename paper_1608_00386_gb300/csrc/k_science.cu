@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) sci_field_kernel(SciLaunch L) {
     const int i0 = (tile % tiles_x) * 8, j0 = (tile / tiles_x) * 8;
     const int n_grids = L.ctx.n_grids;
     const GridView* V = L.ctx.views + (long long)L.view * n_grids;
-    tile_entries(V, n_grids, L.ctx.st->k, i0, j0, 8, s_ex[warp], s_ey[warp], lane, 32);
+    tile_entries<8>(V, n_grids, L.ctx.st->k, i0, j0, s_ex[warp], s_ey[warp], lane, 32);
     __syncwarp();
     float sr = 0.0f, si = 0.0f;
     const int x = lane & 7;

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
         AxisEnt* s_ex = s_u[warp].e[0];
         AxisEnt* s_ey = s_u[warp].e[1];
 
-        tile_entries(V, n_grids, k, i0, j0, NPX, s_ex, s_ey, lane, 32);
+        tile_entries<NPX>(V, n_grids, k, i0, j0, s_ex, s_ey, lane, 32);
         if (lane < n_grids) {
             GridMeta gm;
             gm.data = V[lane].data;
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kFftThreads) wfs_fft_kernel(WfsLaunch L) {
     const GridView* V = L.ctx.views + (long long)sd.wfs * n_grids;
     const long long k = L.ctx.st->k;
 
-    tile_entries(V, n_grids, k, i0, j0, NPX, ex, ey, tid, NT);
+    tile_entries<NPX>(V, n_grids, k, i0, j0, ex, ey, tid, NT);
     if (L.ctx.noise) fill_recip(recip, tid, NT);
     for (int q = tid; q < NFFT; q += NT) {
         float s, c;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(256) wfs_phase_kernel(Ctx ctx, int wi, int N, 
     if (tile >= tiles_x * tiles_x) return;
     const int i0 = (tile % tiles_x) * 8, j0 = (tile / tiles_x) * 8;
     const GridView* V = ctx.views + (long long)wi * ctx.n_grids;
-    tile_entries(V, ctx.n_grids, ctx.st->k, i0, j0, 8, s_ex[warp], s_ey[warp], lane, 32);
+    tile_entries<8>(V, ctx.n_grids, ctx.st->k, i0, j0, s_ex[warp], s_ey[warp], lane, 32);
     __syncwarp();
     for (int q = lane; q < 64; q += 32) {
         int x = q % 8, y = q / 8;

@@ -122,7 +122,9 @@ struct mcao_sim {
     int n_grids = 0;
 
     // reconstructor
-    float* d_R = nullptr;
+    unsigned char* d_R = nullptr;         // stage-tiled reconstructor (bytes, element format r_dtype)
+    float* d_rscale = nullptr;            // per-row scales (FP8 E4M3)
+    int r_dtype = 0;
     int rows_pad = 0;
     float* d_c = nullptr;
     float* d_partial = nullptr;
@@ -330,6 +332,7 @@ mcao_status rebuild_views(mcao_sim* S) {
             gv.vx = to_q32(dt * g.vx / g.pixel);
             gv.vy = to_q32(dt * g.vy / g.pixel);
             gv.sign = g.sign;
+            gv.inv_n = (float)(1.0 / (double)g.n);
             out.push_back(gv);
         }
     }
@@ -535,7 +538,7 @@ void destroy_all(mcao_sim* S) {
     for (auto p : S->d_layer_owned) cudaFree(p);
     S->d_layer_owned.clear();
     dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
-    dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_c); dfree(S->d_partial);
+    dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_rscale); dfree(S->d_c); dfree(S->d_partial);
     dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err); dfree(S->d_work);
     for (auto e : S->prof_pool) cudaEventDestroy(e);
     for (auto e : S->ev_pool) cudaEventDestroy(e);
@@ -756,8 +759,8 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     CKC(cudaMemcpyAsync(S->d_wfs, wdev.data(), sizeof(WfsDev) * wdev.size(), cudaMemcpyHostToDevice, S->s0));
     CKC(dalloc(&S->d_slopes, ns));
     CKC(cudaMemsetAsync(S->d_slopes, 0, sizeof(float) * std::max(ns, 1), S->s0));
-    CKC(dalloc(&S->d_slopes_pad, S->ld));
-    CKC(cudaMemsetAsync(S->d_slopes_pad, 0, sizeof(float) * S->ld, S->s0));
+    CKC(dalloc(&S->d_slopes_pad, (size_t)S->ld + kSlopePadTail));
+    CKC(cudaMemsetAsync(S->d_slopes_pad, 0, sizeof(float) * ((size_t)S->ld + kSlopePadTail), S->s0));
     CKC(dalloc(&S->d_sref, ns));
     CKC(cudaMemsetAsync(S->d_sref, 0, sizeof(float) * std::max(ns, 1), S->s0));
     if (cfg->keep_frames) {
@@ -1000,7 +1003,8 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
                                     int dtype, int on_device) {
     if (!S) return MCAO_E_INVALID_ARG;
     if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "load the DMs before the reconstructor");
-    if (dtype != MCAO_DTYPE_F32) return fail(S, MCAO_E_UNSUPPORTED, "only MCAO_DTYPE_F32 reconstructors");
+    if (dtype != MCAO_DTYPE_F32 && dtype != MCAO_DTYPE_BF16 && dtype != MCAO_DTYPE_FP8_E4M3)
+        return fail(S, MCAO_E_UNSUPPORTED, "unknown reconstructor dtype %d", dtype);
     if (n_cmd != S->n_cmd || n_slopes != S->n_slopes)
         return fail(S, MCAO_E_SHAPE, "reconstructor is %d x %d, configuration needs %d x %d", n_cmd, n_slopes,
                     S->n_cmd, S->n_slopes);
@@ -1009,7 +1013,9 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     CK(cudaSetDevice(S->device));
     { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     dfree(S->d_R);
+    dfree(S->d_rscale);
     dfree(S->d_partial);
+    S->r_dtype = dtype;
     S->recon_loaded = false;
     S->rows_pad = std::max(1, (n_cmd + kReconRowBlock - 1) / kReconRowBlock) * kReconRowBlock;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1065,26 +1071,46 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
         L.n_rq = S->rows_pad / kReconRows;
         L.col0 = F.rcol0;
         L.len = len;
+        // chunk width: at most kReconChunk columns, a multiple of 16, and (trying up to 8 more
+        // chunks) such that each chunk's last stage holds 0 or at least half a stage of vectors
+        const int epv = 16 / recon_esize(dtype);
         int nch = (len + kReconChunk - 1) / kReconChunk;
-        int kc = (len + nch - 1) / nch;
-        L.kc = (kc + 3) / 4 * 4;
+        auto chunk_cols = [&](int n) { return ((len + n - 1) / n + 15) / 16 * 16; };
+        auto ok = [&](int w) {
+            const int rem_full = (w / epv) % kReconSeg;
+            const int last = len - (len + w - 1) / w * w + w;
+            const int rem_last = ((last + epv - 1) / epv) % kReconSeg;
+            return (rem_full == 0 || rem_full >= kReconSeg / 2) && (rem_last == 0 || rem_last >= kReconSeg / 2);
+        };
+        for (int extra = 0; extra <= 8; ++extra)
+            if (ok(chunk_cols(nch + extra))) {
+                nch += extra;
+                break;
+            }
+        L.kc = chunk_cols(nch);
         nch = (len + L.kc - 1) / L.kc;
+        L.dtype = dtype;
         L.chunk0 = chunks;
         L.base = tiled;
         L.s = S->d_slopes_pad;
         L.max_ctas = S->sm_count;  // one resident block per SM beside the sensing kernels
-        L.work = S->d_work + S->wfs.size() + S->slices.size();
         L.err = S->d_err;
         chunks += nch;
-        tiled += recon_slice_floats(L.n_rq, L.len, L.kc);
+        tiled += recon_slice_bytes(L.n_rq, L.len, L.kc, dtype);
         S->slices.push_back(L);
         S->slice_wfs.push_back(u);
     }
+    for (size_t i = 0; i < S->slices.size(); ++i) S->slices[i].work = S->d_work + S->wfs.size() + i;
     // 3) stage-tiled copy used by the product (see ReconLaunch)
-    if (e == cudaSuccess) e = dalloc(&S->d_R, (size_t)std::max<long long>(tiled, 4));
-    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_R, 0, sizeof(float) * (size_t)std::max<long long>(tiled, 4), S->s0);
+    if (e == cudaSuccess) e = dalloc(&S->d_R, (size_t)std::max<long long>(tiled, 16));
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->d_R, 0, (size_t)std::max<long long>(tiled, 16), S->s0);
+    if (e == cudaSuccess && dtype == MCAO_DTYPE_FP8_E4M3) {
+        e = dalloc(&S->d_rscale, (size_t)S->rows_pad);
+        if (e == cudaSuccess) e = launch_recon_scales(tmp, S->rows_pad, S->ld, S->ld, S->d_rscale, S->s0);
+    }
     for (auto& L : S->slices) {
         L.R = S->d_R;
+        L.scale = S->d_rscale;
         if (e == cudaSuccess) e = launch_recon_tile(tmp, S->ld, L, S->s0);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
@@ -1420,6 +1446,28 @@ mcao_status mcao_get_timeline(mcao_sim* S, int32_t* stage, double* start_ms, dou
             if (step) step[out] = (int32_t)q;
         }
     }
+    return MCAO_OK;
+}
+
+mcao_status mcao_quantize_rows(const float* R, int rows, int cols, int ld, int dtype, void* codes, float* scales,
+                               void* stream, char* err, size_t err_len) {
+    auto bad = [&](mcao_status st, const char* msg) {
+        if (err && err_len) snprintf(err, err_len, "%s", msg);
+        return st;
+    };
+    if (dtype != MCAO_DTYPE_BF16 && dtype != MCAO_DTYPE_FP8_E4M3)
+        return bad(MCAO_E_UNSUPPORTED, "dtype must be MCAO_DTYPE_BF16 or MCAO_DTYPE_FP8_E4M3");
+    if (rows < 0 || cols < 0 || ld < cols) return bad(MCAO_E_INVALID_ARG, "rows, cols >= 0 and ld >= cols required");
+    if (rows == 0 || cols == 0) return MCAO_OK;
+    if (!R || !codes || (dtype == MCAO_DTYPE_FP8_E4M3 && !scales)) return bad(MCAO_E_INVALID_ARG, "null pointer");
+    const int epv = 16 / recon_esize(dtype);
+    if (cols % epv != 0) return bad(MCAO_E_SHAPE, "cols must be a multiple of 8 (BF16) or 16 (FP8 E4M3)");
+    if (reinterpret_cast<uintptr_t>(codes) % 16 != 0) return bad(MCAO_E_SHAPE, "codes must be 16-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (dtype == MCAO_DTYPE_FP8_E4M3) e = launch_recon_scales(R, rows, cols, ld, scales, st);
+    if (e == cudaSuccess) e = launch_quantize_rows(R, rows, cols, ld, dtype, codes, scales, st);
+    if (e != cudaSuccess) return bad(MCAO_E_CUDA, cudaGetErrorString(e));
     return MCAO_OK;
 }
 

@@ -26,7 +26,7 @@ struct GridView {
     long long bp;        // grid samples per pupil sample
     long long vx, vy;    // grid samples per step (0 for DMs)
     float sign;          // +1 layers, -1 DMs (residual = layers - DMs)
-    float pad_;
+    float inv_n;         // 1/n rounded to float (periodic wrap without a hardware divide)
 };
 
 // One wavefront sensor.
@@ -142,32 +142,50 @@ cudaError_t launch_wfs_phase(const Ctx& ctx, int wfs, int N, float* out, cudaStr
 constexpr int kReconRowBlock = 32;   // rows of R are padded to a multiple of this
 constexpr int kReconChunk = 4096;    // maximum slope columns per chunk
 
-// One slice of the reconstructor product: the columns of one WFS's slope block.
+// Element formats of the stored reconstructor (values of MCAO_DTYPE_*): float32; bfloat16;
+// FP8 E4M3 with one float scale per row.  Elements are moved in 16-byte vectors of
+// 16 / element-size elements.
+constexpr int kReconF32 = 0, kReconBF16 = 1, kReconE4M3 = 2;
+__host__ __device__ constexpr int recon_esize(int dtype) { return dtype == kReconF32 ? 4 : dtype == kReconBF16 ? 2 : 1; }
+
+// One slice of the reconstructor product: the columns of one WFS's slope block (or of adjacent
+// sensors sharing one kernel launch).
 // R is held stage-tiled in HBM: for each slice, column chunk kc and row quad rq, a contiguous
-// block of 4 x kc floats; inside it, stage t (seg float4 per row, seg = ceil(n4 / nst),
-// nst = ceil(n4 / 128), n4 = the chunk's float4 count) holds its 4 row segments back to back,
-// so every stage is one contiguous bulk copy of up to 8 KB.
+// block of 4 x kc elements; inside it, stage t (128 vectors per row, fewer in the chunk's last
+// stage; nv = the chunk's 16-byte vector count per row) holds its 4 row segments back to back,
+// so every stage is one contiguous bulk copy of up to 8 KB.  The host picks the chunk width so
+// that a chunk's last stage is not tiny (at least half a stage where it can).
 struct ReconLaunch {
-    const float* R;     // stage-tiled reconstructor
-    long long base;     // first float of this slice in R
+    const unsigned char* R;   // stage-tiled reconstructor
+    long long base;     // first byte of this slice in R
+    int dtype;          // kReconF32 / kReconBF16 / kReconE4M3
     int n_cmd, n_rq;    // rows, row quads (rows padded to a multiple of 4)
     int col0;           // first column of the slice in the padded slope layout (multiple of 4)
     int len;            // columns in the slice
-    int kc;             // columns per chunk (multiple of 4)
+    int kc;             // columns per chunk (multiple of 16)
     int chunk0;         // first partial-sum slot of the slice
-    const float* s;     // slopes in the padded layout (zeros in the padding)
+    const float* s;     // slopes in the padded layout (zeros in the padding, 16 spare floats)
+    const float* scale; // per-row scales (kReconE4M3), else null
     float* partial;     // [n_chunks][n_cmd]
     int max_ctas;       // grid size cap (0: enough blocks for every item)
     unsigned int* work; // item counter, zero when the launch starts
     int* err;           // set to a nonzero code if a bounded wait gives up
 };
 constexpr int kReconRows = 4;        // rows per work item (row quad)
-constexpr int kReconSeg = 128;       // float4 per row and stage (at most)
-long long recon_slice_floats(int n_rq, int len, int kc);   // floats of one slice in the tiled R
+constexpr int kReconSeg = 128;       // 16-byte vectors per row and stage (at most)
+constexpr int kSlopePadTail = 16;    // zero floats after the padded slopes (a vector may run past)
+long long recon_slice_bytes(int n_rq, int len, int kc, int dtype);   // bytes of one slice in the tiled R
 cudaError_t recon_prepare();   // kernel attributes (outside stream capture)
 cudaError_t launch_recon(const ReconLaunch& L, cudaStream_t s);
-// Re-lay the row-major, column-padded R [rows][ld] (slice columns from col0) into the tiled slice.
+// Per-row scales of the float32 R [rows][ld] (first cols columns) for kReconE4M3:
+// max |R_r.| / 448 (1 for a zero row).
+cudaError_t launch_recon_scales(const float* src, int rows, int cols, int ld, float* scale, cudaStream_t s);
+// Re-lay the row-major, column-padded float32 R [rows][ld] (slice columns from col0) into the
+// tiled slice, converting to the slice's element format.
 cudaError_t launch_recon_tile(const float* src, int ld, const ReconLaunch& L, cudaStream_t s);
+// Row-major codes [rows][cols] of R [rows][ld] in a reduced format (and its scales).
+cudaError_t launch_quantize_rows(const float* src, int rows, int cols, int ld, int dtype, void* out,
+                                 const float* scale, cudaStream_t s);
 constexpr int kErrReconTimeout = 1;
 
 struct ReduceLaunch {

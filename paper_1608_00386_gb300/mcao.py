@@ -28,8 +28,10 @@ EXPORTS = [
     "mcao_query", "mcao_get_step_index", "mcao_get_slopes", "mcao_get_commands", "mcao_set_commands",
     "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
-    "mcao_reconstruct_noalloc", "mcao_get_timeline",
+    "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows",
 ]
+
+DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
 
 
 class McaoError(RuntimeError):
@@ -107,6 +109,7 @@ def lib():
         "mcao_get_profile": [vp, vp, vp, C.c_int, C.POINTER(C.c_int64)],
         "mcao_reconstruct_noalloc": [vp, C.c_int, C.c_int, C.c_int, vp, vp, C.c_float, vp, C.c_char_p, C.c_size_t],
         "mcao_get_timeline": [vp, vp, vp, vp, vp, C.c_size_t, C.POINTER(C.c_size_t)],
+        "mcao_quantize_rows": [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_char_p, C.c_size_t],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -207,7 +210,7 @@ class Sim:
                          v.ctypes.data_as(C.POINTER(C.c_uint8)), d["surf_n"], d["surf_dx"])
         self._ck(lib().mcao_load_dms(self.h, len(dms), arr))
 
-    def load_reconstructor(self, R, s_ref=None):
+    def load_reconstructor(self, R, s_ref=None, dtype: int = DTYPE_F32):
         if not hasattr(R, "data_ptr"):
             R = np.ascontiguousarray(R, dtype=np.float32)
         addr, k, dev = _addr(R)
@@ -218,7 +221,7 @@ class Sim:
             sp, ks, sdev = _addr(s_ref)
             if sdev != dev:
                 raise ValueError("R and s_ref must both be on the host or both on the device")
-        self._ck(lib().mcao_load_reconstructor(self.h, R.shape[0], R.shape[1], addr, sp, 0, dev))
+        self._ck(lib().mcao_load_reconstructor(self.h, R.shape[0], R.shape[1], addr, sp, int(dtype), dev))
 
     # ---------------------------------------------------------------- loop
     def step(self, n: int = 1):
@@ -339,10 +342,32 @@ def reconstruct_noalloc(R, s, c, gain: float, stream=None) -> None:
         raise McaoError(st, buf.value.decode())
 
 
-def make_sim(cfg: dict, screens, R, s_ref=None, keep_frames: bool = False, stream=None) -> Sim:
-    """Create a simulation and load the atmosphere, the DMs and the reconstructor."""
+def make_sim(cfg: dict, screens, R, s_ref=None, keep_frames: bool = False, stream=None,
+             r_dtype: int = DTYPE_F32) -> Sim:
+    """Create a simulation and load the atmosphere, the DMs and the reconstructor (stored in the
+    element format r_dtype)."""
     s = Sim(cfg, keep_frames=keep_frames, stream=stream)
     s.load_atmosphere(screens)
     s.load_dms()
-    s.load_reconstructor(R, s_ref)
+    s.load_reconstructor(R, s_ref, dtype=r_dtype)
     return s
+
+
+def quantize_rows(R, dtype: int, stream=None):
+    """(codes, scales) of a CUDA float32 matrix R [rows][cols] in a reduced format, computed on the
+    device by mcao_quantize_rows: uint16 bfloat16 codes, or uint8 FP8 E4M3 codes with a float32
+    scale per row (scales is None for bfloat16)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    rows, cols = R.shape
+    codes = torch.empty((rows, cols), dtype=torch.int16 if dtype == DTYPE_BF16 else torch.uint8, device=R.device)
+    scales = torch.empty(rows, dtype=torch.float32, device=R.device) if dtype == DTYPE_FP8_E4M3 else None
+    err = C.create_string_buffer(256)
+    st = lib().mcao_quantize_rows(C.c_void_p(R.data_ptr()), rows, cols, R.stride(0), int(dtype),
+                                  C.c_void_p(codes.data_ptr()), C.c_void_p(scales.data_ptr() if scales is not None else 0),
+                                  C.c_void_p(ptr), err, 256)
+    if st != 0:
+        raise McaoError(st, err.value.decode())
+    return codes, scales
