@@ -104,6 +104,11 @@ typedef struct {
     const mcao_wfs* wfs;
     int n_sci;
     const mcao_science* sci;
+    int n_real;               /* independent realizations advanced together (>= 1): each has
+                                 its own screens, commands, noise key seed + r, slopes and
+                                 Strehl / PSF accumulators; geometry and the reconstructor are
+                                 shared.  With n_real > 1 one step forms the product for all
+                                 realizations at once as a matrix product R S (cuBLAS) */
 } mcao_config;
 
 /* A periodic n x n phase screen with square samples of pixel_m metres, at altitude alt_m,
@@ -139,7 +144,8 @@ typedef enum {
     MCAO_Q_WFS_PHASE = 4,     /* pupil samples of WFS `index`                                 */
     MCAO_Q_DM_SURFACE = 5,    /* surface samples of DM `index`                                */
     MCAO_Q_PSF = 6,           /* PSF pixels of science direction `index`                      */
-    MCAO_Q_STATE = 7          /* bytes of a checkpoint                                        */
+    MCAO_Q_STATE = 7,         /* bytes of a checkpoint                                        */
+    MCAO_Q_REALIZATIONS = 8   /* realizations advanced together (cfg.n_real)                  */
 } mcao_query_kind;
 
 /* Create a simulation for a configuration ("Numerical Simulation Tool": the high-level system
@@ -280,6 +286,13 @@ mcao_status mcao_reconstruct_noalloc(const float* R, int n_cmd, int n_slopes, in
  * codes not 16-byte aligned), MCAO_E_UNSUPPORTED (dtype), MCAO_E_CUDA. */
 mcao_status mcao_quantize_rows(const float* R, int rows, int cols, int ld, int dtype, void* codes,
                                float* scales, void* stream, char* err, size_t err_len);
+
+/* Select the realization (0 <= r < n_real, default 0) that later calls address: the screens
+ * given to mcao_load_atmosphere, and the slopes, commands (get and set), WFS phase, DM
+ * surfaces, frames and PSF / Strehl read back.  mcao_step, mcao_reset_psf and the checkpoint
+ * cover every realization.  No counterpart in the paper: its tool runs one realization per
+ * process.  Errors: MCAO_E_INVALID_ARG (r out of range). */
+mcao_status mcao_set_realization(mcao_sim* sim, int r);
 
 /* Stages timed by the profiler. */
 enum {

@@ -2,7 +2,8 @@
 
 Every translation unit under csrc/ is compiled by nvcc in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and linked into
-``paper_1608_00386_gb300/_build/libmcao.so``.  Nothing is installed outside the repository.
+``paper_1608_00386_gb300/_build/libmcao.so`` (linked against cuBLAS, used for the batched
+realizations' matrix product).  Nothing is installed outside the repository.
 """
 from __future__ import annotations
 
@@ -64,8 +65,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         results = list(ex.map(compile_one, _sources()))
     objs = [o for o, _ in results]
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"], capture_output=True,
-                       text=True)
+    r = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lcublas"],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -18,10 +18,12 @@ __global__ void __launch_bounds__(256) dm_surface_kernel(DmLaunch L) {
     __shared__ float s_Gx[kT][kB + 1];
     __shared__ float s_Gy[kT][kB + 1];
     __shared__ float s_T[kB][kT];
-    if (blockIdx.x == 0) {
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
         if (threadIdx.x == 0 && L.st) L.st->k = L.st->k_next;
         for (int i = threadIdx.x; i < L.n_work; i += blockDim.x) L.work[i] = 0u;
     }
+    const int real = blockIdx.y;   // realization
+    const float* cmd = L.c + (long long)real * L.n_cmd;
     int t = blockIdx.x;
     int m = 0;
     while (m + 1 < L.n_dm && t >= L.tile_start[m + 1]) ++m;
@@ -39,7 +41,7 @@ __global__ void __launch_bounds__(256) dm_surface_kernel(DmLaunch L) {
     for (int bb = wid; bb < nb; bb += 8)
         for (int aa = lane; aa < na; aa += 32) {
             int idx = L.act_map[d.map_off + (long long)(by.x + bb) * d.nx + bx.x + aa];
-            s_C[bb][aa] = (idx >= 0) ? L.c[idx] : 0.0f;
+            s_C[bb][aa] = (idx >= 0) ? cmd[idx] : 0.0f;
         }
     for (int ii = tid >> 3; ii < kT; ii += 32) {
         const int i = i0 + ii;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(256) dm_surface_kernel(DmLaunch L) {
     }
     const int i = i0 + ii;
     if (i < n) {
-        float* out = L.surf + d.surf_off + i;
+        float* out = L.surf + real * L.surf_stride + d.surf_off + i;
         const float acc[4] = {acc0, acc1, acc2, acc3};
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -88,7 +90,7 @@ __global__ void begin_step_kernel(StepState* st, unsigned int* work, int n_work)
 
 cudaError_t launch_dm_surfaces(const DmLaunch& L, cudaStream_t s) {
     if (L.n_dm <= 0) return launch_begin_step(L.st, L.work, L.n_work, s);
-    dm_surface_kernel<<<(unsigned)L.tile_start[L.n_dm], 256, 0, s>>>(L);
+    dm_surface_kernel<<<dim3((unsigned)L.tile_start[L.n_dm], (unsigned)(L.n_real > 0 ? L.n_real : 1)), 256, 0, s>>>(L);
     return cudaGetLastError();
 }
 

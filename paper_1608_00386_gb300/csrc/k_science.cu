@@ -15,9 +15,22 @@ namespace {
 
 constexpr int kRowsPerBlock = 4;
 
-__global__ void __launch_bounds__(256) sci_field_kernel(SciLaunch L) {
+// per-realization views of the launch (grid y = realization)
+__device__ __forceinline__ SciLaunch sci_for_real(const SciLaunch& L0, int r) {
+    SciLaunch L = L0;
+    L.field += (long long)r * L.N * L.N;
+    L.ft += (long long)r * L.M * L.N;
+    L.psf_t += (long long)r * L.M * L.M;
+    L.sr_part += (long long)r * L.n_tiles;
+    L.acc += (long long)r * L.acc_stride;
+    L.ctx.views += r * L.ctx.view_stride;
+    return L;
+}
+
+__global__ void __launch_bounds__(256) sci_field_kernel(SciLaunch L0) {
     __shared__ AxisEnt s_ex[8][kMaxEntries * 8];
     __shared__ AxisEnt s_ey[8][kMaxEntries * 8];
+    const SciLaunch L = sci_for_real(L0, blockIdx.y);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_x = L.N / 8;
     const int tile = blockIdx.x * 8 + warp;
@@ -50,7 +63,8 @@ __device__ __forceinline__ bool psf_step(const SciLaunch& L) {
     return L.psf_every > 0 && (L.ctx.st->k % L.psf_every) == 0;
 }
 
-__global__ void __launch_bounds__(256) sci_rows_kernel(SciLaunch L) {
+__global__ void __launch_bounds__(256) sci_rows_kernel(SciLaunch L0) {
+    const SciLaunch L = sci_for_real(L0, blockIdx.y);
     extern __shared__ float4 smem_raw[];
     float2* A = reinterpret_cast<float2*>(smem_raw);
     float2* B = A + kRowsPerBlock * L.M;
@@ -103,7 +117,8 @@ __global__ void __launch_bounds__(256) sci_rows_kernel(SciLaunch L) {
     }
 }
 
-__global__ void __launch_bounds__(256) sci_cols_kernel(SciLaunch L) {
+__global__ void __launch_bounds__(256) sci_cols_kernel(SciLaunch L0) {
+    const SciLaunch L = sci_for_real(L0, blockIdx.y);
     if (!psf_step(L)) return;
     extern __shared__ float4 smem_raw[];
     float2* A = reinterpret_cast<float2*>(smem_raw);
@@ -131,7 +146,8 @@ __global__ void __launch_bounds__(256) sci_cols_kernel(SciLaunch L) {
 constexpr int kCtRows = 2;
 
 template <int M>
-__global__ void __launch_bounds__(256) sci_rows_ct(SciLaunch L) {
+__global__ void __launch_bounds__(256) sci_rows_ct(SciLaunch L0) {
+    const SciLaunch L = sci_for_real(L0, blockIdx.y);
     extern __shared__ float4 smem_raw[];
     float2* A = reinterpret_cast<float2*>(smem_raw);
     float2* B = A + kCtRows * M;
@@ -181,7 +197,8 @@ __global__ void __launch_bounds__(256) sci_rows_ct(SciLaunch L) {
 }
 
 template <int M>
-__global__ void __launch_bounds__(256) sci_cols_ct(SciLaunch L) {
+__global__ void __launch_bounds__(256) sci_cols_ct(SciLaunch L0) {
+    const SciLaunch L = sci_for_real(L0, blockIdx.y);
     if (!psf_step(L)) return;
     extern __shared__ float4 smem_raw[];
     float2* A = reinterpret_cast<float2*>(smem_raw);
@@ -221,13 +238,13 @@ cudaError_t ct_prepare() {
 
 template <int M>
 cudaError_t ct_rows(const SciLaunch& L, cudaStream_t s) {
-    sci_rows_ct<M><<<(unsigned)((L.N + kCtRows - 1) / kCtRows), 256, ct_smem<M>(), s>>>(L);
+    sci_rows_ct<M><<<dim3((unsigned)((L.N + kCtRows - 1) / kCtRows), (unsigned)L.ctx.n_real), 256, ct_smem<M>(), s>>>(L);
     return cudaGetLastError();
 }
 
 template <int M>
 cudaError_t ct_cols(const SciLaunch& L, cudaStream_t s) {
-    sci_cols_ct<M><<<(unsigned)(M / kCtRows), 256, ct_smem<M>(), s>>>(L);
+    sci_cols_ct<M><<<dim3((unsigned)(M / kCtRows), (unsigned)L.ctx.n_real), 256, ct_smem<M>(), s>>>(L);
     return cudaGetLastError();
 }
 
@@ -246,7 +263,7 @@ cudaError_t set_smem(const void* fn, size_t bytes) {
 
 cudaError_t launch_sci_field(const SciLaunch& L, cudaStream_t s) {
     int tiles = (L.N / 8) * (L.N / 8);
-    sci_field_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(L);
+    sci_field_kernel<<<dim3((unsigned)((tiles + 7) / 8), (unsigned)L.ctx.n_real), 256, 0, s>>>(L);
     return cudaGetLastError();
 }
 
@@ -274,7 +291,7 @@ cudaError_t launch_sci_rows(const SciLaunch& L, cudaStream_t s) {
     MCAO_SCI_CT_SIZES(MCAO_CT_ROWS)
 #undef MCAO_CT_ROWS
     size_t sm = fft_smem_bytes(L.M);
-    sci_rows_kernel<<<(unsigned)((L.N + kRowsPerBlock - 1) / kRowsPerBlock), 256, sm, s>>>(L);
+    sci_rows_kernel<<<dim3((unsigned)((L.N + kRowsPerBlock - 1) / kRowsPerBlock), (unsigned)L.ctx.n_real), 256, sm, s>>>(L);
     return cudaGetLastError();
 }
 
@@ -284,7 +301,7 @@ cudaError_t launch_sci_cols(const SciLaunch& L, cudaStream_t s) {
     MCAO_SCI_CT_SIZES(MCAO_CT_COLS)
 #undef MCAO_CT_COLS
     size_t sm = fft_smem_bytes(L.M);
-    sci_cols_kernel<<<(unsigned)(L.M / kRowsPerBlock), 256, sm, s>>>(L);
+    sci_cols_kernel<<<dim3((unsigned)(L.M / kRowsPerBlock), (unsigned)L.ctx.n_real), 256, sm, s>>>(L);
     return cudaGetLastError();
 }
 

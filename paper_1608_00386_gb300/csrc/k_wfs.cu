@@ -125,14 +125,17 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
         if (lane == 0) v = atomicAdd(L.work, 1u);
         return (int)__shfl_sync(0xffffffffu, v, 0);
     };
-    int sub = L.work ? take() : blockIdx.x * 8 + warp;
+    // items run over (realization, subaperture)
+    const int n_items = L.n_subaps * L.ctx.n_real;
+    int item = L.work ? take() : blockIdx.x * 8 + warp;
     for (;;) {
-        if (sub >= L.n_subaps) break;  // warp-uniform; warp-level sync only from here on
+        if (item >= n_items) break;  // warp-uniform; warp-level sync only from here on
+        const int real = item / L.n_subaps, sub = item - real * L.n_subaps;
         const SubapDev sd = L.subaps[sub];
         const WfsDev& w = L.ctx.wfs[sd.wfs];
         const int i0 = sd.sx * NPX, j0 = sd.sy * NPX;
         const int n_grids = L.ctx.n_grids;
-        const GridView* V = L.ctx.views + (long long)sd.wfs * n_grids;
+        const GridView* V = L.ctx.views + real * L.ctx.view_stride + (long long)sd.wfs * n_grids;
         const long long k = L.ctx.st->k;
         AxisEnt* s_ex = s_u[warp].e[0];
         AxisEnt* s_ey = s_u[warp].e[1];
@@ -282,11 +285,11 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
             float v = lam;
             if (L.ctx.noise) {
                 int n = noise_sample(lam, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
-                                     L.ctx.seed, s_recip);
+                                     L.ctx.seed + real, s_recip);
                 v = (float)n;
-                if (L.frame_out) L.frame_out[w.frame0 + pix0 + o] = n;
+                if (L.frame_out) L.frame_out[real * L.frame_stride + w.frame0 + pix0 + o] = n;
             }
-            if (L.lam_out) L.lam_out[w.frame0 + pix0 + o] = lam;
+            if (L.lam_out) L.lam_out[real * L.frame_stride + w.frame0 + pix0 + o] = lam;
             int my = o / ND, mx = o % ND;
             sv += v;
             sx = fmaf((float)mx - c0, v, sx);
@@ -303,15 +306,17 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
             }
             int ix = w.slope0 + sd.rank, iy = w.slope0 + w.n_valid + sd.rank;
             const float vx = gx - (L.s_ref ? L.s_ref[ix] : 0.0f), vy = gy - (L.s_ref ? L.s_ref[iy] : 0.0f);
-            L.slopes[ix] = vx;
-            L.slopes[iy] = vy;
+            float* slopes = L.slopes + (long long)real * L.slope_stride;
+            slopes[ix] = vx;
+            slopes[iy] = vy;
             if (L.slopes_pad) {
-                L.slopes_pad[w.rcol0 + sd.rank] = vx;
-                L.slopes_pad[w.rcol0 + w.n_valid + sd.rank] = vy;
+                float* pad = L.slopes_pad + (long long)real * L.pad_stride;
+                pad[w.rcol0 + sd.rank] = vx;
+                pad[w.rcol0 + w.n_valid + sd.rank] = vy;
             }
         }
         if (!L.work) break;
-        sub = take();
+        item = take();
         __syncwarp();  // the scratch of this subaperture is read before the next one writes it
     }
 }
@@ -336,11 +341,12 @@ __global__ void __launch_bounds__(kFftThreads) wfs_fft_kernel(WfsLaunch L) {
     float* red = recip + 68;                                       // [3 * NW]
 
     const int tid = threadIdx.x;
-    const SubapDev sd = L.subaps[blockIdx.x];
+    const int real = blockIdx.x / L.n_subaps;   // blocks run over (realization, subaperture)
+    const SubapDev sd = L.subaps[blockIdx.x - real * L.n_subaps];
     const WfsDev& w = L.ctx.wfs[sd.wfs];
     const int i0 = sd.sx * NPX, j0 = sd.sy * NPX;
     const int n_grids = L.ctx.n_grids;
-    const GridView* V = L.ctx.views + (long long)sd.wfs * n_grids;
+    const GridView* V = L.ctx.views + real * L.ctx.view_stride + (long long)sd.wfs * n_grids;
     const long long k = L.ctx.st->k;
 
     tile_entries<NPX>(V, n_grids, k, i0, j0, ex, ey, tid, NT);
@@ -406,11 +412,11 @@ __global__ void __launch_bounds__(kFftThreads) wfs_fft_kernel(WfsLaunch L) {
         float v = lam;
         if (L.ctx.noise) {
             int n = noise_sample(lam, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
-                                 L.ctx.seed, recip);
+                                 L.ctx.seed + real, recip);
             v = (float)n;
-            if (L.frame_out) L.frame_out[w.frame0 + pix0 + o] = n;
+            if (L.frame_out) L.frame_out[real * L.frame_stride + w.frame0 + pix0 + o] = n;
         }
-        if (L.lam_out) L.lam_out[w.frame0 + pix0 + o] = lam;
+        if (L.lam_out) L.lam_out[real * L.frame_stride + w.frame0 + pix0 + o] = lam;
         sv = v;
         sx = ((float)mx - c0) * v;
         sy = ((float)my - c0) * v;
@@ -438,11 +444,13 @@ __global__ void __launch_bounds__(kFftThreads) wfs_fft_kernel(WfsLaunch L) {
         }
         int ix = w.slope0 + sd.rank, iy = w.slope0 + w.n_valid + sd.rank;
         const float vx = gx - (L.s_ref ? L.s_ref[ix] : 0.0f), vy = gy - (L.s_ref ? L.s_ref[iy] : 0.0f);
-        L.slopes[ix] = vx;
-        L.slopes[iy] = vy;
+        float* slopes = L.slopes + (long long)real * L.slope_stride;
+        slopes[ix] = vx;
+        slopes[iy] = vy;
         if (L.slopes_pad) {
-            L.slopes_pad[w.rcol0 + sd.rank] = vx;
-            L.slopes_pad[w.rcol0 + w.n_valid + sd.rank] = vy;
+            float* pad = L.slopes_pad + (long long)real * L.pad_stride;
+            pad[w.rcol0 + sd.rank] = vx;
+            pad[w.rcol0 + w.n_valid + sd.rank] = vy;
         }
     }
 }
@@ -454,7 +462,7 @@ constexpr size_t fft_smem() {
 }
 
 // residual phase on the full pupil grid of one WFS, 8 x 8 tiles, one warp per tile
-__global__ void __launch_bounds__(256) wfs_phase_kernel(Ctx ctx, int wi, int N, float* out) {
+__global__ void __launch_bounds__(256) wfs_phase_kernel(Ctx ctx, int real, int wi, int N, float* out) {
     __shared__ AxisEnt s_ex[8][kMaxEntries * 8];
     __shared__ AxisEnt s_ey[8][kMaxEntries * 8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -462,7 +470,7 @@ __global__ void __launch_bounds__(256) wfs_phase_kernel(Ctx ctx, int wi, int N, 
     const int tile = blockIdx.x * 8 + warp;
     if (tile >= tiles_x * tiles_x) return;
     const int i0 = (tile % tiles_x) * 8, j0 = (tile / tiles_x) * 8;
-    const GridView* V = ctx.views + (long long)wi * ctx.n_grids;
+    const GridView* V = ctx.views + real * ctx.view_stride + (long long)wi * ctx.n_grids;
     tile_entries<8>(V, ctx.n_grids, ctx.st->k, i0, j0, s_ex[warp], s_ey[warp], lane, 32);
     __syncwarp();
     for (int q = lane; q < 64; q += 32) {
@@ -474,7 +482,7 @@ __global__ void __launch_bounds__(256) wfs_phase_kernel(Ctx ctx, int wi, int N, 
 
 template <int NFFT, int NBIN>
 cudaError_t launch_acf(const WfsLaunch& L, cudaStream_t s) {
-    unsigned blocks = (unsigned)((L.n_subaps + 7) / 8);
+    unsigned blocks = (unsigned)(((long long)L.n_subaps * L.ctx.n_real + 7) / 8);
     if (L.work && L.max_blocks > 0 && blocks > (unsigned)L.max_blocks) blocks = (unsigned)L.max_blocks;
     if (blocks) wfs_acf_kernel<NFFT, NBIN><<<blocks, 256, 0, s>>>(L);
     return cudaGetLastError();
@@ -489,7 +497,7 @@ cudaError_t prepare_fft() {
 template <int NPX, int NFFT, int NBIN>
 cudaError_t launch_fft(const WfsLaunch& L, cudaStream_t s) {
     constexpr size_t sm = fft_smem<NPX, NFFT>();
-    if (L.n_subaps) wfs_fft_kernel<NPX, NFFT, NBIN><<<(unsigned)L.n_subaps, kFftThreads, sm, s>>>(L);
+    if (L.n_subaps) wfs_fft_kernel<NPX, NFFT, NBIN><<<(unsigned)(L.n_subaps * L.ctx.n_real), kFftThreads, sm, s>>>(L);
     return cudaGetLastError();
 }
 
@@ -515,9 +523,9 @@ cudaError_t launch_wfs(const WfsLaunch& L, int n_px, int n_fft, int n_bin, cudaS
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_wfs_phase(const Ctx& ctx, int wfs, int N, float* out, cudaStream_t s) {
+cudaError_t launch_wfs_phase(const Ctx& ctx, int r, int wfs, int N, float* out, cudaStream_t s) {
     int tiles = ((N + 7) / 8) * ((N + 7) / 8);
-    wfs_phase_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(ctx, wfs, N, out);
+    wfs_phase_kernel<<<(unsigned)((tiles + 7) / 8), 256, 0, s>>>(ctx, r, wfs, N, out);
     return cudaGetLastError();
 }
 

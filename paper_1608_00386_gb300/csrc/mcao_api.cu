@@ -8,6 +8,7 @@
 //       integrator
 //   s2 (low priority): science field, row FFT (+ Strehl), column FFT (+ PSF accumulation)
 // Every stage is a kernel of this library (k_dm.cu, k_wfs.cu, k_recon.cu, k_science.cu).
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -81,6 +82,9 @@ struct mcao_sim {
     std::string err;
     int device = 0, sm_count = 0;
     int n_slopes = 0, n_frame_px = 0, ld = 0;
+    int n_real = 1;                       // realizations advanced together
+    int cur = 0;                          // realization addressed by loads, getters and setters
+    long long surf_total = 0;             // DM surface floats per realization
 
     cudaStream_t s0 = nullptr, s1 = nullptr, s2 = nullptr, s3 = nullptr;
     cudaStream_t user = nullptr;
@@ -100,9 +104,10 @@ struct mcao_sim {
     // atmosphere
     int n_layers = 0;
     std::vector<mcao_layer> layers;
-    std::vector<float*> d_layer_owned;
-    std::vector<const float*> d_layer_ptr;
-    bool atm_loaded = false;
+    std::vector<float*> d_layer_owned;    // [n_real][n_layers], null where adopted
+    std::vector<const float*> d_layer_ptr;   // [n_real][n_layers]
+    std::vector<char> atm_loaded_r;       // per realization
+    bool atm_loaded = false;              // every realization loaded
 
     // DMs
     int n_dms = 0;
@@ -128,6 +133,13 @@ struct mcao_sim {
     int rows_pad = 0;
     float* d_c = nullptr;
     float* d_partial = nullptr;
+    // batched product (n_real > 1): row-major padded R [rows_pad][ld] (float32 or bfloat16 codes),
+    // bfloat16 slopes, cuBLAS handle and workspace
+    float* d_Rrm = nullptr;
+    void* d_Rrm16 = nullptr;
+    void* d_S16 = nullptr;
+    cublasHandle_t blas = nullptr;
+    void* d_blas_ws = nullptr;
     std::vector<ReconLaunch> slices;      // one per sensor with slopes
     std::vector<std::vector<int>> slice_wfs;  // sensors whose slopes each slice reads
     int n_chunks = 0;
@@ -228,10 +240,14 @@ void release_graph(mcao_sim* S) {
     S->prof_slots.clear();
 }
 
+int pad_stride(const mcao_sim* S) { return S->ld + kSlopePadTail; }
+
 Ctx make_ctx(mcao_sim* S) {
     Ctx c;
     c.views = S->d_views;
     c.n_grids = S->n_grids;
+    c.view_stride = (long long)(S->wfs.size() + S->sci.size()) * S->n_grids;
+    c.n_real = S->n_real;
     c.wfs = S->d_wfs;
     c.st = S->d_st;
     c.seed = S->cfg.seed;
@@ -248,6 +264,9 @@ DmLaunch make_dm_launch(mcao_sim* S) {
     L.act_map = S->d_dm_map;
     L.c = S->d_c;
     L.surf = S->d_dm_surf;
+    L.n_real = S->n_real;
+    L.n_cmd = S->n_cmd;
+    L.surf_stride = S->surf_total;
     for (int m = 0; m <= kMaxDms; ++m) L.tile_start[m] = S->dm_tile_start[m];
     L.st = S->d_st;
     L.work = S->d_work;
@@ -276,6 +295,7 @@ SciLaunch make_sci_launch(mcao_sim* S, int q) {
     for (int i = 0; i < L.n_radices && i < 8; ++i) L.radices[i] = C.radices[i];
     L.st = S->d_st;
     L.acc = S->d_acc + q;
+    L.acc_stride = (int)S->sci.size();
     return L;
 }
 
@@ -291,6 +311,9 @@ WfsLaunch make_wfs_launch(mcao_sim* S, const SubapDev* subaps, int n, unsigned i
     L.slopes_pad = S->d_slopes_pad;
     L.lam_out = S->cfg.keep_frames ? S->d_lam : nullptr;
     L.frame_out = (S->cfg.keep_frames && S->cfg.noise) ? S->d_frames : nullptr;
+    L.slope_stride = S->n_slopes;
+    L.pad_stride = pad_stride(S);
+    L.frame_stride = S->n_frame_px;
     return L;
 }
 
@@ -298,16 +321,25 @@ WfsLaunch make_wfs_launch(mcao_sim* S, const SubapDev* subaps, int n, unsigned i
 // science directions): a pupil sample x of a view with N samples across D at height H maps to
 // the grid index (x (1 - h/H) + h theta + (k dt) v) / pixel + (n - 1)/2.
 mcao_status rebuild_views(mcao_sim* S) {
-    struct G { const float* data; int n, periodic; double pixel, alt, vx, vy; float sign; };
+    struct G { int n, periodic; double pixel, alt, vx, vy; float sign; };
     std::vector<G> grids;
     for (int l = 0; l < S->n_layers; ++l) {
         const mcao_layer& L = S->layers[l];
-        grids.push_back({S->d_layer_ptr[l], L.n, 1, L.pixel_m, L.alt_m, L.vx, L.vy, 1.0f});
+        grids.push_back({L.n, 1, L.pixel_m, L.alt_m, L.vx, L.vy, 1.0f});
     }
     for (int m = 0; m < S->n_dms; ++m) {
         const mcao_dm& d = S->dms[m];
-        grids.push_back({S->d_dm_surf + S->dm_desc[m].surf_off, d.surf_n, 0, d.surf_dx, d.alt_m, 0.0, 0.0, -1.0f});
+        grids.push_back({d.surf_n, 0, d.surf_dx, d.alt_m, 0.0, 0.0, -1.0f});
     }
+    // data of grid g for realization r
+    auto grid_data = [&](int r, int g) -> const float* {
+        if (g < S->n_layers) {
+            const size_t i = (size_t)r * S->n_layers + g;
+            return i < S->d_layer_ptr.size() ? S->d_layer_ptr[i] : nullptr;
+        }
+        const int m = g - S->n_layers;
+        return S->d_dm_surf ? S->d_dm_surf + (size_t)r * S->surf_total + S->dm_desc[m].surf_off : nullptr;
+    };
     if ((int)grids.size() > kMaxEntries)
         return fail(S, MCAO_E_UNSUPPORTED, "layers + DMs = %d exceeds %d", (int)grids.size(), kMaxEntries);
     struct View { int N; double thx, thy, H; };
@@ -317,13 +349,15 @@ mcao_status rebuild_views(mcao_sim* S) {
     for (const auto& c : S->sci) views.push_back({c.N, c.p.theta_x, c.p.theta_y, 0.0});
     std::vector<GridView> out;
     const double D = S->cfg.D, dt = S->cfg.dt;
+    for (int r = 0; r < S->n_real; ++r)
     for (const auto& v : views) {
         const double dxp = D / (double)v.N;
-        for (const auto& g : grids) {
+        for (size_t gi = 0; gi < grids.size(); ++gi) {
+            const G& g = grids[gi];
             double f = (v.H > 0.0) ? 1.0 - g.alt / v.H : 1.0;
             double x0 = (0.0 - 0.5 * (double)(v.N - 1)) * dxp * f;
             GridView gv{};
-            gv.data = g.data;
+            gv.data = grid_data(r, (int)gi);
             gv.n = g.n;
             gv.periodic = g.periodic;
             gv.ax = to_q32((x0 + g.alt * v.thx) / g.pixel + 0.5 * (double)(g.n - 1));
@@ -387,19 +421,6 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
     for (cudaStream_t st : {S->s1, S->s2, S->s3})
         if ((e = cudaStreamWaitEvent(st, ev_fork, 0)) != cudaSuccess) return e;
 
-    // science on s2 (low priority, fills idle SMs)
-    for (size_t q = 0; q < S->sci.size(); ++q) {
-        SciLaunch L = make_sci_launch(S, (int)q);
-        slot = prof_begin(S, ST_SCIENCE, S->s2);
-        if ((e = launch_sci_field(L, S->s2)) != cudaSuccess) return e;
-        if ((e = launch_sci_rows(L, S->s2)) != cudaSuccess) return e;
-        if ((e = launch_sci_cols(L, S->s2)) != cudaSuccess) return e;
-        prof_end(S, slot, S->s2);
-        nl += 3;
-    }
-    cudaEvent_t ev_sci = dep_event(S, used);
-    if ((e = cudaEventRecord(ev_sci, S->s2)) != cudaSuccess) return e;
-
     // block-per-subaperture sensors on s1
     std::vector<cudaEvent_t> ready(S->wfs.size(), nullptr);
     for (const auto& g : S->fft_groups) {
@@ -412,6 +433,26 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         if ((e = cudaEventRecord(ev, S->s1)) != cudaSuccess) return e;
         for (int w : g.wfs) ready[w] = ev;
     }
+
+    // science on s2 (low priority): after the block-per-subaperture sensors, so that it fills
+    // the SMs the first warp-per-subaperture launch leaves rather than racing it for them
+    {
+        cudaEvent_t after = nullptr;
+        for (cudaEvent_t ev : ready)
+            if (ev) after = ev;
+        if (after && (e = cudaStreamWaitEvent(S->s2, after, 0)) != cudaSuccess) return e;
+    }
+    for (size_t q = 0; q < S->sci.size(); ++q) {
+        SciLaunch L = make_sci_launch(S, (int)q);
+        slot = prof_begin(S, ST_SCIENCE, S->s2);
+        if ((e = launch_sci_field(L, S->s2)) != cudaSuccess) return e;
+        if ((e = launch_sci_rows(L, S->s2)) != cudaSuccess) return e;
+        if ((e = launch_sci_cols(L, S->s2)) != cudaSuccess) return e;
+        prof_end(S, slot, S->s2);
+        nl += 3;
+    }
+    cudaEvent_t ev_sci = dep_event(S, used);
+    if ((e = cudaEventRecord(ev_sci, S->s2)) != cudaSuccess) return e;
 
     // warp-per-subaperture sensors, one launch each, on s0
     for (size_t w = 0; w < S->wfs.size(); ++w) {
@@ -426,6 +467,41 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         cudaEvent_t ev = dep_event(S, used);
         if ((e = cudaEventRecord(ev, S->s0)) != cudaSuccess) return e;
         ready[w] = ev;
+    }
+
+    if (S->n_real > 1) {
+        // batched: after every sensor of every realization, C += g R S for all realizations at
+        // once (one pass over R), then the step counter
+        cudaEvent_t ev_s1b = dep_event(S, used);
+        if ((e = cudaEventRecord(ev_s1b, S->s1)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(S->s0, ev_s1b, 0)) != cudaSuccess) return e;
+        slot = prof_begin(S, ST_RECON, S->s0);
+        if (cublasSetStream(S->blas, S->s0) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        const float alpha = (float)S->cfg.gain, beta = 1.0f;
+        cublasStatus_t bs;
+        if (S->d_Rrm) {
+            bs = cublasSgemm(S->blas, CUBLAS_OP_T, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm, S->ld,
+                             S->d_slopes_pad, pad_stride(S), &beta, S->d_c, S->n_cmd);
+        } else {
+            if ((e = launch_slopes_to_bf16(S->d_slopes_pad, S->n_real, S->ld, pad_stride(S), S->d_S16, S->ld, S->s0)) !=
+                cudaSuccess)
+                return e;
+            ++nl;
+            bs = cublasGemmEx(S->blas, CUBLAS_OP_T, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm16,
+                              CUDA_R_16BF, S->ld, S->d_S16, CUDA_R_16BF, S->ld, &beta, S->d_c, CUDA_R_32F, S->n_cmd,
+                              CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+        }
+        if (bs != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        prof_end(S, slot, S->s0);
+        ReduceLaunch fin{0, 0, nullptr, nullptr, 0.0f, S->d_st};
+        if ((e = launch_recon_reduce(fin, S->s0)) != cudaSuccess) return e;
+        nl += 2;
+        if ((e = cudaStreamWaitEvent(S->s0, ev_sci, 0)) != cudaSuccess) return e;
+        cudaEvent_t ev_s3 = dep_event(S, used);   // s3 forked: join it back untouched
+        if ((e = cudaEventRecord(ev_s3, S->s3)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(S->s0, ev_s3, 0)) != cudaSuccess) return e;
+        if (launches) *launches = nl;
+        return cudaSuccess;
     }
 
     // reconstructor slices on s3, each after its sensor, then the reduction
@@ -535,11 +611,17 @@ void destroy_all(mcao_sim* S) {
     dfree(S->d_wfs); dfree(S->d_amp_all); dfree(S->d_slopes); dfree(S->d_slopes_pad); dfree(S->d_sref);
     dfree(S->d_lam);
     dfree(S->d_frames);
-    for (auto p : S->d_layer_owned) cudaFree(p);
+    for (auto p : S->d_layer_owned)
+        if (p) cudaFree(p);
     S->d_layer_owned.clear();
     dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
     dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_rscale); dfree(S->d_c); dfree(S->d_partial);
     dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err); dfree(S->d_work);
+    dfree(S->d_Rrm);
+    if (S->d_Rrm16) cudaFree(S->d_Rrm16);
+    if (S->d_S16) cudaFree(S->d_S16);
+    if (S->d_blas_ws) cudaFree(S->d_blas_ws);
+    if (S->blas) cublasDestroy(S->blas);
     for (auto e : S->prof_pool) cudaEventDestroy(e);
     for (auto e : S->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : {S->ev_user, S->ev_done})
@@ -561,6 +643,7 @@ mcao_status validate_config(const mcao_config* c) {
     if (!(is_fin(c->dt) && c->dt >= 0)) return fail(S, MCAO_E_INVALID_ARG, "dt must be >= 0");
     if (!is_fin(c->gain)) return fail(S, MCAO_E_INVALID_ARG, "gain must be finite");
     if (c->psf_every < 0) return fail(S, MCAO_E_INVALID_ARG, "psf_every must be >= 0");
+    if (c->n_real < 1 || c->n_real > 4096) return fail(S, MCAO_E_INVALID_ARG, "n_real must be in [1, 4096]");
     if (c->n_wfs < 1 || !c->wfs) return fail(S, MCAO_E_INVALID_ARG, "at least one WFS is required");
     if (c->n_sci < 0 || (c->n_sci > 0 && !c->sci)) return fail(S, MCAO_E_INVALID_ARG, "bad science list");
     for (int w = 0; w < c->n_wfs; ++w) {
@@ -629,6 +712,8 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     S->cfg = *cfg;
     S->cfg.wfs = nullptr;
     S->cfg.sci = nullptr;
+    S->n_real = cfg->n_real;
+    S->atm_loaded_r.assign(cfg->n_real, 0);
     auto bail = [&](mcao_status s) {
         g_create_error = S->err;
         destroy_all(S);
@@ -757,17 +842,18 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     for (size_t w = 0; w < wdev.size(); ++w) wdev[w].amp = S->d_amp_all + amp_off[w];
     CKC(dalloc(&S->d_wfs, wdev.size()));
     CKC(cudaMemcpyAsync(S->d_wfs, wdev.data(), sizeof(WfsDev) * wdev.size(), cudaMemcpyHostToDevice, S->s0));
-    CKC(dalloc(&S->d_slopes, ns));
-    CKC(cudaMemsetAsync(S->d_slopes, 0, sizeof(float) * std::max(ns, 1), S->s0));
-    CKC(dalloc(&S->d_slopes_pad, (size_t)S->ld + kSlopePadTail));
-    CKC(cudaMemsetAsync(S->d_slopes_pad, 0, sizeof(float) * ((size_t)S->ld + kSlopePadTail), S->s0));
+    const size_t NR = (size_t)S->n_real;
+    CKC(dalloc(&S->d_slopes, NR * std::max(ns, 1)));
+    CKC(cudaMemsetAsync(S->d_slopes, 0, sizeof(float) * NR * std::max(ns, 1), S->s0));
+    CKC(dalloc(&S->d_slopes_pad, NR * pad_stride(S)));
+    CKC(cudaMemsetAsync(S->d_slopes_pad, 0, sizeof(float) * NR * pad_stride(S), S->s0));
     CKC(dalloc(&S->d_sref, ns));
     CKC(cudaMemsetAsync(S->d_sref, 0, sizeof(float) * std::max(ns, 1), S->s0));
     if (cfg->keep_frames) {
-        CKC(dalloc(&S->d_lam, nframe));
-        CKC(dalloc(&S->d_frames, nframe));
-        CKC(cudaMemsetAsync(S->d_lam, 0, sizeof(float) * std::max(nframe, 1), S->s0));
-        CKC(cudaMemsetAsync(S->d_frames, 0, sizeof(int) * std::max(nframe, 1), S->s0));
+        CKC(dalloc(&S->d_lam, NR * std::max(nframe, 1)));
+        CKC(dalloc(&S->d_frames, NR * std::max(nframe, 1)));
+        CKC(cudaMemsetAsync(S->d_lam, 0, sizeof(float) * NR * std::max(nframe, 1), S->s0));
+        CKC(cudaMemsetAsync(S->d_frames, 0, sizeof(int) * NR * std::max(nframe, 1), S->s0));
     }
 
     // ---- block-per-subaperture sensors: one launch per kernel variant
@@ -807,11 +893,11 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         C.radices = factor_fft(C.M);
         CKC(dalloc(&C.d_amp, A.size()));
         CKC(cudaMemcpyAsync(C.d_amp, A.data(), sizeof(float) * A.size(), cudaMemcpyHostToDevice, S->s0));
-        CKC(dalloc(&C.d_field, (size_t)C.N * C.N));
-        CKC(dalloc(&C.d_ft, (size_t)C.M * C.N));
-        CKC(dalloc(&C.d_psf_t, (size_t)C.M * C.M));
-        CKC(cudaMemsetAsync(C.d_psf_t, 0, sizeof(double) * (size_t)C.M * C.M, S->s0));
-        CKC(dalloc(&C.d_sr_part, C.n_tiles));
+        CKC(dalloc(&C.d_field, NR * C.N * C.N));
+        CKC(dalloc(&C.d_ft, NR * C.M * C.N));
+        CKC(dalloc(&C.d_psf_t, NR * C.M * C.M));
+        CKC(cudaMemsetAsync(C.d_psf_t, 0, sizeof(double) * NR * C.M * C.M, S->s0));
+        CKC(dalloc(&C.d_sr_part, NR * std::max(C.n_tiles, 1)));
         std::vector<float2> W(C.M);
         for (int m = 0; m < C.M; ++m) {
             double a = -2.0 * M_PI * (double)m / (double)C.M;
@@ -832,8 +918,21 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         }
         CKC(sci_prepare(maxM));
     }
-    CKC(dalloc(&S->d_acc, std::max(cfg->n_sci, 1)));
-    CKC(cudaMemsetAsync(S->d_acc, 0, sizeof(SciAcc) * std::max(cfg->n_sci, 1), S->s0));
+    CKC(dalloc(&S->d_acc, NR * std::max(cfg->n_sci, 1)));
+    CKC(cudaMemsetAsync(S->d_acc, 0, sizeof(SciAcc) * NR * std::max(cfg->n_sci, 1), S->s0));
+    if (S->n_real > 1) {
+        if (cublasCreate(&S->blas) != CUBLAS_STATUS_SUCCESS) {
+            fail(S, MCAO_E_CUDA, "cublasCreate failed");
+            return bail(MCAO_E_CUDA);
+        }
+        const size_t ws = (size_t)32 << 20;   // fixed workspace: no allocation inside graph capture
+        CKC(cudaMalloc(&S->d_blas_ws, ws));
+        if (cublasSetWorkspace(S->blas, S->d_blas_ws, ws) != CUBLAS_STATUS_SUCCESS ||
+            cublasSetMathMode(S->blas, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS) {
+            fail(S, MCAO_E_CUDA, "cuBLAS setup failed");
+            return bail(MCAO_E_CUDA);
+        }
+    }
     CKC(dalloc(&S->d_st, 1));
     CKC(cudaMemsetAsync(S->d_st, 0, sizeof(StepState), S->s0));
     CKC(cudaStreamSynchronize(S->s0));
@@ -869,28 +968,47 @@ mcao_status mcao_load_atmosphere(mcao_sim* S, int n_layers, const mcao_layer* la
                 return fail(S, MCAO_E_INVALID_ARG, "layer %d lies above a laser guide star", l);
     }
     { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
-    for (auto p : S->d_layer_owned) cudaFree(p);
-    S->d_layer_owned.clear();
-    S->d_layer_ptr.clear();
-    S->layers.assign(layers, layers + n_layers);
+    // every realization shares the layers' geometry; a different geometry (allowed for
+    // realization 0 only) discards the screens of the other realizations
+    bool same = n_layers == S->n_layers && (int)S->layers.size() == n_layers;
+    for (int l = 0; same && l < n_layers; ++l) {
+        const mcao_layer &a = layers[l], &b = S->layers[l];
+        same = a.n == b.n && a.pixel_m == b.pixel_m && a.alt_m == b.alt_m && a.vx == b.vx && a.vy == b.vy;
+    }
+    if (!same) {
+        if (S->cur != 0)
+            return fail(S, MCAO_E_SHAPE, "realization %d: layers differ from realization 0's geometry", S->cur);
+        for (auto p : S->d_layer_owned)
+            if (p) cudaFree(p);
+        S->d_layer_owned.assign((size_t)S->n_real * n_layers, nullptr);
+        S->d_layer_ptr.assign((size_t)S->n_real * n_layers, nullptr);
+        S->atm_loaded_r.assign(S->n_real, 0);
+        S->layers.assign(layers, layers + n_layers);
+        for (auto& L : S->layers) L.phase = nullptr;
+        S->n_layers = n_layers;
+    }
     S->atm_loaded = false;
     for (int l = 0; l < n_layers; ++l) {
         const mcao_layer& L = layers[l];
+        const size_t slot = (size_t)S->cur * n_layers + l;
+        if (S->d_layer_owned[slot]) {
+            cudaFree(S->d_layer_owned[slot]);
+            S->d_layer_owned[slot] = nullptr;
+        }
         if (L.on_device) {
-            S->d_layer_ptr.push_back(L.phase);
+            S->d_layer_ptr[slot] = L.phase;
         } else {
             float* d = nullptr;
             CK(dalloc(&d, (size_t)L.n * L.n));
-            S->d_layer_owned.push_back(d);
+            S->d_layer_owned[slot] = d;
             CK(cudaMemcpyAsync(d, L.phase, sizeof(float) * (size_t)L.n * L.n, cudaMemcpyHostToDevice, S->s0));
-            S->d_layer_ptr.push_back(d);
+            S->d_layer_ptr[slot] = d;
         }
-        S->layers[l].phase = nullptr;
     }
-    S->n_layers = n_layers;
+    S->atm_loaded_r[S->cur] = 1;
     mcao_status r = rebuild_views(S);
     if (r != MCAO_OK) return r;
-    S->atm_loaded = true;
+    S->atm_loaded = std::all_of(S->atm_loaded_r.begin(), S->atm_loaded_r.end(), [](char c) { return c != 0; });
     CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
@@ -988,10 +1106,11 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     if (!band.empty()) CK(cudaMemcpyAsync(S->d_dm_band, band.data(), sizeof(int2) * band.size(), cudaMemcpyHostToDevice, S->s0));
     CK(dalloc(&S->d_dm_map, map.size()));
     if (!map.empty()) CK(cudaMemcpyAsync(S->d_dm_map, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice, S->s0));
-    CK(dalloc(&S->d_dm_surf, (size_t)surf_total));
-    CK(cudaMemsetAsync(S->d_dm_surf, 0, sizeof(float) * std::max<long long>(surf_total, 1), S->s0));
-    CK(dalloc(&S->d_c, ncmd));
-    CK(cudaMemsetAsync(S->d_c, 0, sizeof(float) * std::max(ncmd, 1), S->s0));
+    S->surf_total = surf_total;
+    CK(dalloc(&S->d_dm_surf, (size_t)S->n_real * std::max<long long>(surf_total, 1)));
+    CK(cudaMemsetAsync(S->d_dm_surf, 0, sizeof(float) * (size_t)S->n_real * std::max<long long>(surf_total, 1), S->s0));
+    CK(dalloc(&S->d_c, (size_t)S->n_real * std::max(ncmd, 1)));
+    CK(cudaMemsetAsync(S->d_c, 0, sizeof(float) * (size_t)S->n_real * std::max(ncmd, 1), S->s0));
     mcao_status r = rebuild_views(S);
     if (r != MCAO_OK) return r;
     S->dms_loaded = true;
@@ -1005,6 +1124,8 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "load the DMs before the reconstructor");
     if (dtype != MCAO_DTYPE_F32 && dtype != MCAO_DTYPE_BF16 && dtype != MCAO_DTYPE_FP8_E4M3)
         return fail(S, MCAO_E_UNSUPPORTED, "unknown reconstructor dtype %d", dtype);
+    if (S->n_real > 1 && dtype == MCAO_DTYPE_FP8_E4M3)
+        return fail(S, MCAO_E_UNSUPPORTED, "FP8 reconstructors are streamed per realization only (n_real = 1)");
     if (n_cmd != S->n_cmd || n_slopes != S->n_slopes)
         return fail(S, MCAO_E_SHAPE, "reconstructor is %d x %d, configuration needs %d x %d", n_cmd, n_slopes,
                     S->n_cmd, S->n_slopes);
@@ -1041,6 +1162,35 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
         if (len > 0 && e == cudaSuccess && n_cmd > 0)
             e = cudaMemcpy2DAsync(tmp + W.rcol0, sizeof(float) * S->ld, R + W.slope0, sizeof(float) * n_slopes,
                                   sizeof(float) * len, n_cmd, kind, S->s0);
+    }
+    if (S->n_real > 1) {
+        // batched product: keep R row-major (float32, or bfloat16 codes) for the matrix product
+        dfree(S->d_Rrm);
+        if (S->d_Rrm16) cudaFree(S->d_Rrm16);
+        if (S->d_S16) cudaFree(S->d_S16);
+        S->d_Rrm16 = S->d_S16 = nullptr;
+        if (dtype == MCAO_DTYPE_F32) {
+            if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
+            S->d_Rrm = tmp;
+            tmp = nullptr;
+        } else {
+            if (e == cudaSuccess) e = cudaMalloc(&S->d_Rrm16, sizeof(uint16_t) * elems);
+            if (e == cudaSuccess) e = launch_rows_to_bf16(tmp, (long long)elems, S->d_Rrm16, S->s0);
+            if (e == cudaSuccess) e = cudaMalloc(&S->d_S16, sizeof(uint16_t) * (size_t)S->n_real * S->ld);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
+            cudaFree(tmp);
+        }
+        CK(e);
+        S->n_chunks = 0;
+        CK(dalloc(&S->d_partial, 1));
+        if (s_ref)
+            CK(cudaMemcpyAsync(S->d_sref, s_ref, sizeof(float) * n_slopes, kind, S->s0));
+        else
+            CK(cudaMemsetAsync(S->d_sref, 0, sizeof(float) * n_slopes, S->s0));
+        CK(cudaStreamSynchronize(S->s0));
+        release_graph(S);
+        S->recon_loaded = true;
+        return MCAO_OK;
     }
     std::vector<std::vector<int>> units;
     for (const auto& g : S->fft_groups) {
@@ -1197,11 +1347,12 @@ mcao_status mcao_query(const mcao_sim* S, int kind, int index, size_t* n) {
             *n = (size_t)S->sci[index].M * S->sci[index].M;
             return MCAO_OK;
         case MCAO_Q_STATE: {
-            size_t b = 4 * sizeof(int64_t) + sizeof(float) * ((size_t)S->n_cmd + S->n_slopes);
-            for (const auto& c : S->sci) b += sizeof(SciAcc) + sizeof(double) * (size_t)c.M * c.M;
-            *n = b;
+            size_t per = sizeof(float) * ((size_t)S->n_cmd + S->n_slopes);
+            for (const auto& c : S->sci) per += sizeof(SciAcc) + sizeof(double) * (size_t)c.M * c.M;
+            *n = 4 * sizeof(int64_t) + per * (size_t)S->n_real;
             return MCAO_OK;
         }
+        case MCAO_Q_REALIZATIONS: *n = (size_t)S->n_real; return MCAO_OK;
         default: return fail(Sm, MCAO_E_INVALID_ARG, "unknown query kind %d", kind);
     }
 }
@@ -1218,14 +1369,14 @@ mcao_status mcao_get_step_index(mcao_sim* S, int64_t* k) {
 mcao_status mcao_get_slopes(mcao_sim* S, float* out, size_t n) {
     if (!S || !out) return MCAO_E_INVALID_ARG;
     if (n < (size_t)S->n_slopes) return fail(S, MCAO_E_SHAPE, "need %d slopes", S->n_slopes);
-    return d2h(S, out, S->d_slopes, sizeof(float) * S->n_slopes);
+    return d2h(S, out, S->d_slopes + (size_t)S->cur * S->n_slopes, sizeof(float) * S->n_slopes);
 }
 
 mcao_status mcao_get_commands(mcao_sim* S, float* out, size_t n) {
     if (!S || !out) return MCAO_E_INVALID_ARG;
     if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");
     if (n < (size_t)S->n_cmd) return fail(S, MCAO_E_SHAPE, "need %d commands", S->n_cmd);
-    return d2h(S, out, S->d_c, sizeof(float) * S->n_cmd);
+    return d2h(S, out, S->d_c + (size_t)S->cur * S->n_cmd, sizeof(float) * S->n_cmd);
 }
 
 mcao_status mcao_set_commands(mcao_sim* S, const float* in, size_t n) {
@@ -1236,7 +1387,7 @@ mcao_status mcao_set_commands(mcao_sim* S, const float* in, size_t n) {
         if (!std::isfinite(in[i])) return fail(S, MCAO_E_INVALID_ARG, "command %zu is not finite", i);
     CK(cudaSetDevice(S->device));
     { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
-    if (n) CK(cudaMemcpyAsync(S->d_c, in, sizeof(float) * n, cudaMemcpyHostToDevice, S->s0));
+    if (n) CK(cudaMemcpyAsync(S->d_c + (size_t)S->cur * S->n_cmd, in, sizeof(float) * n, cudaMemcpyHostToDevice, S->s0));
     CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
@@ -1261,7 +1412,7 @@ mcao_status mcao_get_wfs_phase(mcao_sim* S, int wfs, float* out, size_t n) {
     float* d = nullptr;
     CK(dalloc(&d, (size_t)N * N));
     cudaError_t e = launch_dm_surfaces(make_dm_launch(S), S->s0);
-    if (e == cudaSuccess) e = launch_wfs_phase(make_ctx(S), wfs, N, d, S->s0);
+    if (e == cudaSuccess) e = launch_wfs_phase(make_ctx(S), S->cur, wfs, N, d, S->s0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
     if (e == cudaSuccess) e = cudaMemcpy(out, d, sizeof(float) * (size_t)N * N, cudaMemcpyDeviceToHost);
     cudaFree(d);
@@ -1279,7 +1430,8 @@ mcao_status mcao_get_dm_surface(mcao_sim* S, int dm, float* out, size_t n) {
     { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     CK(launch_dm_surfaces(make_dm_launch(S), S->s0));
     CK(cudaStreamSynchronize(S->s0));
-    CK(cudaMemcpy(out, S->d_dm_surf + S->dm_desc[dm].surf_off, sizeof(float) * cnt, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(out, S->d_dm_surf + (size_t)S->cur * S->surf_total + S->dm_desc[dm].surf_off, sizeof(float) * cnt,
+                  cudaMemcpyDeviceToHost));
     return MCAO_OK;
 }
 
@@ -1291,8 +1443,9 @@ mcao_status mcao_get_frames(mcao_sim* S, int wfs, float* lambda, int32_t* frames
     size_t cnt = (size_t)W.n_valid * W.n_det * W.n_det;
     if (n < cnt) return fail(S, MCAO_E_SHAPE, "need %zu pixels", cnt);
     mcao_status r = MCAO_OK;
-    if (lambda) r = d2h(S, lambda, S->d_lam + W.frame0, sizeof(float) * cnt);
-    if (r == MCAO_OK && frames) r = d2h(S, frames, S->d_frames + W.frame0, sizeof(int32_t) * cnt);
+    const size_t off = (size_t)S->cur * S->n_frame_px + W.frame0;
+    if (lambda) r = d2h(S, lambda, S->d_lam + off, sizeof(float) * cnt);
+    if (r == MCAO_OK && frames) r = d2h(S, frames, S->d_frames + off, sizeof(int32_t) * cnt);
     return r;
 }
 
@@ -1303,13 +1456,13 @@ mcao_status mcao_get_psf(mcao_sim* S, int sci, double* out, size_t n, double* sr
     const size_t M = (size_t)C.M;
     if (out && n < M * M) return fail(S, MCAO_E_SHAPE, "need %zu pixels", M * M);
     SciAcc acc;
-    mcao_status r = d2h(S, &acc, S->d_acc + sci, sizeof(acc));
+    mcao_status r = d2h(S, &acc, S->d_acc + (size_t)S->cur * S->sci.size() + sci, sizeof(acc));
     if (r != MCAO_OK) return r;
     if (sr_long) *sr_long = acc.n_sr ? acc.sr_sum / (double)acc.n_sr : 0.0;
     if (sr_last) *sr_last = acc.sr_last;
     if (out) {
         std::vector<double> t(M * M);
-        r = d2h(S, t.data(), C.d_psf_t, sizeof(double) * M * M);
+        r = d2h(S, t.data(), C.d_psf_t + (size_t)S->cur * M * M, sizeof(double) * M * M);
         if (r != MCAO_OK) return r;
         double norm = acc.n_psf ? 1.0 / ((double)acc.n_psf * C.sum_amp * C.sum_amp) : 0.0;
         for (size_t j = 0; j < M; ++j)
@@ -1323,8 +1476,9 @@ mcao_status mcao_reset_psf(mcao_sim* S) {
     if (!S) return MCAO_E_INVALID_ARG;
     CK(cudaSetDevice(S->device));
     { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
-    for (auto& c : S->sci) CK(cudaMemsetAsync(c.d_psf_t, 0, sizeof(double) * (size_t)c.M * c.M, S->s0));
-    CK(cudaMemsetAsync(S->d_acc, 0, sizeof(SciAcc) * std::max<size_t>(S->sci.size(), 1), S->s0));
+    const size_t NR = (size_t)S->n_real;
+    for (auto& c : S->sci) CK(cudaMemsetAsync(c.d_psf_t, 0, sizeof(double) * NR * c.M * c.M, S->s0));
+    CK(cudaMemsetAsync(S->d_acc, 0, sizeof(SciAcc) * NR * std::max<size_t>(S->sci.size(), 1), S->s0));
     CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
@@ -1343,16 +1497,18 @@ mcao_status mcao_get_state(mcao_sim* S, void* buf, size_t n) {
     int64_t hdr[4] = {0x4d43414f53544154LL, (int64_t)st.k_next, S->n_cmd, S->n_slopes};
     memcpy(p, hdr, sizeof(hdr));
     p += sizeof(hdr);
-    if ((r = d2h(S, p, S->d_c, sizeof(float) * S->n_cmd)) != MCAO_OK) return r;
-    p += sizeof(float) * S->n_cmd;
-    if ((r = d2h(S, p, S->d_slopes, sizeof(float) * S->n_slopes)) != MCAO_OK) return r;
-    p += sizeof(float) * S->n_slopes;
-    for (size_t q = 0; q < S->sci.size(); ++q) {
-        if ((r = d2h(S, p, S->d_acc + q, sizeof(SciAcc))) != MCAO_OK) return r;
-        p += sizeof(SciAcc);
-        size_t b = sizeof(double) * (size_t)S->sci[q].M * S->sci[q].M;
-        if ((r = d2h(S, p, S->sci[q].d_psf_t, b)) != MCAO_OK) return r;
-        p += b;
+    for (int re = 0; re < S->n_real; ++re) {
+        if ((r = d2h(S, p, S->d_c + (size_t)re * S->n_cmd, sizeof(float) * S->n_cmd)) != MCAO_OK) return r;
+        p += sizeof(float) * S->n_cmd;
+        if ((r = d2h(S, p, S->d_slopes + (size_t)re * S->n_slopes, sizeof(float) * S->n_slopes)) != MCAO_OK) return r;
+        p += sizeof(float) * S->n_slopes;
+        for (size_t q = 0; q < S->sci.size(); ++q) {
+            if ((r = d2h(S, p, S->d_acc + (size_t)re * S->sci.size() + q, sizeof(SciAcc))) != MCAO_OK) return r;
+            p += sizeof(SciAcc);
+            const size_t mm = (size_t)S->sci[q].M * S->sci[q].M;
+            if ((r = d2h(S, p, S->sci[q].d_psf_t + (size_t)re * mm, sizeof(double) * mm)) != MCAO_OK) return r;
+            p += sizeof(double) * mm;
+        }
     }
     return MCAO_OK;
 }
@@ -1376,18 +1532,30 @@ mcao_status mcao_set_state(mcao_sim* S, const void* buf, size_t n) {
     st.k = hdr[1];
     st.k_next = hdr[1];
     CK(cudaMemcpyAsync(S->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, S->s0));
-    CK(cudaMemcpyAsync(S->d_c, p, sizeof(float) * S->n_cmd, cudaMemcpyHostToDevice, S->s0));
-    p += sizeof(float) * S->n_cmd;
-    CK(cudaMemcpyAsync(S->d_slopes, p, sizeof(float) * S->n_slopes, cudaMemcpyHostToDevice, S->s0));
-    p += sizeof(float) * S->n_slopes;
-    for (size_t q = 0; q < S->sci.size(); ++q) {
-        CK(cudaMemcpyAsync(S->d_acc + q, p, sizeof(SciAcc), cudaMemcpyHostToDevice, S->s0));
-        p += sizeof(SciAcc);
-        size_t b = sizeof(double) * (size_t)S->sci[q].M * S->sci[q].M;
-        CK(cudaMemcpyAsync(S->sci[q].d_psf_t, p, b, cudaMemcpyHostToDevice, S->s0));
-        p += b;
+    for (int re = 0; re < S->n_real; ++re) {
+        CK(cudaMemcpyAsync(S->d_c + (size_t)re * S->n_cmd, p, sizeof(float) * S->n_cmd, cudaMemcpyHostToDevice, S->s0));
+        p += sizeof(float) * S->n_cmd;
+        CK(cudaMemcpyAsync(S->d_slopes + (size_t)re * S->n_slopes, p, sizeof(float) * S->n_slopes,
+                           cudaMemcpyHostToDevice, S->s0));
+        p += sizeof(float) * S->n_slopes;
+        for (size_t q = 0; q < S->sci.size(); ++q) {
+            CK(cudaMemcpyAsync(S->d_acc + (size_t)re * S->sci.size() + q, p, sizeof(SciAcc), cudaMemcpyHostToDevice,
+                               S->s0));
+            p += sizeof(SciAcc);
+            const size_t mm = (size_t)S->sci[q].M * S->sci[q].M;
+            CK(cudaMemcpyAsync(S->sci[q].d_psf_t + (size_t)re * mm, p, sizeof(double) * mm, cudaMemcpyHostToDevice,
+                               S->s0));
+            p += sizeof(double) * mm;
+        }
     }
     CK(cudaStreamSynchronize(S->s0));
+    return MCAO_OK;
+}
+
+mcao_status mcao_set_realization(mcao_sim* S, int r) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (r < 0 || r >= S->n_real) return fail(S, MCAO_E_INVALID_ARG, "realization %d not in [0, %d)", r, S->n_real);
+    S->cur = r;
     return MCAO_OK;
 }
 

@@ -66,12 +66,18 @@ struct SciAcc {
     long long n_sr, n_psf;
 };
 
+// Realizations: a simulation may advance n_real independent Monte-Carlo realizations of the
+// same system together (own screens, DM commands, noise key seed + r, accumulators; shared
+// geometry and reconstructor).  Per-realization arrays are realization-major with the strides
+// below.
 struct Ctx {
-    const GridView* views;  // [n_views][n_grids]: WFSs first, then science directions
+    const GridView* views;  // [n_real][n_views][n_grids]: WFSs first, then science directions
+    long long view_stride;  // n_views * n_grids
     int n_grids;
+    int n_real;
     const WfsDev* wfs;      // [n_wfs]
     const StepState* st;
-    unsigned long long seed;
+    unsigned long long seed;   // realization r uses seed + r
     int noise;
 };
 
@@ -102,6 +108,9 @@ struct DmLaunch {
     const float* c;          // commands
     float* surf;             // surfaces
     int tile_start[kMaxDms + 1];    // per-DM prefix of 32 x 32 surface tiles
+    int n_real;              // realizations (grid y): commands c + r n_cmd, surfaces surf + r surf_stride
+    int n_cmd;
+    long long surf_stride;
     StepState* st;           // begin of step: k = k_next
     unsigned int* work;      // begin of step: the sensing kernels' work counters are zeroed
     int n_work;
@@ -121,6 +130,9 @@ struct WfsLaunch {
     float* slopes_pad;       // slopes again in the padded column layout of R (16-byte blocks)
     float* lam_out;          // keep_frames: [total pixels] or null
     int* frame_out;
+    int slope_stride;        // per realization: slopes, padded slopes, frame pixels
+    int pad_stride;
+    long long frame_stride;
     // warp-per-subaperture route: with a work counter (zero at launch) the grid is capped at
     // max_blocks and warps take subapertures from the counter, so the launch adapts to the SM
     // slots that the concurrent reconstructor stream leaves; without one, one warp per subaperture
@@ -133,8 +145,8 @@ bool wfs_variant_is_fft(int n_px, int n_fft, int n_bin);   // block-per-subapert
 cudaError_t wfs_prepare();   // kernel attributes (call once per device, outside stream capture)
 cudaError_t launch_wfs(const WfsLaunch& L, int n_px, int n_fft, int n_bin, cudaStream_t s);
 
-// residual phase of one WFS on its full pupil grid (tests)
-cudaError_t launch_wfs_phase(const Ctx& ctx, int wfs, int N, float* out, cudaStream_t s);
+// residual phase of one WFS of realization r on its full pupil grid (tests)
+cudaError_t launch_wfs_phase(const Ctx& ctx, int r, int wfs, int N, float* out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------
 // reconstructor
@@ -196,6 +208,11 @@ struct ReduceLaunch {
     StepState* st;      // k_next = k + 1 (may be null)
 };
 cudaError_t launch_recon_reduce(const ReduceLaunch& L, cudaStream_t s);
+// float32 slopes [n_real][ld_in] -> bfloat16 [n_real][ld_out] (batched bfloat16 product)
+cudaError_t launch_slopes_to_bf16(const float* s, int n_real, int cols, int ld_in, void* out, int ld_out,
+                                  cudaStream_t st);
+// row-major float32 [rows][ld] -> bfloat16 codes [rows][ld] (batched bfloat16 product)
+cudaError_t launch_rows_to_bf16(const float* src, long long n, void* out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------
 // science
@@ -218,6 +235,9 @@ struct SciLaunch {
     int n_radices;
     StepState* st;
     SciAcc* acc;
+    // per realization r: field + r N^2, ft + r M N, psf_t + r M^2, sr_part + r n_tiles,
+    // acc + r * acc_stride
+    int acc_stride;
 };
 cudaError_t sci_prepare(int M);   // kernel attributes (outside stream capture)
 size_t sci_smem_bytes(int M);

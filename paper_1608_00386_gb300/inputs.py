@@ -57,12 +57,13 @@ def phase_screen(n: int, pixel: float, r0: float, L0: float, seed: int) -> np.nd
     return scr.astype(np.float32)
 
 
-def make_screens(cfg: dict) -> list[np.ndarray]:
-    """Screens of every layer of a configuration (each layer carries its own r0 and seed)."""
+def make_screens(cfg: dict, realization: int = 0) -> list[np.ndarray]:
+    """Screens of every layer of a configuration (each layer carries its own r0 and seed);
+    realization r draws independent screens (layer seed + 1000 r)."""
     out = []
     for lay in cfg["layers"]:
         r0_l = lay["r0"]
-        out.append(phase_screen(lay["n"], lay["pixel"], r0_l, lay["L0"], lay["seed"]))
+        out.append(phase_screen(lay["n"], lay["pixel"], r0_l, lay["L0"], lay["seed"] + 1000 * realization))
     return out
 
 

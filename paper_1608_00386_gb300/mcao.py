@@ -18,7 +18,7 @@ _lib = None
 
 STATUS = {0: "MCAO_OK", 1: "MCAO_E_INVALID_ARG", 2: "MCAO_E_SHAPE", 3: "MCAO_E_STATE", 4: "MCAO_E_CUDA",
           5: "MCAO_E_OOM", 6: "MCAO_E_TIMEOUT", 7: "MCAO_E_UNSUPPORTED"}
-Q_SLOPES, Q_COMMANDS, Q_VALID, Q_FRAME, Q_WFS_PHASE, Q_DM_SURFACE, Q_PSF, Q_STATE = range(8)
+Q_SLOPES, Q_COMMANDS, Q_VALID, Q_FRAME, Q_WFS_PHASE, Q_DM_SURFACE, Q_PSF, Q_STATE, Q_REALIZATIONS = range(9)
 STAGES = ["dm", "wfs_main", "wfs_aux", "recon", "recon_reduce", "science"]
 
 # exported names of include/mcao.h (checked by the tests against the built library)
@@ -28,7 +28,7 @@ EXPORTS = [
     "mcao_query", "mcao_get_step_index", "mcao_get_slopes", "mcao_get_commands", "mcao_set_commands",
     "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
-    "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows",
+    "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -56,7 +56,7 @@ class _Config(C.Structure):
     _fields_ = [("struct_size", C.c_size_t), ("D", C.c_double), ("obstruction", C.c_double),
                 ("lambda_ref", C.c_double), ("dt", C.c_double), ("gain", C.c_double), ("seed", C.c_uint64),
                 ("noise", C.c_int), ("psf_every", C.c_int), ("keep_frames", C.c_int), ("n_wfs", C.c_int),
-                ("wfs", C.POINTER(_Wfs)), ("n_sci", C.c_int), ("sci", C.POINTER(_Science))]
+                ("wfs", C.POINTER(_Wfs)), ("n_sci", C.c_int), ("sci", C.POINTER(_Science)), ("n_real", C.c_int)]
 
 
 class _Layer(C.Structure):
@@ -110,6 +110,7 @@ def lib():
         "mcao_reconstruct_noalloc": [vp, C.c_int, C.c_int, C.c_int, vp, vp, C.c_float, vp, C.c_char_p, C.c_size_t],
         "mcao_get_timeline": [vp, vp, vp, vp, vp, C.c_size_t, C.POINTER(C.c_size_t)],
         "mcao_quantize_rows": [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_char_p, C.c_size_t],
+        "mcao_set_realization": [vp, C.c_int],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -134,7 +135,7 @@ def _addr(a):
 class Sim:
     """One closed-loop simulation handle (mcao_sim)."""
 
-    def __init__(self, cfg: dict, keep_frames: bool = False, stream=None):
+    def __init__(self, cfg: dict, keep_frames: bool = False, stream=None, n_real: int = 1):
         L = lib()
         self.cfg = cfg
         nw, nsci = len(cfg["wfs"]), len(cfg["science"])
@@ -152,6 +153,8 @@ class Sim:
         c.dt, c.gain, c.seed = cfg["dt"], cfg["gain"], cfg["seed"]
         c.noise, c.psf_every, c.keep_frames = int(cfg["noise"]), int(cfg.get("psf_every", 1)), int(keep_frames)
         c.n_wfs, c.wfs, c.n_sci, c.sci = nw, self._wfs, nsci, self._sci
+        c.n_real = int(n_real)
+        self.n_real = int(n_real)
         h = C.c_void_p()
         st = L.mcao_sim_create(C.byref(c), C.byref(h))
         if st != 0:
@@ -187,7 +190,13 @@ class Sim:
         self._ck(lib().mcao_set_stream(self.h, C.c_void_p(ptr)))
 
     # ---------------------------------------------------------------- loads
-    def load_atmosphere(self, screens):
+    def set_realization(self, r: int):
+        """Address realization r in later loads of screens, getters and command setters."""
+        self._ck(lib().mcao_set_realization(self.h, int(r)))
+
+    def load_atmosphere(self, screens, realization: int | None = None):
+        if realization is not None:
+            self.set_realization(realization)
         layers = (_Layer * len(screens))()
         keep = []
         for i, (lay, scr) in enumerate(zip(self.cfg["layers"], screens)):
@@ -343,11 +352,17 @@ def reconstruct_noalloc(R, s, c, gain: float, stream=None) -> None:
 
 
 def make_sim(cfg: dict, screens, R, s_ref=None, keep_frames: bool = False, stream=None,
-             r_dtype: int = DTYPE_F32) -> Sim:
+             r_dtype: int = DTYPE_F32, n_real: int = 1) -> Sim:
     """Create a simulation and load the atmosphere, the DMs and the reconstructor (stored in the
-    element format r_dtype)."""
-    s = Sim(cfg, keep_frames=keep_frames, stream=stream)
-    s.load_atmosphere(screens)
+    element format r_dtype).  With n_real > 1, screens is a list of n_real screen lists (one per
+    realization)."""
+    s = Sim(cfg, keep_frames=keep_frames, stream=stream, n_real=n_real)
+    if n_real > 1:
+        for r in range(n_real):
+            s.load_atmosphere(screens[r], realization=r)
+        s.set_realization(0)
+    else:
+        s.load_atmosphere(screens)
     s.load_dms()
     s.load_reconstructor(R, s_ref, dtype=r_dtype)
     return s
