@@ -245,6 +245,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--batch", type=int, default=16, help="realizations per step in the batched variants")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -294,6 +295,25 @@ def main():
     # reduced-precision reconstructor variants (bfloat16; FP8 E4M3 with per-row scales): same
     # workload and timing, R streamed in the narrower format
     variants = {}
+    if not args.no_variants and args.batch > 1:
+        # batched realizations: B realizations per step sharing R (one matrix product), screens
+        # of realization r = the workload's screens rolled by r n / B samples
+        B = args.batch
+        d_scr_b = [[torch.roll(t, shifts=(r * t.shape[1]) // B, dims=1) for t in d_screens] for r in range(B)]
+        for name, dt in (("batched_f32", mcao.DTYPE_F32), ("batched_bf16", mcao.DTYPE_BF16)):
+            bs = mcao.make_sim(cfg, d_scr_b, d_R, stream=stream, r_dtype=dt, n_real=B)
+            ksteps = max(10, args.steps // B)
+            el, bms, _, blps, bck = timed_steps(bs, stream, ksteps, args.warmup, dist, Clocks(local))
+            bs.close()
+            rb = recon_alg_bytes(n_cmd, n_slopes, 2 if dt == mcao.DTYPE_BF16 else 4)
+            variants[name] = {
+                "value": ws * B * ksteps / el, "unit": "realization-steps/s", "realizations": B,
+                "steps": ksteps, "ms_per_step": 1e3 * el / ksteps,
+                "recon_ms_per_step": bms["recon"] / max(1, ksteps),
+                "recon_alg_bytes_per_step": rb, "clocks": bck,
+                "accuracy": ("each realization matches the oracle (float32); bfloat16: long-exposure Strehl within "
+                             "1% of the float32 batch (tests/test_gpu_batched.py)")}
+        del d_scr_b
     if not args.no_variants:
         for name, dt in (("bf16", mcao.DTYPE_BF16), ("fp8_e4m3", mcao.DTYPE_FP8_E4M3)):
             vs = mcao.make_sim(cfg, d_screens, d_R, stream=stream, r_dtype=dt)

@@ -479,7 +479,40 @@ __global__ void rows_to_bf16_kernel(const float2* __restrict__ src, long long n_
     }
 }
 
+// transpose of a row-major float32 [rows][cols] into [cols][ld_out] (float32 or bfloat16),
+// 32 x 32 tiles through shared memory
+template <bool BF16>
+__global__ void transpose_kernel(const float* __restrict__ src, int rows, int cols, void* out, int ld_out) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(long long)r * cols + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < ld_out) {
+            const float v = tile[threadIdx.x][i];
+            if (BF16) {
+                uint32_t h = f32x2_to_bf16x2(v, 0.0f) & 0xffffu;
+                reinterpret_cast<uint16_t*>(out)[(long long)c * ld_out + r] = (uint16_t)h;
+            } else {
+                reinterpret_cast<float*>(out)[(long long)c * ld_out + r] = v;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_transpose(const float* src, int rows, int cols, void* out, int ld_out, int bf16, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((ld_out + 31) / 32)), block(32, 8);
+    if (bf16) transpose_kernel<true><<<grid, block, 0, st>>>(src, rows, cols, out, ld_out);
+    else transpose_kernel<false><<<grid, block, 0, st>>>(src, rows, cols, out, ld_out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_slopes_to_bf16(const float* s, int n_real, int cols, int ld_in, void* out, int ld_out,
                                   cudaStream_t st) {

@@ -133,8 +133,8 @@ struct mcao_sim {
     int rows_pad = 0;
     float* d_c = nullptr;
     float* d_partial = nullptr;
-    // batched product (n_real > 1): row-major padded R [rows_pad][ld] (float32 or bfloat16 codes),
-    // bfloat16 slopes, cuBLAS handle and workspace
+    // batched product (n_real > 1): padded R column-major [ld][rows_pad] (float32 or bfloat16
+    // codes), bfloat16 slopes, cuBLAS handle and workspace
     float* d_Rrm = nullptr;
     void* d_Rrm16 = nullptr;
     void* d_S16 = nullptr;
@@ -480,16 +480,16 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         const float alpha = (float)S->cfg.gain, beta = 1.0f;
         cublasStatus_t bs;
         if (S->d_Rrm) {
-            bs = cublasSgemm(S->blas, CUBLAS_OP_T, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm, S->ld,
-                             S->d_slopes_pad, pad_stride(S), &beta, S->d_c, S->n_cmd);
+            bs = cublasSgemm(S->blas, CUBLAS_OP_N, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm,
+                             S->rows_pad, S->d_slopes_pad, pad_stride(S), &beta, S->d_c, S->n_cmd);
         } else {
             if ((e = launch_slopes_to_bf16(S->d_slopes_pad, S->n_real, S->ld, pad_stride(S), S->d_S16, S->ld, S->s0)) !=
                 cudaSuccess)
                 return e;
             ++nl;
-            bs = cublasGemmEx(S->blas, CUBLAS_OP_T, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm16,
-                              CUDA_R_16BF, S->ld, S->d_S16, CUDA_R_16BF, S->ld, &beta, S->d_c, CUDA_R_32F, S->n_cmd,
-                              CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+            bs = cublasGemmEx(S->blas, CUBLAS_OP_N, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm16,
+                              CUDA_R_16BF, S->rows_pad, S->d_S16, CUDA_R_16BF, S->ld, &beta, S->d_c, CUDA_R_32F,
+                              S->n_cmd, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
         }
         if (bs != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
         prof_end(S, slot, S->s0);
@@ -1164,22 +1164,22 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
                                   sizeof(float) * len, n_cmd, kind, S->s0);
     }
     if (S->n_real > 1) {
-        // batched product: keep R row-major (float32, or bfloat16 codes) for the matrix product
+        // batched product: R for the matrix product (float32, or bfloat16 codes)
         dfree(S->d_Rrm);
         if (S->d_Rrm16) cudaFree(S->d_Rrm16);
         if (S->d_S16) cudaFree(S->d_S16);
         S->d_Rrm16 = S->d_S16 = nullptr;
+        // column-major [ld][rows_pad] (the layout cuBLAS streams best for a few right-hand sides)
         if (dtype == MCAO_DTYPE_F32) {
-            if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
-            S->d_Rrm = tmp;
-            tmp = nullptr;
+            if (e == cudaSuccess) e = dalloc(&S->d_Rrm, elems);
+            if (e == cudaSuccess) e = launch_transpose(tmp, S->rows_pad, S->ld, S->d_Rrm, S->rows_pad, 0, S->s0);
         } else {
             if (e == cudaSuccess) e = cudaMalloc(&S->d_Rrm16, sizeof(uint16_t) * elems);
-            if (e == cudaSuccess) e = launch_rows_to_bf16(tmp, (long long)elems, S->d_Rrm16, S->s0);
+            if (e == cudaSuccess) e = launch_transpose(tmp, S->rows_pad, S->ld, S->d_Rrm16, S->rows_pad, 1, S->s0);
             if (e == cudaSuccess) e = cudaMalloc(&S->d_S16, sizeof(uint16_t) * (size_t)S->n_real * S->ld);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
-            cudaFree(tmp);
         }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
+        cudaFree(tmp);
         CK(e);
         S->n_chunks = 0;
         CK(dalloc(&S->d_partial, 1));

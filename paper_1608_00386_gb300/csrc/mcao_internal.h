@@ -213,6 +213,9 @@ cudaError_t launch_slopes_to_bf16(const float* s, int n_real, int cols, int ld_i
                                   cudaStream_t st);
 // row-major float32 [rows][ld] -> bfloat16 codes [rows][ld] (batched bfloat16 product)
 cudaError_t launch_rows_to_bf16(const float* src, long long n, void* out, cudaStream_t st);
+// row-major float32 [rows][cols] -> [cols][ld_out] (float32, or bfloat16 codes when bf16 != 0);
+// rows >= ld_out are not read, rows in [rows, ld_out) are written as zeros
+cudaError_t launch_transpose(const float* src, int rows, int cols, void* out, int ld_out, int bf16, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------
 // science

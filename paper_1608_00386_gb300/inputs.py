@@ -67,6 +67,16 @@ def make_screens(cfg: dict, realization: int = 0) -> list[np.ndarray]:
     return out
 
 
+def shifted_screens(screens: list[np.ndarray], realization: int, n_real: int) -> list[np.ndarray]:
+    """Screens of realization r as the given screens rolled by r n / n_real samples along x
+    (periodic screens: same statistics, distinct samples; no FFT per realization)."""
+    out = []
+    for s in screens:
+        n = s.shape[1]
+        out.append(np.roll(s, (realization * n) // max(n_real, 1), axis=1))
+    return out
+
+
 # ------------------------------------------------------------------------------------------
 # DM geometry
 # ------------------------------------------------------------------------------------------
