@@ -118,6 +118,7 @@ def lib():
         L.orc_e4m3_to_f32.argtypes = [C.c_uint8]
         L.orc_e4m3_to_f32.restype = C.c_float
         L.orc_quantize_rows.argtypes = [_fp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, _fp]
+        L.orc_set_controller.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_noise_sample.argtypes = [C.c_float, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64]
         L.orc_noise_sample.restype = C.c_int
         L.orc_noise_frame.argtypes = [_fp, C.c_int, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -406,6 +407,10 @@ class Sim:
         c = np.ascontiguousarray(c, dtype=np.float64)
         assert c.size == self.n_cmd
         lib().orc_set_commands(self.h, _ptr(c, C.c_double))
+
+    def set_controller(self, a1: float, a2: float, b0: float, b1: float):
+        """Second-order controller c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1}."""
+        lib().orc_set_controller(self.h, a1, a2, b0, b1)
 
     def dm_surface(self, m: int) -> np.ndarray:
         n = self.cfg["dms"][m]["surf_n"]

@@ -647,6 +647,9 @@ typedef struct {
     uint8_t* Rq;              /* E4M3 codes of R (r_dtype 2)                                     */
     float* r_scale;           /* per-row scales (r_dtype 2)                                      */
     double* c;                /* commands                                                        */
+    double* c_prev;           /* commands of the previous step (second-order controller)         */
+    double* dc_prev;          /* reconstructed update of the previous step                       */
+    double ctl[4];            /* controller a1, a2, b0, b1; NaN a1 = pure integrator of gain g   */
     double* s;                /* last slopes                                                     */
     long k;                   /* step counter                                                    */
     int record;               /* keep float intensities / frames                                 */
@@ -788,6 +791,9 @@ orc_sim* orc_create(const orc_config* cfg) {
     S->s_ref = (double*)calloc(ns ? ns : 1, sizeof(double));
     if (cfg->s_ref) for (int i = 0; i < ns; ++i) S->s_ref[i] = (double)cfg->s_ref[i];
     S->c = (double*)calloc(S->n_cmd ? S->n_cmd : 1, sizeof(double));
+    S->c_prev = (double*)calloc(S->n_cmd ? S->n_cmd : 1, sizeof(double));
+    S->dc_prev = (double*)calloc(S->n_cmd ? S->n_cmd : 1, sizeof(double));
+    S->ctl[0] = NAN;
     S->s = (double*)calloc(ns ? ns : 1, sizeof(double));
 
     S->sci = (sci_state*)calloc(S->n_sci ? S->n_sci : 1, sizeof(sci_state));
@@ -819,7 +825,7 @@ static void sim_free(orc_sim* S) {
     for (int q = 0; q < S->n_sci; ++q) { free(S->sci[q].A); free(S->sci[q].psf); plan_free(S->sci[q].plan); }
     free(S->screen); free(S->surf); free(S->dm_nvalid); free(S->dm_cmd0);
     free(S->wfs); free(S->sci); free(S->wfs_p); free(S->sci_p); free(S->lay_p); free(S->dm_p);
-    free(S->s_ref); free(S->c); free(S->s);
+    free(S->s_ref); free(S->c); free(S->s); free(S->c_prev); free(S->dc_prev);
     free(S->Rb); free(S->Rq); free(S->r_scale);
     free(S);
 }
@@ -965,7 +971,19 @@ int orc_step(orc_sim* S, int n_steps) {
             }
             dc[i] = acc;
         }
-        for (int i = 0; i < S->n_cmd; ++i) S->c[i] += S->cfg.gain * dc[i];
+        if (isnan(S->ctl[0])) {
+            for (int i = 0; i < S->n_cmd; ++i) S->c[i] += S->cfg.gain * dc[i];
+        } else {
+            /* second-order controller ("The closed loop": a pure integrator or a second-order
+             * low-pass filter), read as the recursion per command
+             * c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1} */
+            for (int i = 0; i < S->n_cmd; ++i) {
+                double cn = S->ctl[0] * S->c[i] + S->ctl[1] * S->c_prev[i] + S->ctl[2] * dc[i] + S->ctl[3] * S->dc_prev[i];
+                S->c_prev[i] = S->c[i];
+                S->dc_prev[i] = dc[i];
+                S->c[i] = cn;
+            }
+        }
         free(dc);
         S->k += 1;
     }
@@ -990,7 +1008,18 @@ void orc_get_valid(const orc_sim* S, int w, int* idx) {
 }
 void orc_get_slopes(const orc_sim* S, double* out) { memcpy(out, S->s, sizeof(double) * S->n_slopes); }
 void orc_get_commands(const orc_sim* S, double* out) { memcpy(out, S->c, sizeof(double) * S->n_cmd); }
-void orc_set_commands(orc_sim* S, const double* in) { memcpy(S->c, in, sizeof(double) * S->n_cmd); }
+void orc_set_commands(orc_sim* S, const double* in) {
+    memcpy(S->c, in, sizeof(double) * S->n_cmd);
+    memcpy(S->c_prev, in, sizeof(double) * S->n_cmd);
+    memset(S->dc_prev, 0, sizeof(double) * S->n_cmd);
+}
+/* Second-order controller coefficients (a1, a2, b0, b1); the filter's memory starts from the
+ * current commands and a zero update. */
+void orc_set_controller(orc_sim* S, double a1, double a2, double b0, double b1) {
+    S->ctl[0] = a1; S->ctl[1] = a2; S->ctl[2] = b0; S->ctl[3] = b1;
+    memcpy(S->c_prev, S->c, sizeof(double) * S->n_cmd);
+    memset(S->dc_prev, 0, sizeof(double) * S->n_cmd);
+}
 void orc_get_dm_surface(orc_sim* S, int m, double* out) {
     update_dm_surfaces(S);
     size_t n = (size_t)S->dm_p[m].surf_n;

@@ -304,7 +304,10 @@ def test_marechal_small_phase():
 
 
 # ------------------------------------------------------------------------------------------ loop
-def test_integrator_decay_static_dm_aberration():
+def _static_aberration_loop():
+    """A loop whose only disturbance is a static layer equal to a DM shape c* in the controlled
+    space (noise-free, R = -pinv(D)): in the linear regime the reconstructed update is
+    dc_k = -(c_k - c*)."""
     cfg = inputs.scao_tiny()
     cfg["layers"][0]["vx"] = 0.0
     zero = [np.zeros((256, 256), np.float32)]
@@ -334,11 +337,44 @@ def test_integrator_decay_static_dm_aberration():
     off = (256 - 132) // 2
     scr[off:off + 132, off:off + 132] = surf
     loop = oracle.Sim(cfg, [scr.astype(np.float32)], R.astype(np.float32))
+    return cfg, loop, cstar
+
+
+def test_integrator_decay_static_dm_aberration():
+    cfg, loop, cstar = _static_aberration_loop()
     g = cfg["gain"]
     for k in range(1, 7):
         loop.step(1)
         err = np.linalg.norm(loop.commands() - cstar) / np.linalg.norm(cstar)
         assert err == pytest.approx((1 - g) ** k, abs=2e-3)
+
+
+def test_second_order_controller_recursion():
+    """Low-pass-filtered integrator (update y_k = (1 - beta) y_{k-1} + beta dc_k, c += g y_k),
+    i.e. c_{k+1} = (2 - beta) c_k - (1 - beta) c_{k-1} + g beta dc_k.  With dc_k = -(c_k - c*)
+    the error obeys f_{k+1} = (a1 - b0) f_k + a2 f_{k-1}, f_0 = f_{-1} = 1."""
+    cfg, loop, cstar = _static_aberration_loop()
+    g, beta = 0.5, 0.5
+    a1, a2, b0 = 2 - beta, -(1 - beta), g * beta
+    loop.set_controller(a1, a2, b0, 0.0)
+    f_prev, f = 1.0, 1.0
+    for k in range(1, 9):
+        loop.step(1)
+        f_prev, f = f, (a1 - b0) * f + a2 * f_prev
+        err = np.linalg.norm(loop.commands() - cstar) / np.linalg.norm(cstar)
+        assert err == pytest.approx(abs(f), abs=3e-3)
+
+
+def test_controller_integrator_coefficients_match_gain():
+    """(a1, a2, b0, b1) = (1, 0, g, 0) is the pure integrator."""
+    from _helpers import scao_tiny_inputs
+    cfg, screens, R = scao_tiny_inputs()
+    a = oracle.Sim(cfg, screens, R)
+    b = oracle.Sim(cfg, screens, R)
+    b.set_controller(1.0, 0.0, cfg["gain"], 0.0)
+    a.step(5)
+    b.step(5)
+    np.testing.assert_allclose(b.commands(), a.commands(), rtol=1e-12, atol=1e-12)
 
 
 # ------------------------------------------------------------------------------------------ noise
