@@ -238,6 +238,13 @@ mcao_status mcao_get_frames(mcao_sim* sim, int wfs, float* lambda, int32_t* fram
 mcao_status mcao_get_psf(mcao_sim* sim, int sci, double* out, size_t n, double* sr_long,
                          double* sr_last);
 
+/* Strehl ratio by the Marechal approximation ("The Point Spread Functions (PSFs)": Strehl on
+ * the closed-loop wavefront history) of science direction `sci` (current realization): each
+ * step's residual phase at the science wavelength, piston removed and weighted by the pupil
+ * amplitude, has variance s2_k; *sr_long = exp(-mean_k s2_k), *sr_last = exp(-s2_last).
+ * Either pointer may be NULL.  Errors: MCAO_E_INVALID_ARG. */
+mcao_status mcao_get_marechal(mcao_sim* sim, int sci, double* sr_long, double* sr_last);
+
 /* Reset the PSF and Strehl accumulators (for example after a convergence period). */
 mcao_status mcao_reset_psf(mcao_sim* sim);
 
@@ -286,6 +293,15 @@ mcao_status mcao_reconstruct_noalloc(const float* R, int n_cmd, int n_slopes, in
  * codes not 16-byte aligned), MCAO_E_UNSUPPORTED (dtype), MCAO_E_CUDA. */
 mcao_status mcao_quantize_rows(const float* R, int rows, int cols, int ld, int dtype, void* codes,
                                float* scales, void* stream, char* err, size_t err_len);
+
+/* Controller ("The closed loop": a pure integrator or a second-order low-pass filter), read as
+ * the recursion per command c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1}, dc_k = R s_k,
+ * for every realization.  The default is the pure integrator c_{k+1} = c_k + gain dc_k
+ * (equivalent to (1, 0, gain, 0)).  A low-pass-filtered integrator with filter constant beta is
+ * (2 - beta, -(1 - beta), gain beta, 0).  The filter's memory restarts from the current
+ * commands and a zero update (also after mcao_set_commands for that realization); the
+ * checkpoint keeps it.  Errors: MCAO_E_INVALID_ARG (non-finite), MCAO_E_STATE (DMs not loaded). */
+mcao_status mcao_set_controller(mcao_sim* sim, double a1, double a2, double b0, double b1);
 
 /* Select the realization (0 <= r < n_real, default 0) that later calls address: the screens
  * given to mcao_load_atmosphere, and the slopes, commands (get and set), WFS phase, DM

@@ -119,6 +119,7 @@ def lib():
         L.orc_e4m3_to_f32.restype = C.c_float
         L.orc_quantize_rows.argtypes = [_fp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, _fp]
         L.orc_set_controller.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.orc_marechal.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.orc_noise_sample.argtypes = [C.c_float, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64]
         L.orc_noise_sample.restype = C.c_int
         L.orc_noise_frame.argtypes = [_fp, C.c_int, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -407,6 +408,12 @@ class Sim:
         c = np.ascontiguousarray(c, dtype=np.float64)
         assert c.size == self.n_cmd
         lib().orc_set_commands(self.h, _ptr(c, C.c_double))
+
+    def marechal(self, q: int = 0):
+        """(long-exposure, last-step) Marechal Strehl of science direction q."""
+        a, b = C.c_double(), C.c_double()
+        lib().orc_marechal(self.h, q, C.byref(a), C.byref(b))
+        return a.value, b.value
 
     def set_controller(self, a1: float, a2: float, b0: float, b1: float):
         """Second-order controller c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1}."""

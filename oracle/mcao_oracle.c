@@ -628,6 +628,7 @@ typedef struct {
     double* psf;              /* [M][M] accumulated, fftshifted                                  */
     orc_plan* plan;
     double sr_sum, sr_last;
+    double var_sum, var_last;   /* Marechal: residual phase variance per step (science band)    */
     long n_psf, n_sr;
 } sci_state;
 
@@ -902,6 +903,7 @@ static void science_step(orc_sim* S, int q, int do_psf) {
     int N = C->N, M = C->M;
     double* er = (double*)calloc((size_t)M * M, sizeof(double));
     double* ei = (double*)calloc((size_t)M * M, sizeof(double));
+    double* pw = (double*)calloc((size_t)N * N, sizeof(double));   /* science-band phase */
     #pragma omp parallel for schedule(static)
     for (int j = 0; j < N; ++j)
         for (int i = 0; i < N; ++i) {
@@ -909,15 +911,28 @@ static void science_step(orc_sim* S, int q, int do_psf) {
             double y = ((double)j - 0.5 * (double)(N - 1)) * C->dx;
             double a = C->A[(size_t)j * N + i];
             double ph = scale * residual_phase(S, x, y, C->p.theta_x, C->p.theta_y, 0.0, t);
+            pw[(size_t)j * N + i] = ph;
             er[(size_t)j * M + i] = a * cos(ph);
             ei[(size_t)j * M + i] = a * sin(ph);
         }
-    double fr = 0.0, fi = 0.0;
+    double fr = 0.0, fi = 0.0, s1 = 0.0, s2 = 0.0;
     for (int j = 0; j < N; ++j)
-        for (int i = 0; i < N; ++i) { fr += er[(size_t)j * M + i]; fi += ei[(size_t)j * M + i]; }
+        for (int i = 0; i < N; ++i) {
+            fr += er[(size_t)j * M + i];
+            fi += ei[(size_t)j * M + i];
+            double a = C->A[(size_t)j * N + i], ph = pw[(size_t)j * N + i];
+            s1 += a * ph;
+            s2 += a * ph * ph;
+        }
+    free(pw);
     C->sr_last = (fr * fr + fi * fi) / (C->sumA * C->sumA);
     C->sr_sum += C->sr_last;
     C->n_sr += 1;
+    /* Marechal ("Strehl Ratio on the closed-loop wavefront history"): piston-removed,
+     * amplitude-weighted phase variance over the pupil at the science wavelength */
+    double mean = s1 / C->sumA;
+    C->var_last = s2 / C->sumA - mean * mean;
+    C->var_sum += C->var_last;
     if (do_psf) {
         /* 2-D FFT: rows in parallel, then columns in parallel */
         #pragma omp parallel
@@ -1003,6 +1018,13 @@ int orc_n_slopes(const orc_sim* S) { return S->n_slopes; }
 int orc_n_valid(const orc_sim* S, int w) { return S->wfs[w].n_valid; }
 long orc_step_index(const orc_sim* S) { return S->k; }
 void orc_set_step_index(orc_sim* S, long k) { S->k = k; }
+/* Marechal Strehl of science direction q: exp(-mean over steps of the residual variance) and
+ * exp(-variance) of the last step. */
+void orc_marechal(const orc_sim* S, int q, double* sr_long, double* sr_last) {
+    const sci_state* C = &S->sci[q];
+    *sr_long = C->n_sr ? exp(-C->var_sum / (double)C->n_sr) : 0.0;
+    *sr_last = exp(-C->var_last);
+}
 void orc_get_valid(const orc_sim* S, int w, int* idx) {
     memcpy(idx, S->wfs[w].valid_idx, sizeof(int) * S->wfs[w].n_valid);
 }

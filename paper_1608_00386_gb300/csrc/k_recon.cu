@@ -441,20 +441,41 @@ __global__ void quantize_rows_kernel(const float* __restrict__ src, int rows, in
 }
 
 // c += g sum_k partial[k][row]: eight lanes per row, lane m adds slots m, m + 8, ... (all its
-// loads in flight at once), then a fixed shuffle tree; deterministic
+// loads in flight at once), then a fixed shuffle tree; deterministic.  With the second-order
+// controller: c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1}.  Without partials the
+// update is read from dc_in (batched product), for every realization.
 __global__ void recon_reduce_kernel(ReduceLaunch L) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0 && L.st) L.st->k_next = L.st->k + 1;
-    const int row = t >> 3, m = t & 7;
+    const long long row = t >> 3;
+    const int m = (int)(t & 7);
+    const long long n_rows = (long long)L.n_cmd * (L.partial ? 1 : L.n_real);
     float a = 0.0f;
-    if (row < L.n_cmd) {
+    if (row < n_rows) {
+        if (L.partial) {
 #pragma unroll 4
-        for (int k = m; k < L.n_chunks; k += 8) a += L.partial[(size_t)k * L.n_cmd + row];
+            for (int k = m; k < L.n_chunks; k += 8) a += L.partial[(size_t)k * L.n_cmd + row];
+        } else if (m == 0) {
+            a = L.dc_in[row];
+        }
     }
     a += __shfl_xor_sync(0xffffffffu, a, 4);
     a += __shfl_xor_sync(0xffffffffu, a, 2);
     a += __shfl_xor_sync(0xffffffffu, a, 1);
-    if (m == 0 && row < L.n_cmd) L.c[row] = fmaf(L.gain, a, L.c[row]);
+    if (m == 0 && row < n_rows) {
+        if (!L.use_ctl) {
+            L.c[row] = fmaf(L.gain, a, L.c[row]);
+        } else {
+            const float c0 = L.c[row];
+            float cn = L.a1 * c0;
+            cn = fmaf(L.a2, L.c_prev[row], cn);
+            cn = fmaf(L.b0, a, cn);
+            cn = fmaf(L.b1, L.dc_prev[row], cn);
+            L.c_prev[row] = c0;
+            L.dc_prev[row] = a;
+            L.c[row] = cn;
+        }
+    }
 }
 
 // bfloat16 copies for the batched product (round to nearest even)
@@ -578,7 +599,8 @@ cudaError_t launch_recon_tile(const float* src, int ld, const ReconLaunch& L, cu
 }
 
 cudaError_t launch_recon_reduce(const ReduceLaunch& L, cudaStream_t s) {
-    const long long n = 8LL * (L.n_cmd > 0 ? L.n_cmd : 1);
+    const long long rows = (long long)(L.n_cmd > 0 ? L.n_cmd : 1) * (L.partial ? 1 : (L.n_real > 0 ? L.n_real : 1));
+    const long long n = 8LL * rows;
     recon_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L);
     return cudaGetLastError();
 }

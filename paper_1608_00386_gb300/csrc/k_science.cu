@@ -40,23 +40,59 @@ __global__ void __launch_bounds__(256) sci_field_kernel(SciLaunch L0) {
     const GridView* V = L.ctx.views + (long long)L.view * n_grids;
     tile_entries<8>(V, n_grids, L.ctx.st->k, i0, j0, s_ex[warp], s_ey[warp], lane, 32);
     __syncwarp();
-    float sr = 0.0f, si = 0.0f;
+    float sr = 0.0f, si = 0.0f, s1 = 0.0f, s2 = 0.0f;
     const int x = lane & 7;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
         const int y = (lane >> 3) + 4 * hh;
         float phi = tile_phase(V, n_grids, s_ex[warp], s_ey[warp], 8, x, y);
         float a = __ldg(L.amp + (long long)(j0 + y) * L.N + i0 + x);
+        const float ph = L.scale * phi;
         float sn, cs;
-        sincosf(L.scale * phi, &sn, &cs);
+        sincosf(ph, &sn, &cs);
         float2 e = make_float2(a * cs, a * sn);
         L.field[(long long)(j0 + y) * L.N + i0 + x] = e;
         sr += e.x;
         si += e.y;
+        s1 = fmaf(a, ph, s1);
+        s2 = fmaf(a * ph, ph, s2);
     }
     sr = warp_sum(sr);
     si = warp_sum(si);
-    if (lane == 0) L.sr_part[tile] = make_float2(sr, si);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) L.sr_part[tile] = make_float4(sr, si, s1, s2);
+}
+
+// Strehl of this step from the field partial sums, and the Marechal residual variance
+// (piston removed, amplitude-weighted, science band) from the phase sums; fixed order, double
+__device__ void finalize_strehl(const SciLaunch& L, double* red, int tid, int nthr) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = tid; q < L.n_tiles; q += nthr) {
+        const float4 p = L.sr_part[q];
+        v[0] += p.x;
+        v[1] += p.y;
+        v[2] += p.z;
+        v[3] += p.w;
+    }
+    for (int i = 0; i < 4; ++i) red[i * nthr + tid] = v[i];
+    __syncthreads();
+    for (int o = nthr / 2; o > 0; o >>= 1) {
+        if (tid < o)
+            for (int i = 0; i < 4; ++i) red[i * nthr + tid] += red[i * nthr + tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const double s = (red[0] * red[0] + red[nthr] * red[nthr]) / (L.sum_amp * L.sum_amp);
+        L.acc->sr_sum += s;
+        L.acc->sr_last = s;
+        L.acc->n_sr += 1;
+        const double mean = red[2 * nthr] / L.sum_amp;
+        const double var = red[3 * nthr] / L.sum_amp - mean * mean;
+        L.acc->var_sum += var;
+        L.acc->var_last = var;
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ bool psf_step(const SciLaunch& L) {
@@ -72,32 +108,7 @@ __global__ void __launch_bounds__(256) sci_rows_kernel(SciLaunch L0) {
     double* red = reinterpret_cast<double*>(W + L.M);
     const int tid = threadIdx.x, nthr = blockDim.x;
 
-    if (blockIdx.x == 0) {
-        // Strehl of this step from the field partial sums (fixed order, double)
-        double sr = 0.0, si = 0.0;
-        for (int q = tid; q < L.n_tiles; q += nthr) {
-            float2 p = L.sr_part[q];
-            sr += p.x;
-            si += p.y;
-        }
-        red[tid] = sr;
-        red[nthr + tid] = si;
-        __syncthreads();
-        for (int o = nthr / 2; o > 0; o >>= 1) {
-            if (tid < o) {
-                red[tid] += red[tid + o];
-                red[nthr + tid] += red[nthr + tid + o];
-            }
-            __syncthreads();
-        }
-        if (tid == 0) {
-            double s = (red[0] * red[0] + red[nthr] * red[nthr]) / (L.sum_amp * L.sum_amp);
-            L.acc->sr_sum += s;
-            L.acc->sr_last = s;
-            L.acc->n_sr += 1;
-        }
-        __syncthreads();
-    }
+    if (blockIdx.x == 0) finalize_strehl(L, red, tid, nthr);
     if (!psf_step(L)) return;
 
     const int row0 = blockIdx.x * kRowsPerBlock;
@@ -154,31 +165,7 @@ __global__ void __launch_bounds__(256) sci_rows_ct(SciLaunch L0) {
     float2* W = B + kCtRows * M;
     double* red = reinterpret_cast<double*>(W + M);
     const int tid = threadIdx.x, nthr = blockDim.x;
-    if (blockIdx.x == 0) {
-        double sr = 0.0, si = 0.0;
-        for (int q = tid; q < L.n_tiles; q += nthr) {
-            float2 p = L.sr_part[q];
-            sr += p.x;
-            si += p.y;
-        }
-        red[tid] = sr;
-        red[nthr + tid] = si;
-        __syncthreads();
-        for (int o = nthr / 2; o > 0; o >>= 1) {
-            if (tid < o) {
-                red[tid] += red[tid + o];
-                red[nthr + tid] += red[nthr + tid + o];
-            }
-            __syncthreads();
-        }
-        if (tid == 0) {
-            double s = (red[0] * red[0] + red[nthr] * red[nthr]) / (L.sum_amp * L.sum_amp);
-            L.acc->sr_sum += s;
-            L.acc->sr_last = s;
-            L.acc->n_sr += 1;
-        }
-        __syncthreads();
-    }
+    if (blockIdx.x == 0) finalize_strehl(L, red, tid, nthr);
     if (!psf_step(L)) return;
     const int row0 = blockIdx.x * kCtRows;
     for (int q = tid; q < M; q += nthr) W[q] = L.w[q];
@@ -224,7 +211,7 @@ __global__ void __launch_bounds__(256) sci_cols_ct(SciLaunch L0) {
 
 template <int M>
 size_t ct_smem() {
-    return sizeof(float2) * (2 * kCtRows * (size_t)M + M) + sizeof(double) * 2 * 256;
+    return sizeof(float2) * (2 * kCtRows * (size_t)M + M) + sizeof(double) * 4 * 256;
 }
 
 template <int M>
@@ -252,7 +239,7 @@ cudaError_t ct_cols(const SciLaunch& L, cudaStream_t s) {
 #define MCAO_SCI_CT_SIZES(X) X(128) X(256) X(512) X(640) X(1024) X(1280) X(2048)
 
 size_t fft_smem_bytes(int M) {
-    return sizeof(float2) * (2 * kRowsPerBlock * (size_t)M + M) + sizeof(double) * 2 * 256;
+    return sizeof(float2) * (2 * kRowsPerBlock * (size_t)M + M) + sizeof(double) * 4 * 256;
 }
 
 cudaError_t set_smem(const void* fn, size_t bytes) {

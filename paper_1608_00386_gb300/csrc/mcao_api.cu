@@ -36,7 +36,7 @@ struct Science {
     float2* d_field = nullptr;
     float2* d_ft = nullptr;
     double* d_psf_t = nullptr;
-    float2* d_sr_part = nullptr;
+    float4* d_sr_part = nullptr;
     float2* d_w = nullptr;
     int n_tiles;
     std::vector<int> radices;
@@ -133,6 +133,12 @@ struct mcao_sim {
     int rows_pad = 0;
     float* d_c = nullptr;
     float* d_partial = nullptr;
+    // second-order controller (off: the pure integrator of gain cfg.gain)
+    bool use_ctl = false;
+    float ctl[4] = {1.0f, 0.0f, 0.0f, 0.0f};
+    float* d_c_prev = nullptr;            // [n_real][n_cmd]
+    float* d_dc_prev = nullptr;           // [n_real][n_cmd]
+    float* d_dc = nullptr;                // [n_real][n_cmd] batched update (controller on)
     // batched product (n_real > 1): padded R column-major [ld][rows_pad] (float32 or bfloat16
     // codes), bfloat16 slopes, cuBLAS handle and workspace
     float* d_Rrm = nullptr;
@@ -477,23 +483,31 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         if ((e = cudaStreamWaitEvent(S->s0, ev_s1b, 0)) != cudaSuccess) return e;
         slot = prof_begin(S, ST_RECON, S->s0);
         if (cublasSetStream(S->blas, S->s0) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-        const float alpha = (float)S->cfg.gain, beta = 1.0f;
+        // integrator: C += g R S in place; controller: D = R S, then the filter
+        const float alpha = S->use_ctl ? 1.0f : (float)S->cfg.gain, beta = S->use_ctl ? 0.0f : 1.0f;
+        float* cout = S->use_ctl ? S->d_dc : S->d_c;
         cublasStatus_t bs;
         if (S->d_Rrm) {
             bs = cublasSgemm(S->blas, CUBLAS_OP_N, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm,
-                             S->rows_pad, S->d_slopes_pad, pad_stride(S), &beta, S->d_c, S->n_cmd);
+                             S->rows_pad, S->d_slopes_pad, pad_stride(S), &beta, cout, S->n_cmd);
         } else {
             if ((e = launch_slopes_to_bf16(S->d_slopes_pad, S->n_real, S->ld, pad_stride(S), S->d_S16, S->ld, S->s0)) !=
                 cudaSuccess)
                 return e;
             ++nl;
             bs = cublasGemmEx(S->blas, CUBLAS_OP_N, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm16,
-                              CUDA_R_16BF, S->rows_pad, S->d_S16, CUDA_R_16BF, S->ld, &beta, S->d_c, CUDA_R_32F,
+                              CUDA_R_16BF, S->rows_pad, S->d_S16, CUDA_R_16BF, S->ld, &beta, cout, CUDA_R_32F,
                               S->n_cmd, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
         }
         if (bs != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
         prof_end(S, slot, S->s0);
-        ReduceLaunch fin{0, 0, nullptr, nullptr, 0.0f, S->d_st};
+        ReduceLaunch fin{S->use_ctl ? S->n_cmd : 0, 0, nullptr, S->d_c, 0.0f, S->d_st};
+        fin.use_ctl = S->use_ctl;
+        fin.a1 = S->ctl[0]; fin.a2 = S->ctl[1]; fin.b0 = S->ctl[2]; fin.b1 = S->ctl[3];
+        fin.c_prev = S->d_c_prev;
+        fin.dc_prev = S->d_dc_prev;
+        fin.dc_in = S->d_dc;
+        fin.n_real = S->n_real;
         if ((e = launch_recon_reduce(fin, S->s0)) != cudaSuccess) return e;
         nl += 2;
         if ((e = cudaStreamWaitEvent(S->s0, ev_sci, 0)) != cudaSuccess) return e;
@@ -518,6 +532,11 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         ++nl;
     }
     ReduceLaunch rl{S->n_cmd, S->n_chunks, S->d_partial, S->d_c, (float)S->cfg.gain, S->d_st};
+    rl.use_ctl = S->use_ctl;
+    rl.a1 = S->ctl[0]; rl.a2 = S->ctl[1]; rl.b0 = S->ctl[2]; rl.b1 = S->ctl[3];
+    rl.c_prev = S->d_c_prev;
+    rl.dc_prev = S->d_dc_prev;
+    rl.n_real = 1;
     slot = prof_begin(S, ST_REDUCE, S->s3);
     if ((e = launch_recon_reduce(rl, S->s3)) != cudaSuccess) return e;
     prof_end(S, slot, S->s3);
@@ -618,6 +637,7 @@ void destroy_all(mcao_sim* S) {
     dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_rscale); dfree(S->d_c); dfree(S->d_partial);
     dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err); dfree(S->d_work);
     dfree(S->d_Rrm);
+    dfree(S->d_c_prev); dfree(S->d_dc_prev); dfree(S->d_dc);
     if (S->d_Rrm16) cudaFree(S->d_Rrm16);
     if (S->d_S16) cudaFree(S->d_S16);
     if (S->d_blas_ws) cudaFree(S->d_blas_ws);
@@ -1111,6 +1131,11 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     CK(cudaMemsetAsync(S->d_dm_surf, 0, sizeof(float) * (size_t)S->n_real * std::max<long long>(surf_total, 1), S->s0));
     CK(dalloc(&S->d_c, (size_t)S->n_real * std::max(ncmd, 1)));
     CK(cudaMemsetAsync(S->d_c, 0, sizeof(float) * (size_t)S->n_real * std::max(ncmd, 1), S->s0));
+    for (float** p : {&S->d_c_prev, &S->d_dc_prev, &S->d_dc}) {
+        dfree(*p);
+        CK(dalloc(p, (size_t)S->n_real * std::max(ncmd, 1)));
+        CK(cudaMemsetAsync(*p, 0, sizeof(float) * (size_t)S->n_real * std::max(ncmd, 1), S->s0));
+    }
     mcao_status r = rebuild_views(S);
     if (r != MCAO_OK) return r;
     S->dms_loaded = true;
@@ -1347,7 +1372,7 @@ mcao_status mcao_query(const mcao_sim* S, int kind, int index, size_t* n) {
             *n = (size_t)S->sci[index].M * S->sci[index].M;
             return MCAO_OK;
         case MCAO_Q_STATE: {
-            size_t per = sizeof(float) * ((size_t)S->n_cmd + S->n_slopes);
+            size_t per = sizeof(float) * (3 * (size_t)S->n_cmd + S->n_slopes);
             for (const auto& c : S->sci) per += sizeof(SciAcc) + sizeof(double) * (size_t)c.M * c.M;
             *n = 4 * sizeof(int64_t) + per * (size_t)S->n_real;
             return MCAO_OK;
@@ -1387,7 +1412,12 @@ mcao_status mcao_set_commands(mcao_sim* S, const float* in, size_t n) {
         if (!std::isfinite(in[i])) return fail(S, MCAO_E_INVALID_ARG, "command %zu is not finite", i);
     CK(cudaSetDevice(S->device));
     { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
-    if (n) CK(cudaMemcpyAsync(S->d_c + (size_t)S->cur * S->n_cmd, in, sizeof(float) * n, cudaMemcpyHostToDevice, S->s0));
+    if (n) {
+        const size_t off = (size_t)S->cur * S->n_cmd;
+        CK(cudaMemcpyAsync(S->d_c + off, in, sizeof(float) * n, cudaMemcpyHostToDevice, S->s0));
+        CK(cudaMemcpyAsync(S->d_c_prev + off, in, sizeof(float) * n, cudaMemcpyHostToDevice, S->s0));
+        CK(cudaMemsetAsync(S->d_dc_prev + off, 0, sizeof(float) * n, S->s0));
+    }
     CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
 }
@@ -1472,6 +1502,17 @@ mcao_status mcao_get_psf(mcao_sim* S, int sci, double* out, size_t n, double* sr
     return MCAO_OK;
 }
 
+mcao_status mcao_get_marechal(mcao_sim* S, int sci, double* sr_long, double* sr_last) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (sci < 0 || sci >= (int)S->sci.size()) return fail(S, MCAO_E_INVALID_ARG, "bad science index");
+    SciAcc acc;
+    mcao_status r = d2h(S, &acc, S->d_acc + (size_t)S->cur * S->sci.size() + sci, sizeof(acc));
+    if (r != MCAO_OK) return r;
+    if (sr_long) *sr_long = acc.n_sr ? std::exp(-acc.var_sum / (double)acc.n_sr) : 0.0;
+    if (sr_last) *sr_last = std::exp(-acc.var_last);
+    return MCAO_OK;
+}
+
 mcao_status mcao_reset_psf(mcao_sim* S) {
     if (!S) return MCAO_E_INVALID_ARG;
     CK(cudaSetDevice(S->device));
@@ -1498,8 +1539,10 @@ mcao_status mcao_get_state(mcao_sim* S, void* buf, size_t n) {
     memcpy(p, hdr, sizeof(hdr));
     p += sizeof(hdr);
     for (int re = 0; re < S->n_real; ++re) {
-        if ((r = d2h(S, p, S->d_c + (size_t)re * S->n_cmd, sizeof(float) * S->n_cmd)) != MCAO_OK) return r;
-        p += sizeof(float) * S->n_cmd;
+        for (const float* src : {S->d_c, S->d_c_prev, S->d_dc_prev}) {
+            if ((r = d2h(S, p, src + (size_t)re * S->n_cmd, sizeof(float) * S->n_cmd)) != MCAO_OK) return r;
+            p += sizeof(float) * S->n_cmd;
+        }
         if ((r = d2h(S, p, S->d_slopes + (size_t)re * S->n_slopes, sizeof(float) * S->n_slopes)) != MCAO_OK) return r;
         p += sizeof(float) * S->n_slopes;
         for (size_t q = 0; q < S->sci.size(); ++q) {
@@ -1533,8 +1576,10 @@ mcao_status mcao_set_state(mcao_sim* S, const void* buf, size_t n) {
     st.k_next = hdr[1];
     CK(cudaMemcpyAsync(S->d_st, &st, sizeof(st), cudaMemcpyHostToDevice, S->s0));
     for (int re = 0; re < S->n_real; ++re) {
-        CK(cudaMemcpyAsync(S->d_c + (size_t)re * S->n_cmd, p, sizeof(float) * S->n_cmd, cudaMemcpyHostToDevice, S->s0));
-        p += sizeof(float) * S->n_cmd;
+        for (float* dst : {S->d_c, S->d_c_prev, S->d_dc_prev}) {
+            CK(cudaMemcpyAsync(dst + (size_t)re * S->n_cmd, p, sizeof(float) * S->n_cmd, cudaMemcpyHostToDevice, S->s0));
+            p += sizeof(float) * S->n_cmd;
+        }
         CK(cudaMemcpyAsync(S->d_slopes + (size_t)re * S->n_slopes, p, sizeof(float) * S->n_slopes,
                            cudaMemcpyHostToDevice, S->s0));
         p += sizeof(float) * S->n_slopes;
@@ -1549,6 +1594,25 @@ mcao_status mcao_set_state(mcao_sim* S, const void* buf, size_t n) {
         }
     }
     CK(cudaStreamSynchronize(S->s0));
+    return MCAO_OK;
+}
+
+mcao_status mcao_set_controller(mcao_sim* S, double a1, double a2, double b0, double b1) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (!is_fin(a1) || !is_fin(a2) || !is_fin(b0) || !is_fin(b1))
+        return fail(S, MCAO_E_INVALID_ARG, "controller coefficients must be finite");
+    if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "load the DMs before setting the controller");
+    CK(cudaSetDevice(S->device));
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    S->use_ctl = true;
+    S->ctl[0] = (float)a1; S->ctl[1] = (float)a2; S->ctl[2] = (float)b0; S->ctl[3] = (float)b1;
+    const size_t n = (size_t)S->n_real * S->n_cmd;
+    if (n) {
+        CK(cudaMemcpyAsync(S->d_c_prev, S->d_c, sizeof(float) * n, cudaMemcpyDeviceToDevice, S->s0));
+        CK(cudaMemsetAsync(S->d_dc_prev, 0, sizeof(float) * n, S->s0));
+    }
+    CK(cudaStreamSynchronize(S->s0));
+    release_graph(S);
     return MCAO_OK;
 }
 

@@ -64,6 +64,7 @@ struct StepState {
 struct SciAcc {
     double sr_sum, sr_last;
     long long n_sr, n_psf;
+    double var_sum, var_last;   // Marechal: residual phase variance (science band) per step
 };
 
 // Realizations: a simulation may advance n_real independent Monte-Carlo realizations of the
@@ -202,10 +203,18 @@ constexpr int kErrReconTimeout = 1;
 
 struct ReduceLaunch {
     int n_cmd, n_chunks;
-    const float* partial;
+    const float* partial;   // [n_chunks][n_cmd], or null: the update is dc_in
     float* c;
     float gain;
     StepState* st;      // k_next = k + 1 (may be null)
+    // second-order controller c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1} (when set;
+    // otherwise the pure integrator c += gain dc), over n_real realizations of n_cmd commands
+    int use_ctl;
+    float a1, a2, b0, b1;
+    float* c_prev;
+    float* dc_prev;
+    const float* dc_in;  // [n_real][n_cmd] update (batched product), used when partial is null
+    int n_real;
 };
 cudaError_t launch_recon_reduce(const ReduceLaunch& L, cudaStream_t s);
 // float32 slopes [n_real][ld_in] -> bfloat16 [n_real][ld_out] (batched bfloat16 product)
@@ -229,7 +238,7 @@ struct SciLaunch {
     float2* field;            // [N][N]
     float2* ft;               // [M][N] row-FFT output, transposed
     double* psf_t;            // [M][M] accumulated |FFT|^2, transposed, unshifted
-    float2* sr_part;          // [n tiles] partial sums of the field
+    float4* sr_part;          // [n tiles] partial sums: field (re, im), A phi, A phi^2
     int n_tiles;
     double sum_amp;
     int psf_every;

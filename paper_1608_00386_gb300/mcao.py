@@ -29,6 +29,7 @@ EXPORTS = [
     "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
+    "mcao_set_controller", "mcao_get_marechal",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -111,6 +112,8 @@ def lib():
         "mcao_get_timeline": [vp, vp, vp, vp, vp, C.c_size_t, C.POINTER(C.c_size_t)],
         "mcao_quantize_rows": [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_char_p, C.c_size_t],
         "mcao_set_realization": [vp, C.c_int],
+        "mcao_set_controller": [vp, C.c_double, C.c_double, C.c_double, C.c_double],
+        "mcao_get_marechal": [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -190,6 +193,16 @@ class Sim:
         self._ck(lib().mcao_set_stream(self.h, C.c_void_p(ptr)))
 
     # ---------------------------------------------------------------- loads
+    def marechal(self, q: int = 0):
+        """(long-exposure, last-step) Marechal Strehl of science direction q."""
+        a, b = C.c_double(), C.c_double()
+        self._ck(lib().mcao_get_marechal(self.h, int(q), C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def set_controller(self, a1: float, a2: float, b0: float, b1: float):
+        """Second-order controller c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1}."""
+        self._ck(lib().mcao_set_controller(self.h, float(a1), float(a2), float(b0), float(b1)))
+
     def set_realization(self, r: int):
         """Address realization r in later loads of screens, getters and command setters."""
         self._ck(lib().mcao_set_realization(self.h, int(r)))

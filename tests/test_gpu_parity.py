@@ -136,6 +136,20 @@ def test_closed_loop_scao_100_steps():
     assert np.max(np.abs(pg - po)) <= 1e-4
 
 
+def test_marechal_strehl_matches_oracle():
+    cfg, screens, R = scao_tiny_inputs()
+    g = mcao.make_sim(cfg, screens, R)
+    o = oracle.Sim(cfg, screens, R)
+    g.step(40)
+    o.step(40)
+    gl, gt = g.marechal()
+    ol, ot = o.marechal()
+    assert abs(gl - ol) <= 1e-4 and abs(gt - ot) <= 1e-4
+    # in the corrected regime the Marechal number is close to the exact Strehl
+    _, sr_long, _ = g.psf()
+    assert abs(gl - sr_long) < 0.05
+
+
 def test_eelt_full_size_steps():
     cfg, screens, n_cmd = eelt_inputs(10)
     R = inputs.random_reconstructor(n_cmd, 55608, 1e-4, 3)

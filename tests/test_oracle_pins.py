@@ -301,6 +301,10 @@ def test_marechal_small_phase():
     assert abs(srl - math.exp(-var)) <= var * var
     # the exact definition for the same samples
     assert srl == pytest.approx(abs(np.mean(np.exp(1j * p))) ** 2, rel=1e-12)
+    # the Marechal number is exp(-variance) of the same samples
+    m_long, m_last = sim.marechal()
+    assert m_last == pytest.approx(math.exp(-var), rel=1e-10)
+    assert m_long == pytest.approx(math.exp(-var), rel=1e-10)
 
 
 # ------------------------------------------------------------------------------------------ loop
