@@ -294,6 +294,13 @@ mcao_status mcao_reconstruct_noalloc(const float* R, int n_cmd, int n_slopes, in
 mcao_status mcao_quantize_rows(const float* R, int rows, int cols, int ld, int dtype, void* codes,
                                float* scales, void* stream, char* err, size_t err_len);
 
+/* Sodium layer evolution ("The closed loop": the sodium layer temporal evolution): from the
+ * next step on, laser sensor `wfs` sees the layer at `height` m (its cone projection) with
+ * thickness `na_fwhm` m (its elongation).  Call between steps to follow a profile in time.
+ * Errors: MCAO_E_INVALID_ARG (not a laser sensor, height not above every layer, negative
+ * thickness), MCAO_E_UNSUPPORTED (elongation on a sensor without an elongated-spot kernel). */
+mcao_status mcao_set_sodium(mcao_sim* sim, int wfs, double height, double na_fwhm);
+
 /* Controller ("The closed loop": a pure integrator or a second-order low-pass filter), read as
  * the recursion per command c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1}, dc_k = R s_k,
  * for every realization.  The default is the pure integrator c_{k+1} = c_k + gain dc_k

@@ -120,6 +120,8 @@ def lib():
         L.orc_quantize_rows.argtypes = [_fp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, _fp]
         L.orc_set_controller.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_marechal.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+        L.orc_set_sodium.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+        L.orc_set_sodium.restype = C.c_int
         L.orc_noise_sample.argtypes = [C.c_float, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64]
         L.orc_noise_sample.restype = C.c_int
         L.orc_noise_frame.argtypes = [_fp, C.c_int, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -408,6 +410,11 @@ class Sim:
         c = np.ascontiguousarray(c, dtype=np.float64)
         assert c.size == self.n_cmd
         lib().orc_set_commands(self.h, _ptr(c, C.c_double))
+
+    def set_sodium(self, w: int, height: float, na_fwhm: float):
+        """Sodium layer height and thickness seen by laser sensor w from the next step on."""
+        if lib().orc_set_sodium(self.h, w, height, na_fwhm) != 0:
+            raise ValueError("not a laser sensor, or height not above every layer")
 
     def marechal(self, q: int = 0):
         """(long-exposure, last-step) Marechal Strehl of science direction q."""

@@ -658,6 +658,43 @@ typedef struct {
 
 static void sim_free(orc_sim* S);
 
+/* Elongation of every valid subaperture of a laser star: the spot seen from a subaperture at
+ * distance b from the launch spans b dh / H^2 rad (FWHM) along the launch-to-subaperture
+ * direction (dh the sodium layer thickness, H its height). */
+static void set_elongation(wfs_state* W) {
+    for (int v = 0; v < W->n_valid; ++v) {
+        W->sigma_pix[v] = 0.0;
+        W->dir[2 * v] = W->dir[2 * v + 1] = 0.0;
+    }
+    if (!(W->p.type == 1 && W->p.na_fwhm > 0.0)) return;
+    double pix_rad = W->p.lambda / ((double)W->p.n_fft * W->dx);
+    for (int v = 0; v < W->n_valid; ++v) {
+        int sx = W->valid_idx[v] % W->p.n_sub, sy = W->valid_idx[v] / W->p.n_sub;
+        double cx = ((double)sx - 0.5 * (double)(W->p.n_sub - 1)) * W->p.n_px * W->dx - W->p.launch_x;
+        double cy = ((double)sy - 0.5 * (double)(W->p.n_sub - 1)) * W->p.n_px * W->dx - W->p.launch_y;
+        double b = sqrt(cx * cx + cy * cy);
+        if (b > 0.0) {
+            double fwhm = b * W->p.na_fwhm / (W->p.height * W->p.height);
+            W->sigma_pix[v] = fwhm / (2.0 * sqrt(2.0 * log(2.0))) / pix_rad;
+            W->dir[2 * v] = cx / b; W->dir[2 * v + 1] = cy / b;
+        }
+    }
+}
+
+/* Sodium layer evolution ("The closed loop": the sodium layer temporal evolution may be
+ * considered): new height (cone projection of the laser star) and thickness (elongation) of
+ * the layer seen by laser sensor w, from the next step on.  Returns 0, or -1 for a sensor that
+ * is not a laser star or a height not above every layer. */
+int orc_set_sodium(orc_sim* S, int w, double height, double na_fwhm) {
+    if (w < 0 || w >= S->n_wfs || S->wfs[w].p.type != 1 || !(height > 0.0) || !(na_fwhm >= 0.0)) return -1;
+    for (int l = 0; l < S->n_layers; ++l)
+        if (S->lay_p[l].alt >= height) return -1;
+    S->wfs[w].p.height = height;
+    S->wfs[w].p.na_fwhm = na_fwhm;
+    set_elongation(&S->wfs[w]);
+    return 0;
+}
+
 /* Phase (rad at the reference wavelength) along a direction: layers minus DM surfaces at the
  * cone-beam projection x (1 - h/H) + h theta (H infinite for natural stars), plus the
  * frozen-flow offset (k dt) v for layers.  x, y in metres in the pupil. */
@@ -755,22 +792,7 @@ orc_sim* orc_create(const orc_config* cfg) {
         for (int i = 0; i < nsub2; ++i)
             if (vmap[i]) { W->valid_idx[q] = i; W->frac[q] = fr[i]; ++q; }
         free(vmap); free(fr);
-        /* elongation: spot seen from a subaperture at distance b from the launch spans
-         * b dh / H^2 rad (FWHM) along the launch-to-subaperture direction */
-        if (W->p.type == 1 && W->p.na_fwhm > 0.0) {
-            double pix_rad = W->p.lambda / ((double)W->p.n_fft * W->dx);
-            for (int v = 0; v < W->n_valid; ++v) {
-                int sx = W->valid_idx[v] % W->p.n_sub, sy = W->valid_idx[v] / W->p.n_sub;
-                double cx = ((double)sx - 0.5 * (double)(W->p.n_sub - 1)) * W->p.n_px * W->dx - W->p.launch_x;
-                double cy = ((double)sy - 0.5 * (double)(W->p.n_sub - 1)) * W->p.n_px * W->dx - W->p.launch_y;
-                double b = sqrt(cx * cx + cy * cy);
-                if (b > 0.0) {
-                    double fwhm = b * W->p.na_fwhm / (W->p.height * W->p.height);
-                    W->sigma_pix[v] = fwhm / (2.0 * sqrt(2.0 * log(2.0))) / pix_rad;
-                    W->dir[2 * v] = cx / b; W->dir[2 * v + 1] = cy / b;
-                }
-            }
-        }
+        set_elongation(W);
         W->slope0 = ns;
         ns += 2 * W->n_valid;
         W->plan = plan_new(W->p.n_fft);

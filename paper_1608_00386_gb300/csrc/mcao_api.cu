@@ -222,6 +222,26 @@ std::vector<float> pupil(double D, double obs, int n) {
     return A;
 }
 
+// elongation of one laser-star subaperture: FWHM b dh / H^2 rad along the launch-to-subaperture
+// direction (b the distance from the launch), as the OTF factor exp(-elong_a (u . d)^2)
+void set_elongation(const WfsHost& H, SubapDev& d) {
+    d.elong_a = 0.0f;
+    d.dir_x = d.dir_y = 0.0f;
+    if (!(H.p.type == MCAO_WFS_LGS && H.p.na_fwhm > 0.0)) return;
+    const int npx = H.p.n_px;
+    const double pix_rad = H.p.lambda / ((double)H.p.n_fft * H.dx);
+    const double cx = ((double)d.sx - 0.5 * (double)(H.p.n_sub - 1)) * npx * H.dx - H.p.launch_x;
+    const double cy = ((double)d.sy - 0.5 * (double)(H.p.n_sub - 1)) * npx * H.dx - H.p.launch_y;
+    const double b = std::sqrt(cx * cx + cy * cy);
+    if (b > 0.0) {
+        const double fwhm = b * H.p.na_fwhm / (H.p.height * H.p.height);
+        const double sig = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0))) / pix_rad;
+        d.elong_a = (float)(2.0 * M_PI * M_PI * sig * sig / ((double)H.p.n_fft * H.p.n_fft));
+        d.dir_x = (float)(cx / b);
+        d.dir_y = (float)(cy / b);
+    }
+}
+
 std::vector<int> factor_fft(int M) {
     std::vector<int> r;
     int n = M;
@@ -800,7 +820,6 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         H.frame0 = nframe;
         nframe += H.n_valid * H.n_det * H.n_det;
         bool el = H.p.type == MCAO_WFS_LGS && H.p.na_fwhm > 0;
-        double pix_rad = H.p.lambda / ((double)H.p.n_fft * H.dx);
         for (int v = 0; v < H.n_valid; ++v) {
             SubapDev d{};
             d.wfs = w;
@@ -808,20 +827,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
             d.sy = H.valid[v] / H.p.n_sub;
             d.rank = v;
             d.frac = (float)H.frac[v];
-            if (el) {
-                // elongation: FWHM b dh / H^2 rad along the launch-to-subaperture direction
-                double cx = ((double)d.sx - 0.5 * (double)(H.p.n_sub - 1)) * npx * H.dx - H.p.launch_x;
-                double cy = ((double)d.sy - 0.5 * (double)(H.p.n_sub - 1)) * npx * H.dx - H.p.launch_y;
-                double b = std::sqrt(cx * cx + cy * cy);
-                if (b > 0.0) {
-                    double fwhm = b * H.p.na_fwhm / (H.p.height * H.p.height);
-                    double sig = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0))) / pix_rad;
-                    double a = 2.0 * M_PI * M_PI * sig * sig / ((double)H.p.n_fft * H.p.n_fft);
-                    d.elong_a = (float)a;
-                    d.dir_x = (float)(cx / b);
-                    d.dir_y = (float)(cy / b);
-                }
-            }
+            if (el) set_elongation(H, d);
             H.subaps.push_back(d);
         }
         CKC(dalloc(&H.d_subaps, H.subaps.size()));
@@ -1595,6 +1601,28 @@ mcao_status mcao_set_state(mcao_sim* S, const void* buf, size_t n) {
     }
     CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
+}
+
+mcao_status mcao_set_sodium(mcao_sim* S, int wfs, double height, double na_fwhm) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (wfs < 0 || wfs >= (int)S->wfs.size()) return fail(S, MCAO_E_INVALID_ARG, "bad WFS index");
+    WfsHost& H = S->wfs[wfs];
+    if (H.p.type != MCAO_WFS_LGS) return fail(S, MCAO_E_INVALID_ARG, "WFS %d is not a laser star", wfs);
+    if (!(is_fin(height) && height > 0.0) || !(is_fin(na_fwhm) && na_fwhm >= 0.0))
+        return fail(S, MCAO_E_INVALID_ARG, "height > 0 and na_fwhm >= 0 required");
+    for (const auto& L : S->layers)
+        if (L.alt_m >= height) return fail(S, MCAO_E_INVALID_ARG, "the laser star must stay above every layer");
+    if (H.fft_route && na_fwhm > 0.0)
+        return fail(S, MCAO_E_UNSUPPORTED, "WFS %d has no kernel for an elongated spot", wfs);
+    CK(cudaSetDevice(S->device));
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    H.p.height = height;
+    H.p.na_fwhm = na_fwhm;
+    for (auto& d : H.subaps) set_elongation(H, d);
+    if (!H.subaps.empty())
+        CK(cudaMemcpyAsync(H.d_subaps, H.subaps.data(), sizeof(SubapDev) * H.subaps.size(), cudaMemcpyHostToDevice,
+                           S->s0));
+    return rebuild_views(S);   // cone projection of the new height (synchronises s0)
 }
 
 mcao_status mcao_set_controller(mcao_sim* S, double a1, double a2, double b0, double b1) {

@@ -29,7 +29,7 @@ EXPORTS = [
     "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
-    "mcao_set_controller", "mcao_get_marechal",
+    "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -114,6 +114,7 @@ def lib():
         "mcao_set_realization": [vp, C.c_int],
         "mcao_set_controller": [vp, C.c_double, C.c_double, C.c_double, C.c_double],
         "mcao_get_marechal": [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "mcao_set_sodium": [vp, C.c_int, C.c_double, C.c_double],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -193,6 +194,10 @@ class Sim:
         self._ck(lib().mcao_set_stream(self.h, C.c_void_p(ptr)))
 
     # ---------------------------------------------------------------- loads
+    def set_sodium(self, w: int, height: float, na_fwhm: float):
+        """Sodium layer height and thickness seen by laser sensor w from the next step on."""
+        self._ck(lib().mcao_set_sodium(self.h, int(w), float(height), float(na_fwhm)))
+
     def marechal(self, q: int = 0):
         """(long-exposure, last-step) Marechal Strehl of science direction q."""
         a, b = C.c_double(), C.c_double()

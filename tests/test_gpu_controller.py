@@ -1,5 +1,6 @@
-"""Second-order controller through the C ABI against the oracle's recursion (float32
-tolerances: slopes 1e-4 pixel RMS, commands 1e-5 relative, Strehl 1e-3), single and batched."""
+"""Closed-loop options through the C ABI against the oracle (float32 tolerances: slopes 1e-4
+pixel RMS, commands 1e-5 relative, Strehl 1e-3): the second-order controller (single and
+batched) and the sodium layer evolution of the laser sensors."""
 import numpy as np
 import pytest
 
@@ -83,3 +84,22 @@ def test_controller_rejects_non_finite():
     g = mcao.make_sim(cfg, screens, R)
     with pytest.raises(mcao.McaoError):
         g.set_controller(float("nan"), 0.0, 0.5, 0.0)
+
+
+def test_sodium_evolution_matches_oracle():
+    from _helpers import eelt_inputs
+    cfg, screens, n_cmd = eelt_inputs(10)
+    R = inputs.random_reconstructor(n_cmd, 55608, 1e-4, 3)
+    g = mcao.make_sim(cfg, screens, R)
+    o = oracle.Sim(cfg, screens, R)
+    g.step(1)
+    o.step(1)
+    for w in range(6):                      # the six laser stars: layer 3 km higher, 40 % thicker
+        g.set_sodium(w, 93e3, 14e3)
+        o.set_sodium(w, 93e3, 14e3)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        assert _rms(g.slopes() - o.slopes()) <= 1e-4
+    with pytest.raises(mcao.McaoError):
+        g.set_sodium(7, 90e3, 10e3)         # a natural star

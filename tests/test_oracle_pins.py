@@ -286,6 +286,22 @@ def test_flat_residual_strehl_one_and_psf_parseval():
     assert psf.sum() == pytest.approx(M * M / A.sum(), rel=1e-10)
 
 
+def test_sodium_update_equals_configuration():
+    """Changing the sodium layer before the first step gives the loop of a configuration created
+    with those values (cone projection and elongation both follow)."""
+    cfg = inputs.eelt_mcao(n_layers=2, screen_n=1024)
+    cfg["wfs"] = cfg["wfs"][:1]
+    cfg["science"] = []
+    screens = inputs.make_screens(cfg)
+    a = oracle.Sim(cfg, screens)
+    a.set_sodium(0, 95e3, 14e3)
+    b_cfg = dict(cfg, wfs=[dict(cfg["wfs"][0], height=95e3, na_fwhm=14e3)])
+    b = oracle.Sim(b_cfg, screens)
+    np.testing.assert_array_equal(a.measure(), b.measure())
+    with pytest.raises(ValueError):
+        a.set_sodium(0, 1.0, 10e3)          # below the layers
+
+
 def test_marechal_small_phase():
     cfg = inputs.scao_tiny()
     rng = np.random.default_rng(11)
