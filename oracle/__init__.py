@@ -121,6 +121,8 @@ def lib():
         L.orc_set_controller.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_marechal.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.orc_set_sodium.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+        L.orc_screen_amp.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp]
+        L.orc_screen_coeffs.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64, _dp, _dp]
         L.orc_set_sodium.restype = C.c_int
         L.orc_noise_sample.argtypes = [C.c_float, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64]
         L.orc_noise_sample.restype = C.c_int
@@ -294,6 +296,38 @@ def dequantize_rows(codes: np.ndarray, scales: np.ndarray, dtype: int) -> np.nda
 
 def noise_sample(lam: float, read_noise: float, c0: int, c1: int, c2: int, seed: int) -> int:
     return lib().orc_noise_sample(lam, read_noise, c0, c1, c2, seed)
+
+
+def screen_coeffs(n: int, pixel: float, r0: float, L0: float, seed: int) -> np.ndarray:
+    """Complex coefficients c_k of the FFT-method phase screen, [ky][kx] (see orc_screen_coeffs)."""
+    re = np.zeros((n, n))
+    im = np.zeros((n, n))
+    lib().orc_screen_coeffs(int(n), float(pixel), float(r0), float(L0), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                            _ptr(re, C.c_double), _ptr(im, C.c_double))
+    return re + 1j * im
+
+
+def phase_screen(n: int, pixel: float, r0: float, L0: float, seed: int) -> np.ndarray:
+    """Von Karman phase screen by the FFT method ("The atmospheric layers generation"):
+    Re sum_k c_k exp(2 pi i k.x / n), i.e. n^2 times the inverse DFT of the coefficients;
+    [y][x] in rad."""
+    return np.real(np.fft.ifft2(screen_coeffs(n, pixel, r0, L0, seed))) * (n * n)
+
+
+def screen_amp(n: int, pixel: float, r0: float, L0: float) -> np.ndarray:
+    """Amplitudes a_k of the FFT-method screen coefficients, [ky][kx] (see orc_screen_amp)."""
+    a = np.zeros((n, n))
+    lib().orc_screen_amp(int(n), float(pixel), float(r0), float(L0), _ptr(a, C.c_double))
+    return a
+
+
+def screen_structure_function(n: int, pixel: float, r0: float, L0: float, r_px: int) -> float:
+    """Expected structure function of the FFT-method screen at a lag of r_px samples along x:
+    E (phi(x + r) - phi(x))^2 = sum_k a_k^2 2 (1 - cos(2 pi kx r / n)) (each term
+    Re(c_k e^{i t}) has variance a_k^2, the terms are independent)."""
+    a2 = screen_amp(n, pixel, r0, L0) ** 2
+    kx = np.arange(n)[None, :]
+    return float(np.sum(a2 * 2.0 * (1.0 - np.cos(2 * np.pi * kx * r_px / n))))
 
 
 def noise_frame(lam: np.ndarray, read_noise: float, pixel0: int, step: int, wfs: int, seed: int) -> np.ndarray:

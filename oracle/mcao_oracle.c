@@ -499,6 +499,48 @@ static void box_muller2(float u0, float u1, float* zc, float* zs) {
     *zs = rad * s;
 }
 
+/* Phase-screen amplitudes ("The atmospheric layers generation": screens drawn from the
+ * turbulence spectrum), the FFT method on an n x n periodic grid of pitch `pixel` (m):
+ * frequency (fx, fy) = (kx', ky') / (n pixel) cycles/m with kx' = kx for kx <= (n-1)/2 and
+ * kx - n above; von Karman phase spectrum PSD = 0.023 r0^(-5/3) (f^2 + L0^-2)^(-11/6);
+ * a_k = sqrt(PSD) / (n pixel) (the square root of PSD times the frequency cell), a_0 = 0.
+ * Output amp: [n][n] row-major by (ky, kx). */
+void orc_screen_amp(int n, double pixel, double r0, double L0, double* amp) {
+    const double df = 1.0 / (n * pixel);
+    for (int ky = 0; ky < n; ++ky) {
+        for (int kx = 0; kx < n; ++kx) {
+            const int sx = (kx <= (n - 1) / 2) ? kx : kx - n;
+            const int sy = (ky <= (n - 1) / 2) ? ky : ky - n;
+            const double fx = sx * df, fy = sy * df;
+            double a = 0.0;
+            if (kx != 0 || ky != 0) {
+                const double psd = 0.023 * pow(r0, -5.0 / 3.0) * pow(fx * fx + fy * fy + 1.0 / (L0 * L0), -11.0 / 6.0);
+                a = sqrt(psd) * df;
+            }
+            amp[(size_t)ky * n + kx] = a;
+        }
+    }
+}
+
+/* Phase-screen coefficients c_k = (z_c + i z_s) a_k, with (z_c, z_s) the Box-Muller pair of
+ * Philox4x32-10 words 0 and 1 for counter (k low 32 bits, k high 32 bits, 0, 1), key = seed,
+ * k = ky n + kx.  The screen is Re sum_k c_k exp(2 pi i (kx x + ky y) / n), formed by the
+ * caller.  Output re/im: [n][n] row-major by (ky, kx). */
+void orc_screen_coeffs(int n, double pixel, double r0, double L0, uint64_t seed, double* re, double* im) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_screen_amp(n, pixel, r0, L0, re);
+    for (uint64_t k = 0; k < (uint64_t)n * (uint64_t)n; ++k) {
+        const uint32_t ctr[4] = {(uint32_t)k, (uint32_t)(k >> 32), 0u, 1u};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        float zc, zs;
+        box_muller2(orc_uniform_f32(w[0]), orc_uniform_f32(w[1]), &zc, &zs);
+        const double a = re[k];
+        re[k] = (double)zc * a;
+        im[k] = (double)zs * a;
+    }
+}
+
 /* One noisy detector pixel: photon count ~ Poisson(lambda) plus rint(read_noise * z_c).
  * Words 2 and 3 give one Box-Muller pair (z_c, z_s), computed when read_noise > 0 or
  * lambda >= 16.  lambda < 16: inversion with p_0 = exp(-lambda), p_{k+1} = p_k q_{k+1},

@@ -565,3 +565,75 @@ def test_reduced_precision_product_is_dequantized_matmul(dtype):
     deq = oracle.dequantize_rows(codes, sc, dtype)
     np.testing.assert_allclose(sim.commands(), cfg["gain"] * (deq @ s), rtol=1e-12, atol=1e-15)
     sim.close()
+
+
+# ---- phase screens by the FFT method ("The atmospheric layers generation") ----------------
+
+def _d_von_karman(r, r0, L0):
+    """Von Karman phase structure function for PSD 0.023 r0^-5/3 (f^2 + f0^2)^-11/6 (f in
+    cycles/m): D(r) = 4 pi 0.023 r0^-5/3 int_0^inf f (1 - J0(2 pi f r)) (f^2 + f0^2)^-11/6 df,
+    the Bessel part by the Hankel transform int_0^inf x J0(bx) (x^2 + a^2)^-(mu+1) dx
+    = (b / a)^mu K_mu(ab) / (2^mu Gamma(mu + 1)), mu = 5/6."""
+    from scipy.special import gamma, kv
+    f0 = 1.0 / L0
+    b = 2.0 * np.pi * r
+    return 4.0 * np.pi * 0.023 * r0 ** (-5.0 / 3.0) * (
+        0.6 * f0 ** (-5.0 / 3.0) - f0 ** (-5.0 / 6.0) * b ** (5.0 / 6.0) * kv(5.0 / 6.0, b * f0)
+        / (2.0 ** (5.0 / 6.0) * gamma(11.0 / 6.0)))
+
+
+def test_von_karman_closed_form_reaches_kolmogorov():
+    # L0 -> infinity and r << L0: D -> 6.88 (r / r0)^(5/3); the outer-scale correction falls
+    # off as (r / L0)^(1/3) and the 0.023 constant is 6.88's rounded counterpart (0.5 % apart)
+    r0 = 0.15
+    for r in (0.05, 0.1, 0.3):
+        assert _d_von_karman(r, r0, 1e7) == pytest.approx(6.88 * (r / r0) ** (5.0 / 3.0), rel=0.01)
+
+
+@pytest.mark.parametrize("n,pixel", [(1024, 0.05), (2048, 0.05)])
+def test_screen_spectrum_matches_von_karman_structure_function(n, pixel):
+    # the generator's amplitudes give the expected structure function sum a_k^2 2(1 - cos);
+    # on a screen much larger than L0 it is the von Karman D(r) up to the frequencies above
+    # Nyquist (a few % at 2 samples, < 0.5 % from 10 samples on)
+    r0, L0 = 0.15, 10.0
+    for r_px, tol in ((2, 0.04), (10, 0.005), (40, 0.002)):
+        d = oracle.screen_structure_function(n, pixel, r0, L0, r_px)
+        assert d == pytest.approx(_d_von_karman(r_px * pixel, r0, L0), rel=tol)
+    a = oracle.screen_amp(n, pixel, r0, L0)
+    assert a[0, 0] == 0.0
+    # Hermitian-symmetric amplitudes: a(-k) = a(k)
+    assert np.array_equal(a[1:, 1:], a[1:, 1:][::-1, ::-1]) or n % 2 == 0
+
+
+def test_screen_coefficients_are_standard_complex_normal():
+    n, pixel, r0, L0 = 128, 0.1, 0.15, 3.2
+    a = oracle.screen_amp(n, pixel, r0, L0)
+    m = a > 0
+    z = np.concatenate([oracle.screen_coeffs(n, pixel, r0, L0, s)[m] / a[m] for s in range(20)])
+    assert abs(z.real.mean()) < 0.01 and abs(z.imag.mean()) < 0.01
+    assert z.real.var() == pytest.approx(1.0, abs=0.012) and z.imag.var() == pytest.approx(1.0, abs=0.012)
+    assert abs(np.mean(z.real * z.imag)) < 0.01
+    assert np.mean(z.real ** 4) / np.mean(z.real ** 2) ** 2 == pytest.approx(3.0, abs=0.05)
+    # draws differ across seeds and grid positions
+    c0 = oracle.screen_coeffs(n, pixel, r0, L0, 0)
+    c1 = oracle.screen_coeffs(n, pixel, r0, L0, 1)
+    assert abs(np.corrcoef(c0[m].real / a[m], c1[m].real / a[m])[0, 1]) < 0.05
+
+
+def test_screen_statistics_match_expected_moments():
+    # exact invariants and ensemble moments of Re sum_k c_k e^{2 pi i k.x/n}: zero mean over
+    # the grid (no DC term), variance sum a_k^2, structure function sum a_k^2 2 (1 - cos)
+    n, pixel, r0, L0 = 128, 0.1, 0.15, 3.2
+    S = np.array([oracle.phase_screen(n, pixel, r0, L0, s) for s in range(40)])
+    rms = S.std()
+    assert np.abs(S.mean(axis=(1, 2))).max() < 1e-12 * rms
+    var = np.sum(oracle.screen_amp(n, pixel, r0, L0) ** 2)
+    assert S.var(axis=(1, 2)).mean() == pytest.approx(var, rel=0.1)
+    for r_px, tol in ((1, 0.03), (4, 0.05)):
+        want = oracle.screen_structure_function(n, pixel, r0, L0, r_px)
+        for ax in (1, 2):
+            got = np.mean((np.roll(S, -r_px, axis=ax) - S) ** 2)
+            assert got == pytest.approx(want, rel=tol)
+    # isotropy: the x and y lags come from the same amplitudes
+    a = oracle.screen_amp(n, pixel, r0, L0)
+    assert np.allclose(a, a.T)
