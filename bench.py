@@ -331,6 +331,30 @@ def main():
                 "clocks": vck,
                 "accuracy": "long-exposure Strehl within 1% of the float32 loop (tests/test_gpu_precision.py)"}
 
+    if not args.no_variants:
+        # the workload's layers generated on the device (von Karman FFT method): two FFT passes,
+        # 20 algorithmic bytes per screen point (complex write + read of the intermediate, real
+        # output write; the coefficients are formed in place)
+        lays = cfg["layers"]
+        gen = lambda i: [mcao.generate_screen(l["n"], l["pixel"], l["r0"], l["L0"], l["seed"] + i) for l in lays]
+        for i in range(3):
+            gen(i)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        g0.record(stream)
+        for i in range(reps):
+            gen(10 + i)
+        g1.record(stream)
+        g1.synchronize()
+        gms = g0.elapsed_time(g1) / reps
+        gbytes = 20.0 * sum(l["n"] ** 2 for l in lays)
+        variants["screen_generation"] = {
+            "value": 1e3 / gms, "unit": "atmospheres/s", "ms_per_atmosphere": gms,
+            "layers": [l["n"] for l in lays], "alg_bytes": gbytes,
+            "frac": gbytes / (gms * 1e-3) / 1e9 / peak,
+            "note": "one atmosphere = every layer's screen; timed with CUDA events around the calls"}
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(cfg, screens, R, min(args.steps, 200), dist)

@@ -317,6 +317,21 @@ mcao_status mcao_set_controller(mcao_sim* sim, double a1, double a2, double b0, 
  * process.  Errors: MCAO_E_INVALID_ARG (r out of range). */
 mcao_status mcao_set_realization(mcao_sim* sim, int r);
 
+/* Phase screen of a turbulent layer on the device ("The atmospheric layers generation"): the
+ * FFT method on the periodic n x n grid of pitch pixel_m with the von Karman spectrum
+ * PSD(kappa) = 0.023 r0^(-5/3) (kappa^2 + L0^-2)^(-11/6) (kappa in cycles/m, no DC term), the
+ * complex Gaussian coefficients drawn from Philox4x32-10 (counter (index, 0, 0, 1), key seed,
+ * Box-Muller pair of the detector-noise sampler); the screen is the real part of the
+ * unnormalized inverse DFT, in rad at the wavelength r0 refers to.
+ *   out    device pointer, row-major [n][n] float32.
+ *   stream CUDA stream (cudaStream_t) or NULL; temporaries (8 n^2 + 8 n bytes) are allocated
+ *          and freed in stream order.  Call outside stream capture (sets a kernel attribute).
+ * Errors: MCAO_E_INVALID_ARG (null out, non-positive or non-finite pixel / r0 / L0),
+ * MCAO_E_SHAPE (n outside [2, 4096] or not a product of 2, 3 and 5), MCAO_E_UNSUPPORTED,
+ * MCAO_E_CUDA.  err receives a message on failure (err_len bytes, may be NULL). */
+mcao_status mcao_generate_screen(int n, double pixel_m, double r0_m, double L0_m, uint64_t seed, float* out,
+                                 void* stream, char* err, size_t err_len);
+
 /* Stages timed by the profiler. */
 enum {
     MCAO_STAGE_DM = 0,          /* DM surfaces                                                  */

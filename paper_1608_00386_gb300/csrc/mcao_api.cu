@@ -1731,4 +1731,32 @@ mcao_status mcao_quantize_rows(const float* R, int rows, int cols, int ld, int d
     return MCAO_OK;
 }
 
+mcao_status mcao_generate_screen(int n, double pixel_m, double r0_m, double L0_m, uint64_t seed, float* out,
+                                 void* stream, char* err, size_t err_len) {
+    auto bad = [&](mcao_status st, const char* msg) {
+        if (err && err_len) snprintf(err, err_len, "%s", msg);
+        return st;
+    };
+    if (!out) return bad(MCAO_E_INVALID_ARG, "out is NULL");
+    if (!(is_fin(pixel_m) && pixel_m > 0) || !(is_fin(r0_m) && r0_m > 0) || !(is_fin(L0_m) && L0_m > 0))
+        return bad(MCAO_E_INVALID_ARG, "pixel, r0 and L0 must be finite and > 0");
+    if (n < 2 || n > 4096) return bad(MCAO_E_SHAPE, "n must be in [2, 4096]");
+    const std::vector<int> rad = factor_fft(n);
+    if (rad.empty() || rad.size() > 16) return bad(MCAO_E_SHAPE, "n must be a product of 2, 3 and 5");
+    int dev = 0, smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return bad(MCAO_E_CUDA, cudaGetErrorString(e));
+    if (screen_fft_smem(n) > (size_t)smem) return bad(MCAO_E_UNSUPPORTED, "n too large for the in-shared-memory FFT");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float2 *b = nullptr, *w = nullptr;
+    e = cudaMallocAsync((void**)&b, sizeof(float2) * (size_t)n * n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&w, sizeof(float2) * n, st);
+    if (e == cudaSuccess) e = launch_screen(n, pixel_m, r0_m, L0_m, seed, rad.data(), (int)rad.size(), b, w, out, st);
+    for (float2* p : {b, w})
+        if (p) cudaFreeAsync(p, st);
+    if (e != cudaSuccess) return bad(MCAO_E_CUDA, cudaGetErrorString(e));
+    return MCAO_OK;
+}
+
 }  // extern "C"

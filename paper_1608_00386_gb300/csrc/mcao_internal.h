@@ -257,4 +257,11 @@ cudaError_t launch_sci_field(const SciLaunch& L, cudaStream_t s);
 cudaError_t launch_sci_rows(const SciLaunch& L, cudaStream_t s);
 cudaError_t launch_sci_cols(const SciLaunch& L, cudaStream_t s);
 
+// ---------------------------------------------------------------------------------------------
+// phase screens (von Karman, FFT method)
+// ---------------------------------------------------------------------------------------------
+size_t screen_fft_smem(int n);
+cudaError_t launch_screen(int n, double pixel, double r0, double L0, unsigned long long seed, const int* radices,
+                          int n_radices, float2* work, float2* W, float* out, cudaStream_t s);
+
 }  // namespace mcao

@@ -29,7 +29,7 @@ EXPORTS = [
     "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
-    "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium",
+    "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -115,6 +115,8 @@ def lib():
         "mcao_set_controller": [vp, C.c_double, C.c_double, C.c_double, C.c_double],
         "mcao_get_marechal": [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "mcao_set_sodium": [vp, C.c_int, C.c_double, C.c_double],
+        "mcao_generate_screen": [C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64, vp, vp, C.c_char_p,
+                                 C.c_size_t],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -225,6 +227,16 @@ class Sim:
             layers[i] = _Layer(lay["n"], lay["pixel"], lay["alt"], lay["vx"], lay["vy"], addr, dev)
         self._ck(lib().mcao_load_atmosphere(self.h, len(screens), layers))
         self._keep.append(keep)  # device tensors are adopted: keep them alive
+
+    def generate_atmosphere(self, realization: int | None = None, seed_offset: int = 0):
+        """Generate every layer's screen on the device (mcao_generate_screen with the layer's n,
+        pixel, r0, L0 and seed + seed_offset) and load them for the selected realization."""
+        scr = [generate_screen(lay["n"], lay["pixel"], lay["r0"], lay["L0"], lay["seed"] + seed_offset)
+               for lay in self.cfg["layers"]]
+        import torch
+        torch.cuda.current_stream().synchronize()   # the simulation's streams do not wait on torch's
+        self.load_atmosphere(scr, realization)
+        return scr
 
     def load_dms(self):
         dms = self.cfg["dms"]
@@ -384,6 +396,22 @@ def make_sim(cfg: dict, screens, R, s_ref=None, keep_frames: bool = False, strea
     s.load_dms()
     s.load_reconstructor(R, s_ref, dtype=r_dtype)
     return s
+
+
+def generate_screen(n: int, pixel: float, r0: float, L0: float, seed: int, stream=None):
+    """An n x n von Karman phase screen (rad) generated on the device by mcao_generate_screen;
+    returns a CUDA float32 tensor."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    out = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    err = C.create_string_buffer(256)
+    st = lib().mcao_generate_screen(int(n), float(pixel), float(r0), float(L0), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                    C.c_void_p(out.data_ptr()), C.c_void_p(ptr), err, 256)
+    if st != 0:
+        raise McaoError(st, err.value.decode())
+    return out
 
 
 def quantize_rows(R, dtype: int, stream=None):

@@ -66,3 +66,22 @@ def test_product_does_not_import_the_oracle():
     for f in ("mcao_oracle.c", "__init__.py"):
         text = open(os.path.join(ROOT, "oracle", f)).read()
         assert "paper_1608_00386_gb300" not in text and "mcao.h" not in text
+
+
+@pytest.mark.parametrize("n,pixel,r0,L0,null_out,status", [
+    (64, 0.1, 0.15, 25.0, True, 1),     # null output
+    (64, 0.0, 0.15, 25.0, False, 1),    # pixel <= 0
+    (64, 0.1, -1.0, 25.0, False, 1),    # r0 <= 0
+    (64, 0.1, 0.15, float("inf"), False, 1),
+    (1, 0.1, 0.15, 25.0, False, 2),     # n < 2
+    (77, 0.1, 0.15, 25.0, False, 2),    # 7 * 11: no radix-2/3/5 factorisation
+    (8192, 0.1, 0.15, 25.0, False, 2),  # above 4096
+])
+def test_generate_screen_rejects_before_any_device_call(n, pixel, r0, L0, null_out, status):
+    # argument checks run on the host first; the pointer is never dereferenced
+    import ctypes as C
+    build.build()
+    err = C.create_string_buffer(128)
+    out = None if null_out else C.c_void_p(16)
+    st = mcao.lib().mcao_generate_screen(n, pixel, r0, L0, 1, out, None, err, 128)
+    assert st == status and err.value
