@@ -232,6 +232,49 @@ def cog(img: np.ndarray):
     return sx.value, sy.value
 
 
+def subap_slopes(amp: np.ndarray, phase: np.ndarray, n_fft: int, n_bin: int, sigma_pix: float = 0.0,
+                 direction=(1.0, 0.0)):
+    """Noise-free centre-of-gravity slopes of one subaperture: cog(bin(sh_image)) (phase in rad
+    at the sensing wavelength); the flux normalisation does not change a centroid."""
+    return cog(bin_image(sh_image(amp, phase, n_fft, sigma_pix, direction), n_bin))
+
+
+def subap_jacobian_fd(amp: np.ndarray, phase: np.ndarray, n_fft: int, n_bin: int, sigma_pix: float = 0.0,
+                      direction=(1.0, 0.0), h: float = 1e-4) -> np.ndarray:
+    """d (sx, sy) / d phase of one subaperture by central differences of subap_slopes (the
+    derivative's definition; truncation O(h^2)): [2][n_px][n_px]."""
+    phase = np.array(phase, dtype=np.float64)
+    out = np.zeros((2,) + phase.shape)
+    for j in range(phase.shape[0]):
+        for i in range(phase.shape[1]):
+            p = phase.copy()
+            p[j, i] += h
+            sp = subap_slopes(amp, p, n_fft, n_bin, sigma_pix, direction)
+            p[j, i] -= 2 * h
+            sm = subap_slopes(amp, p, n_fft, n_bin, sigma_pix, direction)
+            out[0, j, i] = (sp[0] - sm[0]) / (2 * h)
+            out[1, j, i] = (sp[1] - sm[1]) / (2 * h)
+    return out
+
+
+def jacobian_fd(sim: "Sim", h: float = 1e-3) -> np.ndarray:
+    """Interaction matrix d slopes / d commands at the simulation's current step and commands by
+    central differences of its measurement (the derivative's definition, truncation O(h^2));
+    the configuration must be noise-free.  Restores the commands."""
+    c0 = sim.commands().copy()
+    D = np.zeros((sim.n_slopes, sim.n_cmd))
+    for j in range(sim.n_cmd):
+        c = c0.copy()
+        c[j] += h
+        sim.set_commands(c)
+        sp = sim.measure()
+        c[j] = c0[j] - h
+        sim.set_commands(c)
+        D[:, j] = (sp - sim.measure()) / (2 * h)
+    sim.set_commands(c0)
+    return D
+
+
 def philox(ctr, key) -> np.ndarray:
     c = np.asarray(ctr, dtype=np.uint32).copy()
     k = np.asarray(key, dtype=np.uint32).copy()

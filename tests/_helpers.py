@@ -42,3 +42,25 @@ def eelt_inputs(n_layers: int = 10):
     screens = inputs.make_screens(cfg)
     n_cmd = inputs.n_commands(cfg)
     return cfg, screens, n_cmd
+
+
+def mcao_small():
+    """8 m two-sensor case for the adjoint tests: one side-launched laser star (8 x 8
+    subapertures of 8 samples, FFT 16, bin 2, elongated spots) and one natural star (2 x 2 of 32,
+    FFT 64, bin 4), two layers, a ground DM and a 5 km DM; noise off."""
+    a = inputs.ARCSEC
+    cfg = {
+        "name": "mcao_small_8m",
+        "D": 8.0, "obstruction": 0.0, "lambda_ref": 500e-9,
+        "dt": 2e-3, "gain": 0.5, "seed": 11, "noise": False, "psf_every": 1, "n_steps": 10,
+        "wfs": [inputs._wfs("lgs", (10 * a, 0.0), 8, 8, 16, 2, 589e-9, 1000.0, height=90e3, na_fwhm=10e3,
+                            launch=(4.2, 0.0)),
+                inputs._wfs("ngs", (0.0, 15 * a), 2, 32, 64, 4, 1.65e-6, 500.0)],
+        "science": [{"theta": (0.0, 0.0), "lambda": 2.2e-6, "n_px": 64, "pad": 2}],
+        "layers": [{"n": 256, "pixel": 0.0625, "alt": 0.0, "vx": 8.0, "vy": 2.0, "r0": 0.2, "L0": 25.0,
+                    "seed": 3},
+                   {"n": 256, "pixel": 0.0625, "alt": 5000.0, "vx": -5.0, "vy": 12.0, "r0": 0.35, "L0": 25.0,
+                    "seed": 4}],
+    }
+    cfg["dms"] = [inputs.dm_spec(cfg, 0.0, 1.0, 0.3), inputs.dm_spec(cfg, 5000.0, 1.4, 0.3)]
+    return cfg

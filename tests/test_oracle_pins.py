@@ -637,3 +637,54 @@ def test_screen_statistics_match_expected_moments():
     # isotropy: the x and y lags come from the same amplitudes
     a = oracle.screen_amp(n, pixel, r0, L0)
     assert np.allclose(a, a.T)
+
+
+# ---- derivatives of the noise-free sensing (interaction matrix by the Jacobian) -------------
+
+@pytest.mark.parametrize("sigma", [0.0, 2.0])
+def test_subap_jacobian_fd_invariants(sigma):
+    # the centroid ignores piston (the derivative sums to zero over the subaperture), samples of
+    # zero amplitude do not act, and halving the step changes the central difference by O(h^2)
+    rng = np.random.default_rng(3)
+    amp = np.ones((8, 8))
+    amp[0, 0] = 0.0
+    amp[0, 7] = 0.5
+    ph = rng.normal(0.0, 0.5, (8, 8))
+    J1 = oracle.subap_jacobian_fd(amp, ph, 16, 2, sigma, (0.6, 0.8), h=1e-4)
+    J2 = oracle.subap_jacobian_fd(amp, ph, 16, 2, sigma, (0.6, 0.8), h=5e-5)
+    scale = np.abs(J1).max()
+    assert scale > 0.01
+    assert np.abs(J1 - J2).max() <= 1e-7 * scale
+    for a in (0, 1):
+        assert abs(J1[a].sum()) <= 1e-8 * scale
+    assert np.all(J1[:, 0, 0] == 0.0)
+    # a phase ramp along x moves the x centroid, not (to first order, for a mirror-symmetric
+    # pupil and flat wavefront) the y one
+    flat = oracle.subap_jacobian_fd(np.ones((8, 8)), np.zeros((8, 8)), 16, 2, 0.0, (1.0, 0.0), h=1e-4)
+    ramp = np.tile(np.arange(8) - 3.5, (8, 1))
+    assert np.sum(flat[0] * ramp) > 0.1
+    assert abs(np.sum(flat[1] * ramp)) <= 1e-8 * abs(np.sum(flat[0] * ramp))
+
+
+def test_interaction_matrix_fd_is_the_derivative():
+    # central differences at h and h/2 agree to O(h^2); the first-order prediction
+    # s(c + e d) - s(c) - e D d shrinks like e^2 (relative error like e), which a wrong D breaks
+    from tests._helpers import mcao_small
+    cfg = mcao_small()
+    o = oracle.Sim(cfg, inputs.make_screens(cfg))
+    rng = np.random.default_rng(1)
+    o.set_commands(rng.normal(0.0, 0.3, o.n_cmd))
+    D1 = oracle.jacobian_fd(o, 1e-3)
+    D2 = oracle.jacobian_fd(o, 5e-4)
+    n = np.linalg.norm
+    assert n(D1 - D2) <= 1e-7 * n(D1)
+    c0 = o.commands()
+    s0 = o.measure()
+    d = rng.normal(0.0, 1.0, o.n_cmd)
+    rel = []
+    for eps in (1e-2, 2.5e-3):
+        o.set_commands(c0 + eps * d)
+        rel.append(n(o.measure() - s0 - eps * (D1 @ d)) / n(eps * (D1 @ d)))
+    assert rel[0] < 2e-3
+    assert 2.5 < rel[0] / rel[1] < 6.0      # linear in eps: ratio 4
+    o.close()
