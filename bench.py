@@ -355,6 +355,39 @@ def main():
             "frac": gbytes / (gms * 1e-3) / 1e9 / peak,
             "note": "one atmosphere = every layer's screen; timed with CUDA events around the calls"}
 
+    if not args.no_variants:
+        # interaction matrix as the exact Jacobian of the noise-free slopes (adjoint sensing +
+        # DM projection) and one command-gradient product, on the workload's geometry and screens
+        js = mcao.Sim(cfg)
+        js.load_atmosphere(d_screens)
+        js.load_dms()
+        js.interaction_matrix()
+        torch.cuda.synchronize()
+        j0, j1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        j0.record(stream)
+        for _ in range(reps):
+            Dm = js.interaction_matrix()
+        j1.record(stream)
+        j1.synchronize()
+        im_ms = j0.elapsed_time(j1) / reps
+        gv = torch.ones(n_slopes, device="cuda")
+        js.slopes_vjp(gv)
+        torch.cuda.synchronize()
+        j0.record(stream)
+        for _ in range(reps):
+            js.slopes_vjp(gv)
+        j1.record(stream)
+        j1.synchronize()
+        vjp_ms = j0.elapsed_time(j1) / reps
+        variants["interaction_matrix"] = {
+            "value": 1e3 / im_ms, "unit": "matrices/s", "ms_per_matrix": im_ms, "shape": list(Dm.shape),
+            "vjp_ms": vjp_ms,
+            "note": ("exact Jacobian d s / d c of the noise-free slopes at the current state; synchronous call "
+                     "timed with CUDA events (includes its zero fill of the matrix and temporary buffers)")}
+        del Dm
+        js.close()
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(cfg, screens, R, min(args.steps, 200), dist)

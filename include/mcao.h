@@ -332,6 +332,34 @@ mcao_status mcao_set_realization(mcao_sim* sim, int r);
 mcao_status mcao_generate_screen(int n, double pixel_m, double r0_m, double L0_m, uint64_t seed, float* out,
                                  void* stream, char* err, size_t err_len);
 
+/* Noise-free (with_noise = 0) or configured-noise (1) slopes of every realization at the current
+ * step and commands, without reconstruction and without advancing time ("The calibration of
+ * the interaction matrices": measurements at a fixed state); read them with mcao_get_slopes.
+ * Errors: MCAO_E_STATE (atmosphere or DMs not loaded), MCAO_E_CUDA. */
+mcao_status mcao_measure(mcao_sim* sim, int with_noise);
+
+/* Interaction matrix as the exact Jacobian D = d s / d c of the noise-free slopes with respect to
+ * the DM commands at the current step, commands and realization ("The calibration of the
+ * interaction matrices"), by the adjoint of the sensing (centre of gravity, binning, elongation,
+ * |FFT|^2, field) and of the DM projection (clamped bilinear sampling of S = Gy C Gx^T).
+ *   D   device pointer, row-major [n_slopes][ld] float32, ld >= n_commands; overwritten (zero
+ *       where no actuator reaches a subaperture: influence weights below 1e-10 are left out).
+ * Synchronous: waits for the device before and after.  Errors: MCAO_E_INVALID_ARG, MCAO_E_SHAPE,
+ * MCAO_E_STATE, MCAO_E_UNSUPPORTED (a subaperture footprint meets more than 128 actuators per
+ * axis), MCAO_E_OOM, MCAO_E_CUDA. */
+mcao_status mcao_interaction_matrix(mcao_sim* sim, float* D, size_t ld);
+
+/* Vector-Jacobian products of the noise-free slopes at the current state: for each of n_vec
+ * vectors g (device, row-major [n_vec][n_slopes]):
+ *   g_commands  device [n_vec][n_commands] = D^T g (or NULL);
+ *   g_phase     device [n_vec][sum over sensors of N_w^2] = (d s / d phi)^T g on each sensor's
+ *               pupil grid (rad at the reference wavelength), sensors concatenated in order, zero
+ *               outside valid subapertures (or NULL).
+ * Outputs are overwritten.  Command gradients are accumulated with atomic adds (summation order
+ * not fixed).  Synchronous.  Errors: MCAO_E_INVALID_ARG (null g, n_vec < 1, both outputs
+ * NULL), MCAO_E_STATE, MCAO_E_UNSUPPORTED, MCAO_E_OOM, MCAO_E_CUDA. */
+mcao_status mcao_slopes_vjp(mcao_sim* sim, const float* g_slopes, int n_vec, float* g_commands, float* g_phase);
+
 /* Stages timed by the profiler. */
 enum {
     MCAO_STAGE_DM = 0,          /* DM surfaces                                                  */

@@ -121,6 +121,7 @@ def lib():
         L.orc_set_controller.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_marechal.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.orc_set_sodium.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+        L.orc_get_elongation.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.orc_screen_amp.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp]
         L.orc_screen_coeffs.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64, _dp, _dp]
         L.orc_set_sodium.restype = C.c_int
@@ -508,6 +509,14 @@ class Sim:
         out = np.zeros((n, n))
         lib().orc_get_dm_surface(self.h, m, _ptr(out, C.c_double))
         return out
+
+    def elongation(self, w: int):
+        """(sigma in image pixels [n_valid], unit direction [n_valid][2]) of sensor w's spots."""
+        nv = lib().orc_n_valid(self.h, w)
+        sig = np.zeros(nv)
+        d = np.zeros((nv, 2))
+        lib().orc_get_elongation(self.h, w, _ptr(sig, C.c_double), _ptr(d, C.c_double))
+        return sig, d
 
     def wfs_phase(self, w: int) -> np.ndarray:
         ww = self.cfg["wfs"][w]

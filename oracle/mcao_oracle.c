@@ -1092,6 +1092,11 @@ void orc_marechal(const orc_sim* S, int q, double* sr_long, double* sr_last) {
 void orc_get_valid(const orc_sim* S, int w, int* idx) {
     memcpy(idx, S->wfs[w].valid_idx, sizeof(int) * S->wfs[w].n_valid);
 }
+/* Elongation of sensor w's valid subapertures: sigma in image pixels and unit direction. */
+void orc_get_elongation(const orc_sim* S, int w, double* sigma_pix, double* dir) {
+    memcpy(sigma_pix, S->wfs[w].sigma_pix, sizeof(double) * S->wfs[w].n_valid);
+    memcpy(dir, S->wfs[w].dir, sizeof(double) * 2 * S->wfs[w].n_valid);
+}
 void orc_get_slopes(const orc_sim* S, double* out) { memcpy(out, S->s, sizeof(double) * S->n_slopes); }
 void orc_get_commands(const orc_sim* S, double* out) { memcpy(out, S->c, sizeof(double) * S->n_cmd); }
 void orc_set_commands(orc_sim* S, const double* in) {

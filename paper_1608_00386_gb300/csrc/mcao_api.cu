@@ -1456,6 +1456,119 @@ mcao_status mcao_get_wfs_phase(mcao_sim* S, int wfs, float* out, size_t n) {
     return MCAO_OK;
 }
 
+// DM surfaces and every sensor at the current step and commands (no reconstruction, no time
+// advance); noise as given
+static cudaError_t enqueue_sensing(mcao_sim* S, int noise) {
+    cudaError_t e = launch_dm_surfaces(make_dm_launch(S), S->s0);
+    if (e != cudaSuccess) return e;
+    auto run = [&](const SubapDev* sub, int n, unsigned int* work, int npx, int nfft, int nbin) {
+        WfsLaunch L = make_wfs_launch(S, sub, n, work);
+        L.ctx.noise = noise;
+        if (!noise) L.frame_out = nullptr;
+        return launch_wfs(L, npx, nfft, nbin, S->s0);
+    };
+    for (const auto& g : S->fft_groups)
+        if ((e = run(g.d_subaps, g.n_subaps, nullptr, g.n_px, g.n_fft, g.n_bin)) != cudaSuccess) return e;
+    for (size_t w = 0; w < S->wfs.size(); ++w) {
+        const WfsHost& W = S->wfs[w];
+        if (W.fft_route || W.n_valid == 0) continue;
+        if ((e = run(W.d_subaps, W.n_valid, S->d_work + w, W.p.n_px, W.p.n_fft, W.p.n_bin)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+mcao_status mcao_measure(mcao_sim* S, int with_noise) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (!S->atm_loaded || !S->dms_loaded) return fail(S, MCAO_E_STATE, "atmosphere and DMs must be loaded");
+    CK(cudaSetDevice(S->device));
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    CK(enqueue_sensing(S, with_noise ? S->cfg.noise : 0));
+    CK(cudaStreamSynchronize(S->s0));
+    return MCAO_OK;
+}
+
+// d slope / d phase of every slope on its subaperture's samples (current realization), then the
+// command rows (D) or the command gradients (gvec -> gc) and the phase gradients
+static mcao_status run_adjoint(mcao_sim* S, float* D, long long ld, const float* gvec, int n_vec, float* gc,
+                               float* g_phase) {
+    int P = 1;
+    for (const auto& W : S->wfs) P = std::max(P, W.p.n_px * W.p.n_px);
+    CK(cudaDeviceSynchronize());   // inputs produced on any stream are complete
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    float* sens = nullptr;
+    int* d_err = nullptr;
+    cudaError_t e = dalloc(&sens, (size_t)S->n_slopes * P);
+    if (e == cudaSuccess) e = dalloc(&d_err, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), S->s0);
+    if (e == cudaSuccess) e = launch_dm_surfaces(make_dm_launch(S), S->s0);
+    long long phase_total = 0;
+    for (const auto& W : S->wfs) phase_total += (long long)W.N * W.N;
+    if (e == cudaSuccess && D) e = cudaMemsetAsync(D, 0, sizeof(float) * (size_t)S->n_slopes * ld, S->s0);
+    if (e == cudaSuccess && gc) e = cudaMemsetAsync(gc, 0, sizeof(float) * (size_t)n_vec * S->n_cmd, S->s0);
+    if (e == cudaSuccess && g_phase) e = cudaMemsetAsync(g_phase, 0, sizeof(float) * (size_t)n_vec * phase_total, S->s0);
+    long long phase_off = 0;
+    for (size_t w = 0; w < S->wfs.size() && e == cudaSuccess; ++w) {
+        const WfsHost& W = S->wfs[w];
+        if (W.n_valid > 0) {
+            SensLaunch L{};
+            L.ctx = make_ctx(S);
+            L.real = S->cur;
+            L.subaps = W.d_subaps;
+            L.n_subaps = W.n_valid;
+            L.sens = sens;
+            L.P = P;
+            e = launch_sens(L, W.p.n_fft, S->s0);
+            ProjLaunch J{};
+            J.ctx = L.ctx;
+            J.real = S->cur;
+            J.n_layers = S->n_layers;
+            J.n_dms = S->n_dms;
+            J.desc = S->d_dm_desc;
+            J.g = S->d_dm_g;
+            J.band = S->d_dm_band;
+            J.act_map = S->d_dm_map;
+            J.subaps = W.d_subaps;
+            J.n_valid = W.n_valid;
+            J.sens = sens;
+            J.P = P;
+            J.D = D;
+            J.ld = ld;
+            J.gvec = gvec;
+            J.n_vec = n_vec;
+            J.n_slopes = S->n_slopes;
+            J.gc = gc;
+            J.n_cmd = S->n_cmd;
+            J.err = d_err;
+            if (e == cudaSuccess && (D || gc)) e = launch_dm_adjoint(J, S->s0);
+            if (e == cudaSuccess && g_phase) e = launch_phase_adjoint(J, g_phase, phase_total, phase_off, S->s0);
+        }
+        phase_off += (long long)W.N * W.N;
+    }
+    int h_err = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
+    if (e == cudaSuccess) e = cudaMemcpy(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(sens);
+    cudaFree(d_err);
+    CK(e);
+    if (h_err) return fail(S, MCAO_E_UNSUPPORTED, "a subaperture footprint meets more than 128 actuators per axis");
+    return MCAO_OK;
+}
+
+mcao_status mcao_interaction_matrix(mcao_sim* S, float* D, size_t ld) {
+    if (!S || !D) return MCAO_E_INVALID_ARG;
+    if (!S->atm_loaded || !S->dms_loaded) return fail(S, MCAO_E_STATE, "atmosphere and DMs must be loaded");
+    if (ld < (size_t)S->n_cmd) return fail(S, MCAO_E_SHAPE, "ld must be >= %d", S->n_cmd);
+    CK(cudaSetDevice(S->device));
+    return run_adjoint(S, D, (long long)ld, nullptr, 0, nullptr, nullptr);
+}
+
+mcao_status mcao_slopes_vjp(mcao_sim* S, const float* g_slopes, int n_vec, float* g_commands, float* g_phase) {
+    if (!S || !g_slopes || n_vec < 1 || (!g_commands && !g_phase)) return MCAO_E_INVALID_ARG;
+    if (!S->atm_loaded || !S->dms_loaded) return fail(S, MCAO_E_STATE, "atmosphere and DMs must be loaded");
+    CK(cudaSetDevice(S->device));
+    return run_adjoint(S, nullptr, 0, g_slopes, n_vec, g_commands, g_phase);
+}
+
 mcao_status mcao_get_dm_surface(mcao_sim* S, int dm, float* out, size_t n) {
     if (!S || !out) return MCAO_E_INVALID_ARG;
     if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");

@@ -264,4 +264,41 @@ size_t screen_fft_smem(int n);
 cudaError_t launch_screen(int n, double pixel, double r0, double L0, unsigned long long seed, const int* radices,
                           int n_radices, float2* work, float2* W, float* out, cudaStream_t s);
 
+
+// ---------------------------------------------------------------------------------------------
+// adjoint of the noise-free sensing (interaction matrix, vector-Jacobian products)
+// ---------------------------------------------------------------------------------------------
+struct SensLaunch {
+    Ctx ctx;
+    int real;
+    const SubapDev* subaps;  // one sensor's valid subapertures
+    int n_subaps;
+    float* sens;             // [n_slopes][P]: d slope / d phase on the slope's subaperture samples
+    int P;                   // row length (largest n_px^2)
+};
+struct ProjLaunch {
+    Ctx ctx;
+    int real, n_layers, n_dms;
+    const DmDesc* desc;
+    const float* g;
+    const int2* band;
+    const int* act_map;
+    const SubapDev* subaps;  // one sensor's valid subapertures
+    int n_valid;
+    const float* sens;
+    int P;
+    float* D;                // interaction matrix rows (or null)
+    long long ld;
+    const float* gvec;       // [n_vec][n_slopes] (or null)
+    int n_vec, n_slopes;
+    float* gc;               // [n_vec][n_cmd] accumulated (or null)
+    int n_cmd;
+    int* err;                // set when a footprint meets more actuators than a block holds
+};
+size_t sens_smem(int n_fft);
+cudaError_t launch_sens(const SensLaunch& L, int n_fft, cudaStream_t s);
+cudaError_t launch_dm_adjoint(const ProjLaunch& L, cudaStream_t s);
+cudaError_t launch_phase_adjoint(const ProjLaunch& L, float* g_phase, long long phase_stride, long long phase_off,
+                                 cudaStream_t s);
+
 }  // namespace mcao

@@ -29,7 +29,8 @@ EXPORTS = [
     "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
-    "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen",
+    "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
+    "mcao_interaction_matrix", "mcao_slopes_vjp",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -117,6 +118,9 @@ def lib():
         "mcao_set_sodium": [vp, C.c_int, C.c_double, C.c_double],
         "mcao_generate_screen": [C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64, vp, vp, C.c_char_p,
                                  C.c_size_t],
+        "mcao_measure": [vp, C.c_int],
+        "mcao_interaction_matrix": [vp, vp, C.c_size_t],
+        "mcao_slopes_vjp": [vp, vp, C.c_int, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -292,6 +296,38 @@ class Sim:
         c = np.ascontiguousarray(c, dtype=np.float32)
         self._ck(lib().mcao_set_commands(self.h, c.ctypes.data, c.size))
 
+    def measure(self, noise: bool = False) -> np.ndarray:
+        """Slopes at the current step and commands without reconstruction or time advance
+        (noise-free unless noise=True and the configuration has noise)."""
+        self._ck(lib().mcao_measure(self.h, int(bool(noise))))
+        return self.slopes()
+
+    def interaction_matrix(self):
+        """Exact Jacobian d slopes / d commands of the noise-free slopes at the current state, as a
+        CUDA float32 tensor [n_slopes][n_commands] (mcao_interaction_matrix)."""
+        import torch
+        D = torch.empty((self.query(Q_SLOPES), self.query(Q_COMMANDS)), dtype=torch.float32, device="cuda")
+        self._ck(lib().mcao_interaction_matrix(self.h, D.data_ptr(), D.shape[1]))
+        return D
+
+    def slopes_vjp(self, g, commands: bool = True, phase: bool = False):
+        """Vector-Jacobian products of the noise-free slopes (mcao_slopes_vjp) for g, a CUDA tensor
+        [n_slopes] or [n_vec][n_slopes]: (command gradients [.., n_commands] or None, pupil-phase
+        gradients [.., sum of N_w^2] or None), shaped like g."""
+        import torch
+        ns, nc = self.query(Q_SLOPES), self.query(Q_COMMANDS)
+        g2 = g.detach().to(device="cuda", dtype=torch.float32).reshape(-1, ns).contiguous()
+        nv = g2.shape[0]
+        gc = torch.empty((nv, nc), dtype=torch.float32, device="cuda") if commands else None
+        nph = sum(self.query(Q_WFS_PHASE, w) for w in range(len(self.cfg["wfs"])))
+        gp = torch.empty((nv, nph), dtype=torch.float32, device="cuda") if phase else None
+        self._ck(lib().mcao_slopes_vjp(self.h, g2.data_ptr(), nv, gc.data_ptr() if gc is not None else None,
+                                       gp.data_ptr() if gp is not None else None))
+        if g.dim() == 1:
+            gc = gc[0] if gc is not None else None
+            gp = gp[0] if gp is not None else None
+        return gc, gp
+
     def valid(self, w: int) -> np.ndarray:
         out = np.empty(self.query(Q_VALID, w), np.int32)
         self._ck(lib().mcao_get_valid(self.h, w, out.ctypes.data, out.size))
@@ -396,6 +432,44 @@ def make_sim(cfg: dict, screens, R, s_ref=None, keep_frames: bool = False, strea
     s.load_dms()
     s.load_reconstructor(R, s_ref, dtype=r_dtype)
     return s
+
+
+def _sensing_function():
+    import torch
+
+    class SensingFunction(torch.autograd.Function):
+        """Noise-free slopes as a differentiable function of the DM commands: forward sets the
+        commands and measures (mcao_measure), backward is the vector-Jacobian product at the
+        same commands (mcao_slopes_vjp)."""
+
+        @staticmethod
+        def forward(ctx, commands, sim):
+            c = commands.detach().to("cpu", torch.float32).numpy()
+            sim.set_commands(c)
+            s = sim.measure(noise=False)
+            ctx.sim = sim
+            ctx.c = c
+            return torch.from_numpy(s.copy()).to(commands.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            ctx.sim.set_commands(ctx.c)
+            gc, _ = ctx.sim.slopes_vjp(g)
+            return gc.to(g.device), None
+
+    return SensingFunction
+
+
+_SENSING = None
+
+
+def sensing(sim: "Sim", commands):
+    """slopes = sensing(sim, commands): autograd-aware noise-free measurement at the current step
+    (sets the simulation's commands; their controller memory restarts as after set_commands)."""
+    global _SENSING
+    if _SENSING is None:
+        _SENSING = _sensing_function()
+    return _SENSING.apply(commands, sim)
 
 
 def generate_screen(n: int, pixel: float, r0: float, L0: float, seed: int, stream=None):
