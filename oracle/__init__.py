@@ -121,6 +121,9 @@ def lib():
         L.orc_set_controller.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_marechal.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.orc_set_sodium.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+        L.orc_set_misregistration.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.orc_dm_surface_misreg.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
+                                            C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
         L.orc_get_elongation.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
         L.orc_screen_amp.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp]
         L.orc_screen_coeffs.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64, _dp, _dp]
@@ -216,6 +219,16 @@ def sh_image(amp: np.ndarray, phase: np.ndarray, n_fft: int, sigma_pix: float = 
     lib().orc_sh_image(amp.shape[0], n_fft, _ptr(amp, C.c_double), _ptr(phase, C.c_double),
                        sigma_pix, direction[0], direction[1], _ptr(img, C.c_double))
     return img
+
+
+def dm_surface_misreg(cmd_grid: np.ndarray, pitch: float, coupling: float, surf_n: int, surf_dx: float,
+                      shift=(0.0, 0.0), rotation: float = 0.0, magnification: float = 1.0) -> np.ndarray:
+    """Surface of a translated, rotated and magnified DM by the direct sum over actuators."""
+    C_ = np.ascontiguousarray(cmd_grid, dtype=np.float64)
+    out = np.zeros((surf_n, surf_n))
+    lib().orc_dm_surface_misreg(C_.shape[1], C_.shape[0], pitch, coupling, surf_n, surf_dx, shift[0], shift[1],
+                                rotation, magnification, _ptr(C_, C.c_double), _ptr(out, C.c_double))
+    return out
 
 
 def bin_image(img: np.ndarray, n_bin: int) -> np.ndarray:
@@ -509,6 +522,12 @@ class Sim:
         out = np.zeros((n, n))
         lib().orc_get_dm_surface(self.h, m, _ptr(out, C.c_double))
         return out
+
+    def set_misregistration(self, m: int, shift_x: float, shift_y: float, rotation: float, magnification: float):
+        """DM m seen through T(q) = magnification R(rotation) q + shift (m, rad) from the next
+        measurement on."""
+        if lib().orc_set_misregistration(self.h, m, shift_x, shift_y, rotation, magnification) != 0:
+            raise ValueError("bad DM index or magnification")
 
     def elongation(self, w: int):
         """(sigma in image pixels [n_valid], unit direction [n_valid][2]) of sensor w's spots."""

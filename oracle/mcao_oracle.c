@@ -298,6 +298,33 @@ void orc_dm_surface(int nx, int ny, double pitch, double coupling, int surf_n, d
     free(Gx); free(Gy); free(T);
 }
 
+/* Surface of a misregistered DM: the DM's own surface function evaluated at T^-1(x, y), where
+ * T(q) = mag R(rot) q + (shift_x, shift_y) maps DM coordinates to the beam's (rotation
+ * counter-clockwise by rot): S(x, y) = sum_{a,b} C[b][a] exp(-|T^-1(x, y) - (x_a, y_b)|^2 / 2 sigma^2),
+ * the direct double sum over every actuator (the DM translated, rotated and magnified as a rigid
+ * body with its influence functions). */
+void orc_dm_surface_misreg(int nx, int ny, double pitch, double coupling, int surf_n, double surf_dx,
+                           double shift_x, double shift_y, double rot, double mag, const double* C, double* S) {
+    double sig = orc_if_sigma(pitch, coupling);
+    double cr = cos(rot), sr = sin(rot);
+    for (int j = 0; j < surf_n; ++j)
+        for (int i = 0; i < surf_n; ++i) {
+            double x = ((double)i - 0.5 * (double)(surf_n - 1)) * surf_dx - shift_x;
+            double y = ((double)j - 0.5 * (double)(surf_n - 1)) * surf_dx - shift_y;
+            double qx = (cr * x + sr * y) / mag, qy = (-sr * x + cr * y) / mag;
+            double acc = 0.0;
+            for (int b = 0; b < ny; ++b) {
+                double yb = ((double)b - 0.5 * (double)(ny - 1)) * pitch;
+                for (int a = 0; a < nx; ++a) {
+                    double xa = ((double)a - 0.5 * (double)(nx - 1)) * pitch;
+                    double d2 = (qx - xa) * (qx - xa) + (qy - yb) * (qy - yb);
+                    acc += C[(size_t)b * nx + a] * exp(-d2 / (2.0 * sig * sig));
+                }
+            }
+            S[(size_t)j * surf_n + i] = acc;
+        }
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Shack-Hartmann spot (a4-a7) and centroid (a9)                                              */
 /* ------------------------------------------------------------------------------------------ */
@@ -683,6 +710,7 @@ typedef struct {
     double** screen;          /* promoted layers                                                 */
     double** surf;            /* DM surfaces [surf_n][surf_n]                                    */
     int* dm_nvalid; int* dm_cmd0;
+    double* misreg;           /* [n_dms][4]: shift_x, shift_y (m), rotation (rad), magnification */
     int n_cmd, n_slopes;
     const float* R; double* s_ref;
     int r_dtype;
@@ -771,7 +799,12 @@ static void update_dm_surfaces(orc_sim* S) {
         int q = S->dm_cmd0[m];
         for (int a = 0; a < M->nx * M->ny; ++a)
             if (M->valid[a]) C[a] = S->c[q++];
-        orc_dm_surface(M->nx, M->ny, M->pitch, M->coupling, M->surf_n, M->surf_dx, C, S->surf[m]);
+        const double* T = &S->misreg[4 * m];
+        if (T[0] == 0.0 && T[1] == 0.0 && T[2] == 0.0 && T[3] == 1.0)
+            orc_dm_surface(M->nx, M->ny, M->pitch, M->coupling, M->surf_n, M->surf_dx, C, S->surf[m]);
+        else
+            orc_dm_surface_misreg(M->nx, M->ny, M->pitch, M->coupling, M->surf_n, M->surf_dx, T[0], T[1], T[2],
+                                  T[3], C, S->surf[m]);
         free(C);
     }
 }
@@ -799,6 +832,8 @@ orc_sim* orc_create(const orc_config* cfg) {
     S->surf = (double**)calloc(S->n_dms ? S->n_dms : 1, sizeof(double*));
     S->dm_nvalid = (int*)calloc(S->n_dms ? S->n_dms : 1, sizeof(int));
     S->dm_cmd0 = (int*)calloc(S->n_dms ? S->n_dms : 1, sizeof(int));
+    S->misreg = (double*)calloc(4 * (size_t)(S->n_dms ? S->n_dms : 1), sizeof(double));
+    for (int m = 0; m < S->n_dms; ++m) S->misreg[4 * m + 3] = 1.0;
     int ncmd = 0;
     for (int m = 0; m < S->n_dms; ++m) {
         orc_dm* M = &S->dm_p[m];
@@ -888,7 +923,7 @@ static void sim_free(orc_sim* S) {
         plan_free(W->plan); free(W->lam); free(W->frames);
     }
     for (int q = 0; q < S->n_sci; ++q) { free(S->sci[q].A); free(S->sci[q].psf); plan_free(S->sci[q].plan); }
-    free(S->screen); free(S->surf); free(S->dm_nvalid); free(S->dm_cmd0);
+    free(S->screen); free(S->surf); free(S->dm_nvalid); free(S->dm_cmd0); free(S->misreg);
     free(S->wfs); free(S->sci); free(S->wfs_p); free(S->sci_p); free(S->lay_p); free(S->dm_p);
     free(S->s_ref); free(S->c); free(S->s); free(S->c_prev); free(S->dc_prev);
     free(S->Rb); free(S->Rq); free(S->r_scale);
@@ -1092,6 +1127,15 @@ void orc_marechal(const orc_sim* S, int q, double* sr_long, double* sr_last) {
 void orc_get_valid(const orc_sim* S, int w, int* idx) {
     memcpy(idx, S->wfs[w].valid_idx, sizeof(int) * S->wfs[w].n_valid);
 }
+/* Misregistration of DM m (shift in m at its conjugate altitude, rotation in rad, magnification)
+ * from the next measurement or step on.  Returns -1 for a bad index or magnification <= 0. */
+int orc_set_misregistration(orc_sim* S, int m, double shift_x, double shift_y, double rot, double mag) {
+    if (m < 0 || m >= S->n_dms || !(mag > 0.0)) return -1;
+    double* T = &S->misreg[4 * m];
+    T[0] = shift_x; T[1] = shift_y; T[2] = rot; T[3] = mag;
+    return 0;
+}
+
 /* Elongation of sensor w's valid subapertures: sigma in image pixels and unit direction. */
 void orc_get_elongation(const orc_sim* S, int w, double* sigma_pix, double* dir) {
     memcpy(sigma_pix, S->wfs[w].sigma_pix, sizeof(double) * S->wfs[w].n_valid);

@@ -688,3 +688,48 @@ def test_interaction_matrix_fd_is_the_derivative():
     assert rel[0] < 2e-3
     assert 2.5 < rel[0] / rel[1] < 6.0      # linear in eps: ratio 4
     o.close()
+
+
+# ---- misregistered DM: the surface of the DM moved as a rigid body ---------------------------
+
+def test_misregistered_surface_identities():
+    # identity transform = the factorised surface; a quarter turn = the aligned surface of the
+    # rotated command grid; a shift by whole surface samples = the shifted surface; a
+    # magnification of 2 on an odd grid = the aligned surface at half the coordinates
+    rng = np.random.default_rng(0)
+    n, pitch, cp, sn, dx = 9, 0.5, 0.3, 41, 0.125
+    C_ = rng.normal(size=(n, n))
+    S0 = oracle.dm_surface(C_, pitch, cp, sn, dx)
+    tol = 1e-12 * np.abs(S0).max()
+    assert np.abs(oracle.dm_surface_misreg(C_, pitch, cp, sn, dx) - S0).max() <= tol
+    Cr = np.zeros_like(C_)
+    for b in range(n):
+        for a in range(n):
+            Cr[a, n - 1 - b] = C_[b, a]          # actuator (x_a, y_b) moves to (-y_b, x_a)
+    S90 = oracle.dm_surface_misreg(C_, pitch, cp, sn, dx, rotation=np.pi / 2)
+    assert np.abs(S90 - oracle.dm_surface(Cr, pitch, cp, sn, dx)).max() <= tol
+    Ssh = oracle.dm_surface_misreg(C_, pitch, cp, sn, dx, shift=(3 * dx, -2 * dx))
+    assert np.abs(Ssh[:-2, 3:] - S0[2:, :-3]).max() <= tol
+    Sm = oracle.dm_surface_misreg(C_, pitch, cp, sn, dx, magnification=2.0)
+    i = np.arange(0, sn, 2)
+    h = 20 + (i - 20) // 2
+    assert np.abs(Sm[np.ix_(i, i)] - S0[np.ix_(h, h)]).max() <= tol
+
+
+def test_misregistration_moves_the_measurement():
+    # identity misregistration leaves the slopes unchanged bit for bit; a shift changes them;
+    # shifting back restores them
+    from tests._helpers import mcao_small
+    cfg = mcao_small()
+    o = oracle.Sim(cfg, inputs.make_screens(cfg))
+    o.set_commands(np.random.default_rng(2).normal(0.0, 0.3, o.n_cmd))
+    s0 = o.measure()
+    o.set_misregistration(0, 0.0, 0.0, 0.0, 1.0)
+    assert np.array_equal(o.measure(), s0)
+    o.set_misregistration(0, 0.3, -0.2, 0.01, 1.01)
+    assert np.abs(o.measure() - s0).max() > 1e-3
+    o.set_misregistration(0, 0.0, 0.0, 0.0, 1.0)
+    assert np.array_equal(o.measure(), s0)
+    with pytest.raises(ValueError):
+        o.set_misregistration(0, 0.0, 0.0, 0.0, 0.0)
+    o.close()
