@@ -332,6 +332,19 @@ mcao_status mcao_set_realization(mcao_sim* sim, int r);
 mcao_status mcao_generate_screen(int n, double pixel_m, double r0_m, double L0_m, uint64_t seed, float* out,
                                  void* stream, char* err, size_t err_len);
 
+/* Misregistration of DM `dm` ("Conclusions": rotation of the DM and its modal basis with respect
+ * to the sensors; also translation and magnification): the DM moves as a rigid body, its
+ * surface at beam coordinates p being the aligned surface at q = R(-rotation)(p - shift) / mag
+ * (shift in m at the DM's conjugate altitude, rotation in rad counter-clockwise, magnification
+ * of actuator pitch and influence width).  Applies to every later step, measurement and
+ * interaction matrix; (0, 0, 0, 1) restores the nominal DM.  Without rotation the transform is
+ * folded into the separable Gaussian tables; with rotation the DM kernel evaluates every surface
+ * sample against the actuators around q (slower).  Errors: MCAO_E_INVALID_ARG (bad index,
+ * non-finite values, |rotation| > pi, magnification outside (0.5, 2)), MCAO_E_STATE (DMs not
+ * loaded), MCAO_E_UNSUPPORTED (too many actuators per surface tile), MCAO_E_CUDA. */
+mcao_status mcao_set_misregistration(mcao_sim* sim, int dm, double shift_x, double shift_y, double rotation,
+                                     double magnification);
+
 /* Noise-free (with_noise = 0) or configured-noise (1) slopes of every realization at the current
  * step and commands, without reconstruction and without advancing time ("The calibration of
  * the interaction matrices": measurements at a fixed state); read them with mcao_get_slopes.

@@ -17,7 +17,8 @@
 // Projection on the DMs: phi(p) = ... - bilinear(S_m, p) and S_m = Gy C Gx^T, so
 //   d phi(p) / d C[b][a] = -((1 - t_x) Gx[i0][a] + t_x Gx[i1][a]) ((1 - t_y) Gy[j0][b] + t_y Gy[j1][b]),
 // the same fixed-point sample positions and clamped bilinear weights as the forward; actuators
-// outside the union of the forward's per-tile bands (weights below 1e-10) are left out.
+// outside the union of the forward's per-tile bands (weights below 1e-10) are left out.  A
+// rotated DM has no separable tables: its weights are evaluated at each bilinear corner.
 #include "device_common.cuh"
 #include "mcao_internal.h"
 
@@ -195,6 +196,83 @@ __global__ void __launch_bounds__(kAdjThreads) wfs_sens_kernel(SensLaunch L) {
     }
 }
 
+// Rotated DM: the weight of actuator (a, b) on surface sample (i, j) is the influence function
+// at q(i, j) = R(-rot)((x_i, y_j) - shift) / mag; the slope's row entry sums the subaperture
+// derivative over the four bilinear corners of every pupil sample.
+__device__ void dm_adjoint_general(const ProjLaunch& L, const GridView& v, const DmDesc& dd, int row, int npx,
+                                   const float* s_L, const AxisEnt* s_ex, const AxisEnt* s_ey, int* s_rng) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const float c0 = 0.5f * (float)(dd.surf_n - 1), ca = 0.5f * (float)(dd.nx - 1), cb = 0.5f * (float)(dd.ny - 1);
+    auto to_act = [&](int i, int j, float& ua, float& ub) {
+        const float x = ((float)i - c0) * dd.dx - dd.shx, y = ((float)j - c0) * dd.dx - dd.shy;
+        ua = (dd.cr * x + dd.sr * y) * dd.inv_mag / dd.pitch + ca;
+        ub = (-dd.sr * x + dd.cr * y) * dd.inv_mag / dd.pitch + cb;
+    };
+    if (tid == 0) {
+        int cx0 = v.n, cx1 = 0, cy0 = v.n, cy1 = 0;
+        for (int q = 0; q < npx; ++q) {
+            cx0 = min(cx0, s_ex[q].idx & 0xffff);
+            cx1 = max(cx1, s_ex[q].idx >> 16);
+            cy0 = min(cy0, s_ey[q].idx & 0xffff);
+            cy1 = max(cy1, s_ey[q].idx >> 16);
+        }
+        float lo_a = 1e30f, hi_a = -1e30f, lo_b = 1e30f, hi_b = -1e30f;
+        for (int c = 0; c < 4; ++c) {
+            float ua, ub;
+            to_act((c & 1) ? cx1 : cx0, (c & 2) ? cy1 : cy0, ua, ub);
+            lo_a = fminf(lo_a, ua); hi_a = fmaxf(hi_a, ua);
+            lo_b = fminf(lo_b, ub); hi_b = fmaxf(hi_b, ub);
+        }
+        int a0 = max(0, (int)ceilf(lo_a - dd.rc)), a1 = min(dd.nx - 1, (int)floorf(hi_a + dd.rc)) + 1;
+        int b0 = max(0, (int)ceilf(lo_b - dd.rc)), b1 = min(dd.ny - 1, (int)floorf(hi_b + dd.rc)) + 1;
+        if (a1 < a0) a1 = a0;
+        if (b1 < b0) b1 = b0;
+        if (a1 - a0 > kAdjMaxBand || b1 - b0 > kAdjMaxBand) {
+            atomicExch(L.err, 1);
+            a1 = a0;
+            b1 = b0;
+        }
+        s_rng[0] = a0; s_rng[1] = a1; s_rng[2] = b0; s_rng[3] = b1;
+    }
+    __syncthreads();
+    const int a0 = s_rng[0], na = s_rng[1] - s_rng[0], b0 = s_rng[2], nbd = s_rng[3] - s_rng[2];
+    for (int idx = tid; idx < na * nbd; idx += nthr) {
+        const int b = idx / na, a = idx - b * na;
+        const float fa = (float)(a0 + a), fb = (float)(b0 + b);
+        float acc = 0.0f;
+        for (int y = 0; y < npx; ++y) {
+            const AxisEnt ey = s_ey[y];
+            const int r0 = ey.idx & 0xffff, r1 = ey.idx >> 16;
+            for (int x = 0; x < npx; ++x) {
+                const float lv = s_L[y * npx + x];
+                if (lv == 0.0f) continue;
+                const AxisEnt ex = s_ex[x];
+                const int q0 = ex.idx & 0xffff, q1 = ex.idx >> 16;
+                float w = 0.0f;
+                for (int c = 0; c < 4; ++c) {
+                    const int i = (c & 1) ? q1 : q0, j = (c & 2) ? r1 : r0;
+                    const float wc = ((c & 1) ? ex.t : 1.0f - ex.t) * ((c & 2) ? ey.t : 1.0f - ey.t);
+                    float ua, ub;
+                    to_act(i, j, ua, ub);
+                    const float da = (ua - fa) * dd.pitch, db = (ub - fb) * dd.pitch;
+                    w = fmaf(wc, expf(-(da * da + db * db) * dd.inv2s2), w);
+                }
+                acc = fmaf(lv, w, acc);
+            }
+        }
+        const float val = v.sign * acc;
+        const int cmd = L.act_map[dd.map_off + (long long)(b0 + b) * dd.nx + a0 + a];
+        if (cmd < 0) continue;
+        if (L.D) L.D[(long long)row * L.ld + cmd] = val;
+        if (L.gc)
+            for (int vv = 0; vv < L.n_vec; ++vv) {
+                const float gv = L.gvec[(long long)vv * L.n_slopes + row];
+                if (gv != 0.0f) atomicAdd(L.gc + (long long)vv * L.n_cmd + cmd, gv * val);
+            }
+    }
+    __syncthreads();
+}
+
 // One block per slope of one sensor: the slope's row of d s / d c from its pupil-sample
 // derivatives, written to D (interaction matrix) and/or accumulated as g_v[row] * row into the
 // command gradients of every vector v.
@@ -222,6 +300,10 @@ __global__ void __launch_bounds__(256) dm_adjoint_kernel(ProjLaunch L) {
         else if (tid < 2 * npx)
             s_ey[tid - npx] = axis_entry(v.ay + (long long)(j0 + tid - npx) * v.bp + k * v.vy, v.n, v.periodic, v.inv_n);
         __syncthreads();
+        if (dd.general) {
+            dm_adjoint_general(L, v, dd, row, npx, s_L, s_ex, s_ey, s_rng);
+            continue;
+        }
         if (tid == 0) {
             int cx0 = v.n, cx1 = 0, cy0 = v.n, cy1 = 0;
             for (int q = 0; q < npx; ++q) {

@@ -3,7 +3,9 @@
 // equal to the coupling.  The Gaussian factorises, so S = Gy C Gx^T exactly.  One block per
 // 32 x 32 tile of the surface: the tile's actuator sub-grid C (rows and columns whose weight on
 // the tile is at least 1e-10; dropped terms are below float rounding of the surface), the
-// matching Gx and Gy rows and T = C Gx^T are staged in shared memory, then S = Gy T.
+// matching Gx and Gy rows and T = C Gx^T are staged in shared memory, then S = Gy T.  A
+// translated or magnified DM has its transform folded into Gx and Gy; a rotated one evaluates
+// every sample against the actuators around its position in the DM's own frame.
 #include "mcao_internal.h"
 
 namespace mcao {
@@ -32,6 +34,34 @@ __global__ void __launch_bounds__(256) dm_surface_kernel(DmLaunch L) {
     const int n = d.surf_n;
     const int ty_i = t / d.tiles_x, tx_i = t % d.tiles_x;
     const int j0 = ty_i * kT, i0 = tx_i * kT;
+    if (d.general) {
+        // rotated DM: each sample q = R(-rot)((x, y) - shift) / mag weighs the actuators within rc
+        // pitches directly
+        const float c0 = 0.5f * (float)(n - 1), ca = 0.5f * (float)(d.nx - 1), cb = 0.5f * (float)(d.ny - 1);
+        for (int q = threadIdx.x; q < kT * kT; q += blockDim.x) {
+            const int i = i0 + (q & (kT - 1)), j = j0 + q / kT;
+            if (i >= n || j >= n) continue;
+            const float x = ((float)i - c0) * d.dx - d.shx, y = ((float)j - c0) * d.dx - d.shy;
+            const float ua = (d.cr * x + d.sr * y) * d.inv_mag / d.pitch + ca;
+            const float ub = (-d.sr * x + d.cr * y) * d.inv_mag / d.pitch + cb;
+            const int a0 = max(0, (int)ceilf(ua - d.rc)), a1 = min(d.nx - 1, (int)floorf(ua + d.rc));
+            const int b0 = max(0, (int)ceilf(ub - d.rc)), b1 = min(d.ny - 1, (int)floorf(ub + d.rc));
+            float acc = 0.0f;
+            for (int b = b0; b <= b1; ++b) {
+                const float dy = (ub - (float)b) * d.pitch;
+                float row = 0.0f;
+                for (int a = a0; a <= a1; ++a) {
+                    const int idx = L.act_map[d.map_off + (long long)b * d.nx + a];
+                    if (idx < 0) continue;
+                    const float dxa = (ua - (float)a) * d.pitch;
+                    row = fmaf(cmd[idx], expf(-dxa * dxa * d.inv2s2), row);
+                }
+                acc = fmaf(expf(-dy * dy * d.inv2s2), row, acc);
+            }
+            L.surf[real * L.surf_stride + d.surf_off + (long long)j * n + i] = acc;
+        }
+        return;
+    }
     const int2 bx = L.band[d.tband_x + tx_i], by = L.band[d.tband_y + ty_i];
     const int na = bx.y - bx.x, nb = by.y - by.x;
     const int tid = threadIdx.x;

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -113,6 +114,7 @@ struct mcao_sim {
     int n_dms = 0;
     std::vector<mcao_dm> dms;
     std::vector<DmDesc> dm_desc;
+    std::vector<std::array<double, 4>> dm_misreg;   // per DM: shift x, y (m), rotation (rad), magnification
     DmDesc* d_dm_desc = nullptr;
     float* d_dm_g = nullptr;
     int2* d_dm_band = nullptr;
@@ -1039,6 +1041,100 @@ mcao_status mcao_load_atmosphere(mcao_sim* S, int n_layers, const mcao_layer* la
     return MCAO_OK;
 }
 
+// Gaussian tables Gx [surf_n][nx], Gy [surf_n][ny] of every DM (with its shift and
+// magnification folded in: sample coordinate (x - shift) / mag), the per-tile actuator bands
+// (weights >= 1e-10) and the misregistration fields of the descriptors.
+static mcao_status build_dm_tables(mcao_sim* S, std::vector<float>& g, std::vector<int2>& band) {
+    g.clear();
+    band.clear();
+    for (int m = 0; m < S->n_dms; ++m) {
+        const mcao_dm& d = S->dms[m];
+        DmDesc& D = S->dm_desc[m];
+        const std::array<double, 4>& T = S->dm_misreg[m];
+        const double sig = d.pitch_m / std::sqrt(2.0 * std::log(1.0 / d.coupling));
+        const double thr = 1e-10;
+        auto table = [&](int na, double shift, long long& tband) {
+            long long off = (long long)g.size();
+            std::vector<int2> rows;
+            for (int i = 0; i < d.surf_n; ++i) {
+                double x = (((double)i - 0.5 * (double)(d.surf_n - 1)) * d.surf_dx - shift) / T[3];
+                int lo = na, hi = 0;
+                for (int a = 0; a < na; ++a) {
+                    double xa = ((double)a - 0.5 * (double)(na - 1)) * d.pitch_m;
+                    double v = std::exp(-(x - xa) * (x - xa) / (2.0 * sig * sig));
+                    g.push_back((float)v);
+                    if (v >= thr) { lo = std::min(lo, a); hi = std::max(hi, a + 1); }
+                }
+                rows.push_back(make_int2(lo, hi));
+            }
+            tband = (long long)band.size();
+            for (int t = 0; t < D.tiles_x; ++t) {
+                int lo = na, hi = 0;
+                for (int i = t * kDmTile; i < std::min(d.surf_n, (t + 1) * kDmTile); ++i)
+                    if (rows[i].y > rows[i].x) { lo = std::min(lo, rows[i].x); hi = std::max(hi, rows[i].y); }
+                if (lo >= hi) { lo = 0; hi = 0; }
+                band.push_back(make_int2(lo, hi));
+            }
+            return off;
+        };
+        D.general = T[2] != 0.0;
+        // with rotation the tables describe the unrotated DM (kept for the band sizes only)
+        D.gx_off = table(d.nx, D.general ? 0.0 : T[0], D.tband_x);
+        D.gy_off = table(d.ny, D.general ? 0.0 : T[1], D.tband_y);
+        if (!D.general)
+            for (int t = 0; t < 2 * D.tiles_x; ++t) {
+                int2 b = band[(t < D.tiles_x ? D.tband_x : D.tband_y) + t % D.tiles_x];
+                if (b.y - b.x > kDmMaxBand)
+                    return fail(S, MCAO_E_UNSUPPORTED, "dm %d: more than %d actuators per axis act on a %d-sample tile",
+                                m, kDmMaxBand, kDmTile);
+            }
+        D.cr = (float)std::cos(T[2]);
+        D.sr = (float)std::sin(T[2]);
+        D.inv_mag = (float)(1.0 / T[3]);
+        D.shx = (float)T[0];
+        D.shy = (float)T[1];
+        D.dx = (float)d.surf_dx;
+        D.pitch = (float)d.pitch_m;
+        D.inv2s2 = (float)(1.0 / (2.0 * sig * sig));
+        D.rc = (float)(sig * std::sqrt(2.0 * std::log(1.0 / thr)) / d.pitch_m);
+    }
+    return MCAO_OK;
+}
+
+mcao_status mcao_set_misregistration(mcao_sim* S, int dm, double shift_x, double shift_y, double rotation,
+                                     double magnification) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");
+    if (dm < 0 || dm >= S->n_dms) return fail(S, MCAO_E_INVALID_ARG, "bad DM index");
+    if (!is_fin(shift_x) || !is_fin(shift_y) || !is_fin(rotation) || std::fabs(rotation) > M_PI ||
+        !(is_fin(magnification) && magnification > 0.5 && magnification < 2.0))
+        return fail(S, MCAO_E_INVALID_ARG, "finite shift, |rotation| <= pi and magnification in (0.5, 2) required");
+    CK(cudaSetDevice(S->device));
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    const std::array<double, 4> old = S->dm_misreg[dm];
+    S->dm_misreg[dm] = {shift_x, shift_y, rotation, magnification};
+    std::vector<float> g;
+    std::vector<int2> band;
+    mcao_status r = build_dm_tables(S, g, band);
+    if (r != MCAO_OK) {
+        S->dm_misreg[dm] = old;
+        std::vector<float> g2;
+        std::vector<int2> b2;
+        build_dm_tables(S, g2, b2);
+        return r;
+    }
+    release_graph(S);
+    dfree(S->d_dm_g);
+    dfree(S->d_dm_band);
+    CK(dalloc(&S->d_dm_g, g.size()));
+    CK(cudaMemcpyAsync(S->d_dm_g, g.data(), sizeof(float) * g.size(), cudaMemcpyHostToDevice, S->s0));
+    CK(dalloc(&S->d_dm_band, band.size()));
+    CK(cudaMemcpyAsync(S->d_dm_band, band.data(), sizeof(int2) * band.size(), cudaMemcpyHostToDevice, S->s0));
+    CK(cudaMemcpyAsync(S->d_dm_desc, S->dm_desc.data(), sizeof(DmDesc) * S->n_dms, cudaMemcpyHostToDevice, S->s0));
+    CK(cudaStreamSynchronize(S->s0));
+    return MCAO_OK;
+}
+
 mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     if (!S) return MCAO_E_INVALID_ARG;
     if (n_dms < 0 || n_dms > kMaxDms || (n_dms > 0 && !dms))
@@ -1074,41 +1170,6 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
         DmDesc D{};
         D.nx = d.nx; D.ny = d.ny; D.surf_n = d.surf_n;
         D.tiles_x = (d.surf_n + kDmTile - 1) / kDmTile;
-        double sig = d.pitch_m / std::sqrt(2.0 * std::log(1.0 / d.coupling));
-        const double thr = 1e-10;
-        // table [surf_n][na]; per 32-sample tile, the actuator range with weight >= thr on it
-        auto table = [&](int na, long long& tband) {
-            long long off = (long long)g.size();
-            std::vector<int2> rows;
-            for (int i = 0; i < d.surf_n; ++i) {
-                double x = ((double)i - 0.5 * (double)(d.surf_n - 1)) * d.surf_dx;
-                int lo = na, hi = 0;
-                for (int a = 0; a < na; ++a) {
-                    double xa = ((double)a - 0.5 * (double)(na - 1)) * d.pitch_m;
-                    double v = std::exp(-(x - xa) * (x - xa) / (2.0 * sig * sig));
-                    g.push_back((float)v);
-                    if (v >= thr) { lo = std::min(lo, a); hi = std::max(hi, a + 1); }
-                }
-                rows.push_back(make_int2(lo, hi));
-            }
-            tband = (long long)band.size();
-            for (int t = 0; t < D.tiles_x; ++t) {
-                int lo = na, hi = 0;
-                for (int i = t * kDmTile; i < std::min(d.surf_n, (t + 1) * kDmTile); ++i)
-                    if (rows[i].y > rows[i].x) { lo = std::min(lo, rows[i].x); hi = std::max(hi, rows[i].y); }
-                if (lo >= hi) { lo = 0; hi = 0; }
-                band.push_back(make_int2(lo, hi));
-            }
-            return off;
-        };
-        D.gx_off = table(d.nx, D.tband_x);
-        D.gy_off = table(d.ny, D.tband_y);
-        for (int t = 0; t < 2 * D.tiles_x; ++t) {
-            int2 b = band[(t < D.tiles_x ? D.tband_x : D.tband_y) + t % D.tiles_x];
-            if (b.y - b.x > kDmMaxBand)
-                return fail(S, MCAO_E_UNSUPPORTED, "dm %d: more than %d actuators per axis act on a %d-sample tile",
-                            m, kDmMaxBand, kDmTile);
-        }
         D.map_off = (long long)map.size();
         int cnt = 0;
         for (int a = 0; a < d.nx * d.ny; ++a) {
@@ -1124,6 +1185,8 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     }
     for (int m = n_dms; m <= kMaxDms; ++m) S->dm_tile_start[m] = tiles;
     S->n_cmd = ncmd;
+    S->dm_misreg.assign(n_dms, {0.0, 0.0, 0.0, 1.0});
+    { mcao_status r_ = build_dm_tables(S, g, band); if (r_ != MCAO_OK) return r_; }
     CK(dalloc(&S->d_dm_desc, S->dm_desc.size()));
     if (n_dms) CK(cudaMemcpyAsync(S->d_dm_desc, S->dm_desc.data(), sizeof(DmDesc) * n_dms, cudaMemcpyHostToDevice, S->s0));
     CK(dalloc(&S->d_dm_g, g.size()));

@@ -96,6 +96,15 @@ struct DmDesc {
     long long tband_y;   // per 32-row tile: actuator rows [lo, hi)
     long long map_off;   // act_map [ny][nx]: command index or -1
     long long surf_off;  // S [surf_n][surf_n]
+    // misregistration: the DM's surface function evaluated at q = R(-rot)((x, y) - shift) / mag.
+    // Without rotation it is folded into Gx and Gy; with rotation (general = 1) every sample
+    // weighs the actuators within rc pitches of q directly (the tables are not used).
+    int general;
+    float cr, sr;        // cos, sin of the rotation
+    float inv_mag, shx, shy;   // 1 / magnification; shift in m
+    float dx, pitch;     // surface sample pitch, actuator pitch (m)
+    float inv2s2;        // 1 / (2 sigma^2) of the influence function (DM coordinates)
+    float rc;            // window radius in actuator pitches (weights below 1e-10 left out)
 };
 constexpr int kDmTile = 32;
 constexpr int kDmMaxBand = 64;   // actuators per tile and axis (checked on the host)

@@ -30,7 +30,7 @@ EXPORTS = [
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
     "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
-    "mcao_interaction_matrix", "mcao_slopes_vjp",
+    "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -121,6 +121,7 @@ def lib():
         "mcao_measure": [vp, C.c_int],
         "mcao_interaction_matrix": [vp, vp, C.c_size_t],
         "mcao_slopes_vjp": [vp, vp, C.c_int, vp, vp],
+        "mcao_set_misregistration": [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -295,6 +296,11 @@ class Sim:
     def set_commands(self, c):
         c = np.ascontiguousarray(c, dtype=np.float32)
         self._ck(lib().mcao_set_commands(self.h, c.ctypes.data, c.size))
+
+    def set_misregistration(self, dm: int, shift_x: float = 0.0, shift_y: float = 0.0, rotation: float = 0.0,
+                            magnification: float = 1.0):
+        """Move DM dm as a rigid body (shift in m, rotation in rad, magnification)."""
+        self._ck(lib().mcao_set_misregistration(self.h, dm, shift_x, shift_y, rotation, magnification))
 
     def measure(self, noise: bool = False) -> np.ndarray:
         """Slopes at the current step and commands without reconstruction or time advance
