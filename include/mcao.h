@@ -367,11 +367,15 @@ mcao_status mcao_interaction_matrix(mcao_sim* sim, float* D, size_t ld);
  *   g_commands  device [n_vec][n_commands] = D^T g (or NULL);
  *   g_phase     device [n_vec][sum over sensors of N_w^2] = (d s / d phi)^T g on each sensor's
  *               pupil grid (rad at the reference wavelength), sensors concatenated in order, zero
- *               outside valid subapertures (or NULL).
- * Outputs are overwritten.  Command gradients are accumulated with atomic adds (summation order
- * not fixed).  Synchronous.  Errors: MCAO_E_INVALID_ARG (null g, n_vec < 1, both outputs
- * NULL), MCAO_E_STATE, MCAO_E_UNSUPPORTED, MCAO_E_OOM, MCAO_E_CUDA. */
-mcao_status mcao_slopes_vjp(mcao_sim* sim, const float* g_slopes, int n_vec, float* g_commands, float* g_phase);
+ *               outside valid subapertures (or NULL);
+ *   g_layers    device [n_vec][sum over layers of n_l^2] = (d s / d screen)^T g on every turbulent
+ *               layer's screen (the adjoint of the cone-beam projection at this step's frozen-flow
+ *               position), layers concatenated in order (or NULL).
+ * Outputs are overwritten.  Command and layer gradients are accumulated with atomic adds
+ * (summation order not fixed).  Synchronous.  Errors: MCAO_E_INVALID_ARG (null g, n_vec < 1,
+ * every output NULL), MCAO_E_STATE, MCAO_E_UNSUPPORTED, MCAO_E_OOM, MCAO_E_CUDA. */
+mcao_status mcao_slopes_vjp(mcao_sim* sim, const float* g_slopes, int n_vec, float* g_commands, float* g_phase,
+                            float* g_layers);
 
 /* Stages timed by the profiler. */
 enum {

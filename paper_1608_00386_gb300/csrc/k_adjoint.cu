@@ -372,20 +372,37 @@ __global__ void __launch_bounds__(256) dm_adjoint_kernel(ProjLaunch L) {
     }
 }
 
-// g_phase[v][off + (j0 + y) N + i0 + x] = g_v[x slope] L_x + g_v[y slope] L_y, one block per subaperture
-__global__ void phase_adjoint_kernel(ProjLaunch L, float* g_phase, long long phase_stride, long long phase_off) {
+// Per subaperture and vector: g_phi = g_v[x slope] L_x + g_v[y slope] L_y on its pupil samples,
+// stored in g_phase[v][off + (j0 + y) N + i0 + x] and/or scattered onto the layers (the adjoint of
+// the periodic bilinear sampling at the frozen-flow position of the step) in g_layers[v][...].
+__global__ void phase_adjoint_kernel(ProjLaunch L, float* g_phase, long long phase_stride, long long phase_off,
+                                     float* g_layers, long long layer_stride, const long long* layer_off) {
     const SubapDev sd = L.subaps[blockIdx.x];
     const WfsDev& w = L.ctx.wfs[sd.wfs];
     const int npx = w.n_px;
     const int rx = w.slope0 + sd.rank, ry = w.slope0 + w.n_valid + sd.rank;
     const int i0 = sd.sx * npx, j0 = sd.sy * npx;
+    const GridView* V = L.ctx.views + L.real * L.ctx.view_stride + (long long)sd.wfs * L.ctx.n_grids;
+    const long long k = L.ctx.st->k;
     for (int vv = 0; vv < L.n_vec; ++vv) {
         const float gx = L.gvec[(long long)vv * L.n_slopes + rx], gy = L.gvec[(long long)vv * L.n_slopes + ry];
-        float* out = g_phase + vv * phase_stride + phase_off;
         for (int q = threadIdx.x; q < npx * npx; q += blockDim.x) {
             const int x = q % npx, y = q / npx;
-            out[(long long)(j0 + y) * w.N + i0 + x] =
-                gx * L.sens[(long long)rx * L.P + q] + gy * L.sens[(long long)ry * L.P + q];
+            const float gp = gx * L.sens[(long long)rx * L.P + q] + gy * L.sens[(long long)ry * L.P + q];
+            if (g_phase) g_phase[vv * phase_stride + phase_off + (long long)(j0 + y) * w.N + i0 + x] = gp;
+            if (!g_layers || gp == 0.0f) continue;
+            for (int l = 0; l < L.n_layers; ++l) {
+                const GridView& v = V[l];
+                const AxisEnt ex = axis_entry(v.ax + (long long)(i0 + x) * v.bp + k * v.vx, v.n, v.periodic, v.inv_n);
+                const AxisEnt ey = axis_entry(v.ay + (long long)(j0 + y) * v.bp + k * v.vy, v.n, v.periodic, v.inv_n);
+                float* gl = g_layers + vv * layer_stride + layer_off[l];
+                const int c0 = ex.idx & 0xffff, c1 = ex.idx >> 16, r0 = ey.idx & 0xffff, r1 = ey.idx >> 16;
+                const float s = v.sign * gp;
+                atomicAdd(gl + (long long)r0 * v.n + c0, s * (1.0f - ex.t) * (1.0f - ey.t));
+                atomicAdd(gl + (long long)r0 * v.n + c1, s * ex.t * (1.0f - ey.t));
+                atomicAdd(gl + (long long)r1 * v.n + c0, s * (1.0f - ex.t) * ey.t);
+                atomicAdd(gl + (long long)r1 * v.n + c1, s * ex.t * ey.t);
+            }
         }
     }
 }
@@ -408,8 +425,10 @@ cudaError_t launch_dm_adjoint(const ProjLaunch& L, cudaStream_t s) {
 }
 
 cudaError_t launch_phase_adjoint(const ProjLaunch& L, float* g_phase, long long phase_stride, long long phase_off,
-                                 cudaStream_t s) {
-    if (L.n_valid) phase_adjoint_kernel<<<(unsigned)L.n_valid, 128, 0, s>>>(L, g_phase, phase_stride, phase_off);
+                                 float* g_layers, long long layer_stride, const long long* layer_off, cudaStream_t s) {
+    if (L.n_valid)
+        phase_adjoint_kernel<<<(unsigned)L.n_valid, 128, 0, s>>>(L, g_phase, phase_stride, phase_off, g_layers,
+                                                                 layer_stride, layer_off);
     return cudaGetLastError();
 }
 

@@ -1553,7 +1553,7 @@ mcao_status mcao_measure(mcao_sim* S, int with_noise) {
 // d slope / d phase of every slope on its subaperture's samples (current realization), then the
 // command rows (D) or the command gradients (gvec -> gc) and the phase gradients
 static mcao_status run_adjoint(mcao_sim* S, float* D, long long ld, const float* gvec, int n_vec, float* gc,
-                               float* g_phase) {
+                               float* g_phase, float* g_layers) {
     int P = 1;
     for (const auto& W : S->wfs) P = std::max(P, W.p.n_px * W.p.n_px);
     CK(cudaDeviceSynchronize());   // inputs produced on any stream are complete
@@ -1569,6 +1569,16 @@ static mcao_status run_adjoint(mcao_sim* S, float* D, long long ld, const float*
     if (e == cudaSuccess && D) e = cudaMemsetAsync(D, 0, sizeof(float) * (size_t)S->n_slopes * ld, S->s0);
     if (e == cudaSuccess && gc) e = cudaMemsetAsync(gc, 0, sizeof(float) * (size_t)n_vec * S->n_cmd, S->s0);
     if (e == cudaSuccess && g_phase) e = cudaMemsetAsync(g_phase, 0, sizeof(float) * (size_t)n_vec * phase_total, S->s0);
+    // layers concatenated: offsets and total length
+    std::vector<long long> loff(S->n_layers + 1, 0);
+    for (int l = 0; l < S->n_layers; ++l) loff[l + 1] = loff[l] + (long long)S->layers[l].n * S->layers[l].n;
+    long long* d_loff = nullptr;
+    if (e == cudaSuccess && g_layers) {
+        e = cudaMemsetAsync(g_layers, 0, sizeof(float) * (size_t)n_vec * loff[S->n_layers], S->s0);
+        if (e == cudaSuccess) e = dalloc(&d_loff, loff.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_loff, loff.data(), sizeof(long long) * loff.size(), cudaMemcpyHostToDevice, S->s0);
+    }
     long long phase_off = 0;
     for (size_t w = 0; w < S->wfs.size() && e == cudaSuccess; ++w) {
         const WfsHost& W = S->wfs[w];
@@ -1603,7 +1613,8 @@ static mcao_status run_adjoint(mcao_sim* S, float* D, long long ld, const float*
             J.n_cmd = S->n_cmd;
             J.err = d_err;
             if (e == cudaSuccess && (D || gc)) e = launch_dm_adjoint(J, S->s0);
-            if (e == cudaSuccess && g_phase) e = launch_phase_adjoint(J, g_phase, phase_total, phase_off, S->s0);
+            if (e == cudaSuccess && (g_phase || g_layers))
+                e = launch_phase_adjoint(J, g_phase, phase_total, phase_off, g_layers, loff[S->n_layers], d_loff, S->s0);
         }
         phase_off += (long long)W.N * W.N;
     }
@@ -1612,6 +1623,7 @@ static mcao_status run_adjoint(mcao_sim* S, float* D, long long ld, const float*
     if (e == cudaSuccess) e = cudaMemcpy(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(sens);
     cudaFree(d_err);
+    cudaFree(d_loff);
     CK(e);
     if (h_err) return fail(S, MCAO_E_UNSUPPORTED, "a subaperture footprint meets more than 128 actuators per axis");
     return MCAO_OK;
@@ -1622,14 +1634,15 @@ mcao_status mcao_interaction_matrix(mcao_sim* S, float* D, size_t ld) {
     if (!S->atm_loaded || !S->dms_loaded) return fail(S, MCAO_E_STATE, "atmosphere and DMs must be loaded");
     if (ld < (size_t)S->n_cmd) return fail(S, MCAO_E_SHAPE, "ld must be >= %d", S->n_cmd);
     CK(cudaSetDevice(S->device));
-    return run_adjoint(S, D, (long long)ld, nullptr, 0, nullptr, nullptr);
+    return run_adjoint(S, D, (long long)ld, nullptr, 0, nullptr, nullptr, nullptr);
 }
 
-mcao_status mcao_slopes_vjp(mcao_sim* S, const float* g_slopes, int n_vec, float* g_commands, float* g_phase) {
-    if (!S || !g_slopes || n_vec < 1 || (!g_commands && !g_phase)) return MCAO_E_INVALID_ARG;
+mcao_status mcao_slopes_vjp(mcao_sim* S, const float* g_slopes, int n_vec, float* g_commands, float* g_phase,
+                            float* g_layers) {
+    if (!S || !g_slopes || n_vec < 1 || (!g_commands && !g_phase && !g_layers)) return MCAO_E_INVALID_ARG;
     if (!S->atm_loaded || !S->dms_loaded) return fail(S, MCAO_E_STATE, "atmosphere and DMs must be loaded");
     CK(cudaSetDevice(S->device));
-    return run_adjoint(S, nullptr, 0, g_slopes, n_vec, g_commands, g_phase);
+    return run_adjoint(S, nullptr, 0, g_slopes, n_vec, g_commands, g_phase, g_layers);
 }
 
 mcao_status mcao_get_dm_surface(mcao_sim* S, int dm, float* out, size_t n) {

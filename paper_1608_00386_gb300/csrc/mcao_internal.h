@@ -308,6 +308,6 @@ size_t sens_smem(int n_fft);
 cudaError_t launch_sens(const SensLaunch& L, int n_fft, cudaStream_t s);
 cudaError_t launch_dm_adjoint(const ProjLaunch& L, cudaStream_t s);
 cudaError_t launch_phase_adjoint(const ProjLaunch& L, float* g_phase, long long phase_stride, long long phase_off,
-                                 cudaStream_t s);
+                                 float* g_layers, long long layer_stride, const long long* layer_off, cudaStream_t s);
 
 }  // namespace mcao

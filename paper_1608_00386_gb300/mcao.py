@@ -120,7 +120,7 @@ def lib():
                                  C.c_size_t],
         "mcao_measure": [vp, C.c_int],
         "mcao_interaction_matrix": [vp, vp, C.c_size_t],
-        "mcao_slopes_vjp": [vp, vp, C.c_int, vp, vp],
+        "mcao_slopes_vjp": [vp, vp, C.c_int, vp, vp, vp],
         "mcao_set_misregistration": [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double],
     }
     for name, args in sig.items():
@@ -316,10 +316,11 @@ class Sim:
         self._ck(lib().mcao_interaction_matrix(self.h, D.data_ptr(), D.shape[1]))
         return D
 
-    def slopes_vjp(self, g, commands: bool = True, phase: bool = False):
+    def slopes_vjp(self, g, commands: bool = True, phase: bool = False, layers: bool = False):
         """Vector-Jacobian products of the noise-free slopes (mcao_slopes_vjp) for g, a CUDA tensor
-        [n_slopes] or [n_vec][n_slopes]: (command gradients [.., n_commands] or None, pupil-phase
-        gradients [.., sum of N_w^2] or None), shaped like g."""
+        [n_slopes] or [n_vec][n_slopes]: command gradients [.., n_commands], pupil-phase gradients
+        [.., sum of N_w^2] and layer gradients [.., sum of n_l^2] (each None unless asked), shaped
+        like g; with layers=True a third element is returned."""
         import torch
         ns, nc = self.query(Q_SLOPES), self.query(Q_COMMANDS)
         g2 = g.detach().to(device="cuda", dtype=torch.float32).reshape(-1, ns).contiguous()
@@ -327,12 +328,13 @@ class Sim:
         gc = torch.empty((nv, nc), dtype=torch.float32, device="cuda") if commands else None
         nph = sum(self.query(Q_WFS_PHASE, w) for w in range(len(self.cfg["wfs"])))
         gp = torch.empty((nv, nph), dtype=torch.float32, device="cuda") if phase else None
-        self._ck(lib().mcao_slopes_vjp(self.h, g2.data_ptr(), nv, gc.data_ptr() if gc is not None else None,
-                                       gp.data_ptr() if gp is not None else None))
+        nly = sum(l["n"] ** 2 for l in self.cfg["layers"])
+        gl = torch.empty((nv, nly), dtype=torch.float32, device="cuda") if layers else None
+        ptr = lambda t: t.data_ptr() if t is not None else None
+        self._ck(lib().mcao_slopes_vjp(self.h, g2.data_ptr(), nv, ptr(gc), ptr(gp), ptr(gl)))
         if g.dim() == 1:
-            gc = gc[0] if gc is not None else None
-            gp = gp[0] if gp is not None else None
-        return gc, gp
+            gc, gp, gl = [t[0] if t is not None else None for t in (gc, gp, gl)]
+        return (gc, gp, gl) if layers else (gc, gp)
 
     def valid(self, w: int) -> np.ndarray:
         out = np.empty(self.query(Q_VALID, w), np.int32)

@@ -158,3 +158,43 @@ def test_vjp_argument_errors():
     L = mcao.lib()
     assert L.mcao_interaction_matrix(g.h, None, 10) == 1
     assert L.mcao_interaction_matrix(g.h, G.data_ptr(), 1) == 2      # ld < n_commands
+
+
+@pytest.mark.parametrize("name", ["scao_tiny", "mcao_small"])
+def test_layer_vjp_matches_directional_derivative(name):
+    # <g_layers, delta> equals g^T (s(screens + e delta) - s(screens - e delta)) / 2e of the oracle,
+    # with delta the perturbation the float32 screens actually carry
+    import torch
+    if name == "scao_tiny":
+        cfg, screens, _ = scao_tiny_inputs()
+        cfg = dict(cfg, noise=False)
+    else:
+        cfg = mcao_small()
+        screens = inputs.make_screens(cfg)
+    _, g, o = _case(name)
+    c = o.commands()
+    rng = np.random.default_rng(8)
+    G = rng.normal(size=(2, o.n_slopes)).astype(np.float32)
+    _, _, gl = g.slopes_vjp(torch.from_numpy(G).cuda(), commands=False, layers=True)
+    gl = gl.cpu().numpy().astype(np.float64)
+    eps = 1e-3
+    delta = [rng.normal(size=s.shape) for s in screens]
+    plus = [(s.astype(np.float64) + eps * d).astype(np.float32) for s, d in zip(screens, delta)]
+    minus = [(s.astype(np.float64) - eps * d).astype(np.float32) for s, d in zip(screens, delta)]
+    act = np.concatenate([(p.astype(np.float64) - m.astype(np.float64)).ravel() / 2.0 for p, m in zip(plus, minus)])
+    sp = oracle.Sim(cfg, plus)
+    sm = oracle.Sim(cfg, minus)
+    sp.set_commands(c)
+    sm.set_commands(c)
+    ds = (sp.measure() - sm.measure()) / 2.0
+    for v in range(2):
+        want = float(G[v].astype(np.float64) @ ds)
+        got = float(gl[v] @ act)
+        assert got == pytest.approx(want, rel=1e-4, abs=1e-6 * np.abs(G[v]).sum() * eps)
+    # samples outside every beam get nothing; the total over a layer is the derivative of a
+    # uniform (piston) layer change, which the centroids ignore
+    n0 = cfg["layers"][0]["n"] ** 2
+    assert np.count_nonzero(gl[0, :n0]) < n0
+    assert abs(gl[0, :n0].sum()) <= 1e-4 * np.abs(gl[0, :n0]).sum()
+    sp.close()
+    sm.close()
