@@ -67,7 +67,10 @@ enum { MCAO_DTYPE_F32 = 0, MCAO_DTYPE_BF16 = 1, MCAO_DTYPE_FP8_E4M3 = 2 };
  * (zero-padded field, requires n_fft >= 2 n_px), binned n_bin x n_bin into
  * (n_fft/n_bin)^2 detector pixels.  Sodium elongation (laser stars, na_fwhm > 0): Gaussian of
  * FWHM b * na_fwhm / height^2 rad along the launch-to-subaperture direction, b that
- * distance.  Flux: n_photons times the illuminated fraction per frame. */
+ * distance.  Flux: n_photons times the illuminated fraction per frame.  Supported shapes
+ * (n_px, n_fft, n_bin), each with or without elongation: (8, 16, 2), (8, 32, 2), (8, 16, 1) on
+ * the warp-per-subaperture autocorrelation route; (16, 32, 2) (a laser star with twice the field
+ * of view of 8 samples) and (32, 64, 4) on the block-per-subaperture FFT route. */
 typedef struct {
     int type;                 /* MCAO_WFS_NGS (source at infinity) or MCAO_WFS_LGS           */
     int n_sub, n_px, n_fft, n_bin;

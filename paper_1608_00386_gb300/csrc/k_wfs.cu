@@ -16,9 +16,10 @@
 //    ACF(ux, uy) = sum_a M_uy[a][a + ux], M_uy[a][b] = sum_r E[r][a] conj(E[r + uy][b]): each
 //    lane keeps three columns of E in registers and forms two entries of every M_uy.  One warp
 //    per subaperture; no N x N array is formed.
-//  * FFT route (large subapertures without elongation, e.g. 2 x 2 low-order sensors):
-//    radix-4 Stockham FFTs of the padded field in shared memory, |.|^2, shift and bin; one
-//    1024-thread block per subaperture.
+//  * FFT route (larger subapertures: 2 x 2 low-order sensors, laser stars with 16 samples per
+//    subaperture for a wider field): radix-4 Stockham FFTs of the padded field in shared
+//    memory, |.|^2, elongation by two more 2-D FFTs and the OTF, shift and bin; one 1024-thread
+//    block per subaperture.
 #include <math.h>
 
 #include "device_common.cuh"
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
 }
 
 // ------------------------------------------------------------------------------------------
-// FFT route: one 1024-thread block per subaperture, no elongation
+// FFT route: one 1024-thread block per subaperture
 // ------------------------------------------------------------------------------------------
 constexpr int kFftThreads = 1024;
 
@@ -383,7 +384,30 @@ __global__ void __launch_bounds__(kFftThreads) wfs_fft_kernel(WfsLaunch L) {
     float2* R1 = stockham_fft(X, Z, NFFT, rad, nr, NPX, NFFT, 1, W, tid, NT);
     float2* R2 = stockham_fft(R1, R1 == X ? Z : X, NFFT, rad, nr, NFFT, 1, NFFT, W, tid, NT);
 
-    // |.|^2, shift by NFFT/2, bin NBIN x NBIN
+    // sodium elongation (block-uniform branch): I <- Re IFFT2(FFT2(I) OTF), the inverse taken as
+    // conj(FFT2(conj .)) and its 1 / N^2 left to the flux normalisation
+    const float2* img = R2;
+    const bool elong = sd.elong_a > 0.0f;
+    if (elong) {
+        float2* A = R2;
+        float2* Bf = (R2 == X) ? Z : X;
+        for (int q = tid; q < NFFT * NFFT; q += NT) A[q] = make_float2(A[q].x * A[q].x + A[q].y * A[q].y, 0.0f);
+        __syncthreads();
+        float2* S1 = stockham_fft(A, Bf, NFFT, rad, nr, NFFT, NFFT, 1, W, tid, NT);
+        S1 = stockham_fft(S1, S1 == A ? Bf : A, NFFT, rad, nr, NFFT, 1, NFFT, W, tid, NT);
+        for (int q = tid; q < NFFT * NFFT; q += NT) {
+            const int kx = q % NFFT, ky = q / NFFT;
+            const float ux = (float)(kx < NFFT / 2 ? kx : kx - NFFT), uy = (float)(ky < NFFT / 2 ? ky : ky - NFFT);
+            const float d = ux * sd.dir_x + uy * sd.dir_y;
+            const float o = expf(-sd.elong_a * d * d);
+            S1[q] = make_float2(S1[q].x * o, -S1[q].y * o);
+        }
+        __syncthreads();
+        float2* S2 = stockham_fft(S1, S1 == A ? Bf : A, NFFT, rad, nr, NFFT, NFFT, 1, W, tid, NT);
+        img = stockham_fft(S2, S2 == A ? Bf : A, NFFT, rad, nr, NFFT, 1, NFFT, W, tid, NT);
+    }
+
+    // |.|^2 (or the elongated image), shift by NFFT/2, bin NBIN x NBIN
     const int lane = tid & 31, warp = tid >> 5;
     float b = 0.0f;
     const int o = tid;
@@ -392,8 +416,8 @@ __global__ void __launch_bounds__(kFftThreads) wfs_fft_kernel(WfsLaunch L) {
         for (int ty = 0; ty < NBIN; ++ty)
             for (int tx = 0; tx < NBIN; ++tx) {
                 int r = (my * NBIN + ty + NFFT / 2) % NFFT, c = (mx * NBIN + tx + NFFT / 2) % NFFT;
-                float2 v = R2[r * NFFT + c];
-                b += v.x * v.x + v.y * v.y;
+                const float2 v = img[r * NFFT + c];
+                b += elong ? v.x : v.x * v.x + v.y * v.y;
             }
     }
     float s = warp_sum(b);
@@ -503,23 +527,30 @@ cudaError_t launch_fft(const WfsLaunch& L, cudaStream_t s) {
 
 }  // namespace
 
-bool wfs_variant_supported(int n_px, int n_fft, int n_bin, bool elongated) {
+bool wfs_variant_supported(int n_px, int n_fft, int n_bin, bool) {
     if (n_px == 8 && n_fft == 16 && n_bin == 2) return true;
     if (n_px == 8 && n_fft == 32 && n_bin == 2) return true;
     if (n_px == 8 && n_fft == 16 && n_bin == 1) return true;
-    if (n_px == 32 && n_fft == 64 && n_bin == 4) return !elongated;
-    return false;
+    return wfs_variant_is_fft(n_px, n_fft, n_bin);
 }
 
-bool wfs_variant_is_fft(int n_px, int n_fft, int n_bin) { return n_px == 32 && n_fft == 64 && n_bin == 4; }
+// block-per-subaperture variants: 2 x 2 low-order sensors (32 samples, FFT 64, bin 4) and
+// laser stars with 16 samples per subaperture (twice the field of view of 8, FFT 32, bin 2)
+bool wfs_variant_is_fft(int n_px, int n_fft, int n_bin) {
+    return (n_px == 32 && n_fft == 64 && n_bin == 4) || (n_px == 16 && n_fft == 32 && n_bin == 2);
+}
 
-cudaError_t wfs_prepare() { return prepare_fft<32, 64, 4>(); }
+cudaError_t wfs_prepare() {
+    cudaError_t e = prepare_fft<32, 64, 4>();
+    return e == cudaSuccess ? prepare_fft<16, 32, 2>() : e;
+}
 
 cudaError_t launch_wfs(const WfsLaunch& L, int n_px, int n_fft, int n_bin, cudaStream_t s) {
     if (n_px == 8 && n_fft == 16 && n_bin == 2) return launch_acf<16, 2>(L, s);
     if (n_px == 8 && n_fft == 32 && n_bin == 2) return launch_acf<32, 2>(L, s);
     if (n_px == 8 && n_fft == 16 && n_bin == 1) return launch_acf<16, 1>(L, s);
     if (n_px == 32 && n_fft == 64 && n_bin == 4) return launch_fft<32, 64, 4>(L, s);
+    if (n_px == 16 && n_fft == 32 && n_bin == 2) return launch_fft<16, 32, 2>(L, s);
     return cudaErrorInvalidValue;
 }
 

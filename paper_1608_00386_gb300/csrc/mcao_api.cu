@@ -1801,7 +1801,7 @@ mcao_status mcao_set_sodium(mcao_sim* S, int wfs, double height, double na_fwhm)
         return fail(S, MCAO_E_INVALID_ARG, "height > 0 and na_fwhm >= 0 required");
     for (const auto& L : S->layers)
         if (L.alt_m >= height) return fail(S, MCAO_E_INVALID_ARG, "the laser star must stay above every layer");
-    if (H.fft_route && na_fwhm > 0.0)
+    if (!wfs_variant_supported(H.p.n_px, H.p.n_fft, H.p.n_bin, na_fwhm > 0.0))
         return fail(S, MCAO_E_UNSUPPORTED, "WFS %d has no kernel for an elongated spot", wfs);
     CK(cudaSetDevice(S->device));
     { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
@@ -1811,6 +1811,16 @@ mcao_status mcao_set_sodium(mcao_sim* S, int wfs, double height, double na_fwhm)
     if (!H.subaps.empty())
         CK(cudaMemcpyAsync(H.d_subaps, H.subaps.data(), sizeof(SubapDev) * H.subaps.size(), cudaMemcpyHostToDevice,
                            S->s0));
+    // block-per-subaperture sensors read their group's concatenated copy
+    for (auto& g : S->fft_groups) {
+        size_t off = 0;
+        for (int w : g.wfs) {
+            if (w == wfs && !H.subaps.empty())
+                CK(cudaMemcpyAsync(g.d_subaps + off, H.subaps.data(), sizeof(SubapDev) * H.subaps.size(),
+                                   cudaMemcpyHostToDevice, S->s0));
+            off += S->wfs[w].subaps.size();
+        }
+    }
     return rebuild_views(S);   // cone projection of the new height (synchronises s0)
 }
 

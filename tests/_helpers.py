@@ -64,3 +64,21 @@ def mcao_small():
     }
     cfg["dms"] = [inputs.dm_spec(cfg, 0.0, 1.0, 0.3), inputs.dm_spec(cfg, 5000.0, 1.4, 0.3)]
     return cfg
+
+
+def wide_lgs():
+    """8 m case with a wide-field laser star: 4 x 4 subapertures of 16 samples (twice the field
+    of view of 8-sample subapertures), FFT 32, bin 2, side launch, 5 km sodium layer (elongated
+    spots on the block-per-subaperture route); one layer, one ground DM; noise off."""
+    cfg = {
+        "name": "wide_lgs_8m",
+        "D": 8.0, "obstruction": 0.0, "lambda_ref": 500e-9,
+        "dt": 2e-3, "gain": 0.5, "seed": 13, "noise": False, "psf_every": 1, "n_steps": 10,
+        "wfs": [inputs._wfs("lgs", (0.0, 0.0), 4, 16, 32, 2, 589e-9, 2000.0, height=90e3, na_fwhm=5e3,
+                            launch=(4.2, 0.0))],
+        "science": [{"theta": (0.0, 0.0), "lambda": 2.2e-6, "n_px": 64, "pad": 2}],
+        "layers": [{"n": 256, "pixel": 0.0625, "alt": 0.0, "vx": 8.0, "vy": 2.0, "r0": 0.15, "L0": 25.0,
+                    "seed": 5}],
+    }
+    cfg["dms"] = [inputs.dm_spec(cfg, 0.0, 1.0, 0.3)]
+    return cfg
