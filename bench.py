@@ -409,6 +409,46 @@ def main():
         del Dm
         js.close()
 
+    if not args.no_variants:
+        # mixed sizes advanced together (mcao_step_group): this workload plus 8 m single-NGS
+        # (16 x 16) and 20 m 3-LGS (40 x 40, 5 layers) systems, 64 in all, each with its own
+        # device-generated layers and random reconstructor; one graph launch per step
+        n_grp = 64
+        grp = [mcao.make_sim(cfg, d_screens, d_R, stream=stream)]
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(11)
+        for i, c in enumerate(inputs.mixed_configs(n_grp - 1)):
+            sm = mcao.Sim(c, stream=stream)
+            sm.generate_atmosphere(seed_offset=1000 * (i + 1))
+            sm.load_dms()
+            ns, nc = sm.query(mcao.Q_SLOPES), sm.query(mcao.Q_COMMANDS)
+            sm.load_reconstructor(torch.randn((nc, ns), generator=gen, device="cuda") * RECON_SIGMA)
+            grp.append(sm)
+        ksteps = 20
+        mcao.step_group(grp, 3)
+        torch.cuda.synchronize()
+        j0, j1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        j0.record(stream)
+        mcao.step_group(grp, ksteps)
+        j1.record(stream)
+        j1.synchronize()
+        grp_ms = j0.elapsed_time(j1)
+        j0.record(stream)
+        for sm in grp:
+            sm.step(ksteps)
+        j1.record(stream)
+        j1.synchronize()
+        seq_ms = j0.elapsed_time(j1)
+        names = [sm.cfg["name"] for sm in grp]
+        variants["mixed_group"] = {
+            "value": n_grp * ksteps / (grp_ms * 1e-3), "unit": "realization-steps/s", "realizations": n_grp,
+            "mix": {n: names.count(n) for n in sorted(set(names))}, "steps": ksteps,
+            "ms_per_group_step": grp_ms / ksteps, "one_after_another_ms_per_step": seq_ms / ksteps,
+            "note": "mcao_step_group: every simulation's step graph as a child of one graph per step"}
+        for sm in grp:
+            sm.close()
+        del grp
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(cfg, screens, R, min(args.steps, 200), dist)

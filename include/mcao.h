@@ -348,6 +348,16 @@ mcao_status mcao_generate_screen(int n, double pixel_m, double r0_m, double L0_m
 mcao_status mcao_set_misregistration(mcao_sim* sim, int dm, double shift_x, double shift_y, double rotation,
                                      double magnification);
 
+/* Advance several simulations of any configurations (sizes, sensors, layers, reconstructor
+ * formats) by n_steps together: each step is one launch of a graph that holds every
+ * simulation's step graph as an independent child, so that small configurations run side by
+ * side on the GPU ("The closed loop" of each, unchanged; results are identical to stepping each
+ * simulation alone).  Ordered after each simulation's earlier work and before its later work
+ * (and after / before the streams set by mcao_set_stream).  Errors: MCAO_E_INVALID_ARG (null or
+ * repeated handles, n_steps < 0, several devices), MCAO_E_STATE (a simulation not fully
+ * loaded), MCAO_E_UNSUPPORTED (the stage profiler is on), MCAO_E_CUDA. */
+mcao_status mcao_step_group(mcao_sim* const* sims, int n_sims, int n_steps);
+
 /* Noise-free (with_noise = 0) or configured-noise (1) slopes of every realization at the current
  * step and commands, without reconstruction and without advancing time ("The calibration of
  * the interaction matrices": measurements at a fixed state); read them with mcao_get_slopes.

@@ -1409,6 +1409,56 @@ mcao_status mcao_step(mcao_sim* S, int n_steps) {
     return signal_user(S);
 }
 
+mcao_status mcao_step_group(mcao_sim* const* sims, int n_sims, int n_steps) {
+    if (!sims || n_sims < 1 || n_steps < 0) return MCAO_E_INVALID_ARG;
+    for (int i = 0; i < n_sims; ++i) {
+        mcao_sim* S = sims[i];
+        if (!S) return MCAO_E_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (sims[j] == S) return fail(S, MCAO_E_INVALID_ARG, "a simulation appears twice in the group");
+        if (!S->atm_loaded || !S->dms_loaded || !S->recon_loaded)
+            return fail(S, MCAO_E_STATE, "load the atmosphere, the DMs and the reconstructor before stepping");
+        if (S->profiling) return fail(S, MCAO_E_UNSUPPORTED, "group steps run without the stage profiler");
+        if (S->device != sims[0]->device) return fail(S, MCAO_E_INVALID_ARG, "the group spans devices");
+    }
+    if (n_steps == 0) return MCAO_OK;
+    mcao_sim* S = sims[0];   // its s0 carries the group launches
+    CK(cudaSetDevice(S->device));
+    for (int i = 0; i < n_sims; ++i) {
+        if (sims[i]->graph_dirty) {
+            mcao_status r = build_graph(sims[i]);
+            if (r != MCAO_OK) return r;
+        }
+        mcao_status r = order_after_user(sims[i]);
+        if (r != MCAO_OK) return r;
+    }
+    // one parent graph: every simulation's step as an independent child
+    cudaGraph_t parent = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphCreate(&parent, 0);
+    for (int i = 0; i < n_sims && e == cudaSuccess; ++i) {
+        cudaGraphNode_t node;
+        e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, sims[i]->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, parent, cudaGraphInstantiateFlagUseNodePriority);
+    // order after each simulation's earlier work, and each simulation's later work after the group
+    for (int i = 1; i < n_sims && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(sims[i]->ev_done, sims[i]->s0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s0, sims[i]->ev_done, 0);
+    }
+    for (int k = 0; k < n_steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, S->s0);
+    if (e == cudaSuccess) e = cudaEventRecord(S->ev_done, S->s0);
+    for (int i = 1; i < n_sims && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(sims[i]->s0, S->ev_done, 0);
+    if (exec) cudaGraphExecDestroy(exec);   // released once the queued launches complete
+    if (parent) cudaGraphDestroy(parent);
+    CK(e);
+    for (int i = 0; i < n_sims; ++i) {
+        mcao_status r = signal_user(sims[i]);
+        if (r != MCAO_OK) return r;
+    }
+    return MCAO_OK;
+}
+
 mcao_status mcao_sync(mcao_sim* S) {
     if (!S) return MCAO_E_INVALID_ARG;
     CK(cudaSetDevice(S->device));

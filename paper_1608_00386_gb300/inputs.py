@@ -181,6 +181,48 @@ def eelt_mcao(noise: bool = False, seed: int = 7, screen_n: int = 2048, n_layers
     return cfg
 
 
+def mcao_20m(noise: bool = False, seed: int = 7) -> dict:
+    """20 m MCAO case: 3 LGS (40 x 40, 8 px, FFT 32, bin 2, elongated) + 1 NGS 2 x 2, 5 layers
+    of 1024^2, 2 DMs (0 and 8 km)."""
+    D = 20.0
+    dx = D / 320.0
+    heights = [0.0, 1.0e3, 3.0e3, 6.0e3, 12.0e3]
+    frac = np.array([0.5, 0.15, 0.15, 0.1, 0.1])
+    layers = []
+    for l, h in enumerate(heights):
+        ang = math.radians(50.0 * l)
+        v = 6.0 + 4.0 * l
+        layers.append({"n": 1024, "pixel": dx, "alt": h, "vx": float(v * math.cos(ang)), "vy": float(v * math.sin(ang)),
+                       "r0": float(0.157 * frac[l] ** (-3.0 / 5.0)), "L0": 25.0, "seed": 21 + l})
+    wfs = []
+    for i in range(3):
+        a = math.radians(120.0 * i)
+        wfs.append(_wfs("lgs", (30 * ARCSEC * math.cos(a), 30 * ARCSEC * math.sin(a)), 40, 8, 32, 2, 589e-9, 1000.0,
+                        height=90e3, na_fwhm=10e3))
+    wfs.append(_wfs("ngs", (40 * ARCSEC, 0.0), 2, 32, 64, 4, 1.65e-6, 500.0))
+    cfg = {
+        "name": "mcao_20m_3lgs",
+        "D": D, "obstruction": 0.2, "lambda_ref": 500e-9,
+        "dt": 2e-3, "gain": 0.5, "seed": seed, "noise": bool(noise), "psf_every": 1, "n_steps": 1000,
+        "wfs": wfs,
+        "science": [{"theta": (0.0, 0.0), "lambda": 2.2e-6, "n_px": 320, "pad": 2}],
+        "layers": layers,
+    }
+    cfg["dms"] = [dm_spec(cfg, 0.0, 0.5, 0.3), dm_spec(cfg, 8000.0, 1.0, 0.3)]
+    return cfg
+
+
+def mixed_configs(n: int, noise: bool = True) -> list[dict]:
+    """n configurations of mixed sizes for group stepping: cycles through the 8 m single-NGS case
+    (16 x 16 subapertures, 1 layer) and the 20 m 3-LGS case (40 x 40, 5 layers), each with its
+    own noise seed."""
+    out = []
+    for i in range(n):
+        cfg = scao_tiny(noise=noise, seed=100 + i) if i % 2 == 0 else mcao_20m(noise=noise, seed=100 + i)
+        out.append(cfg)
+    return out
+
+
 def n_commands(cfg: dict) -> int:
     return int(sum(int(d["valid"].sum()) for d in cfg["dms"]))
 

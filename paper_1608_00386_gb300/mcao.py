@@ -30,7 +30,7 @@ EXPORTS = [
     "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
     "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
-    "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration",
+    "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration", "mcao_step_group",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -122,6 +122,7 @@ def lib():
         "mcao_interaction_matrix": [vp, vp, C.c_size_t],
         "mcao_slopes_vjp": [vp, vp, C.c_int, vp, vp, vp],
         "mcao_set_misregistration": [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double],
+        "mcao_step_group": [C.POINTER(vp), C.c_int, C.c_int],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -440,6 +441,16 @@ def make_sim(cfg: dict, screens, R, s_ref=None, keep_frames: bool = False, strea
     s.load_dms()
     s.load_reconstructor(R, s_ref, dtype=r_dtype)
     return s
+
+
+def step_group(sims, n: int = 1):
+    """Advance simulations of any configurations together (mcao_step_group): one graph launch
+    per step holding every simulation's step."""
+    arr = (C.c_void_p * len(sims))(*[s.h for s in sims])
+    st = lib().mcao_step_group(arr, len(sims), int(n))
+    if st != 0:
+        bad = next((s for s in sims if lib().mcao_last_error(s.h)), sims[0])
+        raise McaoError(st, lib().mcao_last_error(bad.h).decode())
 
 
 def _sensing_function():

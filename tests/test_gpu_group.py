@@ -1,0 +1,63 @@
+"""Group stepping (mcao_step_group): simulations of different configurations advanced by one
+graph launch per step give bit-identical slopes and commands to stepping each alone; the
+argument checks."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_00386_gb300 import build, inputs, mcao
+
+from _helpers import mcao_small, scao_tiny_inputs, wide_lgs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    build.build()
+    oracle.build()
+
+
+def _make():
+    cfg0, screens0, R0 = scao_tiny_inputs()
+    sims = [mcao.make_sim(dict(cfg0, noise=True), screens0, R0)]
+    for k, cfg in enumerate((dict(mcao_small(), noise=True), wide_lgs())):
+        screens = inputs.make_screens(cfg)
+        n_cmd = inputs.n_commands(cfg)
+        g = mcao.Sim(cfg)
+        n_slopes = g.query(mcao.Q_SLOPES)
+        g.close()
+        R = inputs.random_reconstructor(n_cmd, n_slopes, 0.02, 5 + k)
+        sims.append(mcao.make_sim(cfg, screens, R))
+    return sims
+
+
+def test_group_step_is_bit_identical_to_single_steps():
+    a = _make()
+    b = _make()
+    mcao.step_group(a, 4)
+    mcao.step_group(a, 3)
+    for s in b:
+        s.step(7)
+    for x, y in zip(a, b):
+        assert x.step_index == y.step_index == 7
+        assert np.array_equal(x.slopes(), y.slopes())
+        assert np.array_equal(x.commands(), y.commands())
+        q1, q2 = x.psf(0, with_image=False), y.psf(0, with_image=False)
+        assert q1[1:] == q2[1:]
+
+
+def test_group_step_argument_checks():
+    sims = _make()
+    with pytest.raises(mcao.McaoError):
+        mcao.step_group([sims[0], sims[0]], 1)
+    sims[1].set_profiling(True)
+    with pytest.raises(mcao.McaoError):
+        mcao.step_group(sims, 1)
+    sims[1].set_profiling(False)
+    mcao.step_group(sims, 0)
+    mcao.step_group(sims, 1)
+    assert all(s.step_index == 1 for s in sims)
