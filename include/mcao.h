@@ -348,6 +348,16 @@ mcao_status mcao_generate_screen(int n, double pixel_m, double r0_m, double L0_m
 mcao_status mcao_set_misregistration(mcao_sim* sim, int dm, double shift_x, double shift_y, double rotation,
                                      double magnification);
 
+/* Queue, after the work queued so far, a copy of the current realization's commands
+ * (commands: host [n_commands] float32, or NULL) and of every science direction's
+ * (long-exposure, instantaneous) Strehl ratio (strehl: host [n_sci][2] double, or NULL), and
+ * return at once: a closed loop can read each step's result without waiting for it.  The values
+ * are in place after mcao_sync, or once the stream set by mcao_set_stream passes this point.
+ * Host buffers should be pinned (cudaHostAlloc / page-locked) for the copies to overlap the
+ * next steps; the caller keeps them alive until then.  Errors: MCAO_E_INVALID_ARG (both NULL),
+ * MCAO_E_STATE (commands before the DMs are loaded), MCAO_E_CUDA. */
+mcao_status mcao_read_async(mcao_sim* sim, float* commands, double* strehl);
+
 /* Advance several simulations of any configurations (sizes, sensors, layers, reconstructor
  * formats) by n_steps together: each step is one launch of a graph that holds every
  * simulation's step graph as an independent child, so that small configurations run side by

@@ -292,4 +292,22 @@ cudaError_t launch_sci_cols(const SciLaunch& L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+namespace {
+
+// (long-exposure, instantaneous) Strehl ratio of each science direction from its accumulators
+__global__ void strehl_out_kernel(const SciAcc* acc, int n_sci, double* out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_sci) return;
+    const SciAcc a = acc[q];
+    out[2 * q] = a.n_sr ? a.sr_sum / (double)a.n_sr : 0.0;
+    out[2 * q + 1] = a.sr_last;
+}
+
+}  // namespace
+
+cudaError_t launch_strehl_out(const SciAcc* acc, int n_sci, double* out, cudaStream_t s) {
+    if (n_sci > 0) strehl_out_kernel<<<(n_sci + 63) / 64, 64, 0, s>>>(acc, n_sci, out);
+    return cudaGetLastError();
+}
+
 }  // namespace mcao

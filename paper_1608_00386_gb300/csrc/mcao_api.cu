@@ -155,6 +155,7 @@ struct mcao_sim {
 
     StepState* d_st = nullptr;
     SciAcc* d_acc = nullptr;
+    double* d_sr_out = nullptr;           // staging of mcao_read_async's Strehl ratios
     int* d_err = nullptr;                 // device-side error code (bounded waits)
     unsigned int* d_work = nullptr;       // work counters: [n_wfs] sensing launches, [n_wfs + 1] slices
 
@@ -657,7 +658,7 @@ void destroy_all(mcao_sim* S) {
     S->d_layer_owned.clear();
     dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
     dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_rscale); dfree(S->d_c); dfree(S->d_partial);
-    dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err); dfree(S->d_work);
+    dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err); dfree(S->d_work); dfree(S->d_sr_out);
     dfree(S->d_Rrm);
     dfree(S->d_c_prev); dfree(S->d_dc_prev); dfree(S->d_dc);
     if (S->d_Rrm16) cudaFree(S->d_Rrm16);
@@ -947,6 +948,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         CKC(sci_prepare(maxM));
     }
     CKC(dalloc(&S->d_acc, NR * std::max(cfg->n_sci, 1)));
+    CKC(dalloc(&S->d_sr_out, 2 * (size_t)std::max(cfg->n_sci, 1)));
     CKC(cudaMemsetAsync(S->d_acc, 0, sizeof(SciAcc) * NR * std::max(cfg->n_sci, 1), S->s0));
     if (S->n_real > 1) {
         if (cublasCreate(&S->blas) != CUBLAS_STATUS_SUCCESS) {
@@ -1745,6 +1747,22 @@ mcao_status mcao_get_psf(mcao_sim* S, int sci, double* out, size_t n, double* sr
                 out[j * M + i] = t[((i + M / 2) % M) * M + (j + M / 2) % M] * norm;
     }
     return MCAO_OK;
+}
+
+mcao_status mcao_read_async(mcao_sim* S, float* commands, double* strehl) {
+    if (!S || (!commands && !strehl)) return MCAO_E_INVALID_ARG;
+    if (commands && !S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");
+    CK(cudaSetDevice(S->device));
+    mcao_status r = order_after_user(S);
+    if (r != MCAO_OK) return r;
+    if (commands && S->n_cmd > 0)
+        CK(cudaMemcpyAsync(commands, S->d_c + (size_t)S->cur * S->n_cmd, sizeof(float) * S->n_cmd,
+                           cudaMemcpyDeviceToHost, S->s0));
+    if (strehl && !S->sci.empty()) {
+        CK(launch_strehl_out(S->d_acc + (size_t)S->cur * S->sci.size(), (int)S->sci.size(), S->d_sr_out, S->s0));
+        CK(cudaMemcpyAsync(strehl, S->d_sr_out, sizeof(double) * 2 * S->sci.size(), cudaMemcpyDeviceToHost, S->s0));
+    }
+    return signal_user(S);
 }
 
 mcao_status mcao_get_marechal(mcao_sim* S, int sci, double* sr_long, double* sr_last) {

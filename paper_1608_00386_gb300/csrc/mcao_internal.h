@@ -310,4 +310,7 @@ cudaError_t launch_dm_adjoint(const ProjLaunch& L, cudaStream_t s);
 cudaError_t launch_phase_adjoint(const ProjLaunch& L, float* g_phase, long long phase_stride, long long phase_off,
                                  float* g_layers, long long layer_stride, const long long* layer_off, cudaStream_t s);
 
+// per science direction: (long-exposure, instantaneous) Strehl ratio into out[2 q], out[2 q + 1]
+cudaError_t launch_strehl_out(const SciAcc* acc, int n_sci, double* out, cudaStream_t s);
+
 }  // namespace mcao

@@ -31,6 +31,7 @@ EXPORTS = [
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
     "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
     "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration", "mcao_step_group",
+    "mcao_read_async",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -123,6 +124,7 @@ def lib():
         "mcao_slopes_vjp": [vp, vp, C.c_int, vp, vp, vp],
         "mcao_set_misregistration": [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double],
         "mcao_step_group": [C.POINTER(vp), C.c_int, C.c_int],
+        "mcao_read_async": [vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -302,6 +304,13 @@ class Sim:
                             magnification: float = 1.0):
         """Move DM dm as a rigid body (shift in m, rotation in rad, magnification)."""
         self._ck(lib().mcao_set_misregistration(self.h, dm, shift_x, shift_y, rotation, magnification))
+
+    def read_async(self, commands=None, strehl=None):
+        """Queue copies of the commands (float32 [n_commands]) and the (long, last) Strehl ratios
+        (float64 [n_sci][2]) into the given host arrays (pinned: torch tensors with
+        pin_memory(), or numpy views of them) after the queued work; valid after sync()."""
+        ptr = lambda a: (a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data) if a is not None else None
+        self._ck(lib().mcao_read_async(self.h, ptr(commands), ptr(strehl)))
 
     def measure(self, noise: bool = False) -> np.ndarray:
         """Slopes at the current step and commands without reconstruction or time advance

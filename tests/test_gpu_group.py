@@ -61,3 +61,25 @@ def test_group_step_argument_checks():
     mcao.step_group(sims, 0)
     mcao.step_group(sims, 1)
     assert all(s.step_index == 1 for s in sims)
+
+
+def test_read_async_matches_synchronous_reads():
+    import torch
+    cfg, screens, R = scao_tiny_inputs()
+    g = mcao.make_sim(dict(cfg, noise=True), screens, R)
+    n = g.query(mcao.Q_COMMANDS)
+    ring_c = torch.zeros((4, n), dtype=torch.float32).pin_memory()
+    ring_s = torch.zeros((4, 1, 2), dtype=torch.float64).pin_memory()
+    ref = []
+    for k in range(4):
+        g.step(1)
+        g.read_async(ring_c[k], ring_s[k])
+    g.sync()
+    h = mcao.make_sim(dict(cfg, noise=True), screens, R)
+    for k in range(4):
+        h.step(1)
+        _, sl, sn = h.psf(0, with_image=False)
+        assert np.array_equal(ring_c[k].numpy(), h.commands())
+        assert ring_s[k, 0, 0].item() == sl and ring_s[k, 0, 1].item() == sn
+    with pytest.raises(mcao.McaoError):
+        g.read_async(None, None)
