@@ -14,13 +14,16 @@
 // registers, the slopes stay float32, accumulation is float32 and an E4M3 row sum is multiplied
 // by its row's scale before it is written.
 //
-// Streaming.  At most one block per SM (3 warps).  Each warp owns a four-stage ring in
+// Streaming.  At most one block per SM (5 warps).  Each warp owns a two-stage ring in
 // shared memory and keeps it filled with TMA bulk copies (cp.async.bulk, completion counted on a
 // per-stage mbarrier, L2 evict-first policy).  R is held stage-tiled (see ReconLaunch), so each
 // stage -- four row segments of up to 2 KB -- is one contiguous copy of up to 8 KB (bulk copies
-// that small lose bandwidth), and up to 96 KB per SM are in flight.  The block needs
+// that small lose bandwidth), and up to 80 KB per SM are in flight.  The block needs
 // few registers and warps, which leaves each SM room for three wavefront-sensor blocks that run
-// concurrently, hiding their ALU work under the HBM stream.  Every mbarrier wait is bounded
+// concurrently, hiding their ALU work under the HBM stream.  Inside the step, five warps with
+// two stages each stream faster than three with four (same or less shared memory): the block's
+// warps compete for issue slots with the co-resident sensing warps, and more of them get more
+// turns; rings above 96 KB keep the science kernels off the SM and slow the step.  Every mbarrier wait is bounded
 // (about one second of clock); on expiry the warp records kErrReconTimeout, waits (bounded)
 // for its copies in flight and exits.
 #include "mcao_internal.h"
@@ -53,10 +56,10 @@ __device__ __forceinline__ float2 dot4x2(float4 a, float4 b, float2 acc) {
 // ------------------------------------------------------------------------------------------
 // TMA bulk-copy streaming
 // ------------------------------------------------------------------------------------------
-constexpr int kTmaWarps = 3;
+constexpr int kTmaWarps = 5;
 constexpr int kTmaRows = kReconRows;               // rows per item
 constexpr int kTmaSeg = kReconSeg;                 // 16-byte vectors per row segment (2 KB)
-constexpr int kTmaStages = 4;
+constexpr int kTmaStages = 2;
 constexpr long long kWaitCycles = 2000000000ll;    // ~1 s at 2 GHz
 
 struct TmaSmem {
@@ -237,7 +240,7 @@ __device__ __forceinline__ void stage_fma(const uint4 (&rv)[kTmaSeg / 32][kTmaRo
 // receives an item's first stage which item it is (-1 once the counter is exhausted) and issues
 // the copies.  The other lanes follow the slots in order.  Per stage: wait for the slot's copy,
 // pull the stage into registers, let lane 0 refill the slot, then do the multiply-adds -- a slot
-// is held only for its shared-memory loads, which keeps four copies per warp in flight.
+// is held only for its shared-memory loads, which keeps the warp's copies in flight.
 template <int DT>
 __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L) {
     constexpr int SPV = 4 / recon_esize(DT);   // float4 of slopes per 16-byte vector of R
