@@ -36,6 +36,67 @@ __global__ void screen_twiddle_kernel(int n, float2* W) {
     }
 }
 
+// Twiddle table of the compile-time transform laid out stage by stage, so that a warp's
+// butterflies (consecutive k) read consecutive entries: for the stage of sub-length ns and
+// radix R, entry off + (r - 1) ns + k = exp(-2 pi i r k / (ns R)), r = 1 .. R-1, k < ns (the
+// same float values as the single table exp(-2 pi i m / N) at m = r k N / (ns R)).
+template <int N>
+__global__ void screen_stage_twiddles(float2* T) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int off = 0, ns = 1;
+    while (ns < N) {
+        const int R = ct_radix(N / ns);
+        const int cnt = ns * (R - 1);
+        if (e < off + cnt) {
+            const int q = e - off, r = q / ns + 1, k = q - (r - 1) * ns;
+            const int m = (r * k * (N / (ns * R))) % N;
+            double sn, cs;
+            sincospi(-2.0 * (double)m / (double)N, &sn, &cs);
+            T[e] = make_float2((float)cs, (float)sn);
+            return;
+        }
+        off += cnt;
+        ns *= R;
+    }
+}
+
+template <int N, int NS, int R>
+__device__ __forceinline__ void stage_tab(const float2* src, float2* dst, int batch, const float2* T, int tid,
+                                          int nthr) {
+    constexpr int NR = N / R;
+    for (int idx = tid; idx < batch * NR; idx += nthr) {
+        const int f = idx / NR, j = idx - f * NR;
+        const float2* sp = src + f * N;
+        float2* dp = dst + f * N;
+        const int k = j % NS;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = sp[j + r * NR];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], T[(r - 1) * NS + k]);
+        }
+        small_dft<R>(v);
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dp[base + r * NS] = v[r];
+    }
+}
+
+// the compile-time Stockham transform reading the stage-major table; returns the buffer holding
+// the result (a block-wide barrier follows every stage)
+template <int N, int NS = 1, int OFF = 0>
+__device__ __forceinline__ float2* fft_tab(float2* a, float2* b, int batch, const float2* T, int tid, int nthr) {
+    if constexpr (NS >= N) {
+        return a;
+    } else {
+        constexpr int R = ct_radix(N / NS);
+        stage_tab<N, NS, R>(a, b, batch, T + OFF, tid, nthr);
+        __syncthreads();
+        return fft_tab<N, NS * R, OFF + NS * (R - 1)>(b, a, batch, T, tid, nthr);
+    }
+}
+
 struct ScreenPass {
     int n, rows;
     // first pass: coefficients generated in place (amp0 = sqrt(0.023 r0^-5/3) / (n pixel), frequencies
@@ -89,7 +150,7 @@ __global__ void __launch_bounds__(kScreenThreads) screen_fft_pass(ScreenPass P) 
     }
     __syncthreads();
     const float2* R;
-    if constexpr (NCT > 0) R = stockham_fft_ct<NCT>(A, B, rows, NCT, W, tid, nthr);
+    if constexpr (NCT > 0) R = fft_tab<NCT>(A, B, rows, W, tid, nthr);
     else R = stockham_fft(A, B, n, P.radices, P.n_radices, rows, n, 1, W, tid, nthr);
     for (int q = tid; q < rows * n; q += nthr) {
         const int c = q / rows, r = q - c * rows;
@@ -129,7 +190,15 @@ cudaError_t screen_passes(ScreenPass P, unsigned blocks, cudaStream_t s) {
 
 cudaError_t launch_screen(int n, double pixel, double r0, double L0, unsigned long long seed, const int* radices,
                           int n_radices, float2* work, float2* W, float* out, cudaStream_t s) {
-    screen_twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, W);
+    // twiddles: stage-major for the compile-time sizes, the plain table otherwise
+    switch (n) {
+        case 256: screen_stage_twiddles<256><<<1, 256, 0, s>>>(W); break;
+        case 512: screen_stage_twiddles<512><<<2, 256, 0, s>>>(W); break;
+        case 1024: screen_stage_twiddles<1024><<<4, 256, 0, s>>>(W); break;
+        case 2048: screen_stage_twiddles<2048><<<8, 256, 0, s>>>(W); break;
+        case 4096: screen_stage_twiddles<4096><<<16, 256, 0, s>>>(W); break;
+        default: screen_twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, W);
+    }
     ScreenPass P{};
     P.n = n;
     P.rows = screen_rows(n);
