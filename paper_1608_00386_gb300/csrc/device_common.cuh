@@ -247,6 +247,54 @@ __device__ __forceinline__ float2* stockham_fft_ct(float2* a, float2* b, int bat
     }
 }
 
+// The compile-time transform again, with its twiddles in a stage-major table so that a warp's
+// butterflies (consecutive k) read consecutive entries instead of one bank at stride N/(ns R):
+// for the stage of sub-length ns and radix R, entry off + (r - 1) ns + k holds
+// exp(-2 pi i r k / (ns R)) = W[r k N / (ns R)], r = 1 .. R-1, k < ns; off is the sum of the
+// earlier stages' ns (R - 1); N - 1 entries in all (stage_twiddle_count).
+__host__ __device__ constexpr int stage_twiddle_count(int N) {
+    int c = 0;
+    for (int ns = 1; ns < N; ns *= ct_radix(N / ns)) c += ns * (ct_radix(N / ns) - 1);
+    return c;
+}
+
+template <int N, int NS, int R>
+__device__ __forceinline__ void stage_tab(const float2* src, float2* dst, int batch, const float2* T, int tid,
+                                          int nthr) {
+    constexpr int NR = N / R;
+    for (int idx = tid; idx < batch * NR; idx += nthr) {
+        const int f = idx / NR, j = idx - f * NR;
+        const float2* sp = src + f * N;
+        float2* dp = dst + f * N;
+        const int k = j % NS;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = sp[j + r * NR];
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], T[(r - 1) * NS + k]);
+        }
+        small_dft<R>(v);
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dp[base + r * NS] = v[r];
+    }
+}
+
+// the compile-time Stockham transform reading the stage-major table; returns the buffer holding
+// the result (a block-wide barrier follows every stage)
+template <int N, int NS = 1, int OFF = 0>
+__device__ __forceinline__ float2* fft_tab(float2* a, float2* b, int batch, const float2* T, int tid, int nthr) {
+    if constexpr (NS >= N) {
+        return a;
+    } else {
+        constexpr int R = ct_radix(N / NS);
+        stage_tab<N, NS, R>(a, b, batch, T + OFF, tid, nthr);
+        __syncthreads();
+        return fft_tab<N, NS * R, OFF + NS * (R - 1)>(b, a, batch, T, tid, nthr);
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Detector noise.  Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by the
 // seed, counter (pixel, step, WFS, 0); float sampler with a fixed operation order written with

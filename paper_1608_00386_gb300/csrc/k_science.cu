@@ -6,6 +6,9 @@
 // The 2-D FFT runs as two passes of batched radix-4/5/2 Stockham FFTs in shared memory: rows of
 // the field (zero-padded) written transposed, then rows of the transposed array; the PSF
 // accumulator is therefore held transposed and unshifted, [kx][ky] (the host reorders it).
+#include <cmath>
+#include <vector>
+
 #include "device_common.cuh"
 #include "mcao_internal.h"
 
@@ -153,7 +156,8 @@ __global__ void __launch_bounds__(256) sci_cols_kernel(SciLaunch L0) {
     if (blockIdx.x == 0 && tid == 0) L.acc->n_psf += 1;
 }
 
-// Compile-time-size versions of the two FFT passes (2 rows / columns per block).
+// Compile-time-size versions of the two FFT passes (2 rows / columns per block); their twiddle
+// table is stage-major (sci_twiddles).
 constexpr int kCtRows = 2;
 
 template <int M>
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(256) sci_rows_ct(SciLaunch L0) {
         A[q] = (row < L.N && c < L.N) ? L.field[(long long)row * L.N + c] : make_float2(0.0f, 0.0f);
     }
     __syncthreads();
-    float2* R = stockham_fft_ct<M>(A, B, kCtRows, M, W, tid, nthr);
+    float2* R = fft_tab<M>(A, B, kCtRows, W, tid, nthr);
     for (int q = tid; q < kCtRows * M; q += nthr) {
         int c = q / kCtRows, r = q - c * kCtRows;
         int row = row0 + r;
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(256) sci_cols_ct(SciLaunch L0) {
         A[q] = (j < L.N) ? L.ft[(long long)(c0 + r) * L.N + j] : make_float2(0.0f, 0.0f);
     }
     __syncthreads();
-    float2* R = stockham_fft_ct<M>(A, B, kCtRows, M, W, tid, nthr);
+    float2* R = fft_tab<M>(A, B, kCtRows, W, tid, nthr);
     for (int q = tid; q < kCtRows * M; q += nthr) {
         int r = q / M, j = q - r * M;
         float2 v = R[q];
@@ -252,6 +256,34 @@ cudaError_t launch_sci_field(const SciLaunch& L, cudaStream_t s) {
     int tiles = (L.N / 8) * (L.N / 8);
     sci_field_kernel<<<dim3((unsigned)((tiles + 7) / 8), (unsigned)L.ctx.n_real), 256, 0, s>>>(L);
     return cudaGetLastError();
+}
+
+bool sci_ct_size(int M) {
+#define MCAO_CT_IS(n) \
+    if (M == n) return true;
+    MCAO_SCI_CT_SIZES(MCAO_CT_IS)
+#undef MCAO_CT_IS
+    return false;
+}
+
+std::vector<float2> sci_twiddles(int M) {
+    auto w = [M](long long m) {
+        const double a = -2.0 * M_PI * (double)m / (double)M;
+        return make_float2((float)std::cos(a), (float)std::sin(a));
+    };
+    std::vector<float2> W(M);
+    if (!sci_ct_size(M)) {
+        for (int m = 0; m < M; ++m) W[m] = w(m);
+        return W;
+    }
+    int off = 0;
+    for (int ns = 1; ns < M; ns *= ct_radix(M / ns)) {
+        const int R = ct_radix(M / ns);
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < ns; ++k) W[off + (r - 1) * ns + k] = w(((long long)r * k * (M / (ns * R))) % M);
+        off += ns * (R - 1);
+    }
+    return W;
 }
 
 cudaError_t sci_prepare(int M) {

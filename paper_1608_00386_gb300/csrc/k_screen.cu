@@ -60,43 +60,6 @@ __global__ void screen_stage_twiddles(float2* T) {
     }
 }
 
-template <int N, int NS, int R>
-__device__ __forceinline__ void stage_tab(const float2* src, float2* dst, int batch, const float2* T, int tid,
-                                          int nthr) {
-    constexpr int NR = N / R;
-    for (int idx = tid; idx < batch * NR; idx += nthr) {
-        const int f = idx / NR, j = idx - f * NR;
-        const float2* sp = src + f * N;
-        float2* dp = dst + f * N;
-        const int k = j % NS;
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = sp[j + r * NR];
-        if constexpr (NS > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], T[(r - 1) * NS + k]);
-        }
-        small_dft<R>(v);
-        const int base = (j / NS) * NS * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) dp[base + r * NS] = v[r];
-    }
-}
-
-// the compile-time Stockham transform reading the stage-major table; returns the buffer holding
-// the result (a block-wide barrier follows every stage)
-template <int N, int NS = 1, int OFF = 0>
-__device__ __forceinline__ float2* fft_tab(float2* a, float2* b, int batch, const float2* T, int tid, int nthr) {
-    if constexpr (NS >= N) {
-        return a;
-    } else {
-        constexpr int R = ct_radix(N / NS);
-        stage_tab<N, NS, R>(a, b, batch, T + OFF, tid, nthr);
-        __syncthreads();
-        return fft_tab<N, NS * R, OFF + NS * (R - 1)>(b, a, batch, T, tid, nthr);
-    }
-}
-
 struct ScreenPass {
     int n, rows;
     // first pass: coefficients generated in place (amp0 = sqrt(0.023 r0^-5/3) / (n pixel), frequencies

@@ -927,11 +927,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
         CKC(dalloc(&C.d_psf_t, NR * C.M * C.M));
         CKC(cudaMemsetAsync(C.d_psf_t, 0, sizeof(double) * NR * C.M * C.M, S->s0));
         CKC(dalloc(&C.d_sr_part, NR * std::max(C.n_tiles, 1)));
-        std::vector<float2> W(C.M);
-        for (int m = 0; m < C.M; ++m) {
-            double a = -2.0 * M_PI * (double)m / (double)C.M;
-            W[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-        }
+        const std::vector<float2> W = sci_twiddles(C.M);
         CKC(dalloc(&C.d_w, C.M));
         CKC(cudaMemcpyAsync(C.d_w, W.data(), sizeof(float2) * C.M, cudaMemcpyHostToDevice, S->s0));
         maxM = std::max(maxM, C.M);

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <stdint.h>
 
 namespace mcao {
@@ -312,5 +314,9 @@ cudaError_t launch_phase_adjoint(const ProjLaunch& L, float* g_phase, long long 
 
 // per science direction: (long-exposure, instantaneous) Strehl ratio into out[2 q], out[2 q + 1]
 cudaError_t launch_strehl_out(const SciAcc* acc, int n_sci, double* out, cudaStream_t s);
+
+// twiddles of a science FFT of size M in the layout its kernels read (stage-major for the sizes
+// with a compile-time transform, exp(-2 pi i m / M) otherwise)
+std::vector<float2> sci_twiddles(int M);
 
 }  // namespace mcao
