@@ -98,11 +98,28 @@ def timed_steps(sim, stream, steps, warmup, dist, clocks):
     ck = clocks.stop()
     ms, cnt, lps = sim.get_profile()
     sim.set_profiling(False)
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item()), ms, cnt, lps, ck
+    return max_over_ranks(elapsed, dist), ms, cnt, lps, ck
+
+
+def max_over_ranks(seconds, dist, device="cuda"):
+    """The slowest rank's time (barrier, then an all-reduce MAX); the value itself on one rank."""
+    if not dist:
+        return float(seconds)
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, steps, seconds):
+    """Whole-job throughput: every rank advances its own replica by `steps` steps."""
+    return ws * steps / seconds
+
+
+def replica_config(cfg, rank):
+    """Rank r runs an independent replica (noise key 7 + r) of the same workload."""
+    return dict(cfg, seed=7 + rank, noise=True)
 
 
 def peaks():
@@ -261,7 +278,7 @@ def main():
     build.build()
 
     cfg, screens, n_cmd = workload()
-    cfg = dict(cfg, seed=7 + rank, noise=True)
+    cfg = replica_config(cfg, rank)
     R = inputs.random_reconstructor(n_cmd, 55608, RECON_SIGMA, 3)
     # inputs resident in HBM before the timed region
     d_screens = [torch.from_numpy(s).cuda() for s in screens]
@@ -272,7 +289,7 @@ def main():
     sim = mcao.make_sim(cfg, d_screens, d_R, stream=stream)
     n_slopes = sim.query(mcao.Q_SLOPES)
     elapsed, ms, cnt, lps, ck = timed_steps(sim, stream, args.steps, args.warmup, dist, Clocks(local))
-    value = ws * args.steps / elapsed
+    value = job_value(ws, args.steps, elapsed)
 
     # dominant kernel roofline (reconstructor product): one step issues it as one launch per
     # sensor slice; per-step bytes over the summed device time of those launches
