@@ -348,6 +348,13 @@ mcao_status mcao_generate_screen(int n, double pixel_m, double r0_m, double L0_m
 mcao_status mcao_set_misregistration(mcao_sim* sim, int dm, double shift_x, double shift_y, double rotation,
                                      double magnification);
 
+/* Self-check of the device-side timeouts: launches one bounded mbarrier wait that nothing
+ * satisfies (the wait the reconstructor product uses, about one second of clock).  The wait
+ * must expire, record its error flag and let the kernel exit; the call then returns
+ * MCAO_E_TIMEOUT exactly as after a product wait that gave up, the flag is cleared and the
+ * simulation stays usable.  Any other status means the timeout path is broken. */
+mcao_status mcao_check_bounded_wait(mcao_sim* sim);
+
 /* Queue, after the work queued so far, a copy of the current realization's commands
  * (commands: host [n_commands] float32, or NULL) and of every science direction's
  * (long-exposure, instantaneous) Strehl ratio (strehl: host [n_sci][2] double, or NULL), and

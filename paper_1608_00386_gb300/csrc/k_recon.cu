@@ -557,6 +557,26 @@ long long recon_slice_bytes(int n_rq, int len, int kc, int dtype) {
     return chunks * n_rq * (long long)kTmaRows * kc * recon_esize(dtype);
 }
 
+namespace {
+
+// Self-check of the bounded waits: one thread waits on an mbarrier that nothing arrives at (its
+// first phase never completes); the wait must give up after kWaitCycles and report, exactly as
+// a product warp would, and the block then exits normally.
+__global__ void wait_probe_kernel(int* err) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u)) atomicExch(err, kErrReconTimeout);
+}
+
+}  // namespace
+
+cudaError_t launch_wait_probe(int* err, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(err);
+    return cudaGetLastError();
+}
+
 cudaError_t recon_prepare() {
     cudaError_t e = cudaFuncSetAttribute(recon_tma_kernel<kReconF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(TmaSmem));

@@ -1745,6 +1745,14 @@ mcao_status mcao_get_psf(mcao_sim* S, int sci, double* out, size_t n, double* sr
     return MCAO_OK;
 }
 
+mcao_status mcao_check_bounded_wait(mcao_sim* S) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    CK(cudaSetDevice(S->device));
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    CK(launch_wait_probe(S->d_err, S->s0));
+    return sync_all(S);   // reports the expired wait as MCAO_E_TIMEOUT and clears the flag
+}
+
 mcao_status mcao_read_async(mcao_sim* S, float* commands, double* strehl) {
     if (!S || (!commands && !strehl)) return MCAO_E_INVALID_ARG;
     if (commands && !S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");

@@ -319,4 +319,8 @@ cudaError_t launch_strehl_out(const SciAcc* acc, int n_sci, double* out, cudaStr
 // with a compile-time transform, exp(-2 pi i m / M) otherwise)
 std::vector<float2> sci_twiddles(int M);
 
+// one bounded mbarrier wait that nothing satisfies: sets *err to kErrReconTimeout after about a
+// second (self-check of the timeout path)
+cudaError_t launch_wait_probe(int* err, cudaStream_t s);
+
 }  // namespace mcao

@@ -31,7 +31,7 @@ EXPORTS = [
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
     "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
     "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration", "mcao_step_group",
-    "mcao_read_async",
+    "mcao_read_async", "mcao_check_bounded_wait",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -125,6 +125,7 @@ def lib():
         "mcao_set_misregistration": [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double],
         "mcao_step_group": [C.POINTER(vp), C.c_int, C.c_int],
         "mcao_read_async": [vp, vp, vp],
+        "mcao_check_bounded_wait": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -304,6 +305,10 @@ class Sim:
                             magnification: float = 1.0):
         """Move DM dm as a rigid body (shift in m, rotation in rad, magnification)."""
         self._ck(lib().mcao_set_misregistration(self.h, dm, shift_x, shift_y, rotation, magnification))
+
+    def check_bounded_wait(self) -> int:
+        """Status of mcao_check_bounded_wait: 6 (MCAO_E_TIMEOUT) when the device timeouts work."""
+        return lib().mcao_check_bounded_wait(self.h)
 
     def read_async(self, commands=None, strehl=None):
         """Queue copies of the commands (float32 [n_commands]) and the (long, last) Strehl ratios

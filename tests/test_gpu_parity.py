@@ -291,3 +291,18 @@ def test_errors_and_degenerate_calls():
     z = mcao.make_sim(cfg, screens, np.zeros_like(R))
     z.step(3)
     assert np.all(z.commands() == 0)
+
+
+def test_bounded_wait_expires_and_context_stays_usable():
+    # a wait that nothing satisfies gives up after about a second, is reported as a timeout, and
+    # the next steps run and match an untouched simulation
+    cfg, screens, R = scao_tiny_inputs()
+    g = mcao.make_sim(cfg, screens, R)
+    h = mcao.make_sim(cfg, screens, R)
+    g.step(2)
+    assert g.check_bounded_wait() == 6
+    assert g.check_bounded_wait() == 6
+    g.step(3)
+    h.step(5)
+    assert np.array_equal(g.slopes(), h.slopes())
+    assert np.array_equal(g.commands(), h.commands())
