@@ -128,9 +128,9 @@ def lib():
         L.orc_screen_amp.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp]
         L.orc_screen_coeffs.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64, _dp, _dp]
         L.orc_set_sodium.restype = C.c_int
-        L.orc_noise_sample.argtypes = [C.c_float, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64]
-        L.orc_noise_sample.restype = C.c_int
-        L.orc_noise_frame.argtypes = [_fp, C.c_int, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32,
+        L.orc_noise_pair.argtypes = [C.c_float, C.c_float, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32,
+                                     C.c_uint64, _i32p, _i32p]
+        L.orc_noise_frame.argtypes = [_fp, C.c_int, C.c_int, C.c_float, C.c_uint32, C.c_uint32, C.c_uint32,
                                       C.c_uint64, _i32p]
         L.orc_create.argtypes = [C.POINTER(_Config)]
         L.orc_create.restype = C.c_void_p
@@ -351,8 +351,21 @@ def dequantize_rows(codes: np.ndarray, scales: np.ndarray, dtype: int) -> np.nda
     return table[codes] * scales.astype(np.float64)[:, None]
 
 
-def noise_sample(lam: float, read_noise: float, c0: int, c1: int, c2: int, seed: int) -> int:
-    return lib().orc_noise_sample(lam, read_noise, c0, c1, c2, seed)
+def noise_pair(lam_a: float, lam_b: float, read_noise: float, c0: int, c1: int, c2: int, seed: int):
+    """Noisy counts of a pixel pair (see orc_noise_pair)."""
+    a, b = C.c_int32(), C.c_int32()
+    lib().orc_noise_pair(lam_a, lam_b, read_noise, c0, c1, c2, seed, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def noise_frame(lam: np.ndarray, read_noise: float, pixel0: int, step: int, wfs: int, seed: int,
+                frame_px: int) -> np.ndarray:
+    """Noisy frames of a buffer of subaperture frames of frame_px pixels (pairs within frames)."""
+    lam = np.ascontiguousarray(lam, dtype=np.float32).ravel()
+    out = np.zeros(lam.size, dtype=np.int32)
+    lib().orc_noise_frame(_ptr(lam, C.c_float), lam.size, int(frame_px), read_noise, pixel0, step, wfs, seed,
+                          _ptr(out, C.c_int32))
+    return out
 
 
 def screen_coeffs(n: int, pixel: float, r0: float, L0: float, seed: int) -> np.ndarray:
@@ -385,14 +398,6 @@ def screen_structure_function(n: int, pixel: float, r0: float, L0: float, r_px: 
     a2 = screen_amp(n, pixel, r0, L0) ** 2
     kx = np.arange(n)[None, :]
     return float(np.sum(a2 * 2.0 * (1.0 - np.cos(2 * np.pi * kx * r_px / n))))
-
-
-def noise_frame(lam: np.ndarray, read_noise: float, pixel0: int, step: int, wfs: int, seed: int) -> np.ndarray:
-    lam = np.ascontiguousarray(lam, dtype=np.float32).ravel()
-    out = np.zeros(lam.size, dtype=np.int32)
-    lib().orc_noise_frame(_ptr(lam, C.c_float), lam.size, read_noise, pixel0, step, wfs, seed,
-                          _ptr(out, C.c_int32))
-    return out
 
 
 def num_threads() -> int:

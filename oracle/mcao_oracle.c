@@ -574,14 +574,11 @@ void orc_screen_coeffs(int n, double pixel, double r0, double L0, uint64_t seed,
  * q_j = fl(lambda fl(1/j)) (the ratio formed first, then the product), smallest k with
  * u <= F_k, k capped at 64, u from word 0.  lambda >= 16: max(0, rint(lambda + sqrt(lambda) z_s)).
  * Counter = (c0, c1, c2, 0), key = (seed low word, seed high word). */
-int orc_noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1, uint32_t c2, uint64_t seed) {
-    uint32_t ctr[4] = {c0, c1, c2, 0u}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, w[4];
-    orc_philox4x32_10(ctr, key, w);
-    float zc = 0.0f, zs = 0.0f;
-    if (read_noise > 0.0f || !(lam < 16.0f)) box_muller2(orc_uniform_f32(w[2]), orc_uniform_f32(w[3]), &zc, &zs);
-    int n;
+/* Photon count of one pixel: Poisson by inversion for lambda < 16 (the smallest k with
+ * u <= F_k, p_0 = exp(-lambda), p_k = p_{k-1} fl(lambda fl(1/k)), k <= 64), else
+ * max(0, rint(lambda + sqrt(lambda) y)) with the standard normal y. */
+static int photons_f32(float lam, float u, float y) {
     if (lam < 16.0f) {
-        float u = orc_uniform_f32(w[0]);
         float p = orc_exp_f32(-lam), F = p;
         int k = 0;
         while (F < u && k < 64) {
@@ -590,14 +587,38 @@ int orc_noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1, uint
             p = p * q;
             F = F + p;
         }
-        n = k;
-    } else {
-        float v = fmaf(sqrtf(lam), zs, lam);
-        n = (int)lrintf(v);
-        if (n < 0) n = 0;
+        return k;
     }
-    if (read_noise > 0.0f) n += (int)lrintf(read_noise * zc);
-    return n;
+    int n = (int)lrintf(fmaf(sqrtf(lam), y, lam));
+    return n < 0 ? 0 : n;
+}
+
+/* Noisy counts of a pixel pair (pixels o and o + n_det^2/2 of one subaperture frame; c0 the frame
+ * index of pixel o, c1 the step, c2 the sensor): draw A = Philox(c0, c1, c2, 0) gives the two
+ * inversion uniforms (words 0 and 1) and, with read noise, one Box-Muller pair (words 2, 3) whose
+ * outputs are the two pixels' read noise rint(sigma z); draw B = Philox(c0, c1, c2, 2), used only
+ * when a pixel has lambda >= 16, gives one Box-Muller pair (words 2, 3) for the photon normals. */
+void orc_noise_pair(float lam_a, float lam_b, float read_noise, uint32_t c0, uint32_t c1, uint32_t c2, uint64_t seed,
+                    int32_t* na, int32_t* nb) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ca[4] = {c0, c1, c2, 0u}, wa[4];
+    orc_philox4x32_10(ca, key, wa);
+    float ya = 0.0f, yb = 0.0f;
+    if (!(lam_a < 16.0f) || !(lam_b < 16.0f)) {
+        uint32_t cb[4] = {c0, c1, c2, 2u}, wb[4];
+        orc_philox4x32_10(cb, key, wb);
+        box_muller2(orc_uniform_f32(wb[2]), orc_uniform_f32(wb[3]), &ya, &yb);
+    }
+    int a = photons_f32(lam_a, orc_uniform_f32(wa[0]), ya);
+    int b = photons_f32(lam_b, orc_uniform_f32(wa[1]), yb);
+    if (read_noise > 0.0f) {
+        float za, zb;
+        box_muller2(orc_uniform_f32(wa[2]), orc_uniform_f32(wa[3]), &za, &zb);
+        a += (int)lrintf(read_noise * za);
+        b += (int)lrintf(read_noise * zb);
+    }
+    *na = a;
+    *nb = b;
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -664,10 +685,15 @@ void orc_quantize_rows(const float* R, int rows, int cols, int ld, int dtype, vo
 }
 
 /* Noisy frame of n pixels for counters (pixel0 + i, step, wfs). */
-void orc_noise_frame(const float* lam, int n, float read_noise, uint32_t pixel0, uint32_t step,
+/* Noisy frames of n pixels in subaperture frames of frame_px pixels each (pixel i of the buffer
+ * has frame index pixel0 + i; pairs within each frame). */
+void orc_noise_frame(const float* lam, int n, int frame_px, float read_noise, uint32_t pixel0, uint32_t step,
                      uint32_t wfs, uint64_t seed, int32_t* out) {
-    for (int i = 0; i < n; ++i)
-        out[i] = orc_noise_sample(lam[i], read_noise, pixel0 + (uint32_t)i, step, wfs, seed);
+    const int half = frame_px / 2;
+    for (int f = 0; f + frame_px <= n; f += frame_px)
+        for (int q = 0; q < half; ++q)
+            orc_noise_pair(lam[f + q], lam[f + q + half], read_noise, pixel0 + (uint32_t)(f + q), step, wfs, seed,
+                           &out[f + q], &out[f + q + half]);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -979,11 +1005,13 @@ static void measure_slopes(orc_sim* S) {
             size_t base = (size_t)v * nd * nd;
             for (int q = 0; q < nd * nd; ++q) W->lam[base + q] = (float)det[q];
             if (S->cfg.noise) {
-                for (int q = 0; q < nd * nd; ++q) {
-                    int32_t n = orc_noise_sample(W->lam[base + q], (float)W->p.read_noise,
-                                                 (uint32_t)(base + q), (uint32_t)S->k, (uint32_t)w, S->cfg.seed);
-                    W->frames[base + q] = n;
-                    det[q] = (double)n;
+                const int half = nd * nd / 2;
+                for (int q = 0; q < half; ++q) {
+                    orc_noise_pair(W->lam[base + q], W->lam[base + q + half], (float)W->p.read_noise,
+                                   (uint32_t)(base + q), (uint32_t)S->k, (uint32_t)w, S->cfg.seed,
+                                   &W->frames[base + q], &W->frames[base + q + half]);
+                    det[q] = (double)W->frames[base + q];
+                    det[q + half] = (double)W->frames[base + q + half];
                 }
             }
             double gx, gy;

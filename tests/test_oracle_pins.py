@@ -414,22 +414,43 @@ def test_log_sincos_f32_accuracy():
 
 
 def test_photon_and_read_noise_independent():
-    # the photon normal (lambda >= 16) and the read noise come from the two outputs of one
-    # Box-Muller pair: independent, so the variances add
-    lam, sig, n = 40.0, 3.0, 200_000
-    x = np.array([oracle.noise_sample(lam, sig, i, 5, 2, 11) for i in range(n)], dtype=np.float64)
+    # each pixel of a pair: photon normal (lambda >= 16, draw B) and read noise (draw A) are
+    # independent, so the variances add; the two pixels of a pair are independent of each other
+    lam, sig, n = 40.0, 3.0, 100_000
+    x = np.array([oracle.noise_pair(lam, lam, sig, i, 5, 2, 11) for i in range(n)], dtype=np.float64)
     var = lam + sig * sig + 2.0 / 12.0   # two roundings to integers
-    assert x.mean() == pytest.approx(lam, abs=4 * math.sqrt(var / n))
-    assert x.var() == pytest.approx(var, rel=4 * math.sqrt(2.0 / n) + 0.01)
+    for a in (0, 1):
+        assert x[:, a].mean() == pytest.approx(lam, abs=4 * math.sqrt(var / n))
+        assert x[:, a].var() == pytest.approx(var, rel=4 * math.sqrt(2.0 / n) + 0.01)
+    assert abs(np.corrcoef(x[:, 0], x[:, 1])[0, 1]) < 4.0 / math.sqrt(n)
+    # a pair with one dim pixel (inversion) and one bright pixel (normal) keeps both laws
+    y = np.array([oracle.noise_pair(2.5, 60.0, 0.0, i, 9, 1, 3) for i in range(n)], dtype=np.float64)
+    assert y[:, 0].mean() == pytest.approx(2.5, abs=5 * math.sqrt(2.5 / n))
+    assert y[:, 0].var() == pytest.approx(2.5, rel=0.03)
+    assert y[:, 1].mean() == pytest.approx(60.0, abs=5 * math.sqrt(60.0 / n))
+    assert abs(np.corrcoef(y[:, 0], y[:, 1])[0, 1]) < 4.0 / math.sqrt(n)
+
+
+def test_noise_frame_pairs_within_subaperture_frames():
+    # a frame buffer draws pixel pairs (q, q + frame/2) inside each frame: the frame function
+    # equals the pair function applied pair by pair
+    rng = np.random.default_rng(4)
+    lam = rng.uniform(0.0, 40.0, 3 * 64).astype(np.float32)
+    fr = oracle.noise_frame(lam, 2.0, 128, 7, 3, 55, frame_px=64)
+    for f in range(3):
+        for q in range(32):
+            a, b = oracle.noise_pair(float(lam[64 * f + q]), float(lam[64 * f + q + 32]), 2.0, 128 + 64 * f + q, 7,
+                                     3, 55)
+            assert (fr[64 * f + q], fr[64 * f + q + 32]) == (a, b)
 
 
 @pytest.mark.parametrize("lam", [0.0, 0.7, 5.0, 15.9, 16.0, 40.0, 250.0])
 def test_poisson_moments(lam):
-    n = 200_000
-    fr = oracle.noise_frame(np.full(n, lam, np.float32), 0.0, 0, 17, 2, 12345)
+    n = 256 * 800
+    fr = oracle.noise_frame(np.full(n, lam, np.float32), 0.0, 0, 17, 2, 12345, frame_px=256)
     m, v = fr.mean(), fr.var()
     tol_m = 5 * math.sqrt(max(lam, 1e-3) / n)
-    assert abs(m - lam) <= tol_m + (0.51 if lam >= 16 else 0.0) * 0 + 1e-12
+    assert abs(m - lam) <= tol_m + 1e-12
     if lam > 0:
         tol_v = 6 * lam * math.sqrt(2.0 / n) + 6 * math.sqrt(lam / n)
         extra = 1.0 / 12.0 if lam >= 16 else 0.0  # rounding of the normal approximation
@@ -439,14 +460,17 @@ def test_poisson_moments(lam):
 
 
 def test_read_noise_moments_and_determinism():
-    n = 200_000
-    fr = oracle.noise_frame(np.zeros(n, np.float32), 3.0, 0, 1, 0, 99)
+    n = 256 * 800
+    fr = oracle.noise_frame(np.zeros(n, np.float32), 3.0, 0, 1, 0, 99, frame_px=256)
     assert abs(fr.mean()) < 5 * 3.0 / math.sqrt(n)
     assert fr.var() == pytest.approx(9.0 + 1.0 / 12.0, rel=0.02)
-    again = oracle.noise_frame(np.zeros(n, np.float32), 3.0, 0, 1, 0, 99)
+    again = oracle.noise_frame(np.zeros(n, np.float32), 3.0, 0, 1, 0, 99, frame_px=256)
     assert np.array_equal(fr, again)
-    other = oracle.noise_frame(np.zeros(n, np.float32), 3.0, 0, 2, 0, 99)
+    other = oracle.noise_frame(np.zeros(n, np.float32), 3.0, 0, 2, 0, 99, frame_px=256)
     assert not np.array_equal(fr, other)
+    # the two halves of every frame (the pair partners) are uncorrelated
+    f2 = fr.reshape(-1, 2, 128).astype(np.float64)
+    assert abs(np.corrcoef(f2[:, 0].ravel(), f2[:, 1].ravel())[0, 1]) < 4.0 / math.sqrt(n / 2)
 
 
 def test_philox_counter_and_key_dependence():
