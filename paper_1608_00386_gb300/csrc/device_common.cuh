@@ -297,13 +297,16 @@ __device__ __forceinline__ float2* fft_tab(float2* a, float2* b, int batch, cons
 
 // ---------------------------------------------------------------------------------------------
 // Detector noise.  Counter-based Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by the
-// seed, counter (pixel, step, WFS, 0); float sampler with a fixed operation order written with
-// round-to-nearest intrinsics (never contracted), so one float intensity maps to one integer:
-//   words 2, 3: one Box-Muller pair (z_c, z_s), formed when read noise is on or lambda >= 16;
+// seed; float sampler with a fixed operation order written with round-to-nearest intrinsics
+// (never contracted), so one float intensity maps to one integer.  Pixels go in pairs (o and
+// o + n_det^2 / 2 of a subaperture frame, counter word 0 = frame index of o):
+//   draw A (counter word 3 = 0): words 0, 1 the two inversion uniforms; words 2, 3 one
+//     Box-Muller pair, the two pixels' read noise rint(sigma z), formed when read noise is on;
+//   draw B (counter word 3 = 2, only when a pixel has lambda >= 16): words 2, 3 one Box-Muller
+//     pair, the photon normals;
 //   lambda < 16: Poisson by inversion, p0 = exp(-lambda), p_{k+1} = p_k fl(lambda fl(1/(k+1))),
-//                smallest k with u <= F_k (k <= 64), u from word 0;
-//   lambda >= 16: max(0, rint(lambda + sqrt(lambda) z_s));
-//   read noise rint(sigma z_c).
+//                smallest k with u <= F_k (k <= 64);
+//   lambda >= 16: max(0, rint(lambda + sqrt(lambda) y)).
 // exp: Cody-Waite reduction by ln 2 (two-part constant) and a degree-7 Taylor polynomial; log:
 // mantissa in [sqrt(1/2), sqrt(2)) and the atanh series to s^9, s = (m - 1) fl(1/(m + 1));
 // cos and sin of 2 pi u: quadrant reduction and Taylor polynomials of sin / cos on [-pi/4, pi/4].
@@ -412,17 +415,11 @@ __device__ __forceinline__ void fill_recip(float* recip, int tid, int nthr) {
     for (int j = tid; j < kRecipEntries; j += nthr) recip[j] = (j > 0) ? __fdiv_rn(1.0f, (float)j) : 0.0f;
 }
 
-__device__ __forceinline__ int noise_sample(float lam, float read_noise, uint32_t c0, uint32_t c1,
-                                            uint32_t c2, unsigned long long seed, const float* recip) {
-    uint32_t w[4] = {c0, c1, c2, 0u};
-    philox4x32_10(w, (uint32_t)seed, (uint32_t)(seed >> 32));
-    float zc = 0.0f, zs = 0.0f;
-    if (read_noise > 0.0f || !(lam < 16.0f)) nz_box_muller2(nz_uniform(w[2]), nz_uniform(w[3]), zc, zs);
-    int n;
+// Photon count of one pixel: Poisson by inversion for lambda < 16 (uniform u; two terms per
+// pass, formed in the same order as one at a time, stopping at the same k), else
+// max(0, rint(lambda + sqrt(lambda) y)) with the standard normal y.
+__device__ __forceinline__ int nz_photons(float lam, float u, float y, const float* recip) {
     if (lam < 16.0f) {
-        // sequential search, two terms per pass: the terms are formed in the same order as one
-        // at a time and the pass stops at the same k
-        const float u = nz_uniform(w[0]);
         float p = nz_exp(-lam), F = p;
         int k = 0;
         while (F < u && k < 64) {
@@ -436,14 +433,37 @@ __device__ __forceinline__ int noise_sample(float lam, float read_noise, uint32_
             F = __fadd_rn(Fa, p);
             k += 2;
         }
-        n = k;
-    } else {
-        const float v = __fmaf_rn(__fsqrt_rn(lam), zs, lam);
-        n = __float2int_rn(v);
-        if (n < 0) n = 0;
+        return k;
     }
-    if (read_noise > 0.0f) n += __float2int_rn(__fmul_rn(read_noise, zc));
-    return n;
+    const int n = __float2int_rn(__fmaf_rn(__fsqrt_rn(lam), y, lam));
+    return n < 0 ? 0 : n;
+}
+
+// Noisy counts of a pixel pair (pixel o and o + n_det^2 / 2 of one subaperture frame; g the
+// frame index of pixel o): draw A = Philox(g, step, sensor, 0) gives the two inversion uniforms
+// (words 0, 1) and, when read noise is on, one Box-Muller pair (words 2, 3) whose outputs are
+// the two pixels' read noise; draw B = Philox(g, step, sensor, 2), formed only when a pixel has
+// lambda >= 16, gives one Box-Muller pair (words 2, 3) for the two photon normals.
+__device__ __forceinline__ void noise_pair(float lam_a, float lam_b, float read_noise, uint32_t g, uint32_t step,
+                                           uint32_t sensor, unsigned long long seed, const float* recip, int& na,
+                                           int& nb) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    uint32_t w[4] = {g, step, sensor, 0u};
+    philox4x32_10(w, k0, k1);
+    float ya = 0.0f, yb = 0.0f;
+    if (!(lam_a < 16.0f) || !(lam_b < 16.0f)) {
+        uint32_t v[4] = {g, step, sensor, 2u};
+        philox4x32_10(v, k0, k1);
+        nz_box_muller2(nz_uniform(v[2]), nz_uniform(v[3]), ya, yb);
+    }
+    na = nz_photons(lam_a, nz_uniform(w[0]), ya, recip);
+    nb = nz_photons(lam_b, nz_uniform(w[1]), yb, recip);
+    if (read_noise > 0.0f) {
+        float za, zb;
+        nz_box_muller2(nz_uniform(w[2]), nz_uniform(w[3]), za, zb);
+        na += __float2int_rn(__fmul_rn(read_noise, za));
+        nb += __float2int_rn(__fmul_rn(read_noise, zb));
+    }
 }
 
 // warp sum

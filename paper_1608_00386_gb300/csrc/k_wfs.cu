@@ -279,22 +279,33 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
         const float c0 = 0.5f * (float)(ND - 1);
         float sv = 0.0f, sx = 0.0f, sy = 0.0f;
         const long long pix0 = (long long)sd.rank * ND * ND;
+        // pixel pairs (o, o + ND^2 / 2) sit in this lane's slots j and j + PIX_PER_LANE / 2
+        constexpr int HALF = PIX_PER_LANE / 2;
     #pragma unroll
-        for (int j = 0; j < PIX_PER_LANE; ++j) {
-            int o = lane + 32 * j;
-            float lam = B[j] * norm;
-            float v = lam;
+        for (int j = 0; j < HALF; ++j) {
+            const int o = lane + 32 * j;
+            const float lam_a = B[j] * norm, lam_b = B[j + HALF] * norm;
+            float va = lam_a, vb = lam_b;
             if (L.ctx.noise) {
-                int n = noise_sample(lam, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
-                                     L.ctx.seed + real, s_recip);
-                v = (float)n;
-                if (L.frame_out) L.frame_out[real * L.frame_stride + w.frame0 + pix0 + o] = n;
+                int na, nb;
+                noise_pair(lam_a, lam_b, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
+                           L.ctx.seed + real, s_recip, na, nb);
+                va = (float)na;
+                vb = (float)nb;
+                if (L.frame_out) {
+                    L.frame_out[real * L.frame_stride + w.frame0 + pix0 + o] = na;
+                    L.frame_out[real * L.frame_stride + w.frame0 + pix0 + o + 32 * HALF] = nb;
+                }
             }
-            if (L.lam_out) L.lam_out[real * L.frame_stride + w.frame0 + pix0 + o] = lam;
-            int my = o / ND, mx = o % ND;
-            sv += v;
-            sx = fmaf((float)mx - c0, v, sx);
-            sy = fmaf((float)my - c0, v, sy);
+            if (L.lam_out) {
+                L.lam_out[real * L.frame_stride + w.frame0 + pix0 + o] = lam_a;
+                L.lam_out[real * L.frame_stride + w.frame0 + pix0 + o + 32 * HALF] = lam_b;
+            }
+            const int my = o / ND, mx = o % ND, my_b = (o + 32 * HALF) / ND;
+            sv += va + vb;
+            sx = fmaf((float)mx - c0, va + vb, sx);
+            sy = fmaf((float)my - c0, va, sy);
+            sy = fmaf((float)my_b - c0, vb, sy);
         }
         sv = warp_sum(sv);
         sx = warp_sum(sx);
@@ -428,22 +439,37 @@ __global__ void __launch_bounds__(kFftThreads) wfs_fft_kernel(WfsLaunch L) {
     const float norm = (bsum > 0.0f) ? w.n_photons * sd.frac / bsum : 0.0f;
     __syncthreads();
 
+    // pixel pairs (o, o + ND^2 / 2): the intensities go through shared memory (the spectrum
+    // buffer, no longer read), the first ND^2 / 2 threads draw both pixels
+    constexpr int HALF = ND * ND / 2;
+    float* s_lam = reinterpret_cast<float*>(X);
+    if (o < ND * ND) s_lam[o] = b * norm;
+    __syncthreads();
     const float c0 = 0.5f * (float)(ND - 1);
     float sv = 0.0f, sx = 0.0f, sy = 0.0f;
     const long long pix0 = (long long)sd.rank * ND * ND;
-    if (o < ND * ND) {
-        float lam = b * norm;
-        float v = lam;
+    if (o < HALF) {
+        const float lam_a = s_lam[o], lam_b = s_lam[o + HALF];
+        float va = lam_a, vb = lam_b;
         if (L.ctx.noise) {
-            int n = noise_sample(lam, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
-                                 L.ctx.seed + real, recip);
-            v = (float)n;
-            if (L.frame_out) L.frame_out[real * L.frame_stride + w.frame0 + pix0 + o] = n;
+            int na, nb;
+            noise_pair(lam_a, lam_b, w.read_noise, (uint32_t)(pix0 + o), (uint32_t)k, (uint32_t)w.wfs_index,
+                       L.ctx.seed + real, recip, na, nb);
+            va = (float)na;
+            vb = (float)nb;
+            if (L.frame_out) {
+                L.frame_out[real * L.frame_stride + w.frame0 + pix0 + o] = na;
+                L.frame_out[real * L.frame_stride + w.frame0 + pix0 + o + HALF] = nb;
+            }
         }
-        if (L.lam_out) L.lam_out[real * L.frame_stride + w.frame0 + pix0 + o] = lam;
-        sv = v;
-        sx = ((float)mx - c0) * v;
-        sy = ((float)my - c0) * v;
+        if (L.lam_out) {
+            L.lam_out[real * L.frame_stride + w.frame0 + pix0 + o] = lam_a;
+            L.lam_out[real * L.frame_stride + w.frame0 + pix0 + o + HALF] = lam_b;
+        }
+        const int my_b = (o + HALF) / ND;
+        sv = va + vb;
+        sx = ((float)mx - c0) * (va + vb);
+        sy = fmaf((float)my_b - c0, vb, ((float)my - c0) * va);
     }
     sv = warp_sum(sv);
     sx = warp_sum(sx);

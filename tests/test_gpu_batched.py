@@ -72,7 +72,9 @@ def test_batched_noise_frames_bit_exact():
         g.set_realization(r)
         lam, frames = g.frames(wfs)
         k = g.step_index - 1
-        ref = oracle.noise_frame(lam.ravel(), cfg["wfs"][wfs]["read_noise"], 0, k, wfs, cfg["seed"] + r)
+        ww = cfg["wfs"][wfs]
+        ref = oracle.noise_frame(lam.ravel(), ww["read_noise"], 0, k, wfs, cfg["seed"] + r,
+                                 frame_px=(ww["n_fft"] // ww["n_bin"]) ** 2)
         assert np.array_equal(frames.ravel(), ref)
 
 

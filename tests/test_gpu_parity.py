@@ -209,7 +209,8 @@ def test_noise_frames_bit_exact_given_lambda(case, wfs):
     lam, fr = g.frames(wfs)
     k = 2
     w = cfg["wfs"][wfs]
-    ref = oracle.noise_frame(lam.ravel(), w["read_noise"], 0, k, wfs, cfg["seed"])
+    ref = oracle.noise_frame(lam.ravel(), w["read_noise"], 0, k, wfs, cfg["seed"],
+                             frame_px=(w["n_fft"] // w["n_bin"]) ** 2)
     assert np.array_equal(fr.ravel(), ref)
     assert fr.min() < 0 or w["read_noise"] == 0 or fr.size < 1000  # read noise reaches negative counts
 

@@ -59,7 +59,7 @@ def test_wide_lgs_noise_bit_exact_given_lambda_and_noisy_loop():
     o.step(2)
     lam, fr = g.frames(0)
     w = cfg["wfs"][0]
-    ref = oracle.noise_frame(lam.ravel(), w["read_noise"], 0, 1, 0, cfg["seed"])
+    ref = oracle.noise_frame(lam.ravel(), w["read_noise"], 0, 1, 0, cfg["seed"], frame_px=(w["n_fft"] // w["n_bin"]) ** 2)
     assert np.array_equal(fr.ravel(), ref)
     _, fo = o.frames(0)
     flips = int(np.sum(fr != fo))
