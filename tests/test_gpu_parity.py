@@ -307,3 +307,36 @@ def test_bounded_wait_expires_and_context_stays_usable():
     h.step(5)
     assert np.array_equal(g.slopes(), h.slopes())
     assert np.array_equal(g.commands(), h.commands())
+
+
+def test_sensor_without_valid_subapertures_and_dark_frames():
+    # (a) a natural star whose 2 x 2 subapertures are all below the illumination threshold
+    # contributes no slopes; the laser star alone drives the loop, as in the oracle
+    from _helpers import mcao_small
+    cfg = mcao_small()
+    cfg["wfs"][1] = dict(cfg["wfs"][1], valid_thr=0.99)
+    screens = inputs.make_screens(cfg)
+    o = oracle.Sim(cfg, screens)
+    assert o.n_valid(1) == 0
+    R = inputs.random_reconstructor(inputs.n_commands(cfg), o.n_slopes, 0.02, 9)
+    o.close()
+    g = mcao.make_sim(cfg, screens, R)
+    o = oracle.Sim(cfg, screens, R)
+    assert g.query(mcao.Q_VALID, 1) == 0 and g.query(mcao.Q_SLOPES) == o.n_slopes
+    g.step(3)
+    o.step(3)
+    assert _rms(g.slopes() - o.slopes()) <= 1e-4
+    # (b) no photons: read noise only, identical frames, centroids of the same integer frames
+    # (zero slopes wherever a frame's total is not positive)
+    cfg2, screens2, R2 = scao_tiny_inputs()
+    cfg2 = dict(cfg2, noise=True)
+    cfg2["wfs"] = [dict(cfg2["wfs"][0], n_photons=0.0)]
+    g2 = mcao.make_sim(cfg2, screens2, R2, keep_frames=True)
+    o2 = oracle.Sim(cfg2, screens2, R2)
+    g2.step(2)
+    o2.step(2)
+    lam_g, fr_g = g2.frames(0)
+    _, fr_o = o2.frames(0)
+    assert not lam_g.any()
+    assert np.array_equal(fr_g, fr_o)
+    assert _rms(g2.slopes() - o2.slopes()) <= 1e-4
