@@ -144,6 +144,8 @@ struct mcao_sim {
     // batched product (n_real > 1): padded R column-major [ld][rows_pad] (float32 or bfloat16
     // codes), bfloat16 slopes, cuBLAS handle and workspace
     float* d_Rrm = nullptr;
+    float* d_multi_st = nullptr;          // batched product, n_real <= kMultiRhs: transposed slopes
+    float* d_multi_part = nullptr;        // and split-K partials
     void* d_Rrm16 = nullptr;
     void* d_S16 = nullptr;
     cublasHandle_t blas = nullptr;
@@ -509,8 +511,22 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         // integrator: C += g R S in place; controller: D = R S, then the filter
         const float alpha = S->use_ctl ? 1.0f : (float)S->cfg.gain, beta = S->use_ctl ? 0.0f : 1.0f;
         float* cout = S->use_ctl ? S->d_dc : S->d_c;
-        cublasStatus_t bs;
-        if (S->d_Rrm) {
+        cublasStatus_t bs = CUBLAS_STATUS_SUCCESS;
+        if (S->d_multi_part) {
+            // up to kMultiRhs realizations: one hand-written pass over R
+            MultiLaunch M{};
+            M.R = S->d_Rrm ? (const void*)S->d_Rrm : S->d_Rrm16;
+            M.bf16 = S->d_Rrm ? 0 : 1;
+            M.rows_pad = S->rows_pad;
+            M.n_cmd = S->n_cmd;
+            M.K = S->ld;
+            M.s_t = S->d_multi_st;
+            M.partial = S->d_multi_part;
+            if ((e = launch_recon_multi(M, S->n_real, pad_stride(S), S->d_slopes_pad, alpha, beta, cout, S->sm_count,
+                                        S->s0)) != cudaSuccess)
+                return e;
+            nl += 2;
+        } else if (S->d_Rrm) {
             bs = cublasSgemm(S->blas, CUBLAS_OP_N, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm,
                              S->rows_pad, S->d_slopes_pad, pad_stride(S), &beta, cout, S->n_cmd);
         } else {
@@ -785,6 +801,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     CKC(cudaEventCreateWithFlags(&S->ev_done, cudaEventDisableTiming));
     CKC(wfs_prepare());
     CKC(recon_prepare());
+    CKC(multi_prepare());
     CKC(dalloc(&S->d_err, 1));
     CKC(cudaMemsetAsync(S->d_err, 0, sizeof(int), S->s0));
     CKC(dalloc(&S->d_work, (size_t)(2 * cfg->n_wfs + 1)));
@@ -1261,7 +1278,7 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
         if (S->d_Rrm16) cudaFree(S->d_Rrm16);
         if (S->d_S16) cudaFree(S->d_S16);
         S->d_Rrm16 = S->d_S16 = nullptr;
-        // column-major [ld][rows_pad] (the layout cuBLAS streams best for a few right-hand sides)
+        // column-major [ld][rows_pad] (streamed column by column by the product kernels)
         if (dtype == MCAO_DTYPE_F32) {
             if (e == cudaSuccess) e = dalloc(&S->d_Rrm, elems);
             if (e == cudaSuccess) e = launch_transpose(tmp, S->rows_pad, S->ld, S->d_Rrm, S->rows_pad, 0, S->s0);
@@ -1269,6 +1286,15 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
             if (e == cudaSuccess) e = cudaMalloc(&S->d_Rrm16, sizeof(uint16_t) * elems);
             if (e == cudaSuccess) e = launch_transpose(tmp, S->rows_pad, S->ld, S->d_Rrm16, S->rows_pad, 1, S->s0);
             if (e == cudaSuccess) e = cudaMalloc(&S->d_S16, sizeof(uint16_t) * (size_t)S->n_real * S->ld);
+        }
+        // up to kMultiRhs realizations: scratch of the hand-written product (cuBLAS above that)
+        dfree(S->d_multi_st);
+        dfree(S->d_multi_part);
+        S->d_multi_st = S->d_multi_part = nullptr;
+        if (S->n_real <= kMultiRhs) {
+            if (e == cudaSuccess) e = dalloc(&S->d_multi_st, (size_t)S->ld * kMultiRhs);
+            if (e == cudaSuccess)
+                e = dalloc(&S->d_multi_part, (size_t)multi_chunks(S->ld) * kMultiRhs * std::max(n_cmd, 1));
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
         cudaFree(tmp);

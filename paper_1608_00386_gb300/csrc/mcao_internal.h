@@ -323,4 +323,20 @@ std::vector<float2> sci_twiddles(int M);
 // second (self-check of the timeout path)
 cudaError_t launch_wait_probe(int* err, cudaStream_t s);
 
+// batched product for up to kMultiRhs realizations sharing R (column-major [K][rows_pad]):
+// one pass over R, split-K partials, fixed-order reduction into out[r][i] = alpha D + beta out
+constexpr int kMultiRhs = 16;
+struct MultiLaunch {
+    const void* R;           // float32 or bfloat16, column-major [K][rows_pad]
+    int bf16;
+    long long rows_pad;      // multiple of 4
+    int n_cmd, K;
+    const float* s_t;        // [K][kMultiRhs] scratch (transposed slopes)
+    float* partial;          // [multi_chunks(K)][kMultiRhs][n_cmd] scratch
+};
+int multi_chunks(int K);
+cudaError_t multi_prepare();   // kernel attributes (outside stream capture)
+cudaError_t launch_recon_multi(const MultiLaunch& L, int n_real, int pad_stride, const float* slopes_pad, float alpha,
+                               float beta, float* out, int sm_count, cudaStream_t s);
+
 }  // namespace mcao
