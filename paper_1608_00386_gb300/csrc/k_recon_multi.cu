@@ -197,7 +197,7 @@ cudaError_t multi_prepare() {
 cudaError_t launch_recon_multi(const MultiLaunch& L, int n_real, int pad_stride, const float* slopes_pad, float alpha,
                                float beta, float* out, int sm_count, cudaStream_t s) {
     if (n_real < 1 || n_real > kMB) return cudaErrorInvalidValue;
-    slopes_t_kernel<<<256, 256, 0, s>>>(slopes_pad, n_real, L.K, pad_stride, const_cast<float*>(L.s_t));
+    slopes_t_kernel<<<256, 256, 0, s>>>(slopes_pad, n_real, L.K, pad_stride, L.s_t);
     const int items = ((L.n_cmd + kMRows - 1) / kMRows) * multi_chunks(L.K);
     int blocks = (items + kMWarps - 1) / kMWarps;
     if (blocks > 2 * sm_count) blocks = 2 * sm_count;   // two resident blocks per SM

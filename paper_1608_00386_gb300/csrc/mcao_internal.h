@@ -331,7 +331,7 @@ struct MultiLaunch {
     int bf16;
     long long rows_pad;      // multiple of 4
     int n_cmd, K;
-    const float* s_t;        // [K][kMultiRhs] scratch (transposed slopes)
+    float* s_t;              // [K][kMultiRhs] scratch (transposed slopes)
     float* partial;          // [multi_chunks(K)][kMultiRhs][n_cmd] scratch
 };
 int multi_chunks(int K);
