@@ -24,15 +24,16 @@ def fit_misregistration(sim, D_meas, dm: int, p0=(0.0, 0.0, 0.0, 1.0), steps=Non
     import torch
     pitch = float(sim.cfg["dms"][dm]["pitch"])
     h = np.asarray(steps if steps is not None else (0.01 * pitch, 0.01 * pitch, 1e-3, 1e-3), dtype=np.float64)
+    dev = D_meas.device   # the device the model matrices live on
     if cmd_cols is None:
         # the DM's own block of the command vector: a contiguous column range (a view, no copy)
         n_valid = [int(np.count_nonzero(d["valid"])) for d in sim.cfg["dms"]]
         cols = slice(sum(n_valid[:dm]), sum(n_valid[:dm + 1]))
         n_cols = n_valid[dm]
     else:
-        cols = torch.as_tensor(np.asarray(cmd_cols), device="cuda", dtype=torch.long)
+        cols = torch.as_tensor(np.asarray(cmd_cols), device=dev, dtype=torch.long)
         n_cols = cols.numel()
-    D_meas = D_meas.to(device="cuda", dtype=torch.float32)
+    D_meas = D_meas.to(dtype=torch.float32)
     if D_meas.shape[1] != n_cols:
         D_meas = D_meas[:, cols]
     nrm = float(torch.linalg.vector_norm(D_meas))

@@ -4,6 +4,7 @@ call; the product path does not reach the oracle."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1608_00386_gb300 import build, inputs, mcao
@@ -85,3 +86,44 @@ def test_generate_screen_rejects_before_any_device_call(n, pixel, r0, L0, null_o
     out = None if null_out else C.c_void_p(16)
     st = mcao.lib().mcao_generate_screen(n, pixel, r0, L0, 1, out, None, err, 128)
     assert st == status and err.value
+
+
+def test_misregistration_fit_host_logic_on_a_linear_model():
+    # the Gauss-Newton loop against a fake simulation whose matrix is linear in the parameters
+    # (D(p) = D0 + sum_k (p_k - n_k) A_k, n the nominal parameters): one step lands on the truth,
+    # only the DM's own columns are used, and the DM is left at the fitted parameters
+    torch = pytest.importorskip("torch")
+    from paper_1608_00386_gb300 import calibration
+    rng = np.random.default_rng(0)
+    n_slopes, cols = 40, (3, 9)          # DM 1 owns columns 3..8 of 12
+    D0 = torch.from_numpy(rng.normal(size=(n_slopes, 12))).float()
+    A = [torch.from_numpy(rng.normal(size=(n_slopes, 12))).float() for _ in range(4)]
+    nominal = np.array([0.0, 0.0, 0.0, 1.0])
+
+    class FakeSim:
+        cfg = {"dms": [{"pitch": 1.0, "valid": np.ones(3, np.uint8)}, {"pitch": 0.5, "valid": np.ones(6, np.uint8)},
+                       {"pitch": 2.0, "valid": np.ones(3, np.uint8)}]}
+
+        def __init__(self):
+            self.p = nominal.copy()
+
+        def set_misregistration(self, dm, *p):
+            assert dm == 1
+            self.p = np.array(p)
+
+        def interaction_matrix(self):
+            D = D0.clone()
+            for k in range(4):
+                D += float(self.p[k] - nominal[k]) * A[k]
+            return D
+
+    truth = np.array([0.2, -0.1, 0.01, 1.02])
+    sim = FakeSim()
+    sim.set_misregistration(1, *truth)
+    D_meas = sim.interaction_matrix()
+    D_meas[:, :cols[0]] += 5.0            # other DMs' columns must not matter
+    sim.set_misregistration(1, *nominal)
+    p, hist = calibration.fit_misregistration(sim, D_meas, 1, iters=4)
+    assert np.allclose(p, truth, atol=1e-4)
+    assert hist[-1] < 1e-5 < hist[0]
+    assert np.allclose(sim.p, p)
