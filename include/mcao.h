@@ -111,7 +111,8 @@ typedef struct {
                                  its own screens, commands, noise key seed + r, slopes and
                                  Strehl / PSF accumulators; geometry and the reconstructor are
                                  shared.  With n_real > 1 one step forms the product for all
-                                 realizations at once as a matrix product R S (cuBLAS) */
+                                 realizations at once as a matrix product R S over one pass
+                                 of R (our kernel up to 16 realizations, cuBLAS above) */
 } mcao_config;
 
 /* A periodic n x n phase screen with square samples of pixel_m metres, at altitude alt_m,
