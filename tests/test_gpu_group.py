@@ -24,6 +24,9 @@ def _lib():
 def _make():
     cfg0, screens0, R0 = scao_tiny_inputs()
     sims = [mcao.make_sim(dict(cfg0, noise=True), screens0, R0)]
+    # a batched member: two realizations with a bfloat16 reconstructor
+    scr2 = [screens0, inputs.make_screens(cfg0, realization=1)]
+    sims.append(mcao.make_sim(dict(cfg0, noise=True), scr2, R0, r_dtype=mcao.DTYPE_BF16, n_real=2))
     for k, cfg in enumerate((dict(mcao_small(), noise=True), wide_lgs())):
         screens = inputs.make_screens(cfg)
         n_cmd = inputs.n_commands(cfg)
@@ -44,10 +47,13 @@ def test_group_step_is_bit_identical_to_single_steps():
         s.step(7)
     for x, y in zip(a, b):
         assert x.step_index == y.step_index == 7
-        assert np.array_equal(x.slopes(), y.slopes())
-        assert np.array_equal(x.commands(), y.commands())
-        q1, q2 = x.psf(0, with_image=False), y.psf(0, with_image=False)
-        assert q1[1:] == q2[1:]
+        for r in range(x.query(mcao.Q_REALIZATIONS)):
+            x.set_realization(r)
+            y.set_realization(r)
+            assert np.array_equal(x.slopes(), y.slopes())
+            assert np.array_equal(x.commands(), y.commands())
+            q1, q2 = x.psf(0, with_image=False), y.psf(0, with_image=False)
+            assert q1[1:] == q2[1:]
 
 
 def test_group_step_argument_checks():
