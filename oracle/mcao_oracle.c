@@ -31,6 +31,15 @@
  *       |sum A e^{i phi}|^2 / (sum A)^2 and the long-exposure PSF |FFT(pad(A e^{i phi}))|^2
  *       accumulated in double                                           ("The Point Spread
  *       Functions (PSFs)")
+ * Beyond the per-step path, with the same conventions:
+ *   - second-order controller, Marechal Strehl exp(-sigma^2), sodium-layer updates ("The
+ *     closed loop", "The Point Spread Functions (PSFs)");
+ *   - von Karman phase-screen coefficients and amplitudes of the FFT method ("The atmospheric
+ *     layers generation"; the inverse DFT is numpy's, in oracle/__init__.py);
+ *   - DM misregistration: the surface of a translated, rotated and magnified DM by the direct
+ *     sum over actuators ("Conclusions": rotation of the DM and its modal basis);
+ *   - the interaction matrix as a derivative is central differences of this file's noise-free
+ *     measurement (oracle/__init__.py: jacobian_fd, subap_jacobian_fd).
  *
  * Readings of the points the paper leaves open (coordinates, units, centring ramp, elongation
  * geometry, noise sampler) follow one fixed list; each function below states the reading it
@@ -40,8 +49,11 @@
  * Parity status per function: every stage is pinned by closed-form tests (Dirichlet spot,
  * Parseval, exact roll under an integer tilt, affine exactness of bilinear sampling, Gaussian
  * poke, periodised-Gaussian elongation kernel, numpy cross-checks of FFT, matmul and the DM
- * sum, Strehl of a flat wavefront, Marechal regime, integrator recursion).  The one exception
- * is Philox4x32-10, pinned against an independent implementation (cuRAND's) only on a GPU.
+ * sum, Strehl of a flat wavefront, Marechal regime, integrator recursion, controller error
+ * recursion, von Karman structure function and its Kolmogorov limit, screen and noise moments,
+ * piston invariance and step halving of the derivatives, rigid-body identities of the moved
+ * DM).  The one exception is Philox4x32-10, pinned against an independent implementation
+ * (cuRAND's) only on a GPU.
  */
 #include <math.h>
 #include <stdint.h>
