@@ -757,3 +757,19 @@ def test_misregistration_moves_the_measurement():
     with pytest.raises(ValueError):
         o.set_misregistration(0, 0.0, 0.0, 0.0, 0.0)
     o.close()
+
+
+def test_workload_sizes():
+    # the two configurations' sizes: 208 valid subapertures (416 slopes) and a 17 x 17 DM on the
+    # 8 m case; 4632 valid subapertures per laser star, 55 608 slopes and 8051 commands on the
+    # 39 m case (zero screens: only the geometry is exercised)
+    cfg = inputs.scao_tiny()
+    o = oracle.Sim(cfg, [np.zeros((l["n"], l["n"]), np.float32) for l in cfg["layers"]])
+    assert (o.n_valid(0), o.n_slopes) == (208, 416)
+    assert cfg["dms"][0]["nx"] == 17 and o.n_cmd == inputs.n_commands(cfg)
+    o.close()
+    big = inputs.eelt_mcao(screen_n=64)
+    o = oracle.Sim(big, [np.zeros((l["n"], l["n"]), np.float32) for l in big["layers"]])
+    assert [o.n_valid(w) for w in range(6)] == [4632] * 6
+    assert o.n_slopes == 55608 and o.n_cmd == 8051 == inputs.n_commands(big)
+    o.close()
