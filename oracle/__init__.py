@@ -199,6 +199,13 @@ def bilinear_periodic(s: np.ndarray, fx: float, fy: float) -> float:
     return lib().orc_bilinear_periodic(_ptr(s, C.c_double), s.shape[0], fx, fy)
 
 
+def bilinear_clamped(s: np.ndarray, fx: float, fy: float) -> float:
+    """Bilinear sample of a bounded n x n grid (index clamped into [0, n-1]), the rule used for
+    DM surfaces; s is [y][x]."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    return lib().orc_bilinear_clamped(_ptr(s, C.c_double), s.shape[0], fx, fy)
+
+
 def if_sigma(pitch: float, coupling: float) -> float:
     return lib().orc_if_sigma(pitch, coupling)
 

@@ -174,6 +174,125 @@ def test_bilinear_affine_exact_and_periodic():
     assert oracle.bilinear_periodic(r, -1.0, -2.0) == r[n - 2, n - 1]
 
 
+def test_bilinear_clamped_affine_edges_and_library():
+    """The DM sampling rule: exact on an affine grid at fractional indices (unequal x and y
+    coefficients, so a transposed index fails), the edge value beyond both edges, the last cell
+    capped at n - 2, and equal everywhere to scipy's order-1 map_coordinates with nearest-edge
+    extension, an independent implementation of clamped bilinear interpolation."""
+    from scipy import ndimage
+    n = 23
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    s = 0.3 + 1.7 * x - 0.9 * y
+    rng = np.random.default_rng(12)
+    for fx, fy in rng.uniform(0.0, n - 1.0, (60, 2)):
+        assert oracle.bilinear_clamped(s, fx, fy) == pytest.approx(0.3 + 1.7 * fx - 0.9 * fy, abs=1e-12)
+    r = rng.standard_normal((n, n))
+    pts = [tuple(p) for p in rng.uniform(-3.0, n + 2.0, (200, 2))]
+    pts += [(0.0, 0.0), (n - 1.0, n - 1.0), (n - 1.0, 4.5), (4.5, n - 1.0), (n - 1.5, n - 1.25),
+            (-0.5, 6.3), (n - 0.2, 6.3), (6.3, -7.0), (6.3, n + 9.0), (-2.0, n + 2.0), (9.0, 11.0)]
+    for fx, fy in pts:
+        ref = ndimage.map_coordinates(r, [[fy], [fx]], order=1, mode="nearest")[0]
+        assert oracle.bilinear_clamped(r, fx, fy) == pytest.approx(ref, abs=1e-13), (fx, fy)
+    assert oracle.bilinear_clamped(r, -4.2, 7.0) == r[7, 0]
+    assert oracle.bilinear_clamped(r, n + 3.5, 7.0) == r[7, n - 1]
+    assert oracle.bilinear_clamped(r, 5.0, -1.0) == r[0, 5]
+    assert oracle.bilinear_clamped(r, 5.0, n + 1.0) == r[n - 1, 5]
+    assert oracle.bilinear_clamped(r, n - 1.0, n - 1.0) == r[n - 1, n - 1]
+    assert oracle.bilinear_clamped(r, n - 1.75, 3.0) == pytest.approx(0.75 * r[3, n - 2] + 0.25 * r[3, n - 1],
+                                                                       abs=1e-14)
+    assert oracle.bilinear_clamped(r, 9.0, 11.0) == r[11, 9]
+    # the right edge stays in the last cell (columns n-2, n-1): a sample outside it, here the
+    # first sample of the next row, must not enter the sum even with a zero weight
+    r2 = r.copy()
+    r2[5, 0] = np.inf
+    assert oracle.bilinear_clamped(r2, n - 1.0, 4.0) == r2[4, n - 1]
+    assert oracle.bilinear_clamped(r2, n + 2.0, 4.0) == r2[4, n - 1]
+
+
+def _poked_altitude_dm_case(frac_x, frac_y, surf_n):
+    """One laser star at 90 km and one DM at 5 km whose surface pitch is the cone-compressed
+    pupil pitch; the star's direction moves the footprint by (3 + frac_x, -2 + frac_y) surface
+    samples.  Actuator (row 3, column 7) of an 11 x 11 grid is poked to 1.3 rad."""
+    h, H, D = 5000.0, 90e3, 4.0
+    N = 4 * 8
+    dx = D / N
+    f = 1.0 - h / H
+    sdx = dx * f
+    theta = ((3.0 + frac_x) * sdx / h, (-2.0 + frac_y) * sdx / h)
+    cfg = _small_cfg(alt=0.0, kind="lgs", theta=theta)
+    nx, pitch, coup = 11, 0.5, 0.3
+    cfg["dms"] = [{"alt": h, "pitch": pitch, "coupling": coup, "nx": nx, "ny": nx,
+                   "valid": np.ones((nx, nx), np.uint8), "surf_n": surf_n, "surf_dx": sdx}]
+    sim = oracle.Sim(cfg, [np.zeros((256, 256), np.float32)])
+    c = np.zeros(sim.n_cmd)
+    c[3 * nx + 7] = 1.3
+    sim.set_commands(c)
+    X = (np.arange(N) - 0.5 * (N - 1)) * dx
+    u = X[None, :] * f + h * theta[0] + 0.0 * X[:, None]
+    v = X[:, None] * f + h * theta[1] + 0.0 * X[None, :]
+    return sim, u, v, sdx, (nx, pitch, coup)
+
+
+def test_dm_at_altitude_on_grid_is_gaussian_closed_form():
+    """Every pupil sample of the laser star projects onto a surface sample of the 5 km DM
+    (whole-sample offset), so the residual phase must be minus the Gaussian poke evaluated at
+    the cone-beam point x (1 - h/H) + h theta: a closed form through the projection and the
+    clamped sampler with no interpolation."""
+    sim, u, v, _, (nx, pitch, coup) = _poked_altitude_dm_case(0.0, 0.0, 48)
+    ph = sim.wfs_phase(0)
+    sig = pitch / math.sqrt(2.0 * math.log(1.0 / coup))
+    xa, yb = (7 - 0.5 * (nx - 1)) * pitch, (3 - 0.5 * (nx - 1)) * pitch
+    ref = -1.3 * np.exp(-((u - xa) ** 2 + (v - yb) ** 2) / (2.0 * sig * sig))
+    assert np.max(np.abs(ph - ref)) < 1e-12
+    assert ph.min() < -0.5
+
+
+def test_dm_at_altitude_fractional_and_off_grid():
+    """A fractional footprint offset, with part of the footprint beyond the surface grid on two
+    sides: the residual phase equals minus scipy's clamped bilinear interpolation of the surface
+    at the projected indices u / dx + (n - 1) / 2."""
+    from scipy import ndimage
+    surf_n = 30
+    sim, u, v, sdx, _ = _poked_altitude_dm_case(0.37, -0.21, surf_n)
+    ph = sim.wfs_phase(0)
+    S = sim.dm_surface(0)
+    fx = u / sdx + 0.5 * (surf_n - 1)
+    fy = v / sdx + 0.5 * (surf_n - 1)
+    assert fx.max() > surf_n - 1 and fy.min() < 0.0          # the footprint leaves the grid
+    ref = -ndimage.map_coordinates(S, [fy.ravel(), fx.ravel()], order=1, mode="nearest").reshape(ph.shape)
+    assert np.max(np.abs(ph - ref)) < 1e-12
+    assert np.max(np.abs(ph)) > 0.1
+
+
+def test_flux_is_photons_times_illuminated_fraction():
+    """Noise-free detector frames sum to n_photons times the subaperture's illuminated fraction
+    (flux reading), the fraction counted here by brute force over the annular pupil samples.
+    Covers partially illuminated subapertures, an elongated laser spot and a natural star."""
+    D, obs, nsub, npx = 4.0, 0.3, 8, 8
+    cfg = _small_cfg(alt=0.0, kind="lgs")
+    cfg["obstruction"] = obs
+    cfg["wfs"] = [inputs._wfs("lgs", (6 * inputs.ARCSEC, 0.0), nsub, npx, 16, 2, 589e-9, 750.0, height=90e3,
+                              na_fwhm=10e3, launch=(1.1, -0.4)),
+                  inputs._wfs("ngs", (0.0, 3 * inputs.ARCSEC), nsub, npx, 16, 1, 500e-9, 320.0)]
+    scr = inputs.phase_screen(256, 0.125, 0.2, 25.0, 5)
+    sim = oracle.Sim(cfg, [scr])
+    sim.measure()
+    n = nsub * npx
+    partial = 0
+    for w, ww in enumerate(cfg["wfs"]):
+        lam, _ = sim.frames(w)
+        for q, idx in enumerate(sim.valid(w)):
+            sy, sx = divmod(int(idx), nsub)
+            yy = (sy * npx + np.arange(npx)[:, None] - 0.5 * (n - 1)) * (D / n)
+            xx = (sx * npx + np.arange(npx)[None, :] - 0.5 * (n - 1)) * (D / n)
+            r2 = xx * xx + yy * yy
+            frac = np.sum((r2 <= (D / 2) ** 2) & (r2 >= (obs * D / 2) ** 2)) / float(npx * npx)
+            partial += frac < 1.0
+            expect = ww["n_photons"] * frac
+            assert abs(float(lam[q].sum(dtype=np.float64)) - expect) <= 1e-6 * expect, (w, q)
+    assert partial >= 8
+
+
 def test_valid_subaps_brute_force():
     for D, obs, ns, npx, expect in [(8.0, 0.0, 16, 8, None), (39.0, 0.28, 80, 8, None), (39.0, 0.28, 2, 32, 4)]:
         A = oracle.pupil(D, obs, ns * npx)
