@@ -111,8 +111,9 @@ typedef struct {
                                  its own screens, commands, noise key seed + r, slopes and
                                  Strehl / PSF accumulators; geometry and the reconstructor are
                                  shared.  With n_real > 1 one step forms the product for all
-                                 realizations at once as a matrix product R S over one pass
-                                 of R (our kernel up to 16 realizations, cuBLAS above) */
+                                 realizations at once as a matrix product R S: a bfloat16 R on
+                                 the tensor cores (64 realizations per pass over R), a float32
+                                 R on the CUDA cores (16 per pass); FP8 R needs n_real = 1 */
 } mcao_config;
 
 /* A periodic n x n phase screen with square samples of pixel_m metres, at altitude alt_m,
@@ -266,14 +267,15 @@ mcao_status mcao_set_state(mcao_sim* sim, const void* buf, size_t n);
  * stray cudaMalloc would fragment or oversubscribe that pool.  It needs no mcao_sim handle and
  * calls no cudaMalloc, cudaFree or allocating library routine.
  *   R      device pointer, row-major [n_cmd][ld] float32, 16-byte aligned; ld >= n_slopes and
- *          ld a multiple of 4; columns n_slopes..ld-1 are read and multiplied by zero, so they
- *          must hold finite values.
+ *          ld a multiple of 4; columns n_slopes..ld-1 are never read (they may hold anything).
  *   s      device pointer, [n_slopes] float32.     c  device pointer, [n_cmd] float32, updated.
  *   err    optional host buffer of err_len bytes that receives a message on failure.
  * Split-K partial sums live in one fixed device array of 524288 floats (2 MiB) inside the
  * library, created on every device that loads the library and kept until the process exits;
- * n_cmd times ceil(n_slopes / 4096) must not exceed that size (else MCAO_E_SHAPE, nothing is
- * launched).  Each partial sum is written before it is read, so nothing needs clearing between
+ * n_cmd times ceil(n_slopes / 4096) must not exceed that size, and ceil(n_slopes / 4096) must
+ * not exceed 65535 (else MCAO_E_SHAPE, nothing is launched).  A CUDA error already pending
+ * when the call is made (left by the caller's earlier work) is returned as MCAO_E_CUDA with
+ * that error's text, before anything is launched.  Each partial sum is written before it is read, so nothing needs clearing between
  * calls.  The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  * under a lock); make that first call before any stream capture.  All calls share the array:
  * calls whose kernels overlap on the GPU (different streams, or concurrent host threads on
@@ -407,6 +409,19 @@ mcao_status mcao_interaction_matrix(mcao_sim* sim, float* D, size_t ld);
  * every output NULL), MCAO_E_STATE, MCAO_E_UNSUPPORTED, MCAO_E_OOM, MCAO_E_CUDA. */
 mcao_status mcao_slopes_vjp(mcao_sim* sim, const float* g_slopes, int n_vec, float* g_commands, float* g_phase,
                             float* g_layers);
+
+/* Reconstructor product of a batch of slope vectors with the loaded control matrix ("The closed
+ * loop": slopes times the control matrix), by the kernels of the batched step: out[r] = R s_r for
+ * r < n_rhs, with no integrator and no change to the simulation's commands.  A bfloat16 matrix is
+ * multiplied on the tensor cores with float32 slopes (each split exactly into three bfloat16
+ * terms) and float32 accumulation; a float32 matrix on the CUDA cores.
+ *   slopes device pointer, row-major [n_rhs][n_slopes] float32 (the layout of mcao_get_slopes).
+ *   out    device pointer, row-major [n_rhs][n_commands] float32, overwritten.
+ * Needs a simulation created with n_real > 1 (else MCAO_E_UNSUPPORTED) and 1 <= n_rhs <= n_real.
+ * Synchronous: waits for the device before and after; reuses the step's padded-slope scratch,
+ * which the next step rewrites.  Errors: MCAO_E_INVALID_ARG, MCAO_E_STATE (no reconstructor),
+ * MCAO_E_SHAPE, MCAO_E_UNSUPPORTED, MCAO_E_TIMEOUT, MCAO_E_CUDA. */
+mcao_status mcao_reconstruct_batch(mcao_sim* sim, const float* slopes, int n_rhs, float* out);
 
 /* Stages timed by the profiler. */
 enum {

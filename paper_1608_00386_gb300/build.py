@@ -2,8 +2,8 @@
 
 Every translation unit under csrc/ is compiled by nvcc in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and linked into
-``paper_1608_00386_gb300/_build/libmcao.so`` (linked against cuBLAS, used for the batched
-realizations' matrix product).  Nothing is installed outside the repository.
+``paper_1608_00386_gb300/_build/libmcao.so`` (CUDA runtime only: every kernel is the library's
+own).  Nothing is installed outside the repository.
 """
 from __future__ import annotations
 
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         results = list(ex.map(compile_one, _sources()))
     objs = [o for o, _ in results]
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lcublas"],
+    r = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -481,28 +481,6 @@ __global__ void recon_reduce_kernel(ReduceLaunch L) {
     }
 }
 
-// bfloat16 copies for the batched product (round to nearest even)
-__global__ void slopes_to_bf16_kernel(const float* __restrict__ s, int n_real, int cols, int ld_in, uint32_t* out,
-                                      int ld_out) {
-    const long long pairs_per_row = ld_out / 2;
-    const long long total = (long long)n_real * pairs_per_row;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long r = i / pairs_per_row;
-        const int c = (int)(i - r * pairs_per_row) * 2;
-        const float x0 = c < cols ? s[r * ld_in + c] : 0.0f, x1 = c + 1 < cols ? s[r * ld_in + c + 1] : 0.0f;
-        out[i] = f32x2_to_bf16x2(x0, x1);
-    }
-}
-
-__global__ void rows_to_bf16_kernel(const float2* __restrict__ src, long long n_pairs, uint32_t* out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_pairs;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float2 v = src[i];
-        out[i] = f32x2_to_bf16x2(v.x, v.y);
-    }
-}
-
 // transpose of a row-major float32 [rows][cols] into [cols][ld_out] (float32 or bfloat16),
 // 32 x 32 tiles through shared memory
 template <bool BF16>
@@ -535,20 +513,6 @@ cudaError_t launch_transpose(const float* src, int rows, int cols, void* out, in
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((ld_out + 31) / 32)), block(32, 8);
     if (bf16) transpose_kernel<true><<<grid, block, 0, st>>>(src, rows, cols, out, ld_out);
     else transpose_kernel<false><<<grid, block, 0, st>>>(src, rows, cols, out, ld_out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_slopes_to_bf16(const float* s, int n_real, int cols, int ld_in, void* out, int ld_out,
-                                  cudaStream_t st) {
-    if (n_real <= 0 || ld_out <= 0) return cudaSuccess;
-    slopes_to_bf16_kernel<<<152, 256, 0, st>>>(s, n_real, cols, ld_in, reinterpret_cast<uint32_t*>(out), ld_out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_rows_to_bf16(const float* src, long long n, void* out, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    rows_to_bf16_kernel<<<2048, 256, 0, st>>>(reinterpret_cast<const float2*>(src), n / 2,
-                                              reinterpret_cast<uint32_t*>(out));
     return cudaGetLastError();
 }
 

@@ -35,7 +35,9 @@ __device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
 
 // Block (rb, kc): rows [32 rb, 32 rb + 32) times columns [kc kc_len, ...) of R, row sums to
 // partial[kc][row].  Rows past n_cmd re-read the last row (their sums are not stored), so the
-// caller's R needs no row padding.
+// caller's R needs no row padding.  Only columns below n_slopes are read: the last chunk's
+// ragged tail (n_slopes not a multiple of 4) is loaded element by element, so whatever the
+// caller keeps in the padding columns n_slopes..ld-1 (even NaN) never enters a sum.
 __global__ void __launch_bounds__(256) noalloc_gemv(const float* __restrict__ R, int n_cmd, int n_slopes, int ld,
                                                     const float* __restrict__ s, float* __restrict__ partial,
                                                     int kc_len) {
@@ -45,6 +47,7 @@ __global__ void __launch_bounds__(256) noalloc_gemv(const float* __restrict__ R,
     int ncols = n_slopes - c_begin;
     if (ncols > kc_len) ncols = kc_len;
     const int n4 = (ncols + 3) / 4;
+    const int nfull = ncols / 4;                       // whole 16-byte vectors inside the chunk
     for (int i = threadIdx.x; i < n4; i += blockDim.x) {
         int c = c_begin + 4 * i;
         float4 v;
@@ -65,10 +68,21 @@ __global__ void __launch_bounds__(256) noalloc_gemv(const float* __restrict__ R,
         rp[q] = reinterpret_cast<const float4*>(R) + (size_t)row * ld4 + c_begin / 4;
     }
     float acc[kRowsPerWarp] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int i = lane; i < n4; i += 32) {
+    for (int i = lane; i < nfull; i += 32) {
         float4 sv = s_sh[i];
 #pragma unroll
         for (int q = 0; q < kRowsPerWarp; ++q) acc[q] = dot4(__ldcs(rp[q] + i), sv, acc[q]);
+    }
+    if (nfull < n4 && lane == (nfull & 31)) {          // 1-3 columns left, read one by one
+        const float4 sv = s_sh[nfull];
+        const int rem = ncols - 4 * nfull;
+#pragma unroll
+        for (int q = 0; q < kRowsPerWarp; ++q) {
+            const float* rq = reinterpret_cast<const float*>(rp[q] + nfull);
+            acc[q] = fmaf(rq[0], sv.x, acc[q]);
+            if (rem > 1) acc[q] = fmaf(rq[1], sv.y, acc[q]);
+            if (rem > 2) acc[q] = fmaf(rq[2], sv.z, acc[q]);
+        }
     }
 #pragma unroll
     for (int q = 0; q < kRowsPerWarp; ++q) {
@@ -123,8 +137,16 @@ extern "C" mcao_status mcao_reconstruct_noalloc(const float* R, int n_cmd, int n
         return report(err, err_len, MCAO_E_SHAPE,
                       "n_cmd x column chunks = %d x %d exceeds the %lld-float scratch of the allocation-free update",
                       n_cmd, n_chunks, kScratchFloats);
+    if (n_chunks > 65535)
+        return report(err, err_len, MCAO_E_SHAPE, "%d column chunks exceed the launch's 65535 grid rows", n_chunks);
+    // An error left pending by earlier work of the caller would otherwise be reported as this
+    // call's launch failure: name it as such and launch nothing.
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return report(err, err_len, MCAO_E_CUDA, "a CUDA error was pending before this call: %s",
+                      cudaGetErrorString(e));
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return report(err, err_len, MCAO_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return report(err, err_len, MCAO_E_UNSUPPORTED, "device %d out of range", dev);
     float* scratch = nullptr;

@@ -8,7 +8,6 @@
 //       integrator
 //   s2 (low priority): science field, row FFT (+ Strehl), column FFT (+ PSF accumulation)
 // Every stage is a kernel of this library (k_dm.cu, k_wfs.cu, k_recon.cu, k_science.cu).
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -141,15 +140,13 @@ struct mcao_sim {
     float* d_c_prev = nullptr;            // [n_real][n_cmd]
     float* d_dc_prev = nullptr;           // [n_real][n_cmd]
     float* d_dc = nullptr;                // [n_real][n_cmd] batched update (controller on)
-    // batched product (n_real > 1): padded R column-major [ld][rows_pad] (float32 or bfloat16
-    // codes), bfloat16 slopes, cuBLAS handle and workspace
+    // batched product (n_real > 1).  float32 R: column-major [ld][rows_pad] copy streamed by the
+    // CUDA-core product in groups of kMultiRhs realizations; bfloat16 R: the tensor-core product
+    // (its own bfloat16 copy, split slopes and partials)
     float* d_Rrm = nullptr;
-    float* d_multi_st = nullptr;          // batched product, n_real <= kMultiRhs: transposed slopes
+    float* d_multi_st = nullptr;          // float32 batched product: transposed slopes
     float* d_multi_part = nullptr;        // and split-K partials
-    void* d_Rrm16 = nullptr;
-    void* d_S16 = nullptr;
-    cublasHandle_t blas = nullptr;
-    void* d_blas_ws = nullptr;
+    TcProduct* tc = nullptr;
     std::vector<ReconLaunch> slices;      // one per sensor with slopes
     std::vector<std::vector<int>> slice_wfs;  // sensors whose slopes each slice reads
     int n_chunks = 0;
@@ -439,6 +436,37 @@ void prof_end(mcao_sim* S, int slot, cudaStream_t st) {
 }
 
 // Queue one step (captured into the graph).  Returns the first launch error.
+// Product of the first n realizations' padded slopes with the shared R:
+// out[r][i] = alpha sum_j R[i][j] s_r[j] + beta out[r][i], on s0.  bfloat16 R runs on the tensor
+// cores (64 realizations per pass over R), float32 R on the CUDA-core kernel (kMultiRhs per pass).
+cudaError_t enqueue_batched_product(mcao_sim* S, int n, float alpha, float beta, float* out, int* nl) {
+    cudaError_t e = cudaSuccess;
+    if (S->tc) {
+        int n_tc = 0;
+        if ((e = tc_launch(S->tc, S->d_slopes_pad, pad_stride(S), n, alpha, beta, out, S->d_err, S->s0, &n_tc)) !=
+            cudaSuccess)
+            return e;
+        *nl += n_tc;
+        return cudaSuccess;
+    }
+    MultiLaunch M{};
+    M.R = S->d_Rrm;
+    M.bf16 = 0;
+    M.rows_pad = S->rows_pad;
+    M.n_cmd = S->n_cmd;
+    M.K = S->ld;
+    M.s_t = S->d_multi_st;
+    M.partial = S->d_multi_part;
+    for (int r0 = 0; r0 < n; r0 += kMultiRhs) {
+        const int nb = std::min(kMultiRhs, n - r0);
+        if ((e = launch_recon_multi(M, nb, pad_stride(S), S->d_slopes_pad + (size_t)r0 * pad_stride(S), alpha, beta,
+                                    out + (size_t)r0 * S->n_cmd, S->sm_count, S->s0)) != cudaSuccess)
+            return e;
+        *nl += 3;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t enqueue_step(mcao_sim* S, int* launches) {
     cudaError_t e;
     int nl = 0;
@@ -507,38 +535,10 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         if ((e = cudaEventRecord(ev_s1b, S->s1)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(S->s0, ev_s1b, 0)) != cudaSuccess) return e;
         slot = prof_begin(S, ST_RECON, S->s0);
-        if (cublasSetStream(S->blas, S->s0) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
         // integrator: C += g R S in place; controller: D = R S, then the filter
         const float alpha = S->use_ctl ? 1.0f : (float)S->cfg.gain, beta = S->use_ctl ? 0.0f : 1.0f;
-        float* cout = S->use_ctl ? S->d_dc : S->d_c;
-        cublasStatus_t bs = CUBLAS_STATUS_SUCCESS;
-        if (S->d_multi_part) {
-            // up to kMultiRhs realizations: one hand-written pass over R
-            MultiLaunch M{};
-            M.R = S->d_Rrm ? (const void*)S->d_Rrm : S->d_Rrm16;
-            M.bf16 = S->d_Rrm ? 0 : 1;
-            M.rows_pad = S->rows_pad;
-            M.n_cmd = S->n_cmd;
-            M.K = S->ld;
-            M.s_t = S->d_multi_st;
-            M.partial = S->d_multi_part;
-            if ((e = launch_recon_multi(M, S->n_real, pad_stride(S), S->d_slopes_pad, alpha, beta, cout, S->sm_count,
-                                        S->s0)) != cudaSuccess)
-                return e;
-            nl += 2;
-        } else if (S->d_Rrm) {
-            bs = cublasSgemm(S->blas, CUBLAS_OP_N, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm,
-                             S->rows_pad, S->d_slopes_pad, pad_stride(S), &beta, cout, S->n_cmd);
-        } else {
-            if ((e = launch_slopes_to_bf16(S->d_slopes_pad, S->n_real, S->ld, pad_stride(S), S->d_S16, S->ld, S->s0)) !=
-                cudaSuccess)
-                return e;
-            ++nl;
-            bs = cublasGemmEx(S->blas, CUBLAS_OP_N, CUBLAS_OP_N, S->n_cmd, S->n_real, S->ld, &alpha, S->d_Rrm16,
-                              CUDA_R_16BF, S->rows_pad, S->d_S16, CUDA_R_16BF, S->ld, &beta, cout, CUDA_R_32F,
-                              S->n_cmd, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-        }
-        if (bs != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+        if ((e = enqueue_batched_product(S, S->n_real, alpha, beta, S->use_ctl ? S->d_dc : S->d_c, &nl)) != cudaSuccess)
+            return e;
         prof_end(S, slot, S->s0);
         ReduceLaunch fin{S->use_ctl ? S->n_cmd : 0, 0, nullptr, S->d_c, 0.0f, S->d_st};
         fin.use_ctl = S->use_ctl;
@@ -677,10 +677,8 @@ void destroy_all(mcao_sim* S) {
     dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err); dfree(S->d_work); dfree(S->d_sr_out);
     dfree(S->d_Rrm);
     dfree(S->d_c_prev); dfree(S->d_dc_prev); dfree(S->d_dc);
-    if (S->d_Rrm16) cudaFree(S->d_Rrm16);
-    if (S->d_S16) cudaFree(S->d_S16);
-    if (S->d_blas_ws) cudaFree(S->d_blas_ws);
-    if (S->blas) cublasDestroy(S->blas);
+    tc_destroy(S->tc);
+    dfree(S->d_multi_st); dfree(S->d_multi_part);
     for (auto e : S->prof_pool) cudaEventDestroy(e);
     for (auto e : S->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : {S->ev_user, S->ev_done})
@@ -963,19 +961,6 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     CKC(dalloc(&S->d_acc, NR * std::max(cfg->n_sci, 1)));
     CKC(dalloc(&S->d_sr_out, 2 * (size_t)std::max(cfg->n_sci, 1)));
     CKC(cudaMemsetAsync(S->d_acc, 0, sizeof(SciAcc) * NR * std::max(cfg->n_sci, 1), S->s0));
-    if (S->n_real > 1) {
-        if (cublasCreate(&S->blas) != CUBLAS_STATUS_SUCCESS) {
-            fail(S, MCAO_E_CUDA, "cublasCreate failed");
-            return bail(MCAO_E_CUDA);
-        }
-        const size_t ws = (size_t)32 << 20;   // fixed workspace: no allocation inside graph capture
-        CKC(cudaMalloc(&S->d_blas_ws, ws));
-        if (cublasSetWorkspace(S->blas, S->d_blas_ws, ws) != CUBLAS_STATUS_SUCCESS ||
-            cublasSetMathMode(S->blas, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS) {
-            fail(S, MCAO_E_CUDA, "cuBLAS setup failed");
-            return bail(MCAO_E_CUDA);
-        }
-    }
     CKC(dalloc(&S->d_st, 1));
     CKC(cudaMemsetAsync(S->d_st, 0, sizeof(StepState), S->s0));
     CKC(cudaStreamSynchronize(S->s0));
@@ -1273,28 +1258,24 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
                                   sizeof(float) * len, n_cmd, kind, S->s0);
     }
     if (S->n_real > 1) {
-        // batched product: R for the matrix product (float32, or bfloat16 codes)
+        // batched product: float32 R column-major for the CUDA-core product, or the tensor-core
+        // product's bfloat16 copy
         dfree(S->d_Rrm);
-        if (S->d_Rrm16) cudaFree(S->d_Rrm16);
-        if (S->d_S16) cudaFree(S->d_S16);
-        S->d_Rrm16 = S->d_S16 = nullptr;
-        // column-major [ld][rows_pad] (streamed column by column by the product kernels)
-        if (dtype == MCAO_DTYPE_F32) {
-            if (e == cudaSuccess) e = dalloc(&S->d_Rrm, elems);
-            if (e == cudaSuccess) e = launch_transpose(tmp, S->rows_pad, S->ld, S->d_Rrm, S->rows_pad, 0, S->s0);
-        } else {
-            if (e == cudaSuccess) e = cudaMalloc(&S->d_Rrm16, sizeof(uint16_t) * elems);
-            if (e == cudaSuccess) e = launch_transpose(tmp, S->rows_pad, S->ld, S->d_Rrm16, S->rows_pad, 1, S->s0);
-            if (e == cudaSuccess) e = cudaMalloc(&S->d_S16, sizeof(uint16_t) * (size_t)S->n_real * S->ld);
-        }
-        // up to kMultiRhs realizations: scratch of the hand-written product (cuBLAS above that)
         dfree(S->d_multi_st);
         dfree(S->d_multi_part);
-        S->d_multi_st = S->d_multi_part = nullptr;
-        if (S->n_real <= kMultiRhs) {
+        S->d_Rrm = S->d_multi_st = S->d_multi_part = nullptr;
+        tc_destroy(S->tc);
+        S->tc = nullptr;
+        if (dtype == MCAO_DTYPE_F32) {
+            // column-major [ld][rows_pad] (streamed column by column), scratch for kMultiRhs
+            // realizations per pass
+            if (e == cudaSuccess) e = dalloc(&S->d_Rrm, elems);
+            if (e == cudaSuccess) e = launch_transpose(tmp, S->rows_pad, S->ld, S->d_Rrm, S->rows_pad, 0, S->s0);
             if (e == cudaSuccess) e = dalloc(&S->d_multi_st, (size_t)S->ld * kMultiRhs);
             if (e == cudaSuccess)
                 e = dalloc(&S->d_multi_part, (size_t)multi_chunks(S->ld) * kMultiRhs * std::max(n_cmd, 1));
+        } else if (e == cudaSuccess && n_cmd > 0) {
+            e = tc_create(tmp, S->rows_pad, S->ld, n_cmd, S->n_real, S->sm_count, S->s0, &S->tc);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
         cudaFree(tmp);
@@ -1622,6 +1603,28 @@ mcao_status mcao_measure(mcao_sim* S, int with_noise) {
     CK(enqueue_sensing(S, with_noise ? S->cfg.noise : 0));
     CK(cudaStreamSynchronize(S->s0));
     return MCAO_OK;
+}
+
+mcao_status mcao_reconstruct_batch(mcao_sim* S, const float* slopes, int n_rhs, float* out) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (!S->recon_loaded) return fail(S, MCAO_E_STATE, "load the reconstructor first");
+    if (S->n_real < 2) return fail(S, MCAO_E_UNSUPPORTED, "the batched product needs n_real > 1");
+    if (!slopes || !out) return fail(S, MCAO_E_INVALID_ARG, "slopes and out must be device pointers");
+    if (n_rhs < 1 || n_rhs > S->n_real) return fail(S, MCAO_E_SHAPE, "n_rhs must be in [1, %d]", S->n_real);
+    CK(cudaSetDevice(S->device));
+    CK(cudaDeviceSynchronize());   // inputs produced on any stream are complete
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    // the user layout [n_rhs][n_slopes] scattered into the padded layout of the product
+    const int ps = pad_stride(S);
+    CK(cudaMemsetAsync(S->d_slopes_pad, 0, sizeof(float) * (size_t)n_rhs * ps, S->s0));
+    for (const WfsHost& W : S->wfs)
+        if (W.n_valid > 0)
+            CK(cudaMemcpy2DAsync(S->d_slopes_pad + W.rcol0, sizeof(float) * ps, slopes + W.slope0,
+                                 sizeof(float) * S->n_slopes, sizeof(float) * 2 * W.n_valid, n_rhs,
+                                 cudaMemcpyDeviceToDevice, S->s0));
+    int nl = 0;
+    CK(enqueue_batched_product(S, n_rhs, 1.0f, 0.0f, out, &nl));
+    return sync_all(S);
 }
 
 // d slope / d phase of every slope on its subaperture's samples (current realization), then the

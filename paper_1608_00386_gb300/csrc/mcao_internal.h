@@ -228,11 +228,6 @@ struct ReduceLaunch {
     int n_real;
 };
 cudaError_t launch_recon_reduce(const ReduceLaunch& L, cudaStream_t s);
-// float32 slopes [n_real][ld_in] -> bfloat16 [n_real][ld_out] (batched bfloat16 product)
-cudaError_t launch_slopes_to_bf16(const float* s, int n_real, int cols, int ld_in, void* out, int ld_out,
-                                  cudaStream_t st);
-// row-major float32 [rows][ld] -> bfloat16 codes [rows][ld] (batched bfloat16 product)
-cudaError_t launch_rows_to_bf16(const float* src, long long n, void* out, cudaStream_t st);
 // row-major float32 [rows][cols] -> [cols][ld_out] (float32, or bfloat16 codes when bf16 != 0);
 // rows >= ld_out are not read, rows in [rows, ld_out) are written as zeros
 cudaError_t launch_transpose(const float* src, int rows, int cols, void* out, int ld_out, int bf16, cudaStream_t st);
@@ -338,5 +333,19 @@ int multi_chunks(int K);
 cudaError_t multi_prepare();   // kernel attributes (outside stream capture)
 cudaError_t launch_recon_multi(const MultiLaunch& L, int n_real, int pad_stride, const float* slopes_pad, float alpha,
                                float beta, float* out, int sm_count, cudaStream_t s);
+
+// batched product for a bfloat16 R on the tensor cores (tcgen05, TMA, TMEM accumulators):
+// out[r][i] = alpha sum_j R[i][j] s_r[j] + beta out[r][i] for every realization r, float32
+// slopes (split exactly into three bfloat16 terms) and float32 accumulation; up to 64
+// realizations per pass over R.  tc_create converts the row-major float32 staging copy
+// [rows_in][ld] (rows_in >= n_cmd) once and sizes the kernel for n_rhs realizations (outside
+// stream capture); tc_launch queues the split, product and reduction kernels of every pass.
+struct TcProduct;
+cudaError_t tc_create(const float* R_rm, int rows_in, int ld, int n_cmd, int n_rhs, int sm_count, cudaStream_t st,
+                      TcProduct** out);
+void tc_destroy(TcProduct* P);
+cudaError_t tc_launch(TcProduct* P, const float* slopes_pad, int pad_stride, int n_real, float alpha, float beta,
+                      float* out, int* err, cudaStream_t st, int* launches);
+long long tc_bytes(const TcProduct* P);   // bytes of its bfloat16 R
 
 }  // namespace mcao

@@ -31,7 +31,7 @@ EXPORTS = [
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
     "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
     "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration", "mcao_step_group",
-    "mcao_read_async", "mcao_check_bounded_wait",
+    "mcao_read_async", "mcao_check_bounded_wait", "mcao_reconstruct_batch",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -126,6 +126,7 @@ def lib():
         "mcao_step_group": [C.POINTER(vp), C.c_int, C.c_int],
         "mcao_read_async": [vp, vp, vp],
         "mcao_check_bounded_wait": [vp],
+        "mcao_reconstruct_batch": [vp, vp, C.c_int, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -306,6 +307,18 @@ class Sim:
         """Move DM dm as a rigid body (shift in m, rotation in rad, magnification)."""
         self._ck(lib().mcao_set_misregistration(self.h, dm, shift_x, shift_y, rotation, magnification))
 
+    def reconstruct_batch(self, S):
+        """R s_r for every row s_r of the CUDA float32 tensor S [n_rhs][n_slopes] with the loaded
+        control matrix, by the batched step's product kernels (mcao_reconstruct_batch); returns a
+        CUDA float32 tensor [n_rhs][n_commands]."""
+        import torch
+        if not (isinstance(S, torch.Tensor) and S.is_cuda and S.dtype == torch.float32 and S.dim() == 2
+                and S.is_contiguous() and S.shape[1] == self.query(Q_SLOPES)):
+            raise McaoError(1, "S must be a contiguous CUDA float32 tensor [n_rhs][n_slopes]")
+        out = torch.empty((S.shape[0], self.query(Q_COMMANDS)), dtype=torch.float32, device=S.device)
+        self._ck(lib().mcao_reconstruct_batch(self.h, S.data_ptr(), S.shape[0], out.data_ptr()))
+        return out
+
     def check_bounded_wait(self) -> int:
         """Status of mcao_check_bounded_wait: 6 (MCAO_E_TIMEOUT) when the device timeouts work."""
         return lib().mcao_check_bounded_wait(self.h)
@@ -425,16 +438,30 @@ class Sim:
 
 
 def reconstruct_noalloc(R, s, c, gain: float, stream=None) -> None:
-    """c <- c + gain R s with the allocation-free entry point; R [n_cmd][ld], s and c are CUDA
-    tensors (float32).  Queued on ``stream`` (torch stream or raw handle; default: the current
-    torch stream)."""
+    """c <- c + gain R s with the allocation-free entry point.  R is a float32 CUDA tensor of n_cmd
+    rows with unit column stride whose first s.numel() columns are used (its row stride is the
+    leading dimension, so a column slice of a padded matrix works); s [n_slopes] and c [n_cmd] are
+    contiguous float32 CUDA tensors, all on the current device.  Queued on ``stream`` (torch stream
+    or raw handle; default: the current torch stream)."""
     import torch
+    dev = torch.cuda.current_device()
+    for name, t in (("R", R), ("s", s), ("c", c)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
+            raise McaoError(1, f"{name} must be a float32 CUDA tensor")
+        if t.device.index != dev:
+            raise McaoError(1, f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+    if R.dim() != 2 or R.stride(1) != 1:
+        raise McaoError(1, "R must be a 2-D tensor with unit column stride")
+    if not (s.is_contiguous() and c.is_contiguous()):
+        raise McaoError(1, "s and c must be contiguous")
+    n_cmd, n_slopes, ld = R.shape[0], s.numel(), R.stride(0)
+    if R.shape[1] < n_slopes or c.numel() != n_cmd:
+        raise McaoError(2, f"R is {tuple(R.shape)}, s has {n_slopes} and c {c.numel()} elements")
     if stream is None:
         stream = torch.cuda.current_stream()
     ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
-    n_cmd, ld = R.shape
     buf = C.create_string_buffer(256)
-    st = lib().mcao_reconstruct_noalloc(R.data_ptr(), n_cmd, s.numel(), ld, s.data_ptr(), c.data_ptr(),
+    st = lib().mcao_reconstruct_noalloc(R.data_ptr(), n_cmd, n_slopes, ld, s.data_ptr(), c.data_ptr(),
                                         float(gain), C.c_void_p(ptr), buf, 256)
     if st != 0:
         raise McaoError(st, buf.value.decode())

@@ -105,8 +105,8 @@ def test_batched_full_size_step():
 
 
 def test_batched_bf16_strehl_within_one_percent():
-    """bfloat16 reconstructor and bfloat16 slopes in the batched product (tensor-core matrix
-    product, float32 accumulation): long-exposure Strehl within 1 % of the float32 batch."""
+    """bfloat16 reconstructor in the batched product (tensor cores, float32 slopes, float32
+    accumulation): long-exposure Strehl within 1 % of the float32 batch."""
     cfg, _, R = scao_tiny_inputs()
     n = 2
     ref, _ = _batch(cfg, R, n)
@@ -147,3 +147,107 @@ def test_realization_index_checked():
         g.set_realization(2)
     with pytest.raises(mcao.McaoError):
         g.set_realization(-1)
+
+
+# ------------------------------------------------------------------------------------------ product
+def _eelt_product_sim(n_real, dtype, seed):
+    """39 m configuration with n_real realizations, DMs and a random R on the device (no
+    atmosphere: the product needs only the reconstructor).  For bfloat16 the float32 entries
+    have their low 16 bits cleared, so R is exactly representable and the stored codes are R."""
+    import torch
+    cfg, _, n_cmd = eelt_inputs(10)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    R = torch.randn((n_cmd, 55608), generator=g, device="cuda", dtype=torch.float32)
+    if dtype == mcao.DTYPE_BF16:
+        R = (R.view(torch.int32) & -65536).view(torch.float32)
+    sim = mcao.Sim(cfg, n_real=n_real)
+    sim.load_dms()
+    sim.load_reconstructor(R, dtype=dtype)
+    return sim, R, g
+
+
+@pytest.mark.parametrize("dtype,n_real,n_rhs", [(mcao.DTYPE_BF16, 2, 1), (mcao.DTYPE_BF16, 16, 16),
+                                                (mcao.DTYPE_BF16, 17, 17), (mcao.DTYPE_BF16, 64, 64),
+                                                (mcao.DTYPE_BF16, 80, 80), (mcao.DTYPE_F32, 17, 17)])
+def test_batched_product_full_size_matches_float64(dtype, n_real, n_rhs):
+    """The batched step's product at the 39 m size (8051 x 55608) against a float64 product:
+    bfloat16 R on the tensor cores with float32 slopes (1, 16, 17 and 64 realizations in one pass
+    over R, 80 in two passes), float32 R on the CUDA cores in groups of 16.  Each element within
+    1e-5 |R_i| |s_r| (float32 accumulation), which also bounds the whole-vector error."""
+    import torch
+    sim, R, g = _eelt_product_sim(n_real, dtype, 100 + n_rhs)
+    S = torch.randn((n_rhs, 55608), generator=g, device="cuda", dtype=torch.float32)
+    for _ in range(2):                                  # a second call reuses every scratch buffer
+        D = sim.reconstruct_batch(S)
+        ref = (S.double() @ R.double().t())             # [n_rhs][n_cmd]
+        bound = 1e-5 * S.double().norm(dim=1)[:, None] * R.double().norm(dim=1)[None, :]
+        err = (D.double() - ref).abs()
+        assert bool((err <= bound).all()), float((err / bound).max())
+        rel = float((D.double() - ref).norm() / ref.norm())
+        assert rel <= 1e-5
+        S = S.flip(0).contiguous()
+
+
+def _bf16_loop_against_oracle(n, steps):
+    # The 8 m loop passes a sensitive transient near step 30 (an edge actuator's command swings
+    # from -200 to -129 rad) where even the single-realization float32 loop differs from the oracle
+    # by 1.2e-5 relative; at 10, 20 and 50 steps every path is within 1.5e-6.  The comparisons
+    # are made away from it.
+    cfg, _, R = scao_tiny_inputs()
+    g, screens = _batch(cfg, R, n, r_dtype=mcao.DTYPE_BF16)
+    orc = [oracle.Sim(dict(cfg, seed=cfg["seed"] + r), screens[r], R, r_dtype=oracle.DTYPE_BF16) for r in range(n)]
+    g.step(steps)
+    for o in orc:
+        o.step(steps)
+    for r in range(n):
+        g.set_realization(r)
+        assert _rms(g.slopes() - orc[r].slopes()) <= 1e-4, r
+        cg, co = g.commands(), orc[r].commands()
+        assert np.linalg.norm(cg - co) / np.linalg.norm(co) <= 1e-5, r
+        _, srg, _ = g.psf()
+        _, sro, _ = orc[r].psf()
+        assert abs(srg - sro) <= 1e-3, r
+
+
+def test_batched_bf16_loop_17_realizations_matches_oracle_bf16():
+    """17 realizations (more than one 16-wide group) with a bfloat16 R, every realization against
+    the oracle's bfloat16 variant (represented values of R, float slopes, double product) run
+    alone on its inputs, at the float32 tolerances."""
+    _bf16_loop_against_oracle(17, 50)
+
+
+def test_batched_bf16_loop_64_realizations_matches_oracle_bf16():
+    """The batched configuration's 64 realizations with a bfloat16 R, every realization against
+    the oracle's bfloat16 variant."""
+    _bf16_loop_against_oracle(64, 12)
+
+
+def test_batched_f32_loop_17_realizations_matches_oracle():
+    """17 realizations with a float32 R (two passes of the CUDA-core product), every realization
+    against the oracle."""
+    cfg, _, R = scao_tiny_inputs()
+    n = 17
+    g, screens = _batch(cfg, R, n)
+    orc = [oracle.Sim(dict(cfg, seed=cfg["seed"] + r), screens[r], R) for r in range(n)]
+    g.step(20)
+    for o in orc:
+        o.step(20)
+    for r in range(n):
+        g.set_realization(r)
+        assert _rms(g.slopes() - orc[r].slopes()) <= 1e-4, r
+        cg, co = g.commands(), orc[r].commands()
+        assert np.linalg.norm(cg - co) / np.linalg.norm(co) <= 1e-5, r
+
+
+def test_reconstruct_batch_checks_its_arguments():
+    import torch
+    cfg, _, R = scao_tiny_inputs()
+    g, _ = _batch(cfg, R, 2)
+    S = torch.zeros((3, 416), device="cuda")
+    with pytest.raises(mcao.McaoError):
+        g.reconstruct_batch(S)                       # more vectors than realizations
+    with pytest.raises(mcao.McaoError):
+        g.reconstruct_batch(torch.zeros((2, 415), device="cuda"))
+    one = mcao.make_sim(cfg, inputs.make_screens(cfg), R)
+    with pytest.raises(mcao.McaoError):
+        one.reconstruct_batch(torch.zeros((1, 416), device="cuda"))
