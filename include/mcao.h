@@ -59,7 +59,9 @@ enum { MCAO_WFS_NGS = 0, MCAO_WFS_LGS = 1 };
 /* Element format of the stored control matrix (mcao_load_reconstructor, mcao_quantize_rows):
  * float32; bfloat16 (round to nearest even); FP8 E4M3 in the OCP 8-bit format (round to nearest
  * even, saturating to +-448) with one float32 scale per row, scale = max|row| / 448 (1 for an
- * all-zero row).  The product always accumulates in float32 against float32 slopes. */
+ * all-zero row, and for a row whose max|row| / 448 is below the smallest normal float 2^-126: its
+ * entries are then stored as zero).  The product always accumulates in float32 against float32
+ * slopes. */
 enum { MCAO_DTYPE_F32 = 0, MCAO_DTYPE_BF16 = 1, MCAO_DTYPE_FP8_E4M3 = 2 };
 
 /* One Shack-Hartmann wavefront sensor.  Its pupil grid has n_sub * n_px samples across D.
@@ -291,7 +293,8 @@ mcao_status mcao_reconstruct_noalloc(const float* R, int n_cmd, int n_slopes, in
  *   dtype  MCAO_DTYPE_BF16 (codes: uint16 per element) or MCAO_DTYPE_FP8_E4M3 (uint8 per element).
  *   codes  device pointer, row-major [rows][cols] codes, 16-byte aligned; cols must be a multiple
  *          of 8 (BF16) or 16 (FP8 E4M3).
- *   scales device pointer [rows] float32: written for FP8 E4M3 (max|row| / 448, 1 for a zero row);
+ *   scales device pointer [rows] float32: written for FP8 E4M3 (max|row| / 448; 1 for a zero row or a
+ *          row whose max|row| / 448 is below 2^-126, whose codes are then zero);
  *          may be NULL for BF16.
  *   stream CUDA stream (cudaStream_t) or NULL for the legacy stream; the call only queues work.
  * err receives a message on failure (err_len bytes, may be NULL).  Errors: MCAO_E_INVALID_ARG
@@ -422,6 +425,31 @@ mcao_status mcao_slopes_vjp(mcao_sim* sim, const float* g_slopes, int n_vec, flo
  * which the next step rewrites.  Errors: MCAO_E_INVALID_ARG, MCAO_E_STATE (no reconstructor),
  * MCAO_E_SHAPE, MCAO_E_UNSUPPORTED, MCAO_E_TIMEOUT, MCAO_E_CUDA. */
 mcao_status mcao_reconstruct_batch(mcao_sim* sim, const float* slopes, int n_rhs, float* out);
+
+/* Control matrix by Tikhonov-regularised least squares, computed in FP64 on the GPU ("Control
+ * Matrix": the reconstructor is a pseudo-inverse of the interaction matrix; MCAO least squares is
+ * ill-posed, hence the regularisation coefficient):
+ *   R = -(D^T D + lambda I)^(-1) D^T,   lambda = alpha tr(D^T D) / n_cmd.
+ * The minus sign follows the library's conventions: D = d s / d c is measured with the DM
+ * subtracted from the wavefront (mcao_interaction_matrix) and the loop applies c <- c + g R s, so
+ * R = -D^+ in the limit alpha -> 0 for a full-rank D.  No mcao_sim handle is needed.
+ *   D       device pointer, row-major [n_slopes][ld_d] float32, ld_d >= n_cmd (read only).
+ *   R       device pointer, row-major [n_cmd][ld_r], ld_r >= n_slopes: float32 (r_fp64 = 0, the
+ *           format mcao_load_reconstructor takes) or float64 (r_fp64 = 1); overwritten.
+ *   stream  CUDA stream (cudaStream_t) or NULL for the legacy stream.
+ *   lambda  optional host pointer: receives lambda.
+ * Every step runs in double precision in the library's kernels on 64 x 64 tiles: the Gram matrix
+ * (tiles of D that hold only zeros are skipped: a subaperture sees only nearby actuators), its
+ * regularisation, a blocked Cholesky factorisation L L^T, L^(-1), M^(-1) = L^-T L^-1 and
+ * -M^(-1) D^T (zero tiles skipped again); float32 output is rounded once, at the store.
+ * Temporaries of 2 (64 ceil(n_cmd / 64))^2 doubles are allocated and freed by the call (1.04 GB
+ * for n_cmd = 8051).  Synchronous.  Errors: MCAO_E_INVALID_ARG (null pointers, alpha < 0 or not
+ * finite, r_fp64 not 0 or 1), MCAO_E_SHAPE, MCAO_E_OOM, MCAO_E_UNSUPPORTED (a Cholesky pivot <= 0:
+ * the regularised matrix is not positive definite in double precision; raise alpha), MCAO_E_CUDA.
+ * err receives a message on failure (err_len bytes, may be NULL). */
+mcao_status mcao_tikhonov_reconstructor(const float* D, int n_slopes, int n_cmd, size_t ld_d, double alpha, void* R,
+                                        size_t ld_r, int r_fp64, void* stream, double* lambda, char* err,
+                                        size_t err_len);
 
 /* Stages timed by the profiler. */
 enum {

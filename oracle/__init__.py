@@ -407,6 +407,20 @@ def screen_structure_function(n: int, pixel: float, r0: float, L0: float, r_px: 
     return float(np.sum(a2 * 2.0 * (1.0 - np.cos(2 * np.pi * kx * r_px / n))))
 
 
+def tikhonov_reconstructor(D: np.ndarray, alpha: float):
+    """Control matrix by Tikhonov-regularised least squares ("Control Matrix": the reconstructor is
+    a regularised pseudo-inverse of the interaction matrix, MCAO least squares being ill-posed):
+    R = -(D^T D + lam I)^-1 D^T with lam = alpha tr(D^T D) / n_cmd (reading: the regularisation
+    weight is relative to the mean eigenvalue of D^T D), in double, the normal equations solved by
+    LAPACK (numpy.linalg.solve).  The minus sign: D is measured with the DM subtracted from the
+    wavefront and the loop adds g R s to the commands.  D is [n_slopes][n_cmd]; returns (R, lam),
+    R [n_cmd][n_slopes]."""
+    D = np.asarray(D, dtype=np.float64)
+    G = D.T @ D
+    lam = alpha * np.trace(G) / G.shape[0]
+    return -np.linalg.solve(G + lam * np.eye(G.shape[0]), D.T), lam
+
+
 def num_threads() -> int:
     return lib().orc_num_threads()
 

@@ -55,6 +55,7 @@
  * DM).  The one exception is Philox4x32-10, pinned against an independent implementation
  * (cuRAND's) only on a GPU.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -689,7 +690,11 @@ void orc_quantize_rows(const float* R, int rows, int cols, int ld, int dtype, vo
             uint8_t* o = (uint8_t*)out + (size_t)r * cols;
             float amax = 0.0f;
             for (int j = 0; j < cols; ++j) amax = fmaxf(amax, fabsf(row[j]));
-            float sc = amax > 0.0f ? amax / 448.0f : 1.0f;
+            /* a scale below the smallest normal float (2^-126; also 0 when the row is zero or
+             * max / 448 underflows) is replaced by 1: the row's entries are then all below
+             * 448 2^-126 and encode to zero, instead of 0 / 0 codes */
+            float sc = amax / 448.0f;
+            if (!(sc >= FLT_MIN)) sc = 1.0f;
             for (int j = 0; j < cols; ++j) o[j] = orc_e4m3_rn_sat(row[j] / sc);
             if (scales) scales[r] = sc;
         }

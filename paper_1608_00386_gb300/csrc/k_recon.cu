@@ -409,7 +409,9 @@ __global__ void recon_tile_kernel(const float* __restrict__ src, long long ld, R
     }
 }
 
-// per-row scale for E4M3: fl(max |R_r.| / 448), 1 for an all-zero row
+// per-row scale for E4M3: fl(max |R_r.| / 448), 1 for an all-zero row and for a row whose
+// fl(max / 448) is below the smallest normal float 2^-126 (there every entry is below 448 2^-126
+// and encodes to zero; a scale that underflowed to 0 would make 0 / 0 codes)
 __global__ void recon_scale_kernel(const float* __restrict__ src, int cols, int ld, float* scale) {
     const long long r = blockIdx.x;
     float m = 0.0f;
@@ -422,7 +424,8 @@ __global__ void recon_scale_kernel(const float* __restrict__ src, int cols, int 
     if (threadIdx.x == 0) {
         float a = 0.0f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmaxf(a, red[w]);
-        scale[r] = a > 0.0f ? __fdiv_rn(a, 448.0f) : 1.0f;
+        const float sc = __fdiv_rn(a, 448.0f);
+        scale[r] = sc >= 1.17549435e-38f ? sc : 1.0f;
     }
 }
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
     "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
     "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration", "mcao_step_group",
-    "mcao_read_async", "mcao_check_bounded_wait", "mcao_reconstruct_batch",
+    "mcao_read_async", "mcao_check_bounded_wait", "mcao_reconstruct_batch", "mcao_tikhonov_reconstructor",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -127,6 +127,8 @@ def lib():
         "mcao_read_async": [vp, vp, vp],
         "mcao_check_bounded_wait": [vp],
         "mcao_reconstruct_batch": [vp, vp, C.c_int, vp],
+        "mcao_tikhonov_reconstructor": [vp, C.c_int, C.c_int, C.c_size_t, C.c_double, vp, C.c_size_t, C.c_int, vp,
+                                        C.POINTER(C.c_double), C.c_char_p, C.c_size_t],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -465,6 +467,29 @@ def reconstruct_noalloc(R, s, c, gain: float, stream=None) -> None:
                                         float(gain), C.c_void_p(ptr), buf, 256)
     if st != 0:
         raise McaoError(st, buf.value.decode())
+
+
+def tikhonov_reconstructor(D, alpha: float, fp64: bool = False, stream=None):
+    """Control matrix R = -(D^T D + lambda I)^-1 D^T, lambda = alpha tr(D^T D) / n_cmd, computed in FP64
+    on the GPU (mcao_tikhonov_reconstructor).  D: CUDA float32 tensor [n_slopes][n_cmd] with unit column
+    stride (its row stride is the leading dimension).  Returns (R, lambda), R a CUDA tensor
+    [n_cmd][n_slopes] of float32 (or float64 with fp64=True)."""
+    import torch
+    if not (isinstance(D, torch.Tensor) and D.is_cuda and D.dtype == torch.float32 and D.dim() == 2
+            and D.stride(1) == 1):
+        raise McaoError(1, "D must be a CUDA float32 tensor [n_slopes][n_cmd] with unit column stride")
+    n_slopes, n_cmd = D.shape
+    R = torch.empty((n_cmd, n_slopes), dtype=torch.float64 if fp64 else torch.float32, device=D.device)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    lam = C.c_double()
+    buf = C.create_string_buffer(256)
+    st = lib().mcao_tikhonov_reconstructor(D.data_ptr(), n_slopes, n_cmd, D.stride(0), float(alpha), R.data_ptr(),
+                                           n_slopes, int(bool(fp64)), C.c_void_p(ptr), C.byref(lam), buf, 256)
+    if st != 0:
+        raise McaoError(st, buf.value.decode())
+    return R, lam.value
 
 
 def make_sim(cfg: dict, screens, R, s_ref=None, keep_frames: bool = False, stream=None,

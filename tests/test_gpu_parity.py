@@ -111,7 +111,8 @@ def test_slopes_one_step_noise_free(case):
     sg, so = g.slopes(), o.slopes()
     assert sg.shape == so.shape
     assert _rms(sg - so) <= 1e-4
-    assert np.max(np.abs(sg - so)) <= 2e-3
+    # every slope, not only the RMS: the largest difference measured at 39 m is 2.0e-6 pixel
+    assert np.max(np.abs(sg - so)) <= 2e-5
     # slopes are not trivially zero
     assert _rms(so) > 0.05
 
@@ -134,6 +135,54 @@ def test_closed_loop_scao_100_steps():
     assert abs(srg - sro) <= 1e-3 and abs(lastg - lasto) <= 1e-3
     assert 0.75 < sro < 0.95          # K-band Strehl of the corrected 8 m loop
     assert np.max(np.abs(pg - po)) <= 1e-4
+
+
+def _flipped_slopes(g, o, cfg):
+    """Flipped detector counts of the last step (GPU vs oracle) and a mask over the slope vector
+    that is False on the x and y slopes of every subaperture with a flipped pixel."""
+    keep = np.ones(g.query(mcao.Q_SLOPES), bool)
+    flips, off = 0, 0
+    for w in range(len(cfg["wfs"])):
+        _, fg = g.frames(w)
+        _, fo = o.frames(w)
+        bad = np.any((fg != fo).reshape(fg.shape[0], -1), axis=1)
+        flips += int(np.sum(fg != fo))
+        nv = fg.shape[0]
+        keep[off:off + nv] &= ~bad
+        keep[off + nv:off + 2 * nv] &= ~bad
+        off += 2 * nv
+    return flips, keep
+
+
+@pytest.mark.parametrize("dtype", [mcao.DTYPE_F32, mcao.DTYPE_BF16, mcao.DTYPE_FP8_E4M3])
+def test_eelt_noisy_20_steps_flip_counts(dtype):
+    """The 39 m workload with photon and read noise for 20 steps, against the oracle in the same
+    reconstructor format.  The GPU's intensities are float and the oracle's double, so counts at
+    a sampler boundary flip (13-124 per step of 7.1 M pixels measured); a flipped count moves its
+    subaperture's slopes by up to a few tenths of a pixel.  Each step: at most 2e-5 of the pixels
+    flip, the slopes of the subapertures without a flip agree to 3e-4 pixel RMS (three times the
+    noise-free bar, which absorbs the spread of earlier flips through the commands), and every
+    slope to 0.5 pixel; after 20 steps the commands agree to 1e-3 relative and the Strehl to
+    1e-3."""
+    cfg, screens, n_cmd = eelt_inputs(10)
+    cfg = dict(cfg, noise=True)
+    R = inputs.random_reconstructor(n_cmd, 55608, 1e-4, 3)
+    g = mcao.make_sim(cfg, screens, R, r_dtype=dtype, keep_frames=True)
+    o = oracle.Sim(cfg, screens, R, r_dtype=dtype)
+    n_px = sum(g.query(mcao.Q_FRAME, w) for w in range(len(cfg["wfs"])))
+    for _ in range(20):
+        g.step(1)
+        o.step(1)
+        flips, keep = _flipped_slopes(g, o, cfg)
+        d = g.slopes() - o.slopes()
+        assert 0 <= flips <= 2e-5 * n_px
+        assert _rms(d[keep]) <= 3e-4
+        assert np.max(np.abs(d)) <= 0.5
+    cg, co = g.commands(), o.commands()
+    assert np.linalg.norm(cg - co) / np.linalg.norm(co) <= 1e-3
+    _, srg, _ = g.psf(0, with_image=False)
+    _, sro, _ = o.psf(0)
+    assert abs(srg - sro) <= 1e-3
 
 
 def test_marechal_strehl_matches_oracle():

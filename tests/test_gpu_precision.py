@@ -42,6 +42,10 @@ def test_quantized_codes_bit_exact(dtype):
     R[3, :] = 0.0
     R[7, :cols] = 0.0
     R[5, 11] = 1e-30            # below every format's resolution after scaling
+    R[11, :] = 0.0
+    R[11, 7] = -4e-40           # the row's max / 448 underflows: scale 1, codes zero (not 0 / 0)
+    R[13, :] = 0.0
+    R[13, 3] = 3e-36            # max / 448 just below the smallest normal float
     R[9, 2] = -3.0e5            # dominates its row
     R[:, cols:] = 1e30          # outside the quantized columns: must not reach the scales
     d = torch.from_numpy(R).cuda()

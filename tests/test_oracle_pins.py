@@ -675,6 +675,23 @@ def test_e4m3_codes_match_torch_and_saturate():
         assert oracle.e4m3_rn_sat(v) == 0x7E and oracle.e4m3_rn_sat(-v) == 0xFE
 
 
+def test_e4m3_tiny_rows_are_zero_with_unit_scale():
+    """A row whose max / 448 is not a normal float gets scale 1 and zero codes (reading: the
+    per-row scale must be a normal float; the row's entries are below 448 2^-126).  A row just
+    above that threshold keeps its scale and a nonzero largest code."""
+    R = np.zeros((3, 16), np.float32)
+    R[0, 4] = -4e-40
+    R[1, 2] = 3e-36
+    R[2, 9] = 6e-36                      # 6e-36 / 448 = 1.3e-38 >= 2^-126
+    codes, sc = oracle.quantize_rows(R, oracle.DTYPE_FP8_E4M3)
+    assert sc[0] == 1.0 and sc[1] == 1.0
+    assert not (codes[0] & 0x7F).any() and not (codes[1] & 0x7F).any()     # +0 or -0 (0x80)
+    assert sc[2] == np.float32(np.float32(6e-36) / np.float32(448.0))
+    assert codes[2, 9] == 0x7e and np.count_nonzero(codes[2]) == 1
+    deq = oracle.dequantize_rows(codes, sc, oracle.DTYPE_FP8_E4M3)
+    assert np.all(np.isfinite(deq))
+
+
 def test_quantize_rows_scales_and_error_bound():
     rng = np.random.default_rng(5)
     R = (rng.normal(0, 1e-2, (37, 301)) * rng.uniform(0.1, 10, (37, 1))).astype(np.float32)
@@ -876,6 +893,36 @@ def test_misregistration_moves_the_measurement():
     with pytest.raises(ValueError):
         o.set_misregistration(0, 0.0, 0.0, 0.0, 0.0)
     o.close()
+
+
+# ------------------------------------------------------------------------------------------ control matrix
+def test_tikhonov_equals_svd_filter_form():
+    """The regularised normal equations equal the SVD filter form -V diag(s / (s^2 + lam)) U^T, an
+    independent route (a dropped lambda, a transposed D or a lost sign fails here), and lam is
+    alpha times the mean diagonal of D^T D."""
+    rng = np.random.default_rng(31)
+    D = rng.standard_normal((90, 40)) @ np.diag(np.logspace(0, -4, 40))
+    R, lam = oracle.tikhonov_reconstructor(D, 1e-3)
+    assert lam == pytest.approx(1e-3 * np.sum(D * D) / 40, rel=1e-13)
+    U, sv, Vt = np.linalg.svd(D, full_matrices=False)
+    ref = -(Vt.T * (sv / (sv * sv + lam))) @ U.T
+    assert np.max(np.abs(R - ref)) <= 1e-10 * np.max(np.abs(ref))
+    res = (D.T @ D + lam * np.eye(40)) @ R + D.T
+    assert np.max(np.abs(res)) <= 1e-10 * np.max(np.abs(D))
+
+
+def test_tikhonov_limits():
+    """alpha -> 0 with full column rank gives -pinv(D); orthogonal columns of norm c give the
+    closed form -c / (c^2 + lam) per column direction."""
+    rng = np.random.default_rng(32)
+    D = rng.standard_normal((60, 25))
+    R0, _ = oracle.tikhonov_reconstructor(D, 0.0)
+    assert np.max(np.abs(R0 + np.linalg.pinv(D))) <= 1e-10
+    Q, _ = np.linalg.qr(rng.standard_normal((60, 25)))
+    c = 3.0
+    R1, lam = oracle.tikhonov_reconstructor(c * Q, 0.1)
+    assert lam == pytest.approx(0.1 * c * c, rel=1e-13)
+    assert np.max(np.abs(R1 + (c / (c * c + lam)) * Q.T)) <= 1e-12
 
 
 def test_workload_sizes():
