@@ -398,6 +398,25 @@ mcao_status mcao_measure(mcao_sim* sim, int with_noise);
  * axis), MCAO_E_OOM, MCAO_E_CUDA. */
 mcao_status mcao_interaction_matrix(mcao_sim* sim, float* D, size_t ld);
 
+/* Gauss-Newton normal equations of a DM misregistration fit ("Conclusions": the rotation of the DM
+ * and its modal basis with respect to the sensors; also translation and magnification).  With DM
+ * `dm` at its current misregistration p = (shift_x m, shift_y m, rotation rad, magnification)
+ * (mcao_set_misregistration), D(p) the exact interaction matrix restricted to that DM's columns
+ * and D_meas a measured one, for J(p) = ||D(p) - D_meas||_F^2:
+ *   cost = J(p);  Jte[i] = sum dD/dp_i (D - D_meas);  JtJ[4][4] = sum dD/dp_i dD/dp_j (row-major,
+ *   symmetric);  meas_sq = ||D_meas||_F^2 over the same entries,
+ * so that (JtJ) dp = -Jte is the Gauss-Newton step and 2 Jte the gradient of J.  The derivatives are
+ * analytic: every influence function is evaluated at the four bilinear corners of each pupil
+ * sample in the DM's own frame and differentiated with respect to p; no model matrix is formed.
+ *   D_meas  device pointer, row-major [n_slopes][ld] float32, column j = the DM's command j (its
+ *           block of the command vector, in order; pass a full matrix's pointer offset to the
+ *           DM's first command), ld >= the DM's command count.
+ * Any output pointer may be NULL.  Sums in double in a fixed order.  Synchronous.  Errors:
+ * MCAO_E_INVALID_ARG, MCAO_E_SHAPE, MCAO_E_STATE (atmosphere or DMs not loaded), MCAO_E_OOM,
+ * MCAO_E_CUDA. */
+mcao_status mcao_misreg_normal_equations(mcao_sim* sim, int dm, const float* D_meas, size_t ld, double* JtJ,
+                                         double* Jte, double* cost, double* meas_sq);
+
 /* Vector-Jacobian products of the noise-free slopes at the current state: for each of n_vec
  * vectors g (device, row-major [n_vec][n_slopes]):
  *   g_commands  device [n_vec][n_commands] = D^T g (or NULL);

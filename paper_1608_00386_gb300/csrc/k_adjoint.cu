@@ -273,6 +273,154 @@ __device__ void dm_adjoint_general(const ProjLaunch& L, const GridView& v, const
     __syncthreads();
 }
 
+// Gauss-Newton terms of a DM misregistration fit, one block per slope row of one sensor, for DM m
+// only.  The row of the model matrix D(p) (the exact Jacobian with the DM moved by p = (shift_x,
+// shift_y, rotation, magnification)) and its four derivatives dD/dp_i are formed by evaluating
+// each actuator's influence function at the four bilinear corners of every pupil sample, in the
+// DM's own frame (as the general adjoint does), and differentiating that evaluation:
+//   u = R(-theta)(q - shift) / mag  (q a surface grid point, metres),  phi = exp(-|u - x_a|^2 / 2 s^2),
+//   d phi / dp = -phi (u - x_a) . du/dp / s^2, with du/d shift_x = (-cos, sin) / mag,
+//   du/d shift_y = (-sin, -cos) / mag, du/d theta = (B, -A) / mag, du/d mag = -(A, B) / mag^2
+// (A, B the rotated offset before the division).  Against the measured row (columns of DM m) the
+// block accumulates in double: cost = sum e^2 (e = D - D_meas), Jte_i = sum dD_i e, the upper
+// triangle of JtJ_ij = sum dD_i dD_j, and sum D_meas^2; one record of 16 doubles per row.
+__global__ void __launch_bounds__(256) misreg_gn_kernel(ProjLaunch L, int m, const float* __restrict__ D_meas,
+                                                        long long ld_meas, int cmd0, double* __restrict__ rec) {
+    __shared__ float s_L[kMaxNpx * kMaxNpx];
+    __shared__ AxisEnt s_ex[kMaxNpx], s_ey[kMaxNpx];
+    __shared__ int s_rng[4];
+    __shared__ double s_red[8][16];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int axis = blockIdx.x / L.n_valid, rank = blockIdx.x - axis * L.n_valid;
+    const SubapDev sd = L.subaps[rank];
+    const WfsDev& w = L.ctx.wfs[sd.wfs];
+    const int npx = w.n_px;
+    const int row = w.slope0 + axis * w.n_valid + sd.rank;
+    const int i0 = sd.sx * npx, j0 = sd.sy * npx;
+    const GridView* V = L.ctx.views + L.real * L.ctx.view_stride + (long long)sd.wfs * L.ctx.n_grids;
+    const long long k = L.ctx.st->k;
+    for (int q = tid; q < npx * npx; q += nthr) s_L[q] = L.sens[(long long)row * L.P + q];
+    const GridView& v = V[L.n_layers + m];
+    const DmDesc dd = L.desc[m];
+    if (tid < npx)
+        s_ex[tid] = axis_entry(v.ax + (long long)(i0 + tid) * v.bp + k * v.vx, v.n, v.periodic, v.inv_n);
+    else if (tid < 2 * npx)
+        s_ey[tid - npx] = axis_entry(v.ay + (long long)(j0 + tid - npx) * v.bp + k * v.vy, v.n, v.periodic, v.inv_n);
+    __syncthreads();
+    const float c0 = 0.5f * (float)(dd.surf_n - 1), ca = 0.5f * (float)(dd.nx - 1), cb = 0.5f * (float)(dd.ny - 1);
+    // offset of grid point (i, j) from the shift, rotated: (A, B), metres
+    auto rot = [&](int i, int j, float& A, float& B) {
+        const float x = ((float)i - c0) * dd.dx - dd.shx, y = ((float)j - c0) * dd.dx - dd.shy;
+        A = dd.cr * x + dd.sr * y;
+        B = -dd.sr * x + dd.cr * y;
+    };
+    if (tid == 0) {
+        int cx0 = v.n, cx1 = 0, cy0 = v.n, cy1 = 0;
+        for (int q = 0; q < npx; ++q) {
+            cx0 = min(cx0, s_ex[q].idx & 0xffff);
+            cx1 = max(cx1, s_ex[q].idx >> 16);
+            cy0 = min(cy0, s_ey[q].idx & 0xffff);
+            cy1 = max(cy1, s_ey[q].idx >> 16);
+        }
+        float lo_a = 1e30f, hi_a = -1e30f, lo_b = 1e30f, hi_b = -1e30f;
+        for (int c = 0; c < 4; ++c) {
+            float A, B;
+            rot((c & 1) ? cx1 : cx0, (c & 2) ? cy1 : cy0, A, B);
+            const float ua = A * dd.inv_mag / dd.pitch + ca, ub = B * dd.inv_mag / dd.pitch + cb;
+            lo_a = fminf(lo_a, ua); hi_a = fmaxf(hi_a, ua);
+            lo_b = fminf(lo_b, ub); hi_b = fmaxf(hi_b, ub);
+        }
+        int a0 = max(0, (int)ceilf(lo_a - dd.rc)), a1 = min(dd.nx - 1, (int)floorf(hi_a + dd.rc)) + 1;
+        int b0 = max(0, (int)ceilf(lo_b - dd.rc)), b1 = min(dd.ny - 1, (int)floorf(hi_b + dd.rc)) + 1;
+        if (a1 < a0) a1 = a0;
+        if (b1 < b0) b1 = b0;
+        s_rng[0] = a0; s_rng[1] = a1; s_rng[2] = b0; s_rng[3] = b1;
+    }
+    __syncthreads();
+    const int a0 = s_rng[0], na = s_rng[1] - s_rng[0], b0 = s_rng[2], nbd = s_rng[3] - s_rng[2];
+    const float im = dd.inv_mag, tws = 2.0f * dd.inv2s2;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int idx = tid; idx < na * nbd; idx += nthr) {
+        const int b = idx / na, a = idx - b * na;
+        const int cmd = L.act_map[dd.map_off + (long long)(b0 + b) * dd.nx + a0 + a];
+        if (cmd < 0) continue;
+        const float xa = ((float)(a0 + a) - ca) * dd.pitch, yb = ((float)(b0 + b) - cb) * dd.pitch;
+        float val = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, g3 = 0.0f;
+        for (int y = 0; y < npx; ++y) {
+            const AxisEnt ey = s_ey[y];
+            const int r0 = ey.idx & 0xffff, r1 = ey.idx >> 16;
+            for (int x = 0; x < npx; ++x) {
+                const float lv = s_L[y * npx + x];
+                if (lv == 0.0f) continue;
+                const AxisEnt ex = s_ex[x];
+                const int q0 = ex.idx & 0xffff, q1 = ex.idx >> 16;
+                for (int c = 0; c < 4; ++c) {
+                    const int i = (c & 1) ? q1 : q0, j = (c & 2) ? r1 : r0;
+                    const float wl = lv * ((c & 1) ? ex.t : 1.0f - ex.t) * ((c & 2) ? ey.t : 1.0f - ey.t);
+                    float A, B;
+                    rot(i, j, A, B);
+                    const float da = A * im - xa, db = B * im - yb;
+                    const float ph = wl * expf(-(da * da + db * db) * dd.inv2s2);
+                    val += ph;
+                    const float gg = -tws * ph;   // d/dp of exp(-r^2 / 2 s^2) = -(r . dr/dp) / s^2 exp(..)
+                    g0 = fmaf(gg, (-da * dd.cr + db * dd.sr) * im, g0);
+                    g1 = fmaf(gg, (-da * dd.sr - db * dd.cr) * im, g1);
+                    g2 = fmaf(gg, (da * B - db * A) * im, g2);
+                    g3 = fmaf(gg, -(da * A + db * B) * im * im, g3);
+                }
+            }
+        }
+        const double dv = (double)(v.sign * val);
+        const double d[4] = {(double)(v.sign * g0), (double)(v.sign * g1), (double)(v.sign * g2),
+                             (double)(v.sign * g3)};
+        const double meas = (double)D_meas[(long long)row * ld_meas + (cmd - cmd0)];
+        const double e = dv - meas;
+        acc[0] += e * e;
+        acc[15] += meas * meas;
+        int t = 5;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            acc[1 + p] += d[p] * e;
+#pragma unroll
+            for (int q = p; q < 4; ++q) acc[t++] += d[p] * d[q];
+        }
+    }
+    // block sum in a fixed order: warp shuffles, then warp 0 over the warps
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) s_red[warp][q] = acc[q];
+    __syncthreads();
+    if (tid < 16) {
+        double sum = 0.0;
+        for (int wv = 0; wv < (nthr >> 5); ++wv) sum += s_red[wv][tid];
+        rec[(long long)row * 16 + tid] = sum;
+    }
+}
+
+// rows' records summed in row order into out[16] (one block; fixed order)
+__global__ void misreg_sum_kernel(const double* __restrict__ rec, int n_rows, double* __restrict__ out) {
+    __shared__ double s[256];
+    for (int q = 0; q < 16; ++q) {
+        double sum = 0.0;
+        for (int r = threadIdx.x; r < n_rows; r += blockDim.x) sum += rec[(long long)r * 16 + q];
+        s[threadIdx.x] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < (int)blockDim.x; ++i) t += s[i];
+            out[q] = t;
+        }
+        __syncthreads();
+    }
+}
+
 // One block per slope of one sensor: the slope's row of d s / d c from its pupil-sample
 // derivatives, written to D (interaction matrix) and/or accumulated as g_v[row] * row into the
 // command gradients of every vector v.
@@ -421,6 +569,17 @@ cudaError_t launch_sens(const SensLaunch& L, int n_fft, cudaStream_t s) {
 
 cudaError_t launch_dm_adjoint(const ProjLaunch& L, cudaStream_t s) {
     if (L.n_valid && L.n_dms) dm_adjoint_kernel<<<(unsigned)(2 * L.n_valid), 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_misreg_gn(const ProjLaunch& L, int m, const float* D_meas, long long ld_meas, int cmd0, double* rec,
+                             cudaStream_t s) {
+    if (L.n_valid) misreg_gn_kernel<<<(unsigned)(2 * L.n_valid), 256, 0, s>>>(L, m, D_meas, ld_meas, cmd0, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_misreg_sum(const double* rec, int n_rows, double* out, cudaStream_t s) {
+    misreg_sum_kernel<<<1, 256, 0, s>>>(rec, n_rows, out);
     return cudaGetLastError();
 }
 

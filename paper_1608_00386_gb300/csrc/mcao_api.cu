@@ -113,6 +113,7 @@ struct mcao_sim {
     int n_dms = 0;
     std::vector<mcao_dm> dms;
     std::vector<DmDesc> dm_desc;
+    std::vector<int> dm_cmd0;          // first command of each DM (and the total)
     std::vector<std::array<double, 4>> dm_misreg;   // per DM: shift x, y (m), rotation (rad), magnification
     DmDesc* d_dm_desc = nullptr;
     float* d_dm_g = nullptr;
@@ -1160,6 +1161,7 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     S->dms.assign(dms, dms + n_dms);
     S->n_dms = n_dms;
     S->dm_desc.clear();
+    S->dm_cmd0.assign(n_dms + 1, 0);
     std::vector<float> g;
     std::vector<int2> band;
     std::vector<int> map;
@@ -1177,6 +1179,7 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
             else map.push_back(-1);
         }
         ncmd += cnt;
+        S->dm_cmd0[m + 1] = ncmd;
         D.surf_off = surf_total;
         surf_total += (long long)d.surf_n * d.surf_n;
         S->dm_tile_start[m] = tiles;
@@ -1703,6 +1706,73 @@ static mcao_status run_adjoint(mcao_sim* S, float* D, long long ld, const float*
     cudaFree(d_loff);
     CK(e);
     if (h_err) return fail(S, MCAO_E_UNSUPPORTED, "a subaperture footprint meets more than 128 actuators per axis");
+    return MCAO_OK;
+}
+
+mcao_status mcao_misreg_normal_equations(mcao_sim* S, int dm, const float* D_meas, size_t ld, double* JtJ, double* Jte,
+                                         double* cost, double* meas_sq) {
+    if (!S || !D_meas) return MCAO_E_INVALID_ARG;
+    if (!S->atm_loaded || !S->dms_loaded) return fail(S, MCAO_E_STATE, "atmosphere and DMs must be loaded");
+    if (dm < 0 || dm >= S->n_dms) return fail(S, MCAO_E_INVALID_ARG, "bad DM index");
+    const int cmd0 = S->dm_cmd0[dm], n_cols = S->dm_cmd0[dm + 1] - cmd0;
+    if (ld < (size_t)n_cols) return fail(S, MCAO_E_SHAPE, "ld must be >= %d (the DM's commands)", n_cols);
+    CK(cudaSetDevice(S->device));
+    int P = 1;
+    for (const auto& W : S->wfs) P = std::max(P, W.p.n_px * W.p.n_px);
+    CK(cudaDeviceSynchronize());   // D_meas may come from any stream
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    float* sens = nullptr;
+    double* rec = nullptr;
+    cudaError_t e = dalloc(&sens, (size_t)S->n_slopes * P);
+    if (e == cudaSuccess) e = cudaMalloc(&rec, sizeof(double) * ((size_t)S->n_slopes * 16 + 16));
+    if (e == cudaSuccess) e = cudaMemsetAsync(rec, 0, sizeof(double) * (size_t)S->n_slopes * 16, S->s0);
+    if (e == cudaSuccess) e = launch_dm_surfaces(make_dm_launch(S), S->s0);
+    for (size_t w = 0; w < S->wfs.size() && e == cudaSuccess; ++w) {
+        const WfsHost& W = S->wfs[w];
+        if (W.n_valid == 0) continue;
+        SensLaunch L{};
+        L.ctx = make_ctx(S);
+        L.real = S->cur;
+        L.subaps = W.d_subaps;
+        L.n_subaps = W.n_valid;
+        L.sens = sens;
+        L.P = P;
+        e = launch_sens(L, W.p.n_fft, S->s0);
+        ProjLaunch J{};
+        J.ctx = L.ctx;
+        J.real = S->cur;
+        J.n_layers = S->n_layers;
+        J.n_dms = S->n_dms;
+        J.desc = S->d_dm_desc;
+        J.g = S->d_dm_g;
+        J.band = S->d_dm_band;
+        J.act_map = S->d_dm_map;
+        J.subaps = W.d_subaps;
+        J.n_valid = W.n_valid;
+        J.sens = sens;
+        J.P = P;
+        J.n_slopes = S->n_slopes;
+        J.n_cmd = S->n_cmd;
+        if (e == cudaSuccess) e = launch_misreg_gn(J, dm, D_meas, (long long)ld, cmd0, rec, S->s0);
+    }
+    double* out = rec + (size_t)S->n_slopes * 16;
+    double h[16] = {0};
+    if (e == cudaSuccess) e = launch_misreg_sum(rec, S->n_slopes, out, S->s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
+    if (e == cudaSuccess) e = cudaMemcpy(h, out, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(sens);
+    cudaFree(rec);
+    CK(e);
+    // records: cost, Jte[4], upper triangle of JtJ row by row, sum D_meas^2
+    if (cost) *cost = h[0];
+    if (Jte)
+        for (int p = 0; p < 4; ++p) Jte[p] = h[1 + p];
+    if (JtJ) {
+        int t = 5;
+        for (int p = 0; p < 4; ++p)
+            for (int q = p; q < 4; ++q, ++t) JtJ[p * 4 + q] = JtJ[q * 4 + p] = h[t];
+    }
+    if (meas_sq) *meas_sq = h[15];
     return MCAO_OK;
 }
 

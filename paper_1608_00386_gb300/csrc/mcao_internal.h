@@ -304,6 +304,11 @@ struct ProjLaunch {
 size_t sens_smem(int n_fft);
 cudaError_t launch_sens(const SensLaunch& L, int n_fft, cudaStream_t s);
 cudaError_t launch_dm_adjoint(const ProjLaunch& L, cudaStream_t s);
+// Gauss-Newton records (16 doubles per slope row) of DM m's misregistration fit against D_meas
+// (columns = DM m's commands, from cmd0), then their fixed-order sum
+cudaError_t launch_misreg_gn(const ProjLaunch& L, int m, const float* D_meas, long long ld_meas, int cmd0, double* rec,
+                             cudaStream_t s);
+cudaError_t launch_misreg_sum(const double* rec, int n_rows, double* out, cudaStream_t s);
 cudaError_t launch_phase_adjoint(const ProjLaunch& L, float* g_phase, long long phase_stride, long long phase_off,
                                  float* g_layers, long long layer_stride, const long long* layer_off, cudaStream_t s);
 

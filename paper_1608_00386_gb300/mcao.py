@@ -32,6 +32,7 @@ EXPORTS = [
     "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
     "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration", "mcao_step_group",
     "mcao_read_async", "mcao_check_bounded_wait", "mcao_reconstruct_batch", "mcao_tikhonov_reconstructor",
+    "mcao_misreg_normal_equations",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -129,6 +130,8 @@ def lib():
         "mcao_reconstruct_batch": [vp, vp, C.c_int, vp],
         "mcao_tikhonov_reconstructor": [vp, C.c_int, C.c_int, C.c_size_t, C.c_double, vp, C.c_size_t, C.c_int, vp,
                                         C.POINTER(C.c_double), C.c_char_p, C.c_size_t],
+        "mcao_misreg_normal_equations": [vp, C.c_int, vp, C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -320,6 +323,22 @@ class Sim:
         out = torch.empty((S.shape[0], self.query(Q_COMMANDS)), dtype=torch.float32, device=S.device)
         self._ck(lib().mcao_reconstruct_batch(self.h, S.data_ptr(), S.shape[0], out.data_ptr()))
         return out
+
+    def misreg_normal_equations(self, dm: int, D_meas):
+        """Gauss-Newton terms of DM dm's misregistration fit at its current misregistration
+        (mcao_misreg_normal_equations): D_meas is a CUDA float32 tensor [n_slopes][>= the DM's
+        commands] with unit column stride whose column j is the DM's command j.  Returns (JtJ
+        [4][4], Jte [4], cost, meas_sq) as numpy / floats."""
+        import torch
+        if not (isinstance(D_meas, torch.Tensor) and D_meas.is_cuda and D_meas.dtype == torch.float32
+                and D_meas.dim() == 2 and D_meas.stride(1) == 1 and D_meas.shape[0] == self.query(Q_SLOPES)):
+            raise McaoError(1, "D_meas must be a CUDA float32 tensor [n_slopes][n] with unit column stride")
+        JtJ = (C.c_double * 16)()
+        Jte = (C.c_double * 4)()
+        cost, msq = C.c_double(), C.c_double()
+        self._ck(lib().mcao_misreg_normal_equations(self.h, int(dm), D_meas.data_ptr(), D_meas.stride(0), JtJ, Jte,
+                                                    C.byref(cost), C.byref(msq)))
+        return np.array(JtJ[:]).reshape(4, 4), np.array(Jte[:]), cost.value, msq.value
 
     def check_bounded_wait(self) -> int:
         """Status of mcao_check_bounded_wait: 6 (MCAO_E_TIMEOUT) when the device timeouts work."""

@@ -117,6 +117,15 @@ def test_misregistration_fit_host_logic_on_a_linear_model():
                 D += float(self.p[k] - nominal[k]) * A[k]
             return D
 
+        def misreg_normal_equations(self, dm, Dm):
+            # what the library returns for this linear model: dD/dp_k = A_k on the DM's columns
+            assert dm == 1 and Dm.shape[1] == cols[1] - cols[0]
+            e = (self.interaction_matrix()[:, cols[0]:cols[1]] - Dm).double().numpy()
+            J = [a[:, cols[0]:cols[1]].double().numpy() for a in A]
+            JtJ = np.array([[np.sum(J[i] * J[j]) for j in range(4)] for i in range(4)])
+            Jte = np.array([np.sum(J[i] * e) for i in range(4)])
+            return JtJ, Jte, float(np.sum(e * e)), float(np.sum(Dm.double().numpy() ** 2))
+
     truth = np.array([0.2, -0.1, 0.01, 1.02])
     sim = FakeSim()
     sim.set_misregistration(1, *truth)

@@ -93,3 +93,43 @@ def test_fit_recovers_misregistration_from_oracle_matrix(true):
     assert abs(p[2] - true[3]) <= 1e-6
     assert abs(p[3] - true[4]) <= 1e-6
     assert hist[-1] <= 1e-5 < hist[0]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_normal_equations_model_equals_interaction_matrix(case):
+    """The model matrix the Gauss-Newton kernel forms (influence functions at the bilinear corners
+    of each pupil sample, in the DM's frame) is the interaction matrix of the misregistered DM:
+    against mcao_interaction_matrix at the same misregistration the cost vanishes (float32
+    rounding of two summation orders) and the gradient with it."""
+    cfg, g, _ = _pair(case)
+    D = calibration.dm_columns(g, g.interaction_matrix(), case[0])
+    JtJ, Jte, cost, msq = g.misreg_normal_equations(case[0], D)
+    assert msq > 0.0
+    assert np.sqrt(cost / msq) <= 1e-5
+    assert np.all(np.abs(Jte) <= 1e-5 * np.sqrt(np.diag(JtJ) * msq))
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_normal_equations_gradient_is_the_derivative(case):
+    """2 Jte is the gradient of the cost: against central differences of the call's own cost in
+    each parameter (steps 1e-3 pitch, 1e-4 rad, 1e-4), measured 0.3 pitch / 1 deg / 1 % away from
+    the matrix's misregistration; JtJ is symmetric positive semidefinite."""
+    cfg, g, _ = _pair(case)
+    dm = case[0]
+    pitch = cfg["dms"][dm]["pitch"]
+    D = calibration.dm_columns(g, g.interaction_matrix(), dm).clone()
+    p = np.array(case[1:], dtype=np.float64) + np.array([0.3 * pitch, -0.2 * pitch, np.radians(1.0), 0.01])
+    g.set_misregistration(dm, *p)
+    JtJ, Jte, cost, _ = g.misreg_normal_equations(dm, D)
+    h = np.array([1e-3 * pitch, 1e-3 * pitch, 1e-4, 1e-4])
+    for i in range(4):
+        e = np.zeros(4)
+        e[i] = h[i]
+        g.set_misregistration(dm, *(p + e))
+        cp = g.misreg_normal_equations(dm, D)[2]
+        g.set_misregistration(dm, *(p - e))
+        cm = g.misreg_normal_equations(dm, D)[2]
+        fd = (cp - cm) / (2.0 * h[i])
+        assert abs(2.0 * Jte[i] - fd) <= 2e-3 * abs(fd) + 1e-6 * cost / h[i], (i, 2.0 * Jte[i], fd)
+    assert np.allclose(JtJ, JtJ.T)
+    assert np.min(np.linalg.eigvalsh(JtJ)) >= -1e-9 * np.max(np.abs(JtJ))
