@@ -433,6 +433,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="realizations per step in the batched variants")
+    ap.add_argument("--no-autotune", action="store_true", help="time the default launch shapes")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -461,6 +462,12 @@ def main():
     stream = torch.cuda.current_stream()
     sim = mcao.make_sim(cfg, d_screens, d_R, s_ref=d_sref, stream=stream)
     n_slopes = sim.query(mcao.Q_SLOPES)
+    tuning = {"chosen": sim.tuning(), "report": "defaults (--no-autotune)"}
+    if not args.no_autotune:
+        # the library's autotuner times its launch-shape candidates on this workload (state
+        # restored afterwards); the timed steps then run with its choice
+        chosen, report = sim.autotune(steps_per_trial=100)
+        tuning = {"chosen": chosen, "report": report}
     elapsed, ms, cnt, lps, ck = timed_steps(sim, stream, args.steps, args.warmup, dist, Clocks(local))
     value = job_value(ws, args.steps, elapsed)
     q_f32 = loop_quality(sim)
@@ -669,7 +676,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_block(cfg, n_cmd, n_slopes),
             "parallelism": f"replicas x{ws}", "timing": "CUDA events on the launching stream around the K steps",
-            "reconstructor_values": r_info,
+            "reconstructor_values": r_info, "tuning": tuning,
             "loop_quality": {"strehl_long": q_f32["strehl_long"], "wf_rms_nm": q_f32["wf_rms_nm"],
                              "steps": total_steps, "science": "on-axis, 2.2 um"},
             "roofline": roof,

@@ -470,6 +470,44 @@ mcao_status mcao_tikhonov_reconstructor(const float* D, int n_slopes, int n_cmd,
                                         size_t ld_r, int r_fp64, void* stream, double* lambda, char* err,
                                         size_t err_len);
 
+/* Launch shapes ("tuning") of a simulation, in this order (values per MCAO_TUNE_*):
+ *   MCAO_TUNE_SENSE_BLOCKS_PER_SM  warp-per-subaperture sensing launches: blocks per SM, [1, 8] (4)
+ *   MCAO_TUNE_RECON_CTAS_PCT       reconstructor slices: blocks per SM x 100, [25, 400] (100)
+ *   MCAO_TUNE_SCIENCE_AFTER_AUX    science waits for the block-per-subaperture sensors, 0 or 1 (1)
+ *   MCAO_TUNE_TC_CHUNK             tensor-core batched product: k-blocks per TMEM accumulator,
+ *                                  [1, 64] (8)
+ *   MCAO_TUNE_MULTI_BLOCKS_PER_SM  batched float32 product: blocks per SM, [1, 2] (2)
+ * No counterpart in the paper.  Results do not depend on them, except MCAO_TUNE_TC_CHUNK, which
+ * regroups the tensor-core product's float32 sums (float32 rounding only). */
+enum {
+    MCAO_TUNE_SENSE_BLOCKS_PER_SM = 0,
+    MCAO_TUNE_RECON_CTAS_PCT = 1,
+    MCAO_TUNE_SCIENCE_AFTER_AUX = 2,
+    MCAO_TUNE_TC_CHUNK = 3,
+    MCAO_TUNE_MULTI_BLOCKS_PER_SM = 4,
+    MCAO_N_TUNE = 5
+};
+
+/* Current launch shapes into values[MCAO_N_TUNE] (n >= MCAO_N_TUNE, else MCAO_E_INVALID_ARG). */
+mcao_status mcao_get_tuning(const mcao_sim* sim, int* values, int n);
+
+/* Set the launch shapes (n == MCAO_N_TUNE, each within its range, else MCAO_E_SHAPE /
+ * MCAO_E_INVALID_ARG); applies from the next step. */
+mcao_status mcao_set_tuning(mcao_sim* sim, const int* values, int n);
+
+/* Autotuner: for each launch shape that applies to this configuration (the sensing grid when it
+ * has warp-per-subaperture sensors, the slices' grid without batching, the science ordering when
+ * it has block-per-subaperture sensors, the batched products' shapes with batching), in that order,
+ * time steps_per_trial steps (after 2 warm-up steps) for every candidate value with the others
+ * held at their best so far, and keep the fastest (coordinate descent, CUDA events on the device).
+ * The trials advance the simulation; its state is saved first and restored at the end (as
+ * mcao_get_state / mcao_set_state), so the caller's run continues as if no trial had run.  The
+ * chosen shapes stay set; values (n >= MCAO_N_TUNE, may be NULL) receives them and report (may be
+ * NULL) the measured ms/step of every trial ("knob: value=ms ... -> chosen").  Errors:
+ * MCAO_E_INVALID_ARG (steps_per_trial outside [1, 100000]), MCAO_E_SHAPE, MCAO_E_STATE (not fully
+ * loaded), MCAO_E_UNSUPPORTED (stage profiler on), MCAO_E_CUDA. */
+mcao_status mcao_autotune(mcao_sim* sim, int steps_per_trial, int* values, int n, char* report, size_t report_len);
+
 /* Stages timed by the profiler. */
 enum {
     MCAO_STAGE_DM = 0,          /* DM surfaces                                                  */

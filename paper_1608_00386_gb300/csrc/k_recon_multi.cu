@@ -195,12 +195,13 @@ cudaError_t multi_prepare() {
 }
 
 cudaError_t launch_recon_multi(const MultiLaunch& L, int n_real, int pad_stride, const float* slopes_pad, float alpha,
-                               float beta, float* out, int sm_count, cudaStream_t s) {
+                               float beta, float* out, int sm_count, int blocks_per_sm, cudaStream_t s) {
     if (n_real < 1 || n_real > kMB) return cudaErrorInvalidValue;
     slopes_t_kernel<<<256, 256, 0, s>>>(slopes_pad, n_real, L.K, pad_stride, L.s_t);
     const int items = ((L.n_cmd + kMRows - 1) / kMRows) * multi_chunks(L.K);
     int blocks = (items + kMWarps - 1) / kMWarps;
-    if (blocks > 2 * sm_count) blocks = 2 * sm_count;   // two resident blocks per SM
+    const int cap = (blocks_per_sm > 0 ? blocks_per_sm : 2) * sm_count;   // at most two resident per SM
+    if (blocks > cap) blocks = cap;
     if (L.bf16)
         recon_multi_kernel<true><<<blocks, kMWarps * 32, sizeof(MultiRing<true>), s>>>(L);
     else

@@ -571,7 +571,7 @@ cudaError_t tc_create(const float* R_rm, int rows_in, int ld, int n_cmd, int n_r
 long long tc_bytes(const TcProduct* P) { return P ? (long long)P->rows * P->ldb * 2 : 0; }
 
 cudaError_t tc_launch(TcProduct* P, const float* slopes_pad, int pad_stride, int n_real, float alpha, float beta,
-                      float* out, int* err, cudaStream_t st, int* launches) {
+                      float* out, int* err, int chunk, cudaStream_t st, int* launches) {
     int nl = 0;
     for (int r0 = 0; r0 < n_real; r0 += P->npad) {
         const int nb = std::min(P->npad, n_real - r0);
@@ -587,7 +587,7 @@ cudaError_t tc_launch(TcProduct* P, const float* slopes_pad, int pad_stride, int
         prm.n_rhs = nb;
         prm.stages = P->stages;
         prm.maxseg = P->maxseg;
-        prm.chunk = kTcChunk;
+        prm.chunk = chunk > 0 ? chunk : kTcChunk;
         prm.nbuf = P->nbuf;
         prm.tmem_cols = P->tmem_cols;
         prm.partial = P->partial;

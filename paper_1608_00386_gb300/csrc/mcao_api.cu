@@ -114,6 +114,7 @@ struct mcao_sim {
     std::vector<mcao_dm> dms;
     std::vector<DmDesc> dm_desc;
     std::vector<int> dm_cmd0;          // first command of each DM (and the total)
+    Tuning tune;                          // launch shapes (defaults or mcao_autotune's choice)
     std::vector<std::array<double, 4>> dm_misreg;   // per DM: shift x, y (m), rotation (rad), magnification
     DmDesc* d_dm_desc = nullptr;
     float* d_dm_g = nullptr;
@@ -331,7 +332,7 @@ SciLaunch make_sci_launch(mcao_sim* S, int q) {
 WfsLaunch make_wfs_launch(mcao_sim* S, const SubapDev* subaps, int n, unsigned int* work = nullptr) {
     WfsLaunch L{};
     L.work = work;
-    L.max_blocks = 4 * S->sm_count;  // blocks of the warp-per-subaperture kernel resident per SM
+    L.max_blocks = S->tune.sense_blocks_per_sm * S->sm_count;  // warp-per-subaperture blocks per SM
     L.ctx = make_ctx(S);
     L.subaps = subaps;
     L.n_subaps = n;
@@ -444,8 +445,8 @@ cudaError_t enqueue_batched_product(mcao_sim* S, int n, float alpha, float beta,
     cudaError_t e = cudaSuccess;
     if (S->tc) {
         int n_tc = 0;
-        if ((e = tc_launch(S->tc, S->d_slopes_pad, pad_stride(S), n, alpha, beta, out, S->d_err, S->s0, &n_tc)) !=
-            cudaSuccess)
+        if ((e = tc_launch(S->tc, S->d_slopes_pad, pad_stride(S), n, alpha, beta, out, S->d_err, S->tune.tc_chunk,
+                           S->s0, &n_tc)) != cudaSuccess)
             return e;
         *nl += n_tc;
         return cudaSuccess;
@@ -461,7 +462,8 @@ cudaError_t enqueue_batched_product(mcao_sim* S, int n, float alpha, float beta,
     for (int r0 = 0; r0 < n; r0 += kMultiRhs) {
         const int nb = std::min(kMultiRhs, n - r0);
         if ((e = launch_recon_multi(M, nb, pad_stride(S), S->d_slopes_pad + (size_t)r0 * pad_stride(S), alpha, beta,
-                                    out + (size_t)r0 * S->n_cmd, S->sm_count, S->s0)) != cudaSuccess)
+                                    out + (size_t)r0 * S->n_cmd, S->sm_count, S->tune.multi_blocks_per_sm, S->s0)) !=
+            cudaSuccess)
             return e;
         *nl += 3;
     }
@@ -500,7 +502,8 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         cudaEvent_t after = nullptr;
         for (cudaEvent_t ev : ready)
             if (ev) after = ev;
-        if (after && (e = cudaStreamWaitEvent(S->s2, after, 0)) != cudaSuccess) return e;
+        if (S->tune.science_after_aux && after && (e = cudaStreamWaitEvent(S->s2, after, 0)) != cudaSuccess)
+            return e;
     }
     for (size_t q = 0; q < S->sci.size(); ++q) {
         SciLaunch L = make_sci_launch(S, (int)q);
@@ -567,7 +570,9 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
             last = ev;
         }
         slot = prof_begin(S, ST_RECON, S->s3);
-        if ((e = launch_recon(S->slices[i], S->s3)) != cudaSuccess) return e;
+        ReconLaunch rl_i = S->slices[i];
+        rl_i.max_ctas = std::max(1, S->sm_count * S->tune.recon_ctas_pct / 100);
+        if ((e = launch_recon(rl_i, S->s3)) != cudaSuccess) return e;
         prof_end(S, slot, S->s3);
         ++nl;
     }
@@ -1706,6 +1711,143 @@ static mcao_status run_adjoint(mcao_sim* S, float* D, long long ld, const float*
     cudaFree(d_loff);
     CK(e);
     if (h_err) return fail(S, MCAO_E_UNSUPPORTED, "a subaperture footprint meets more than 128 actuators per axis");
+    return MCAO_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// launch-shape tuning
+// ------------------------------------------------------------------------------------------
+static const int kTuneMin[kTuningKnobs] = {1, 25, 0, 1, 1};
+static const int kTuneMax[kTuningKnobs] = {8, 400, 1, 64, 2};
+
+static void tuning_to(const Tuning& t, int* v) {
+    v[0] = t.sense_blocks_per_sm;
+    v[1] = t.recon_ctas_pct;
+    v[2] = t.science_after_aux;
+    v[3] = t.tc_chunk;
+    v[4] = t.multi_blocks_per_sm;
+}
+
+static Tuning tuning_from(const int* v) {
+    Tuning t;
+    t.sense_blocks_per_sm = v[0];
+    t.recon_ctas_pct = v[1];
+    t.science_after_aux = v[2];
+    t.tc_chunk = v[3];
+    t.multi_blocks_per_sm = v[4];
+    return t;
+}
+
+mcao_status mcao_get_tuning(const mcao_sim* S, int* values, int n) {
+    if (!S || !values || n < kTuningKnobs) return MCAO_E_INVALID_ARG;
+    tuning_to(S->tune, values);
+    return MCAO_OK;
+}
+
+mcao_status mcao_set_tuning(mcao_sim* S, const int* values, int n) {
+    if (!S || !values) return MCAO_E_INVALID_ARG;
+    if (n != kTuningKnobs) return fail(S, MCAO_E_SHAPE, "%d tuning values, expected %d", n, kTuningKnobs);
+    for (int i = 0; i < kTuningKnobs; ++i)
+        if (values[i] < kTuneMin[i] || values[i] > kTuneMax[i])
+            return fail(S, MCAO_E_INVALID_ARG, "tuning value %d = %d outside [%d, %d]", i, values[i], kTuneMin[i],
+                        kTuneMax[i]);
+    CK(cudaSetDevice(S->device));
+    { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
+    S->tune = tuning_from(values);
+    release_graph(S);
+    return MCAO_OK;
+}
+
+mcao_status mcao_autotune(mcao_sim* S, int steps_per_trial, int* values, int n, char* report, size_t report_len) {
+    if (!S) return MCAO_E_INVALID_ARG;
+    if (steps_per_trial < 1 || steps_per_trial > 100000)
+        return fail(S, MCAO_E_INVALID_ARG, "steps_per_trial must be in [1, 100000]");
+    if (values && n < kTuningKnobs) return fail(S, MCAO_E_SHAPE, "values needs %d entries", kTuningKnobs);
+    if (!S->atm_loaded || !S->dms_loaded || !S->recon_loaded)
+        return fail(S, MCAO_E_STATE, "load the atmosphere, the DMs and the reconstructor before tuning");
+    if (S->profiling) return fail(S, MCAO_E_UNSUPPORTED, "switch the stage profiler off before tuning");
+    CK(cudaSetDevice(S->device));
+    // the trials advance the simulation: keep its state and restore it afterwards
+    size_t sz = 0;
+    mcao_status r = mcao_query(S, MCAO_Q_STATE, 0, &sz);
+    if (r != MCAO_OK) return r;
+    std::vector<char> blob(sz);
+    if ((r = mcao_get_state(S, blob.data(), sz)) != MCAO_OK) return r;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto trial = [&](float& ms) -> mcao_status {
+        release_graph(S);
+        mcao_status q = mcao_step(S, 2);   // builds the graph, warms up
+        if (q != MCAO_OK) return q;
+        CK(cudaEventRecord(e0, S->s0));
+        if ((q = mcao_step(S, steps_per_trial)) != MCAO_OK) return q;
+        CK(cudaEventRecord(e1, S->s0));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= (float)steps_per_trial;
+        return sync_all(S);
+    };
+    // knobs that shape this configuration's step, with their candidates (the current value first)
+    bool acf = false, fft = false;
+    for (const auto& W : S->wfs) {
+        if (W.n_valid == 0) continue;
+        (W.fft_route ? fft : acf) = true;
+    }
+    const bool batched = S->n_real > 1;
+    std::vector<std::pair<int, std::vector<int>>> knobs;
+    if (acf) knobs.push_back({0, {2, 3, 4, 6}});
+    if (!batched) knobs.push_back({1, {75, 100, 125, 150}});
+    if (!S->sci.empty() && fft) knobs.push_back({2, {0, 1}});
+    if (batched && S->tc) knobs.push_back({3, {4, 8, 16}});
+    if (batched && !S->tc) knobs.push_back({4, {1, 2}});
+    int cur[kTuningKnobs];
+    tuning_to(S->tune, cur);
+    const char* names[kTuningKnobs] = {"sense_blocks_per_sm", "recon_ctas_pct", "science_after_aux", "tc_chunk",
+                                       "multi_blocks_per_sm"};
+    std::string rep;
+    float best_ms = 0.0f;
+    r = trial(best_ms);
+    char line[256];
+    snprintf(line, sizeof(line), "start %.4f ms/step", best_ms);
+    rep += line;
+    for (auto& kn : knobs) {
+        const int k = kn.first;
+        int best = cur[k];
+        rep += std::string("; ") + names[k] + ":";
+        for (int c : kn.second) {
+            if (r != MCAO_OK) break;
+            int v[kTuningKnobs];
+            std::copy(cur, cur + kTuningKnobs, v);
+            v[k] = c;
+            S->tune = tuning_from(v);
+            float ms = 0.0f;
+            r = trial(ms);
+            snprintf(line, sizeof(line), " %d=%.4f", c, ms);
+            rep += line;
+            if (r == MCAO_OK && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        cur[k] = best;
+        snprintf(line, sizeof(line), " -> %d", best);
+        rep += line;
+    }
+    S->tune = tuning_from(cur);
+    release_graph(S);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    mcao_status rs = mcao_set_state(S, blob.data(), sz);
+    if (r != MCAO_OK) return r;
+    if (rs != MCAO_OK) return rs;
+    snprintf(line, sizeof(line), "; chosen %.4f ms/step", best_ms);
+    rep += line;
+    if (values) tuning_to(S->tune, values);
+    if (report && report_len) {
+        strncpy(report, rep.c_str(), report_len - 1);
+        report[report_len - 1] = '\0';
+    }
     return MCAO_OK;
 }
 

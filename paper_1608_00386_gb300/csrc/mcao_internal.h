@@ -9,6 +9,18 @@
 namespace mcao {
 
 constexpr int kMaxEntries = 16;   // layers + DMs sampled along one direction
+
+// Launch shapes of one simulation: the defaults, or what mcao_autotune measured fastest for its
+// configuration (the knobs of the C ABI's MCAO_TUNE_* values, in that order).  None of them
+// changes a result except tc_chunk, which regroups the tensor-core product's float32 sums.
+struct Tuning {
+    int sense_blocks_per_sm = 4;    // warp-per-subaperture sensing: grid cap, blocks per SM
+    int recon_ctas_pct = 100;       // reconstructor slices: blocks per SM x 100
+    int science_after_aux = 1;      // science waits for the block-per-subaperture sensors
+    int tc_chunk = 8;               // tensor-core product: k-blocks per TMEM accumulator
+    int multi_blocks_per_sm = 2;    // batched float32 product: blocks per SM
+};
+constexpr int kTuningKnobs = 5;
 constexpr int kMaxNpx = 32;       // pupil samples per subaperture side
 constexpr int kMaxNd = 32;        // detector pixels per subaperture side
 constexpr int kMaxDms = 4;
@@ -337,7 +349,7 @@ struct MultiLaunch {
 int multi_chunks(int K);
 cudaError_t multi_prepare();   // kernel attributes (outside stream capture)
 cudaError_t launch_recon_multi(const MultiLaunch& L, int n_real, int pad_stride, const float* slopes_pad, float alpha,
-                               float beta, float* out, int sm_count, cudaStream_t s);
+                               float beta, float* out, int sm_count, int blocks_per_sm, cudaStream_t s);
 
 // batched product for a bfloat16 R on the tensor cores (tcgen05, TMA, TMEM accumulators):
 // out[r][i] = alpha sum_j R[i][j] s_r[j] + beta out[r][i] for every realization r, float32
@@ -350,7 +362,7 @@ cudaError_t tc_create(const float* R_rm, int rows_in, int ld, int n_cmd, int n_r
                       TcProduct** out);
 void tc_destroy(TcProduct* P);
 cudaError_t tc_launch(TcProduct* P, const float* slopes_pad, int pad_stride, int n_real, float alpha, float beta,
-                      float* out, int* err, cudaStream_t st, int* launches);
+                      float* out, int* err, int chunk, cudaStream_t st, int* launches);
 long long tc_bytes(const TcProduct* P);   // bytes of its bfloat16 R
 
 }  // namespace mcao

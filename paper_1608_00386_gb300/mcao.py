@@ -32,7 +32,7 @@ EXPORTS = [
     "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
     "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration", "mcao_step_group",
     "mcao_read_async", "mcao_check_bounded_wait", "mcao_reconstruct_batch", "mcao_tikhonov_reconstructor",
-    "mcao_misreg_normal_equations",
+    "mcao_misreg_normal_equations", "mcao_get_tuning", "mcao_set_tuning", "mcao_autotune",
 ]
 
 DTYPE_F32, DTYPE_BF16, DTYPE_FP8_E4M3 = 0, 1, 2
@@ -132,6 +132,9 @@ def lib():
                                         C.POINTER(C.c_double), C.c_char_p, C.c_size_t],
         "mcao_misreg_normal_equations": [vp, C.c_int, vp, C.c_size_t, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "mcao_get_tuning": [vp, C.POINTER(C.c_int), C.c_int],
+        "mcao_set_tuning": [vp, C.POINTER(C.c_int), C.c_int],
+        "mcao_autotune": [vp, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_char_p, C.c_size_t],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -339,6 +342,33 @@ class Sim:
         self._ck(lib().mcao_misreg_normal_equations(self.h, int(dm), D_meas.data_ptr(), D_meas.stride(0), JtJ, Jte,
                                                     C.byref(cost), C.byref(msq)))
         return np.array(JtJ[:]).reshape(4, 4), np.array(Jte[:]), cost.value, msq.value
+
+    TUNING = ("sense_blocks_per_sm", "recon_ctas_pct", "science_after_aux", "tc_chunk", "multi_blocks_per_sm")
+
+    def tuning(self) -> dict:
+        """Current launch shapes (mcao_get_tuning), by name."""
+        v = (C.c_int * len(self.TUNING))()
+        self._ck(lib().mcao_get_tuning(self.h, v, len(self.TUNING)))
+        return dict(zip(self.TUNING, v[:]))
+
+    def set_tuning(self, **kw):
+        """Change launch shapes by name (mcao_set_tuning); the others keep their values."""
+        cur = self.tuning()
+        for k, val in kw.items():
+            if k not in cur:
+                raise McaoError(1, f"unknown tuning knob {k}")
+            cur[k] = int(val)
+        v = (C.c_int * len(self.TUNING))(*[cur[k] for k in self.TUNING])
+        self._ck(lib().mcao_set_tuning(self.h, v, len(self.TUNING)))
+
+    def autotune(self, steps_per_trial: int = 50):
+        """Time every candidate launch shape of this configuration and keep the fastest
+        (mcao_autotune); the simulation's state is restored afterwards.  Returns (chosen shapes by
+        name, report string)."""
+        v = (C.c_int * len(self.TUNING))()
+        buf = C.create_string_buffer(4096)
+        self._ck(lib().mcao_autotune(self.h, int(steps_per_trial), v, len(self.TUNING), buf, 4096))
+        return dict(zip(self.TUNING, v[:])), buf.value.decode()
 
     def check_bounded_wait(self) -> int:
         """Status of mcao_check_bounded_wait: 6 (MCAO_E_TIMEOUT) when the device timeouts work."""
