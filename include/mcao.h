@@ -114,8 +114,10 @@ typedef struct {
                                  Strehl / PSF accumulators; geometry and the reconstructor are
                                  shared.  With n_real > 1 one step forms the product for all
                                  realizations at once as a matrix product R S: a bfloat16 R on
-                                 the tensor cores (64 realizations per pass over R), a float32
-                                 R on the CUDA cores (16 per pass); FP8 R needs n_real = 1 */
+                                 the tensor cores (64 realizations per pass over R), an FP8
+                                 E4M3 R there too (its code values, exact in bfloat16, with the
+                                 row scales applied after the sum), a float32 R on the CUDA
+                                 cores (16 per pass) */
 } mcao_config;
 
 /* A periodic n x n phase screen with square samples of pixel_m metres, at altitude alt_m,

@@ -411,7 +411,7 @@ __global__ void tc_split_kernel(const float* __restrict__ slopes_pad, int pad_st
 // partials + beta out (beta = 0: out not read)
 __global__ void tc_reduce_kernel(const float* __restrict__ partial, const int2* __restrict__ cover, long long T, int G,
                                  int KB, int maxseg, int npad, int nb, int r0, int n_cmd, float alpha, float beta,
-                                 float* __restrict__ out) {
+                                 const float* __restrict__ scale, float* __restrict__ out) {
     const long long total = (long long)nb * n_cmd;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -424,6 +424,7 @@ __global__ void tc_reduce_kernel(const float* __restrict__ partial, const int2* 
             const int seg = m - (int)(blo / KB);
             s += partial[((size_t)(blk * maxseg + seg) * npad + b) * kTcM + r];
         }
+        if (scale) s *= scale[row];   // FP8 E4M3: the row's scale times its code-value sum
         float* o = out + (long long)(r0 + b) * n_cmd + row;
         *o = beta == 0.0f ? alpha * s : fmaf(alpha, s, beta * *o);
     }
@@ -450,6 +451,42 @@ __global__ void tc_pack_kernel(const float* __restrict__ src, int rows_in, int l
             if (j + 1 < ld) x1 = src[(long long)row * ld + j + 1];
         }
         dst[i] = bf16x2_rn(x0, x1);
+    }
+}
+
+// FP8 E4M3 R: code = e4m3(fl(R / scale_row)) (round to nearest even, saturating), the stored
+// format's own rule; its value is exact in bfloat16, so the tiles hold the code values and the
+// reduction multiplies each row sum by the row's scale
+__device__ __forceinline__ float e4m3_value(float x, float scale) {
+    const float q = __fdiv_rn(x, scale);
+    uint16_t code;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(code) : "f"(0.0f), "f"(q));
+    uint32_t h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(code));
+    float v;
+    asm("{\n\t.reg .f16 a, b;\n\tmov.b32 {a, b}, %1;\n\tcvt.f32.f16 %0, a;\n\t}" : "=f"(v) : "r"(h2));
+    return v;
+}
+
+__global__ void tc_pack_e4m3_kernel(const float* __restrict__ src, int rows_in, int ld, int rows, int ldb,
+                                    const float* __restrict__ scale, uint32_t* __restrict__ dst) {
+    const int half = ldb / 2;
+    const int KB = ldb / kTcK;
+    const long long total = (long long)rows * half;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long tile = i / (kTcM * (kTcK / 2));
+        const int in_tile = (int)(i - tile * (kTcM * (kTcK / 2)));
+        const int r = in_tile / (kTcK / 2), c2 = in_tile - r * (kTcK / 2);
+        const int m = (int)(tile / KB), kb = (int)(tile - (long long)m * KB);
+        const int row = m * kTcM + r, j = kb * kTcK + 2 * c2;
+        float x0 = 0.0f, x1 = 0.0f;
+        if (row < rows_in) {
+            const float sc = scale[row];
+            if (j < ld) x0 = e4m3_value(src[(long long)row * ld + j], sc);
+            if (j + 1 < ld) x1 = e4m3_value(src[(long long)row * ld + j + 1], sc);
+        }
+        dst[i] = bf16x2_rn(x0, x1);   // exact: an E4M3 value has at most 4 significant bits
     }
 }
 
@@ -490,6 +527,7 @@ struct TcProduct {
     uint16_t* R = nullptr;       // [n_mt][KB][128][64]
     uint16_t* S = nullptr;       // [KB][3][npad][64]
     float* partial = nullptr;    // [G][maxseg][npad][128]
+    float* scale = nullptr;      // [rows]: FP8 E4M3 row scales (null for bfloat16)
     int2* cover = nullptr;       // [n_mt] first and last block of each row tile
     int n_cmd = 0, rows = 0, ld = 0, ldb = 0, n_mt = 0, KB = 0, G = 0, npad = 0, stages = 0, maxseg = 0, nbuf = 0;
     uint32_t tmem_cols = 0;
@@ -503,11 +541,12 @@ void tc_destroy(TcProduct* P) {
     cudaFree(P->S);
     cudaFree(P->partial);
     cudaFree(P->cover);
+    cudaFree(P->scale);
     delete P;
 }
 
-cudaError_t tc_create(const float* R_rm, int rows_in, int ld, int n_cmd, int n_rhs, int sm_count, cudaStream_t st,
-                      TcProduct** out) {
+cudaError_t tc_create(const float* R_rm, int rows_in, int ld, int n_cmd, int n_rhs, int sm_count, int fp8,
+                      cudaStream_t st, TcProduct** out) {
     *out = nullptr;
     if (n_cmd < 1 || ld < 1 || n_rhs < 1 || rows_in < n_cmd) return cudaErrorInvalidValue;
     TcProduct* P = new TcProduct();
@@ -548,7 +587,15 @@ cudaError_t tc_create(const float* R_rm, int rows_in, int ld, int n_cmd, int n_r
     if (e == cudaSuccess) e = cudaMalloc(&P->cover, sizeof(int2) * P->n_mt);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(P->cover, cover.data(), sizeof(int2) * P->n_mt, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && fp8) {
+        e = cudaMalloc(&P->scale, sizeof(float) * (size_t)std::max(P->rows, rows_in));
+        if (e == cudaSuccess) e = launch_recon_scales(R_rm, rows_in, ld, ld, P->scale, st);
+        if (e == cudaSuccess) {
+            tc_pack_e4m3_kernel<<<2048, 256, 0, st>>>(R_rm, rows_in, ld, P->rows, P->ldb, P->scale,
+                                                      reinterpret_cast<uint32_t*>(P->R));
+            e = cudaGetLastError();
+        }
+    } else if (e == cudaSuccess) {
         tc_pack_kernel<<<2048, 256, 0, st>>>(R_rm, rows_in, ld, P->rows, P->ldb, reinterpret_cast<uint32_t*>(P->R));
         e = cudaGetLastError();
     }
@@ -595,7 +642,7 @@ cudaError_t tc_launch(TcProduct* P, const float* slopes_pad, int pad_stride, int
         recon_tc_kernel<<<P->G, kTcThreads, P->smem, st>>>(P->tmA, P->tmB, prm);
         const long long tot = (long long)nb * P->n_cmd;
         tc_reduce_kernel<<<(int)std::min<long long>(4096, (tot + 255) / 256), 256, 0, st>>>(
-            P->partial, P->cover, P->T, P->G, P->KB, P->maxseg, P->npad, nb, r0, P->n_cmd, alpha, beta, out);
+            P->partial, P->cover, P->T, P->G, P->KB, P->maxseg, P->npad, nb, r0, P->n_cmd, alpha, beta, P->scale, out);
         nl += 3;
     }
     if (launches) *launches = nl;

@@ -1226,8 +1226,6 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     if (!S->dms_loaded) return fail(S, MCAO_E_STATE, "load the DMs before the reconstructor");
     if (dtype != MCAO_DTYPE_F32 && dtype != MCAO_DTYPE_BF16 && dtype != MCAO_DTYPE_FP8_E4M3)
         return fail(S, MCAO_E_UNSUPPORTED, "unknown reconstructor dtype %d", dtype);
-    if (S->n_real > 1 && dtype == MCAO_DTYPE_FP8_E4M3)
-        return fail(S, MCAO_E_UNSUPPORTED, "FP8 reconstructors are streamed per realization only (n_real = 1)");
     if (n_cmd != S->n_cmd || n_slopes != S->n_slopes)
         return fail(S, MCAO_E_SHAPE, "reconstructor is %d x %d, configuration needs %d x %d", n_cmd, n_slopes,
                     S->n_cmd, S->n_slopes);
@@ -1283,7 +1281,8 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
             if (e == cudaSuccess)
                 e = dalloc(&S->d_multi_part, (size_t)multi_chunks(S->ld) * kMultiRhs * std::max(n_cmd, 1));
         } else if (e == cudaSuccess && n_cmd > 0) {
-            e = tc_create(tmp, S->rows_pad, S->ld, n_cmd, S->n_real, S->sm_count, S->s0, &S->tc);
+            e = tc_create(tmp, S->rows_pad, S->ld, n_cmd, S->n_real, S->sm_count, dtype == MCAO_DTYPE_FP8_E4M3 ? 1 : 0,
+                          S->s0, &S->tc);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->s0);
         cudaFree(tmp);

@@ -354,12 +354,14 @@ cudaError_t launch_recon_multi(const MultiLaunch& L, int n_real, int pad_stride,
 // batched product for a bfloat16 R on the tensor cores (tcgen05, TMA, TMEM accumulators):
 // out[r][i] = alpha sum_j R[i][j] s_r[j] + beta out[r][i] for every realization r, float32
 // slopes (split exactly into three bfloat16 terms) and float32 accumulation; up to 64
-// realizations per pass over R.  tc_create converts the row-major float32 staging copy
+// realizations per pass over R.  An FP8 E4M3 matrix (fp8 = 1) is stored as its code values
+// (exact in bfloat16) with the per-row scales applied in the reduction: same product, the
+// bytes of bfloat16.  tc_create converts the row-major float32 staging copy
 // [rows_in][ld] (rows_in >= n_cmd) once and sizes the kernel for n_rhs realizations (outside
 // stream capture); tc_launch queues the split, product and reduction kernels of every pass.
 struct TcProduct;
-cudaError_t tc_create(const float* R_rm, int rows_in, int ld, int n_cmd, int n_rhs, int sm_count, cudaStream_t st,
-                      TcProduct** out);
+cudaError_t tc_create(const float* R_rm, int rows_in, int ld, int n_cmd, int n_rhs, int sm_count, int fp8,
+                      cudaStream_t st, TcProduct** out);
 void tc_destroy(TcProduct* P);
 cudaError_t tc_launch(TcProduct* P, const float* slopes_pad, int pad_stride, int n_real, float alpha, float beta,
                       float* out, int* err, int chunk, cudaStream_t st, int* launches);

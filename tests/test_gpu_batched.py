@@ -251,3 +251,44 @@ def test_reconstruct_batch_checks_its_arguments():
     one = mcao.make_sim(cfg, inputs.make_screens(cfg), R)
     with pytest.raises(mcao.McaoError):
         one.reconstruct_batch(torch.zeros((1, 416), device="cuda"))
+
+
+def test_batched_product_fp8_full_size_matches_oracle_dequantized():
+    """FP8 E4M3 R in the batched product (code values on the tensor cores, row scales after the
+    sum), 17 realizations at the 39 m size, against float64 products of the oracle's own
+    quantization of R (codes and per-row scales): every element within 1e-5 |R_i||s_r|."""
+    import torch
+    cfg, _, n_cmd = eelt_inputs(10)
+    g = torch.Generator(device="cuda").manual_seed(71)
+    R = torch.randn((n_cmd, 55608), generator=g, device="cuda", dtype=torch.float32) * 0.01
+    sim = mcao.Sim(cfg, n_real=17)
+    sim.load_dms()
+    sim.load_reconstructor(R, dtype=mcao.DTYPE_FP8_E4M3)
+    codes, scales = oracle.quantize_rows(R.cpu().numpy(), oracle.DTYPE_FP8_E4M3)
+    Rq = torch.from_numpy(oracle.dequantize_rows(codes, scales, oracle.DTYPE_FP8_E4M3)).cuda()
+    del codes
+    S = torch.randn((17, 55608), generator=g, device="cuda", dtype=torch.float32)
+    D = sim.reconstruct_batch(S).double()
+    ref = S.double() @ Rq.double().t()
+    bound = 1e-5 * S.double().norm(dim=1)[:, None] * Rq.double().norm(dim=1)[None, :]
+    assert bool(((D - ref).abs() <= bound).all())
+    assert float((D - ref).norm() / ref.norm()) <= 1e-5
+
+
+def test_batched_fp8_loop_17_realizations_matches_oracle_fp8():
+    """17 realizations with an FP8 E4M3 R, every realization against the oracle's FP8 variant
+    (the represented values scale x code, float slopes, double product) at the float32
+    tolerances."""
+    cfg, _, R = scao_tiny_inputs()
+    n = 17
+    g, screens = _batch(cfg, R, n, r_dtype=mcao.DTYPE_FP8_E4M3)
+    orc = [oracle.Sim(dict(cfg, seed=cfg["seed"] + r), screens[r], R, r_dtype=oracle.DTYPE_FP8_E4M3)
+           for r in range(n)]
+    g.step(50)
+    for o in orc:
+        o.step(50)
+    for r in range(n):
+        g.set_realization(r)
+        assert _rms(g.slopes() - orc[r].slopes()) <= 1e-4, r
+        cg, co = g.commands(), orc[r].commands()
+        assert np.linalg.norm(cg - co) / np.linalg.norm(co) <= 1e-5, r
