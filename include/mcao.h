@@ -515,8 +515,10 @@ enum {
     MCAO_STAGE_DM = 0,          /* DM surfaces                                                  */
     MCAO_STAGE_WFS_MAIN = 1,    /* wavefront-sensor kernel of the largest group (laser stars)   */
     MCAO_STAGE_WFS_AUX = 2,     /* other wavefront-sensor kernels (concurrent stream)           */
-    MCAO_STAGE_RECON = 3,       /* reconstructor product R s                                    */
-    MCAO_STAGE_RECON_REDUCE = 4,/* partial-sum reduction and integrator                         */
+    MCAO_STAGE_RECON = 3,       /* reconstructor product R s; in a single-realization step the  */
+                                /* last slice also sums the partials and applies the integrator */
+    MCAO_STAGE_RECON_REDUCE = 4,/* separate partial-sum reduction (recorded only when no slice  */
+                                /* carries it)                                                  */
     MCAO_STAGE_SCIENCE = 5,     /* science field, Strehl and PSF (concurrent stream)            */
     MCAO_N_STAGES = 6
 };

@@ -233,6 +233,41 @@ __device__ __forceinline__ void stage_fma(const uint4 (&rv)[kTmaSeg / 32][kTmaRo
     }
 }
 
+// c += g sum_k partial[k][row] for one row: eight lanes per row (m = 0..7, consecutive lanes of
+// one warp), lane m adds slots m, m + 8, ... (all its loads in flight at once), then a fixed
+// shuffle tree; deterministic.  With the second-order controller:
+// c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1}.  Without partials the update is read
+// from dc_in (batched product).  The partials are read from L2 (written by other SMs in the same
+// launch when the last slice applies the update).  Every lane of the warp must call it.
+__device__ __forceinline__ void reduce_row(const ReduceLaunch& L, long long row, int m, long long n_rows) {
+    float a = 0.0f;
+    if (row < n_rows) {
+        if (L.partial) {
+#pragma unroll 4
+            for (int k = m; k < L.n_chunks; k += 8) a += __ldcg(L.partial + (size_t)k * L.n_cmd + row);
+        } else if (m == 0) {
+            a = L.dc_in[row];
+        }
+    }
+    a += __shfl_xor_sync(0xffffffffu, a, 4);
+    a += __shfl_xor_sync(0xffffffffu, a, 2);
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    if (m == 0 && row < n_rows) {
+        if (!L.use_ctl) {
+            L.c[row] = fmaf(L.gain, a, L.c[row]);
+        } else {
+            const float c0 = L.c[row];
+            float cn = L.a1 * c0;
+            cn = fmaf(L.a2, L.c_prev[row], cn);
+            cn = fmaf(L.b0, a, cn);
+            cn = fmaf(L.b1, L.dc_prev[row], cn);
+            L.c_prev[row] = c0;
+            L.dc_prev[row] = a;
+            L.c[row] = cn;
+        }
+    }
+}
+
 // Work items i = kc * n_rq + rq (row quad rq, chunk kc) are handed out one at a time by the
 // slice's counter (zero when the step starts), so blocks that become resident late -- the
 // sensing kernels share the SMs -- take only what is left.  Lane 0 of each warp is the producer:
@@ -354,6 +389,22 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
             for (int q = 0; q < kTmaRows; ++q)
                 if (row0 + q < L.n_cmd) out[row0 + q] = DT == kReconE4M3 ? acc[q] * L.scale[row0 + q] : acc[q];
         }
+        if (L.fuse_reduce) {
+            // arrival of chunk kc of row quad rq (the fence publishes its partials first); the
+            // last of the slice's chunks to arrive applies the update of the quad's four rows
+            // (lanes 8 q .. 8 q + 7 row q), every other slice's partials being complete already
+            unsigned int arrived = 0;
+            if (lane == 0) {
+                __threadfence();
+                arrived = atomicAdd(L.rq_done + rq, 1u);
+            }
+            arrived = __shfl_sync(0xffffffffu, arrived, 0);
+            if (arrived == (unsigned int)(g.n_chunks - 1)) {
+                __threadfence();
+                if (rq == 0 && lane == 0 && L.red.st) L.red.st->k_next = L.red.st->k + 1;
+                reduce_row(L.red, (long long)rq * kTmaRows + (lane >> 3), lane & 7, L.n_cmd);
+            }
+        }
     }
 }
 
@@ -446,42 +497,12 @@ __global__ void quantize_rows_kernel(const float* __restrict__ src, int rows, in
     }
 }
 
-// c += g sum_k partial[k][row]: eight lanes per row, lane m adds slots m, m + 8, ... (all its
-// loads in flight at once), then a fixed shuffle tree; deterministic.  With the second-order
-// controller: c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1}.  Without partials the
-// update is read from dc_in (batched product), for every realization.
+// the update as a kernel of its own: eight lanes per row (reduce_row); the step counter
 __global__ void recon_reduce_kernel(ReduceLaunch L) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0 && L.st) L.st->k_next = L.st->k + 1;
-    const long long row = t >> 3;
-    const int m = (int)(t & 7);
     const long long n_rows = (long long)L.n_cmd * (L.partial ? 1 : L.n_real);
-    float a = 0.0f;
-    if (row < n_rows) {
-        if (L.partial) {
-#pragma unroll 4
-            for (int k = m; k < L.n_chunks; k += 8) a += L.partial[(size_t)k * L.n_cmd + row];
-        } else if (m == 0) {
-            a = L.dc_in[row];
-        }
-    }
-    a += __shfl_xor_sync(0xffffffffu, a, 4);
-    a += __shfl_xor_sync(0xffffffffu, a, 2);
-    a += __shfl_xor_sync(0xffffffffu, a, 1);
-    if (m == 0 && row < n_rows) {
-        if (!L.use_ctl) {
-            L.c[row] = fmaf(L.gain, a, L.c[row]);
-        } else {
-            const float c0 = L.c[row];
-            float cn = L.a1 * c0;
-            cn = fmaf(L.a2, L.c_prev[row], cn);
-            cn = fmaf(L.b0, a, cn);
-            cn = fmaf(L.b1, L.dc_prev[row], cn);
-            L.c_prev[row] = c0;
-            L.dc_prev[row] = a;
-            L.c[row] = cn;
-        }
-    }
+    reduce_row(L, t >> 3, (int)(t & 7), n_rows);
 }
 
 // transpose of a row-major float32 [rows][cols] into [cols][ld_out] (float32 or bfloat16),

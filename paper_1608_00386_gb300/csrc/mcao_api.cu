@@ -136,6 +136,7 @@ struct mcao_sim {
     int rows_pad = 0;
     float* d_c = nullptr;
     float* d_partial = nullptr;
+    unsigned int* d_rq_done = nullptr;   // [rows_pad / 4] row-quad arrival counters of the last slice
     // second-order controller (off: the pure integrator of gain cfg.gain)
     bool use_ctl = false;
     float ctl[4] = {1.0f, 0.0f, 0.0f, 0.0f};
@@ -301,6 +302,8 @@ DmLaunch make_dm_launch(mcao_sim* S) {
     L.st = S->d_st;
     L.work = S->d_work;
     L.n_work = (int)(S->wfs.size() + S->slices.size());
+    L.rq_done = S->d_rq_done;
+    L.n_rq = S->d_rq_done ? S->rows_pad / kReconRows : 0;
     return L;
 }
 
@@ -561,7 +564,13 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         return cudaSuccess;
     }
 
-    // reconstructor slices on s3, each after its sensor, then the reduction
+    // reconstructor slices on s3, each after its sensor; the last one also applies the update
+    ReduceLaunch rl{S->n_cmd, S->n_chunks, S->d_partial, S->d_c, (float)S->cfg.gain, S->d_st};
+    rl.use_ctl = S->use_ctl;
+    rl.a1 = S->ctl[0]; rl.a2 = S->ctl[1]; rl.b0 = S->ctl[2]; rl.b1 = S->ctl[3];
+    rl.c_prev = S->d_c_prev;
+    rl.dc_prev = S->d_dc_prev;
+    rl.n_real = 1;
     for (size_t i = 0; i < S->slices.size(); ++i) {
         cudaEvent_t last = nullptr;
         for (int w : S->slice_wfs[i]) {
@@ -572,20 +581,22 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         slot = prof_begin(S, ST_RECON, S->s3);
         ReconLaunch rl_i = S->slices[i];
         rl_i.max_ctas = std::max(1, S->sm_count * S->tune.recon_ctas_pct / 100);
+        if (i + 1 == S->slices.size()) {
+            rl_i.fuse_reduce = 1;
+            rl_i.rq_done = S->d_rq_done;
+            rl_i.red = rl;
+        }
         if ((e = launch_recon(rl_i, S->s3)) != cudaSuccess) return e;
         prof_end(S, slot, S->s3);
         ++nl;
     }
-    ReduceLaunch rl{S->n_cmd, S->n_chunks, S->d_partial, S->d_c, (float)S->cfg.gain, S->d_st};
-    rl.use_ctl = S->use_ctl;
-    rl.a1 = S->ctl[0]; rl.a2 = S->ctl[1]; rl.b0 = S->ctl[2]; rl.b1 = S->ctl[3];
-    rl.c_prev = S->d_c_prev;
-    rl.dc_prev = S->d_dc_prev;
-    rl.n_real = 1;
-    slot = prof_begin(S, ST_REDUCE, S->s3);
-    if ((e = launch_recon_reduce(rl, S->s3)) != cudaSuccess) return e;
-    prof_end(S, slot, S->s3);
-    ++nl;
+    if (S->slices.empty()) {
+        // no slice to carry it (never the case with a loaded reconstructor): the step counter alone
+        slot = prof_begin(S, ST_REDUCE, S->s3);
+        if ((e = launch_recon_reduce(rl, S->s3)) != cudaSuccess) return e;
+        prof_end(S, slot, S->s3);
+        ++nl;
+    }
 
     // join every branch back into s0
     cudaEvent_t ev_gemv = dep_event(S, used);
@@ -680,6 +691,7 @@ void destroy_all(mcao_sim* S) {
     S->d_layer_owned.clear();
     dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
     dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_rscale); dfree(S->d_c); dfree(S->d_partial);
+    dfree(S->d_rq_done);
     dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err); dfree(S->d_work); dfree(S->d_sr_out);
     dfree(S->d_Rrm);
     dfree(S->d_c_prev); dfree(S->d_dc_prev); dfree(S->d_dc);
@@ -1160,7 +1172,7 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     CK(cudaSetDevice(S->device));
     { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
-    dfree(S->d_dm_surf); dfree(S->d_c); dfree(S->d_partial);
+    dfree(S->d_dm_surf); dfree(S->d_c); dfree(S->d_partial); dfree(S->d_rq_done);
     S->dms_loaded = false;
     S->recon_loaded = false;  // command count may change
     S->dms.assign(dms, dms + n_dms);
@@ -1236,6 +1248,7 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     dfree(S->d_R);
     dfree(S->d_rscale);
     dfree(S->d_partial);
+    dfree(S->d_rq_done);
     S->r_dtype = dtype;
     S->recon_loaded = false;
     S->rows_pad = std::max(1, (n_cmd + kReconRowBlock - 1) / kReconRowBlock) * kReconRowBlock;
@@ -1375,6 +1388,8 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     S->n_chunks = chunks;
     CK(dalloc(&S->d_partial, (size_t)std::max(chunks, 1) * std::max(n_cmd, 1)));
     for (auto& L : S->slices) L.partial = S->d_partial;
+    CK(dalloc(&S->d_rq_done, (size_t)(S->rows_pad / kReconRows)));
+    CK(cudaMemsetAsync(S->d_rq_done, 0, sizeof(unsigned int) * (size_t)(S->rows_pad / kReconRows), S->s0));
     if (s_ref)
         CK(cudaMemcpyAsync(S->d_sref, s_ref, sizeof(float) * n_slopes, kind, S->s0));
     else

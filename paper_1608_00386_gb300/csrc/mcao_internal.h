@@ -138,9 +138,12 @@ struct DmLaunch {
     StepState* st;           // begin of step: k = k_next
     unsigned int* work;      // begin of step: the sensing kernels' work counters are zeroed
     int n_work;
+    unsigned int* rq_done;   // begin of step: the product's row-quad arrival counters are zeroed
+    int n_rq;
 };
 cudaError_t launch_dm_surfaces(const DmLaunch& L, cudaStream_t s);
-cudaError_t launch_begin_step(StepState* st, unsigned int* work, int n_work, cudaStream_t s);
+cudaError_t launch_begin_step(StepState* st, unsigned int* work, int n_work, unsigned int* rq_done, int n_rq,
+                              cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------
 // wavefront sensors
@@ -191,6 +194,23 @@ __host__ __device__ constexpr int recon_esize(int dtype) { return dtype == kReco
 // stage; nv = the chunk's 16-byte vector count per row) holds its 4 row segments back to back,
 // so every stage is one contiguous bulk copy of up to 8 KB.  The host picks the chunk width so
 // that a chunk's last stage is not tiny (at least half a stage where it can).
+struct ReduceLaunch {
+    int n_cmd, n_chunks;
+    const float* partial;   // [n_chunks][n_cmd], or null: the update is dc_in
+    float* c;
+    float gain;
+    StepState* st;      // k_next = k + 1 (may be null)
+    // second-order controller c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1} (when set;
+    // otherwise the pure integrator c += gain dc), over n_real realizations of n_cmd commands
+    int use_ctl;
+    float a1, a2, b0, b1;
+    float* c_prev;
+    float* dc_prev;
+    const float* dc_in;  // [n_real][n_cmd] update (batched product), used when partial is null
+    int n_real;
+};
+cudaError_t launch_recon_reduce(const ReduceLaunch& L, cudaStream_t s);
+
 struct ReconLaunch {
     const unsigned char* R;   // stage-tiled reconstructor
     long long base;     // first byte of this slice in R
@@ -206,6 +226,12 @@ struct ReconLaunch {
     int max_ctas;       // grid size cap (0: enough blocks for every item)
     unsigned int* work; // item counter, zero when the launch starts
     int* err;           // set to a nonzero code if a bounded wait gives up
+    // The step's last slice also applies the update (fuse_reduce != 0): per row quad, the item
+    // that completes it last (rq_done[rq] counts the slice's finished chunks of the quad, zero
+    // when the launch starts) adds every partial of its rows exactly as recon_reduce_kernel does.
+    int fuse_reduce;
+    unsigned int* rq_done;   // [n_rq]
+    ReduceLaunch red;        // the update (partial = this launch's partial, n_real = 1)
 };
 constexpr int kReconRows = 4;        // rows per work item (row quad)
 constexpr int kReconSeg = 128;       // 16-byte vectors per row and stage (at most)
@@ -224,22 +250,6 @@ cudaError_t launch_quantize_rows(const float* src, int rows, int cols, int ld, i
                                  const float* scale, cudaStream_t s);
 constexpr int kErrReconTimeout = 1;
 
-struct ReduceLaunch {
-    int n_cmd, n_chunks;
-    const float* partial;   // [n_chunks][n_cmd], or null: the update is dc_in
-    float* c;
-    float gain;
-    StepState* st;      // k_next = k + 1 (may be null)
-    // second-order controller c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1} (when set;
-    // otherwise the pure integrator c += gain dc), over n_real realizations of n_cmd commands
-    int use_ctl;
-    float a1, a2, b0, b1;
-    float* c_prev;
-    float* dc_prev;
-    const float* dc_in;  // [n_real][n_cmd] update (batched product), used when partial is null
-    int n_real;
-};
-cudaError_t launch_recon_reduce(const ReduceLaunch& L, cudaStream_t s);
 // row-major float32 [rows][cols] -> [cols][ld_out] (float32, or bfloat16 codes when bf16 != 0);
 // rows >= ld_out are not read, rows in [rows, ld_out) are written as zeros
 cudaError_t launch_transpose(const float* src, int rows, int cols, void* out, int ld_out, int bf16, cudaStream_t st);
