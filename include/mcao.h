@@ -479,6 +479,9 @@ mcao_status mcao_tikhonov_reconstructor(const float* D, int n_slopes, int n_cmd,
  *   MCAO_TUNE_TC_CHUNK             tensor-core batched product: k-blocks per TMEM accumulator,
  *                                  [1, 64] (8)
  *   MCAO_TUNE_MULTI_BLOCKS_PER_SM  batched float32 product: blocks per SM, [1, 2] (2)
+ *   MCAO_TUNE_STEPS_PER_GRAPH      steps captured in one CUDA graph, [1, 16] (1): mcao_step(n)
+ *                                  launches it n / k times, then the one-step graph n % k times
+ *                                  (always the one-step graph while the stage profiler is on)
  * No counterpart in the paper.  Results do not depend on them, except MCAO_TUNE_TC_CHUNK, which
  * regroups the tensor-core product's float32 sums (float32 rounding only). */
 enum {
@@ -487,7 +490,8 @@ enum {
     MCAO_TUNE_SCIENCE_AFTER_AUX = 2,
     MCAO_TUNE_TC_CHUNK = 3,
     MCAO_TUNE_MULTI_BLOCKS_PER_SM = 4,
-    MCAO_N_TUNE = 5
+    MCAO_TUNE_STEPS_PER_GRAPH = 5,
+    MCAO_N_TUNE = 6
 };
 
 /* Current launch shapes into values[MCAO_N_TUNE] (n >= MCAO_N_TUNE, else MCAO_E_INVALID_ARG). */
@@ -499,7 +503,8 @@ mcao_status mcao_set_tuning(mcao_sim* sim, const int* values, int n);
 
 /* Autotuner: for each launch shape that applies to this configuration (the sensing grid when it
  * has warp-per-subaperture sensors, the slices' grid without batching, the science ordering when
- * it has block-per-subaperture sensors, the batched products' shapes with batching), in that order,
+ * it has block-per-subaperture sensors, the batched products' shapes with batching, the steps per
+ * graph among 1, 2, 4 and 8), in that order,
  * time steps_per_trial steps (after 2 warm-up steps) for every candidate value with the others
  * held at their best so far, and keep the fastest (coordinate descent, CUDA events on the device).
  * The trials advance the simulation; its state is saved first and restored at the end (as

@@ -118,6 +118,7 @@ struct mcao_sim {
     std::vector<std::array<double, 4>> dm_misreg;   // per DM: shift x, y (m), rotation (rad), magnification
     DmDesc* d_dm_desc = nullptr;
     float* d_dm_g = nullptr;
+    int dm_nb = 1;                        // largest actuator band of a 64 x 64 DM block (either axis)
     int2* d_dm_band = nullptr;
     int* d_dm_map = nullptr;
     float* d_dm_surf = nullptr;
@@ -165,6 +166,11 @@ struct mcao_sim {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_dirty = true;
+    bool graph_prof = false;              // the built graphs hold the profiler's event-record nodes
+    bool capture_prof = false;            // set while a profiled step is captured
+    cudaGraph_t graph_k = nullptr;        // tune.steps_per_graph steps in one graph (profiler off)
+    cudaGraphExec_t exec_k = nullptr;
+    int graph_k_steps = 0;
     std::vector<ProfSlot> prof_slots;
     bool profiling = false;
     std::vector<cudaEvent_t> prof_pool;
@@ -261,8 +267,13 @@ std::vector<int> factor_fft(int M) {
 void release_graph(mcao_sim* S) {
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->graph) cudaGraphDestroy(S->graph);
+    if (S->exec_k) cudaGraphExecDestroy(S->exec_k);
+    if (S->graph_k) cudaGraphDestroy(S->graph_k);
     S->exec = nullptr;
     S->graph = nullptr;
+    S->exec_k = nullptr;
+    S->graph_k = nullptr;
+    S->graph_k_steps = 0;
     S->graph_dirty = true;
     for (auto& p : S->prof_slots) {
         if (p.tpl_a) cudaEventDestroy(p.tpl_a);
@@ -289,7 +300,8 @@ Ctx make_ctx(mcao_sim* S) {
 DmLaunch make_dm_launch(mcao_sim* S) {
     DmLaunch L{};
     L.n_dm = S->n_dms;
-    L.desc = S->d_dm_desc;
+    for (int m = 0; m < S->n_dms && m < kMaxDms; ++m) L.desc[m] = S->dm_desc[m];
+    L.nb = S->dm_nb;
     L.g = S->d_dm_g;
     L.band = S->d_dm_band;
     L.act_map = S->d_dm_map;
@@ -424,9 +436,10 @@ cudaEvent_t dep_event(mcao_sim* S, size_t& used) {
     return S->ev_pool[used++];
 }
 
-// profiling: an event-record node before and after a launch (recorded into per-step events
-// only while profiling is on)
+// profiling: an event-record node before and after a launch, present only in graphs captured
+// with the profiler on (each node is a dependency hop between the kernels it separates)
 int prof_begin(mcao_sim* S, int stage, cudaStream_t st) {
+    if (!S->capture_prof) return -1;
     ProfSlot p;
     p.stage = stage;
     cudaEventCreate(&p.tpl_a);
@@ -437,6 +450,7 @@ int prof_begin(mcao_sim* S, int stage, cudaStream_t st) {
 }
 
 void prof_end(mcao_sim* S, int slot, cudaStream_t st) {
+    if (slot < 0) return;
     cudaEventRecordWithFlags(S->prof_slots[slot].tpl_b, st, cudaEventRecordExternal);
 }
 
@@ -609,11 +623,11 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
     return cudaSuccess;
 }
 
-mcao_status build_graph(mcao_sim* S) {
-    release_graph(S);
+// capture n consecutive steps into one graph (the streams join back into s0 after each step)
+static mcao_status capture_steps(mcao_sim* S, int n, cudaGraph_t* out, int* launches) {
     CK(cudaStreamBeginCapture(S->s0, cudaStreamCaptureModeThreadLocal));
-    int nl = 0;
-    cudaError_t e = enqueue_step(S, &nl);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = enqueue_step(S, launches);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(S->s0, &g);
     if (e != cudaSuccess) {
@@ -621,7 +635,18 @@ mcao_status build_graph(mcao_sim* S) {
         return fail(S, MCAO_E_CUDA, "step capture: %s", cudaGetErrorString(e));
     }
     if (e2 != cudaSuccess) return fail(S, MCAO_E_CUDA, "end capture: %s", cudaGetErrorString(e2));
-    S->graph = g;
+    *out = g;
+    return MCAO_OK;
+}
+
+mcao_status build_graph(mcao_sim* S) {
+    release_graph(S);
+    int nl = 0;
+    S->capture_prof = S->profiling;
+    mcao_status r = capture_steps(S, 1, &S->graph, &nl);
+    S->capture_prof = false;
+    if (r != MCAO_OK) return r;
+    S->graph_prof = S->profiling;
     CK(cudaGraphInstantiate(&S->exec, S->graph, cudaGraphInstantiateFlagUseNodePriority));
     // locate the profiling event-record nodes
     size_t n = 0;
@@ -640,6 +665,15 @@ mcao_status build_graph(mcao_sim* S) {
         }
     }
     S->launches_per_step = nl;
+    // several steps per graph launch when the profiler is off: the steps inside one graph follow
+    // one another through plain graph edges instead of a graph launch boundary each
+    if (!S->profiling && S->tune.steps_per_graph > 1) {
+        int nk = 0;
+        r = capture_steps(S, S->tune.steps_per_graph, &S->graph_k, &nk);
+        if (r != MCAO_OK) return r;
+        CK(cudaGraphInstantiate(&S->exec_k, S->graph_k, cudaGraphInstantiateFlagUseNodePriority));
+        S->graph_k_steps = S->tune.steps_per_graph;
+    }
     S->graph_dirty = false;
     return MCAO_OK;
 }
@@ -1065,6 +1099,7 @@ mcao_status mcao_load_atmosphere(mcao_sim* S, int n_layers, const mcao_layer* la
 static mcao_status build_dm_tables(mcao_sim* S, std::vector<float>& g, std::vector<int2>& band) {
     g.clear();
     band.clear();
+    S->dm_nb = 1;
     for (int m = 0; m < S->n_dms; ++m) {
         const mcao_dm& d = S->dms[m];
         DmDesc& D = S->dm_desc[m];
@@ -1099,6 +1134,27 @@ static mcao_status build_dm_tables(mcao_sim* S, std::vector<float>& g, std::vect
         // with rotation the tables describe the unrotated DM (kept for the band sizes only)
         D.gx_off = table(d.nx, D.general ? 0.0 : T[0], D.tband_x);
         D.gy_off = table(d.ny, D.general ? 0.0 : T[1], D.tband_y);
+        // the same tables transposed ([actuator][sample]) for the forward kernel's staging
+        auto transposed = [&](long long off, int na) {
+            const long long toff = (long long)g.size();
+            for (int a = 0; a < na; ++a)
+                for (int i = 0; i < d.surf_n; ++i) {
+                    const float v = g[off + (long long)i * na + a];
+                    g.push_back(v);
+                }
+            return toff;
+        };
+        D.gxt_off = transposed(D.gx_off, d.nx);
+        D.gyt_off = transposed(D.gy_off, d.ny);
+        // block bands (union of two tiles' bands): the forward kernel's shared memory
+        for (long long tb : {D.tband_x, D.tband_y})
+            for (int t = 0; t < (D.tiles_x + 1) / 2; ++t) {
+                const int2 a = band[tb + 2 * t];
+                const int2 b = 2 * t + 1 < D.tiles_x ? band[tb + 2 * t + 1] : make_int2(0, 0);
+                int w = std::max(a.y - a.x, b.y - b.x);
+                if (a.y > a.x && b.y > b.x) w = std::max(a.y, b.y) - std::min(a.x, b.x);
+                S->dm_nb = std::max(S->dm_nb, w);
+            }
         if (!D.general)
             for (int t = 0; t < 2 * D.tiles_x; ++t) {
                 int2 b = band[(t < D.tiles_x ? D.tband_x : D.tband_y) + t % D.tiles_x];
@@ -1142,6 +1198,7 @@ mcao_status mcao_set_misregistration(mcao_sim* S, int dm, double shift_x, double
         return r;
     }
     release_graph(S);
+    CK(dm_prepare());
     dfree(S->d_dm_g);
     dfree(S->d_dm_band);
     CK(dalloc(&S->d_dm_g, g.size()));
@@ -1200,13 +1257,14 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
         D.surf_off = surf_total;
         surf_total += (long long)d.surf_n * d.surf_n;
         S->dm_tile_start[m] = tiles;
-        tiles += D.tiles_x * D.tiles_x;
+        tiles += ((D.tiles_x + 1) / 2) * ((D.tiles_x + 1) / 2);   // 64 x 64 blocks
         S->dm_desc.push_back(D);
     }
     for (int m = n_dms; m <= kMaxDms; ++m) S->dm_tile_start[m] = tiles;
     S->n_cmd = ncmd;
     S->dm_misreg.assign(n_dms, {0.0, 0.0, 0.0, 1.0});
     { mcao_status r_ = build_dm_tables(S, g, band); if (r_ != MCAO_OK) return r_; }
+    CK(dm_prepare());
     CK(dalloc(&S->d_dm_desc, S->dm_desc.size()));
     if (n_dms) CK(cudaMemcpyAsync(S->d_dm_desc, S->dm_desc.data(), sizeof(DmDesc) * n_dms, cudaMemcpyHostToDevice, S->s0));
     CK(dalloc(&S->d_dm_g, g.size()));
@@ -1406,13 +1464,16 @@ mcao_status mcao_step(mcao_sim* S, int n_steps) {
         return fail(S, MCAO_E_STATE, "load the atmosphere, the DMs and the reconstructor before stepping");
     if (n_steps == 0) return MCAO_OK;
     CK(cudaSetDevice(S->device));
-    if (S->graph_dirty) {
+    if (S->graph_dirty || S->graph_prof != S->profiling) {
         mcao_status r = build_graph(S);
         if (r != MCAO_OK) return r;
     }
     mcao_status r = order_after_user(S);
     if (r != MCAO_OK) return r;
-    for (int i = 0; i < n_steps; ++i) {
+    int i = 0;
+    if (S->graph_k_steps > 1)
+        for (; i + S->graph_k_steps <= n_steps; i += S->graph_k_steps) CK(cudaGraphLaunch(S->exec_k, S->s0));
+    for (; i < n_steps; ++i) {
         if (S->profiling) {
             S->prof_step_begin.push_back(S->prof_records.size());
             for (const auto& p : S->prof_slots) {
@@ -1452,7 +1513,7 @@ mcao_status mcao_step_group(mcao_sim* const* sims, int n_sims, int n_steps) {
     mcao_sim* S = sims[0];   // its s0 carries the group launches
     CK(cudaSetDevice(S->device));
     for (int i = 0; i < n_sims; ++i) {
-        if (sims[i]->graph_dirty) {
+        if (sims[i]->graph_dirty || sims[i]->graph_prof) {
             mcao_status r = build_graph(sims[i]);
             if (r != MCAO_OK) return r;
         }
@@ -1731,8 +1792,8 @@ static mcao_status run_adjoint(mcao_sim* S, float* D, long long ld, const float*
 // ------------------------------------------------------------------------------------------
 // launch-shape tuning
 // ------------------------------------------------------------------------------------------
-static const int kTuneMin[kTuningKnobs] = {1, 25, 0, 1, 1};
-static const int kTuneMax[kTuningKnobs] = {8, 400, 1, 64, 2};
+static const int kTuneMin[kTuningKnobs] = {1, 25, 0, 1, 1, 1};
+static const int kTuneMax[kTuningKnobs] = {8, 400, 1, 64, 2, 16};
 
 static void tuning_to(const Tuning& t, int* v) {
     v[0] = t.sense_blocks_per_sm;
@@ -1740,6 +1801,7 @@ static void tuning_to(const Tuning& t, int* v) {
     v[2] = t.science_after_aux;
     v[3] = t.tc_chunk;
     v[4] = t.multi_blocks_per_sm;
+    v[5] = t.steps_per_graph;
 }
 
 static Tuning tuning_from(const int* v) {
@@ -1749,6 +1811,7 @@ static Tuning tuning_from(const int* v) {
     t.science_after_aux = v[2];
     t.tc_chunk = v[3];
     t.multi_blocks_per_sm = v[4];
+    t.steps_per_graph = v[5];
     return t;
 }
 
@@ -1815,10 +1878,11 @@ mcao_status mcao_autotune(mcao_sim* S, int steps_per_trial, int* values, int n, 
     if (!S->sci.empty() && fft) knobs.push_back({2, {0, 1}});
     if (batched && S->tc) knobs.push_back({3, {4, 8, 16}});
     if (batched && !S->tc) knobs.push_back({4, {1, 2}});
+    knobs.push_back({5, {1, 2, 4, 8}});
     int cur[kTuningKnobs];
     tuning_to(S->tune, cur);
     const char* names[kTuningKnobs] = {"sense_blocks_per_sm", "recon_ctas_pct", "science_after_aux", "tc_chunk",
-                                       "multi_blocks_per_sm"};
+                                       "multi_blocks_per_sm", "steps_per_graph"};
     std::string rep;
     float best_ms = 0.0f;
     r = trial(best_ms);

@@ -19,8 +19,9 @@ struct Tuning {
     int science_after_aux = 1;      // science waits for the block-per-subaperture sensors
     int tc_chunk = 8;               // tensor-core product: k-blocks per TMEM accumulator
     int multi_blocks_per_sm = 2;    // batched float32 product: blocks per SM
+    int steps_per_graph = 1;        // steps captured in one graph launch (stage profiler off)
 };
-constexpr int kTuningKnobs = 5;
+constexpr int kTuningKnobs = 6;
 constexpr int kMaxNpx = 32;       // pupil samples per subaperture side
 constexpr int kMaxNd = 32;        // detector pixels per subaperture side
 constexpr int kMaxDms = 4;
@@ -100,12 +101,15 @@ struct Ctx {
 // DM surfaces
 // ---------------------------------------------------------------------------------------------
 // One DM in the concatenated DM buffers.  S = Gy C Gx^T (the Gaussian influence function
-// factorises in x and y), evaluated per 32 x 32 surface tile over the actuators whose weight on
-// the tile is at least 1e-10.
+// factorises in x and y), evaluated per 64 x 64 block of the surface over the actuators whose
+// weight on the block is at least 1e-10 (the bands are kept per 32-sample tile, the granularity
+// the adjoint uses; a block takes the union of its two tiles' bands per axis).
 struct DmDesc {
     int nx, ny, surf_n, tiles_x;   // tiles_x: 32-sample tiles per side of the surface
     long long gx_off;    // Gx [surf_n][nx] in the table buffer
     long long gy_off;    // Gy [surf_n][ny]
+    long long gxt_off;   // Gx transposed, [nx][surf_n]
+    long long gyt_off;   // Gy transposed, [ny][surf_n]
     long long tband_x;   // per 32-column tile: actuator columns [lo, hi) in the band buffer
     long long tband_y;   // per 32-row tile: actuator rows [lo, hi)
     long long map_off;   // act_map [ny][nx]: command index or -1
@@ -122,16 +126,21 @@ struct DmDesc {
 };
 constexpr int kDmTile = 32;
 constexpr int kDmMaxBand = 64;   // actuators per tile and axis (checked on the host)
+constexpr int kDmBlock = 2 * kDmTile;   // surface samples per side of one block of the DM kernel
+// shared memory of the DM kernel for blocks of at most nb actuators per axis
+size_t dm_smem_bytes(int nb);
+cudaError_t dm_prepare();   // kernel attribute admitting any block band <= 2 kDmMaxBand (outside capture)
 
 struct DmLaunch {
     int n_dm;
-    const DmDesc* desc;      // [n_dm] device
+    DmDesc desc[kMaxDms];    // by value: read from the parameter bank, no dependent load
+    int nb;                  // largest actuator band of a block on either axis (shared memory)
     const float* g;          // Gaussian tables
     const int2* band;        // tile bands
     const int* act_map;      // actuator maps
     const float* c;          // commands
     float* surf;             // surfaces
-    int tile_start[kMaxDms + 1];    // per-DM prefix of 32 x 32 surface tiles
+    int tile_start[kMaxDms + 1];    // per-DM prefix of 64 x 64 surface blocks
     int n_real;              // realizations (grid y): commands c + r n_cmd, surfaces surf + r surf_stride
     int n_cmd;
     long long surf_stride;

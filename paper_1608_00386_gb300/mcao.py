@@ -343,7 +343,8 @@ class Sim:
                                                     C.byref(cost), C.byref(msq)))
         return np.array(JtJ[:]).reshape(4, 4), np.array(Jte[:]), cost.value, msq.value
 
-    TUNING = ("sense_blocks_per_sm", "recon_ctas_pct", "science_after_aux", "tc_chunk", "multi_blocks_per_sm")
+    TUNING = ("sense_blocks_per_sm", "recon_ctas_pct", "science_after_aux", "tc_chunk", "multi_blocks_per_sm",
+              "steps_per_graph")
 
     def tuning(self) -> dict:
         """Current launch shapes (mcao_get_tuning), by name."""

@@ -1,6 +1,7 @@
 """Launch shapes and the autotuner (mcao_get_tuning / mcao_set_tuning / mcao_autotune) through the
 C ABI.  The shapes change how work is laid on the GPU, not what is computed: the sensing grid,
-the reconstructor slices' grid, the science ordering and the batched float32 product's grid leave
+the reconstructor slices' grid, the science ordering, the batched float32 product's grid and the
+steps per graph launch leave
 every result bit-identical; the tensor-core product's chunk regroups float32 sums only.  The
 autotuner's trials run on a checkpoint of the simulation, so a tuned run continues exactly as an
 untuned one."""
@@ -39,10 +40,11 @@ def test_tuning_round_trip_and_checks():
     g = _mcao_small_sim()
     t = g.tuning()
     assert t == {"sense_blocks_per_sm": 4, "recon_ctas_pct": 100, "science_after_aux": 1, "tc_chunk": 8,
-                 "multi_blocks_per_sm": 2}
+                 "multi_blocks_per_sm": 2, "steps_per_graph": 1}
     g.set_tuning(sense_blocks_per_sm=2, recon_ctas_pct=150)
     assert g.tuning()["sense_blocks_per_sm"] == 2 and g.tuning()["recon_ctas_pct"] == 150
-    for bad in ({"sense_blocks_per_sm": 0}, {"recon_ctas_pct": 1000}, {"science_after_aux": 2}, {"tc_chunk": 0}):
+    for bad in ({"sense_blocks_per_sm": 0}, {"recon_ctas_pct": 1000}, {"science_after_aux": 2}, {"tc_chunk": 0},
+                {"steps_per_graph": 17}):
         with pytest.raises(mcao.McaoError):
             g.set_tuning(**bad)
     with pytest.raises(mcao.McaoError):
@@ -51,12 +53,13 @@ def test_tuning_round_trip_and_checks():
 
 def test_shapes_leave_results_bit_identical():
     """A laser star and a natural star, noise on: default shapes against the sensing grid at 2
-    blocks per SM, the slices at 50 % of the SMs and the science started at the step's start."""
+    blocks per SM, the slices at 50 % of the SMs, the science started at the step's start and
+    four steps per graph."""
     a = _mcao_small_sim()
     b = _mcao_small_sim()
-    b.set_tuning(sense_blocks_per_sm=2, recon_ctas_pct=50, science_after_aux=0)
+    b.set_tuning(sense_blocks_per_sm=2, recon_ctas_pct=50, science_after_aux=0, steps_per_graph=4)
     a.step(15)
-    b.step(15)
+    b.step(15)   # three launches of the four-step graph, then three one-step launches
     assert np.array_equal(a.slopes(), b.slopes())
     assert np.array_equal(a.commands(), b.commands())
     assert a.psf(0, with_image=False) == b.psf(0, with_image=False)
@@ -70,8 +73,8 @@ def test_autotune_restores_the_run():
     chosen, report = a.autotune(steps_per_trial=10)
     assert chosen["sense_blocks_per_sm"] in (2, 3, 4, 6)
     assert chosen["recon_ctas_pct"] in (75, 100, 125, 150)
-    assert chosen["science_after_aux"] in (0, 1)
-    for name in ("sense_blocks_per_sm:", "recon_ctas_pct:", "science_after_aux:", "chosen"):
+    assert chosen["science_after_aux"] in (0, 1) and chosen["steps_per_graph"] in (1, 2, 4, 8)
+    for name in ("sense_blocks_per_sm:", "recon_ctas_pct:", "science_after_aux:", "steps_per_graph:", "chosen"):
         assert name in report
     assert a.tuning() == chosen
     assert a.step_index == b.step_index == 5
