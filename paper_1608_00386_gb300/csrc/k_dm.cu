@@ -35,7 +35,6 @@ __global__ void __launch_bounds__(kDmThreads, 3) dm_surface_kernel(DmLaunch L) {
     if (blockIdx.x == 0 && blockIdx.y == 0) {
         if (threadIdx.x == 0 && L.st) L.st->k = L.st->k_next;
         for (int i = threadIdx.x; i < L.n_work; i += blockDim.x) L.work[i] = 0u;
-        for (int i = threadIdx.x; i < L.n_rq; i += blockDim.x) L.rq_done[i] = 0u;
     }
     const int real = blockIdx.y;   // realization
     const float* cmd = L.c + (long long)real * L.n_cmd;
@@ -175,10 +174,9 @@ __global__ void __launch_bounds__(kDmThreads, 3) dm_surface_kernel(DmLaunch L) {
     }
 }
 
-__global__ void begin_step_kernel(StepState* st, unsigned int* work, int n_work, unsigned int* rq_done, int n_rq) {
+__global__ void begin_step_kernel(StepState* st, unsigned int* work, int n_work) {
     if (threadIdx.x == 0 && st) st->k = st->k_next;
     for (int i = threadIdx.x; i < n_work; i += blockDim.x) work[i] = 0u;
-    for (int i = threadIdx.x; i < n_rq; i += blockDim.x) rq_done[i] = 0u;
 }
 
 }  // namespace
@@ -193,16 +191,15 @@ cudaError_t dm_prepare() {
 }
 
 cudaError_t launch_dm_surfaces(const DmLaunch& L, cudaStream_t s) {
-    if (L.n_dm <= 0) return launch_begin_step(L.st, L.work, L.n_work, L.rq_done, L.n_rq, s);
+    if (L.n_dm <= 0) return launch_begin_step(L.st, L.work, L.n_work, s);
     dm_surface_kernel<<<dim3((unsigned)L.tile_start[L.n_dm], (unsigned)(L.n_real > 0 ? L.n_real : 1)), kDmThreads,
                         dm_smem_bytes(L.nb), s>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_begin_step(StepState* st, unsigned int* work, int n_work, unsigned int* rq_done, int n_rq,
-                              cudaStream_t s) {
-    if (!st && n_work <= 0 && n_rq <= 0) return cudaSuccess;
-    begin_step_kernel<<<1, 128, 0, s>>>(st, work, n_work, rq_done, n_rq);
+cudaError_t launch_begin_step(StepState* st, unsigned int* work, int n_work, cudaStream_t s) {
+    if (!st && n_work <= 0) return cudaSuccess;
+    begin_step_kernel<<<1, 32, 0, s>>>(st, work, n_work);
     return cudaGetLastError();
 }
 

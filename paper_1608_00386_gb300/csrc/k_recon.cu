@@ -389,22 +389,6 @@ __global__ void __launch_bounds__(kTmaWarps * 32) recon_tma_kernel(ReconLaunch L
             for (int q = 0; q < kTmaRows; ++q)
                 if (row0 + q < L.n_cmd) out[row0 + q] = DT == kReconE4M3 ? acc[q] * L.scale[row0 + q] : acc[q];
         }
-        if (L.fuse_reduce) {
-            // arrival of chunk kc of row quad rq (the fence publishes its partials first); the
-            // last of the slice's chunks to arrive applies the update of the quad's four rows
-            // (lanes 8 q .. 8 q + 7 row q), every other slice's partials being complete already
-            unsigned int arrived = 0;
-            if (lane == 0) {
-                __threadfence();
-                arrived = atomicAdd(L.rq_done + rq, 1u);
-            }
-            arrived = __shfl_sync(0xffffffffu, arrived, 0);
-            if (arrived == (unsigned int)(g.n_chunks - 1)) {
-                __threadfence();
-                if (rq == 0 && lane == 0 && L.red.st) L.red.st->k_next = L.red.st->k + 1;
-                reduce_row(L.red, (long long)rq * kTmaRows + (lane >> 3), lane & 7, L.n_cmd);
-            }
-        }
     }
 }
 

@@ -137,7 +137,6 @@ struct mcao_sim {
     int rows_pad = 0;
     float* d_c = nullptr;
     float* d_partial = nullptr;
-    unsigned int* d_rq_done = nullptr;   // [rows_pad / 4] row-quad arrival counters of the last slice
     // second-order controller (off: the pure integrator of gain cfg.gain)
     bool use_ctl = false;
     float ctl[4] = {1.0f, 0.0f, 0.0f, 0.0f};
@@ -166,13 +165,14 @@ struct mcao_sim {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_dirty = true;
-    bool graph_prof = false;              // the built graphs hold the profiler's event-record nodes
-    bool capture_prof = false;            // set while a profiled step is captured
+    unsigned int graph_mask = 0;          // stages whose event-record nodes the built graphs hold
+    unsigned int capture_mask = 0;        // stages timed by the step being captured
     cudaGraph_t graph_k = nullptr;        // tune.steps_per_graph steps in one graph (profiler off)
     cudaGraphExec_t exec_k = nullptr;
     int graph_k_steps = 0;
     std::vector<ProfSlot> prof_slots;
-    bool profiling = false;
+    bool profiling = false;               // prof_mask != 0
+    unsigned int prof_mask = 0;           // stages the profiler times (bit 1 << stage)
     std::vector<cudaEvent_t> prof_pool;
     size_t prof_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_records;
@@ -314,8 +314,6 @@ DmLaunch make_dm_launch(mcao_sim* S) {
     L.st = S->d_st;
     L.work = S->d_work;
     L.n_work = (int)(S->wfs.size() + S->slices.size());
-    L.rq_done = S->d_rq_done;
-    L.n_rq = S->d_rq_done ? S->rows_pad / kReconRows : 0;
     return L;
 }
 
@@ -439,7 +437,7 @@ cudaEvent_t dep_event(mcao_sim* S, size_t& used) {
 // profiling: an event-record node before and after a launch, present only in graphs captured
 // with the profiler on (each node is a dependency hop between the kernels it separates)
 int prof_begin(mcao_sim* S, int stage, cudaStream_t st) {
-    if (!S->capture_prof) return -1;
+    if (!(S->capture_mask & (1u << stage))) return -1;
     ProfSlot p;
     p.stage = stage;
     cudaEventCreate(&p.tpl_a);
@@ -578,7 +576,7 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         return cudaSuccess;
     }
 
-    // reconstructor slices on s3, each after its sensor; the last one also applies the update
+    // reconstructor slices on s3, each after its sensor, then the reduction
     ReduceLaunch rl{S->n_cmd, S->n_chunks, S->d_partial, S->d_c, (float)S->cfg.gain, S->d_st};
     rl.use_ctl = S->use_ctl;
     rl.a1 = S->ctl[0]; rl.a2 = S->ctl[1]; rl.b0 = S->ctl[2]; rl.b1 = S->ctl[3];
@@ -595,22 +593,14 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         slot = prof_begin(S, ST_RECON, S->s3);
         ReconLaunch rl_i = S->slices[i];
         rl_i.max_ctas = std::max(1, S->sm_count * S->tune.recon_ctas_pct / 100);
-        if (i + 1 == S->slices.size()) {
-            rl_i.fuse_reduce = 1;
-            rl_i.rq_done = S->d_rq_done;
-            rl_i.red = rl;
-        }
         if ((e = launch_recon(rl_i, S->s3)) != cudaSuccess) return e;
         prof_end(S, slot, S->s3);
         ++nl;
     }
-    if (S->slices.empty()) {
-        // no slice to carry it (never the case with a loaded reconstructor): the step counter alone
-        slot = prof_begin(S, ST_REDUCE, S->s3);
-        if ((e = launch_recon_reduce(rl, S->s3)) != cudaSuccess) return e;
-        prof_end(S, slot, S->s3);
-        ++nl;
-    }
+    slot = prof_begin(S, ST_REDUCE, S->s3);
+    if ((e = launch_recon_reduce(rl, S->s3)) != cudaSuccess) return e;
+    prof_end(S, slot, S->s3);
+    ++nl;
 
     // join every branch back into s0
     cudaEvent_t ev_gemv = dep_event(S, used);
@@ -642,11 +632,11 @@ static mcao_status capture_steps(mcao_sim* S, int n, cudaGraph_t* out, int* laun
 mcao_status build_graph(mcao_sim* S) {
     release_graph(S);
     int nl = 0;
-    S->capture_prof = S->profiling;
+    S->capture_mask = S->prof_mask;
     mcao_status r = capture_steps(S, 1, &S->graph, &nl);
-    S->capture_prof = false;
+    S->capture_mask = 0;
     if (r != MCAO_OK) return r;
-    S->graph_prof = S->profiling;
+    S->graph_mask = S->prof_mask;
     CK(cudaGraphInstantiate(&S->exec, S->graph, cudaGraphInstantiateFlagUseNodePriority));
     // locate the profiling event-record nodes
     size_t n = 0;
@@ -725,7 +715,6 @@ void destroy_all(mcao_sim* S) {
     S->d_layer_owned.clear();
     dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
     dfree(S->d_dm_surf); dfree(S->d_views); dfree(S->d_R); dfree(S->d_rscale); dfree(S->d_c); dfree(S->d_partial);
-    dfree(S->d_rq_done);
     dfree(S->d_st); dfree(S->d_acc); dfree(S->d_err); dfree(S->d_work); dfree(S->d_sr_out);
     dfree(S->d_Rrm);
     dfree(S->d_c_prev); dfree(S->d_dc_prev); dfree(S->d_dc);
@@ -1229,7 +1218,7 @@ mcao_status mcao_load_dms(mcao_sim* S, int n_dms, const mcao_dm* dms) {
     CK(cudaSetDevice(S->device));
     { mcao_status r_ = sync_all(S); if (r_ != MCAO_OK) return r_; }
     dfree(S->d_dm_desc); dfree(S->d_dm_g); dfree(S->d_dm_band); dfree(S->d_dm_map);
-    dfree(S->d_dm_surf); dfree(S->d_c); dfree(S->d_partial); dfree(S->d_rq_done);
+    dfree(S->d_dm_surf); dfree(S->d_c); dfree(S->d_partial);
     S->dms_loaded = false;
     S->recon_loaded = false;  // command count may change
     S->dms.assign(dms, dms + n_dms);
@@ -1306,7 +1295,6 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     dfree(S->d_R);
     dfree(S->d_rscale);
     dfree(S->d_partial);
-    dfree(S->d_rq_done);
     S->r_dtype = dtype;
     S->recon_loaded = false;
     S->rows_pad = std::max(1, (n_cmd + kReconRowBlock - 1) / kReconRowBlock) * kReconRowBlock;
@@ -1446,8 +1434,6 @@ mcao_status mcao_load_reconstructor(mcao_sim* S, int n_cmd, int n_slopes, const 
     S->n_chunks = chunks;
     CK(dalloc(&S->d_partial, (size_t)std::max(chunks, 1) * std::max(n_cmd, 1)));
     for (auto& L : S->slices) L.partial = S->d_partial;
-    CK(dalloc(&S->d_rq_done, (size_t)(S->rows_pad / kReconRows)));
-    CK(cudaMemsetAsync(S->d_rq_done, 0, sizeof(unsigned int) * (size_t)(S->rows_pad / kReconRows), S->s0));
     if (s_ref)
         CK(cudaMemcpyAsync(S->d_sref, s_ref, sizeof(float) * n_slopes, kind, S->s0));
     else
@@ -1464,7 +1450,7 @@ mcao_status mcao_step(mcao_sim* S, int n_steps) {
         return fail(S, MCAO_E_STATE, "load the atmosphere, the DMs and the reconstructor before stepping");
     if (n_steps == 0) return MCAO_OK;
     CK(cudaSetDevice(S->device));
-    if (S->graph_dirty || S->graph_prof != S->profiling) {
+    if (S->graph_dirty || S->graph_mask != S->prof_mask) {
         mcao_status r = build_graph(S);
         if (r != MCAO_OK) return r;
     }
@@ -1513,7 +1499,7 @@ mcao_status mcao_step_group(mcao_sim* const* sims, int n_sims, int n_steps) {
     mcao_sim* S = sims[0];   // its s0 carries the group launches
     CK(cudaSetDevice(S->device));
     for (int i = 0; i < n_sims; ++i) {
-        if (sims[i]->graph_dirty || sims[i]->graph_prof) {
+        if (sims[i]->graph_dirty || sims[i]->graph_mask) {
             mcao_status r = build_graph(sims[i]);
             if (r != MCAO_OK) return r;
         }
@@ -1874,7 +1860,7 @@ mcao_status mcao_autotune(mcao_sim* S, int steps_per_trial, int* values, int n, 
     const bool batched = S->n_real > 1;
     std::vector<std::pair<int, std::vector<int>>> knobs;
     if (acf) knobs.push_back({0, {2, 3, 4, 6}});
-    if (!batched) knobs.push_back({1, {75, 100, 125, 150}});
+    if (!batched) knobs.push_back({1, {50, 75, 100, 125}});
     if (!S->sci.empty() && fft) knobs.push_back({2, {0, 1}});
     if (batched && S->tc) knobs.push_back({3, {4, 8, 16}});
     if (batched && !S->tc) knobs.push_back({4, {1, 2}});
@@ -2242,8 +2228,15 @@ mcao_status mcao_set_realization(mcao_sim* S, int r) {
 }
 
 mcao_status mcao_set_profiling(mcao_sim* S, int on) {
+    return mcao_set_profiling_stages(S, on ? (1u << MCAO_N_STAGES) - 1u : 0u);
+}
+
+mcao_status mcao_set_profiling_stages(mcao_sim* S, unsigned int mask) {
     if (!S) return MCAO_E_INVALID_ARG;
-    S->profiling = on != 0;
+    if (mask >> MCAO_N_STAGES) return fail(S, MCAO_E_INVALID_ARG, "stage mask 0x%x has bits above the %d stages", mask,
+                                           MCAO_N_STAGES);
+    S->prof_mask = mask;
+    S->profiling = mask != 0;
     S->prof_used = 0;
     S->prof_records.clear();
     S->prof_step_begin.clear();

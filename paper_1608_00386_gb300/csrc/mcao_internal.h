@@ -147,12 +147,9 @@ struct DmLaunch {
     StepState* st;           // begin of step: k = k_next
     unsigned int* work;      // begin of step: the sensing kernels' work counters are zeroed
     int n_work;
-    unsigned int* rq_done;   // begin of step: the product's row-quad arrival counters are zeroed
-    int n_rq;
 };
 cudaError_t launch_dm_surfaces(const DmLaunch& L, cudaStream_t s);
-cudaError_t launch_begin_step(StepState* st, unsigned int* work, int n_work, unsigned int* rq_done, int n_rq,
-                              cudaStream_t s);
+cudaError_t launch_begin_step(StepState* st, unsigned int* work, int n_work, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------
 // wavefront sensors
@@ -235,12 +232,6 @@ struct ReconLaunch {
     int max_ctas;       // grid size cap (0: enough blocks for every item)
     unsigned int* work; // item counter, zero when the launch starts
     int* err;           // set to a nonzero code if a bounded wait gives up
-    // The step's last slice also applies the update (fuse_reduce != 0): per row quad, the item
-    // that completes it last (rq_done[rq] counts the slice's finished chunks of the quad, zero
-    // when the launch starts) adds every partial of its rows exactly as recon_reduce_kernel does.
-    int fuse_reduce;
-    unsigned int* rq_done;   // [n_rq]
-    ReduceLaunch red;        // the update (partial = this launch's partial, n_real = 1)
 };
 constexpr int kReconRows = 4;        // rows per work item (row quad)
 constexpr int kReconSeg = 128;       // 16-byte vectors per row and stage (at most)

@@ -27,7 +27,7 @@ EXPORTS = [
     "mcao_load_atmosphere", "mcao_load_dms", "mcao_load_reconstructor", "mcao_step", "mcao_sync",
     "mcao_query", "mcao_get_step_index", "mcao_get_slopes", "mcao_get_commands", "mcao_set_commands",
     "mcao_get_valid", "mcao_get_wfs_phase", "mcao_get_dm_surface", "mcao_get_frames", "mcao_get_psf",
-    "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_get_profile",
+    "mcao_reset_psf", "mcao_get_state", "mcao_set_state", "mcao_set_profiling", "mcao_set_profiling_stages", "mcao_get_profile",
     "mcao_reconstruct_noalloc", "mcao_get_timeline", "mcao_quantize_rows", "mcao_set_realization",
     "mcao_set_controller", "mcao_get_marechal", "mcao_set_sodium", "mcao_generate_screen", "mcao_measure",
     "mcao_interaction_matrix", "mcao_slopes_vjp", "mcao_set_misregistration", "mcao_step_group",
@@ -110,6 +110,7 @@ def lib():
         "mcao_get_state": [vp, vp, C.c_size_t],
         "mcao_set_state": [vp, vp, C.c_size_t],
         "mcao_set_profiling": [vp, C.c_int],
+        "mcao_set_profiling_stages": [vp, C.c_uint],
         "mcao_get_profile": [vp, vp, vp, C.c_int, C.POINTER(C.c_int64)],
         "mcao_reconstruct_noalloc": [vp, C.c_int, C.c_int, C.c_int, vp, vp, C.c_float, vp, C.c_char_p, C.c_size_t],
         "mcao_get_timeline": [vp, vp, vp, vp, vp, C.c_size_t, C.POINTER(C.c_size_t)],
@@ -464,8 +465,13 @@ class Sim:
         buf = (C.c_char * len(blob)).from_buffer_copy(blob)
         self._ck(lib().mcao_set_state(self.h, buf, len(blob)))
 
-    def set_profiling(self, on: bool):
-        self._ck(lib().mcao_set_profiling(self.h, int(on)))
+    def set_profiling(self, on: bool, stages=None):
+        """Stage profiler on or off; with stages (names from STAGES), time only those."""
+        if stages is None:
+            self._ck(lib().mcao_set_profiling(self.h, int(on)))
+        else:
+            mask = sum(1 << STAGES.index(s) for s in stages) if on else 0
+            self._ck(lib().mcao_set_profiling_stages(self.h, mask))
 
     def get_profile(self):
         ms = (C.c_double * len(STAGES))()

@@ -72,7 +72,7 @@ def test_autotune_restores_the_run():
     b.step(5)
     chosen, report = a.autotune(steps_per_trial=10)
     assert chosen["sense_blocks_per_sm"] in (2, 3, 4, 6)
-    assert chosen["recon_ctas_pct"] in (75, 100, 125, 150)
+    assert chosen["recon_ctas_pct"] in (50, 75, 100, 125)
     assert chosen["science_after_aux"] in (0, 1) and chosen["steps_per_graph"] in (1, 2, 4, 8)
     for name in ("sense_blocks_per_sm:", "recon_ctas_pct:", "science_after_aux:", "steps_per_graph:", "chosen"):
         assert name in report
