@@ -474,7 +474,9 @@ mcao_status mcao_tikhonov_reconstructor(const float* D, int n_slopes, int n_cmd,
 
 /* Launch shapes ("tuning") of a simulation, in this order (values per MCAO_TUNE_*):
  *   MCAO_TUNE_SENSE_BLOCKS_PER_SM  warp-per-subaperture sensing launches: blocks per SM, [1, 8] (4)
- *   MCAO_TUNE_RECON_CTAS_PCT       reconstructor slices: blocks per SM x 100, [25, 400] (100)
+ *   MCAO_TUNE_RECON_CTAS_PCT       reconstructor slices: blocks per SM x 100, [25, 400] (100); the
+ *                                  step's last slice, which runs after the last sensor, takes at
+ *                                  least one block per SM
  *   MCAO_TUNE_SCIENCE_AFTER_AUX    science waits for the block-per-subaperture sensors, 0 or 1 (1)
  *   MCAO_TUNE_TC_CHUNK             tensor-core batched product: k-blocks per TMEM accumulator,
  *                                  [1, 64] (8)

@@ -97,13 +97,15 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
     constexpr int LPC = 32 / ND;      // lanes per column of the column transform
     constexpr int QB = ND / LPC;      // outputs per lane of the column transform
     static_assert(ND == 8 || ND == 16, "detector of 8 or 16 pixels per side");
-    // per warp: axis entries (dead after the field, then reused for the row transform),
+    // per warp: axis entries (dead after the field, then reused for the second lag row of each
+    // pass and for the row transform),
     // grid metadata, the field (reused for M_uy), the lag products; per block: twiddles and
     // reciprocals.  About 30 KB per block, so three blocks fit beside a reconstructor block.
     union Scratch {
         AxisEnt e[2][kMaxEntries * NPX];
         float2 y[NPX * ND];
     };
+    static_assert(sizeof(Scratch) >= NPX * NPX * sizeof(float2), "room for one lag row's M");
     __shared__ Scratch s_u[8];
     __shared__ GridMeta s_gm[8][kMaxEntries];
     __shared__ float2 s_EM[8][NPX * NPX];
@@ -184,31 +186,50 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
                 cb0[r] = s_EM[warp][r * NPX + cb_i];
                 cb1[r] = s_EM[warp][r * NPX + cb_i + 4];
             }
-            __syncwarp();  // every lane holds its columns: the buffer now receives M_uy
+            __syncwarp();  // every lane holds its columns: the buffers now receive M_uy
+            // two lag rows per pass: M_uy in the field's buffer, M_{uy+1} in this warp's axis-entry
+            // scratch (dead after the field); lanes 0..14 sum the diagonals of row uy, lanes
+            // 16..30 those of row uy + 1 (ux = (lane mod 16) - 7)
+            float2* s_M1 = reinterpret_cast<float2*>(&s_u[warp]);
+            const int half = lane >> 4, uxl = lane & 15;
+            const bool diag = uxl < NL;
+            const int ux = uxl - (NPX - 1);
             float2 hx = make_float2(0.0f, 0.0f);
-            if (lane < NL) hx = w.h[lane];  // h(ux), ux = lane - 7
-            const int ux = lane - (NPX - 1);
+            if (diag) hx = w.h[uxl];  // h(ux)
     #pragma unroll
-            for (int uy = 0; uy < NPX; ++uy) {
+            for (int uy0 = 0; uy0 < NPX; uy0 += 2) {
                 float m0r = 0.0f, m0i = 0.0f, m1r = 0.0f, m1i = 0.0f;
+                float n0r = 0.0f, n0i = 0.0f, n1r = 0.0f, n1i = 0.0f;
     #pragma unroll
-                for (int r = 0; r + uy < NPX; ++r) {
-                    float2 a = ca[r], b0 = cb0[r + uy], b1 = cb1[r + uy];
+                for (int r = 0; r + uy0 < NPX; ++r) {
+                    float2 a = ca[r], b0 = cb0[r + uy0], b1 = cb1[r + uy0];
                     m0r = fmaf(a.x, b0.x, fmaf(a.y, b0.y, m0r));
                     m0i = fmaf(a.y, b0.x, fmaf(-a.x, b0.y, m0i));
                     m1r = fmaf(a.x, b1.x, fmaf(a.y, b1.y, m1r));
                     m1i = fmaf(a.y, b1.x, fmaf(-a.x, b1.y, m1i));
                 }
+    #pragma unroll
+                for (int r = 0; r + uy0 + 1 < NPX; ++r) {
+                    float2 a = ca[r], b0 = cb0[r + uy0 + 1], b1 = cb1[r + uy0 + 1];
+                    n0r = fmaf(a.x, b0.x, fmaf(a.y, b0.y, n0r));
+                    n0i = fmaf(a.y, b0.x, fmaf(-a.x, b0.y, n0i));
+                    n1r = fmaf(a.x, b1.x, fmaf(a.y, b1.y, n1r));
+                    n1i = fmaf(a.y, b1.x, fmaf(-a.x, b1.y, n1i));
+                }
                 s_EM[warp][ca_i * NPX + cb_i] = make_float2(m0r, m0i);
                 s_EM[warp][ca_i * NPX + cb_i + 4] = make_float2(m1r, m1i);
+                s_M1[ca_i * NPX + cb_i] = make_float2(n0r, n0i);
+                s_M1[ca_i * NPX + cb_i + 4] = make_float2(n1r, n1i);
                 __syncwarp();
-                if (lane < NL) {
+                if (diag) {
+                    const float2* M = half ? s_M1 : s_EM[warp];
+                    const int uy = uy0 + half;
                     float ar = 0.0f, ai = 0.0f;
     #pragma unroll
                     for (int a = 0; a < NPX; ++a) {
                         int b = a + ux;
                         if (b >= 0 && b < NPX) {
-                            float2 m = s_EM[warp][a * NPX + b];
+                            float2 m = M[a * NPX + b];
                             ar += m.x;
                             ai += m.y;
                         }
@@ -219,7 +240,7 @@ __global__ void __launch_bounds__(256, 4) wfs_acf_kernel(WfsLaunch L) {
                         otf = expf(-sd.elong_a * d * d);
                     }
                     float2 hh = cmul(hx, w.h[uy + NPX - 1]);
-                    s_P[warp][uy * NL + lane] = cmul(make_float2(ar * otf, ai * otf), hh);
+                    s_P[warp][uy * NL + uxl] = cmul(make_float2(ar * otf, ai * otf), hh);
                 }
                 __syncwarp();
             }

@@ -593,6 +593,8 @@ cudaError_t enqueue_step(mcao_sim* S, int* launches) {
         slot = prof_begin(S, ST_RECON, S->s3);
         ReconLaunch rl_i = S->slices[i];
         rl_i.max_ctas = std::max(1, S->sm_count * S->tune.recon_ctas_pct / 100);
+        // the last slice follows the last sensor and has the SMs to itself: one block per SM
+        if (i + 1 == S->slices.size()) rl_i.max_ctas = std::max(rl_i.max_ctas, S->sm_count);
         if ((e = launch_recon(rl_i, S->s3)) != cudaSuccess) return e;
         prof_end(S, slot, S->s3);
         ++nl;
