@@ -106,3 +106,27 @@ def test_autotune_batched_float32_grid():
     g = mcao.make_sim(cfg, [inputs.make_screens(cfg, realization=r) for r in range(4)], R, n_real=4)
     chosen, report = g.autotune(steps_per_trial=5)
     assert chosen["multi_blocks_per_sm"] in (1, 2) and "multi_blocks_per_sm:" in report
+
+
+def test_profiler_stage_mask_and_graph_nodes_leave_results_bit_identical():
+    """The stage profiler's event-record nodes are in the step graph only for the stages asked
+    (mcao_set_profiling_stages): timing the product alone records only its launches, timing
+    every stage records all of them, and neither changes what a step computes."""
+    a = _mcao_small_sim()
+    b = _mcao_small_sim()
+    b.set_profiling(True, stages=["recon"])
+    b.step(3)
+    tl = b.get_timeline()
+    assert tl and {name for _, name, _, _ in tl} == {"recon"}
+    ms, cnt, lps = b.get_profile()
+    assert cnt["recon"] > 0 and cnt["dm"] == 0 and cnt["wfs_main"] == 0 and lps > 0
+    b.set_profiling(True)
+    b.step(2)
+    names = {name for _, name, _, _ in b.get_timeline()}
+    assert {"dm", "wfs_main", "recon", "recon_reduce"} <= names
+    b.set_profiling(False)
+    b.step(5)
+    a.step(10)
+    assert np.array_equal(a.slopes(), b.slopes())
+    assert np.array_equal(a.commands(), b.commands())
+    assert mcao.lib().mcao_set_profiling_stages(b.h, 1 << len(mcao.STAGES)) == 1   # MCAO_E_INVALID_ARG
