@@ -71,12 +71,24 @@ __global__ void __launch_bounds__(256) sci_field_kernel(SciLaunch L0) {
 // (piston removed, amplitude-weighted, science band) from the phase sums; fixed order, double
 __device__ void finalize_strehl(const SciLaunch& L, double* red, int tid, int nthr) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int q = tid; q < L.n_tiles; q += nthr) {
-        const float4 p = L.sr_part[q];
-        v[0] += p.x;
-        v[1] += p.y;
-        v[2] += p.z;
-        v[3] += p.w;
+    // the thread's partials q = tid, tid + nthr, ... in that order, loaded eight at a time (the
+    // loads of a batch in flight together)
+    constexpr int kBatch = 8;
+    for (int q0 = tid; q0 < L.n_tiles; q0 += kBatch * nthr) {
+        float4 p[kBatch];
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+            const int q = q0 + i * nthr;
+            p[i] = q < L.n_tiles ? L.sr_part[q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+            if (q0 + i * nthr >= L.n_tiles) break;
+            v[0] += p[i].x;
+            v[1] += p[i].y;
+            v[2] += p[i].z;
+            v[3] += p[i].w;
+        }
     }
     for (int i = 0; i < 4; ++i) red[i * nthr + tid] = v[i];
     __syncthreads();
@@ -156,9 +168,12 @@ __global__ void __launch_bounds__(256) sci_cols_kernel(SciLaunch L0) {
     if (blockIdx.x == 0 && tid == 0) L.acc->n_psf += 1;
 }
 
-// Compile-time-size versions of the two FFT passes (2 rows / columns per block); their twiddle
-// table is stage-major (sci_twiddles).
+// Compile-time-size versions of the two FFT passes (2 rows / columns per block, 256 threads);
+// their twiddle table is stage-major (sci_twiddles).  Global loads are issued a whole pass at a
+// time into registers before anything is stored, so that a block waits for about one memory
+// round trip per pass rather than one per element.
 constexpr int kCtRows = 2;
+constexpr int kCtThreads = 256;
 
 template <int M>
 __global__ void __launch_bounds__(256) sci_rows_ct(SciLaunch L0) {
@@ -171,18 +186,29 @@ __global__ void __launch_bounds__(256) sci_rows_ct(SciLaunch L0) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     if (blockIdx.x == 0) finalize_strehl(L, red, tid, nthr);
     if (!psf_step(L)) return;
+    static_assert((kCtRows * M) % kCtThreads == 0, "whole passes per thread");
+    constexpr int PER = kCtRows * M / kCtThreads, PW = (M + kCtThreads - 1) / kCtThreads;
     const int row0 = blockIdx.x * kCtRows;
-    for (int q = tid; q < M; q += nthr) W[q] = L.w[q];
-    for (int q = tid; q < kCtRows * M; q += nthr) {
-        int r = q / M, c = q - r * M;
-        int row = row0 + r;
-        A[q] = (row < L.N && c < L.N) ? L.field[(long long)row * L.N + c] : make_float2(0.0f, 0.0f);
+    {
+        float2 w[PW], v[PER];
+#pragma unroll
+        for (int i = 0; i < PW; ++i) w[i] = tid + i * kCtThreads < M ? L.w[tid + i * kCtThreads] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int q = tid + i * kCtThreads, r = q / M, c = q - r * M, row = row0 + r;
+            v[i] = (row < L.N && c < L.N) ? L.field[(long long)row * L.N + c] : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int i = 0; i < PW; ++i)
+            if (tid + i * kCtThreads < M) W[tid + i * kCtThreads] = w[i];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) A[tid + i * kCtThreads] = v[i];
     }
     __syncthreads();
     float2* R = fft_tab<M>(A, B, kCtRows, W, tid, nthr);
-    for (int q = tid; q < kCtRows * M; q += nthr) {
-        int c = q / kCtRows, r = q - c * kCtRows;
-        int row = row0 + r;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int q = tid + i * kCtThreads, c = q / kCtRows, r = q - c * kCtRows, row = row0 + r;
         if (row < L.N) L.ft[(long long)c * L.N + row] = R[r * M + c];
     }
 }
@@ -196,19 +222,37 @@ __global__ void __launch_bounds__(256) sci_cols_ct(SciLaunch L0) {
     float2* B = A + kCtRows * M;
     float2* W = B + kCtRows * M;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    static_assert((kCtRows * M) % kCtThreads == 0, "whole passes per thread");
+    constexpr int PER = kCtRows * M / kCtThreads, PW = (M + kCtThreads - 1) / kCtThreads;
     const int c0 = blockIdx.x * kCtRows;
-    for (int q = tid; q < M; q += nthr) W[q] = L.w[q];
-    for (int q = tid; q < kCtRows * M; q += nthr) {
-        int r = q / M, j = q - r * M;
-        A[q] = (j < L.N) ? L.ft[(long long)(c0 + r) * L.N + j] : make_float2(0.0f, 0.0f);
+    {
+        float2 w[PW], v[PER];
+#pragma unroll
+        for (int i = 0; i < PW; ++i) w[i] = tid + i * kCtThreads < M ? L.w[tid + i * kCtThreads] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int q = tid + i * kCtThreads, r = q / M, j = q - r * M;
+            v[i] = (j < L.N) ? L.ft[(long long)(c0 + r) * L.N + j] : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int i = 0; i < PW; ++i)
+            if (tid + i * kCtThreads < M) W[tid + i * kCtThreads] = w[i];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) A[tid + i * kCtThreads] = v[i];
     }
+    // this block's PSF accumulator entries, read while the transform runs
+    double acc[PER];
+    double* psf = L.psf_t + (long long)c0 * M;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) acc[i] = psf[tid + i * kCtThreads];
     __syncthreads();
     float2* R = fft_tab<M>(A, B, kCtRows, W, tid, nthr);
-    for (int q = tid; q < kCtRows * M; q += nthr) {
-        int r = q / M, j = q - r * M;
-        float2 v = R[q];
-        float p = fmaf(v.x, v.x, v.y * v.y);   // frame intensity in float, accumulated in double
-        L.psf_t[(long long)(c0 + r) * M + j] += (double)p;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int q = tid + i * kCtThreads;
+        const float2 v = R[q];
+        const float p = fmaf(v.x, v.x, v.y * v.y);   // frame intensity in float, accumulated in double
+        psf[q] = acc[i] + (double)p;
     }
     if (blockIdx.x == 0 && tid == 0) L.acc->n_psf += 1;
 }
