@@ -123,7 +123,11 @@ __global__ void __launch_bounds__(256) sci_rows_kernel(SciLaunch L0) {
     double* red = reinterpret_cast<double*>(W + L.M);
     const int tid = threadIdx.x, nthr = blockDim.x;
 
-    if (blockIdx.x == 0) finalize_strehl(L, red, tid, nthr);
+    // the grid's last block only reduces the Strehl partials; it runs beside the FFT blocks
+    if (blockIdx.x == gridDim.x - 1) {
+        finalize_strehl(L, red, tid, nthr);
+        return;
+    }
     if (!psf_step(L)) return;
 
     const int row0 = blockIdx.x * kRowsPerBlock;
@@ -184,7 +188,12 @@ __global__ void __launch_bounds__(256) sci_rows_ct(SciLaunch L0) {
     float2* W = B + kCtRows * M;
     double* red = reinterpret_cast<double*>(W + M);
     const int tid = threadIdx.x, nthr = blockDim.x;
-    if (blockIdx.x == 0) finalize_strehl(L, red, tid, nthr);
+    // the grid's last block only reduces the Strehl partials (on the FP64 pipe of one SM, about
+    // as long as an FFT block's work); it runs beside the FFT blocks
+    if (blockIdx.x == gridDim.x - 1) {
+        finalize_strehl(L, red, tid, nthr);
+        return;
+    }
     if (!psf_step(L)) return;
     static_assert((kCtRows * M) % kCtThreads == 0, "whole passes per thread");
     constexpr int PER = kCtRows * M / kCtThreads, PW = (M + kCtThreads - 1) / kCtThreads;
@@ -273,7 +282,7 @@ cudaError_t ct_prepare() {
 
 template <int M>
 cudaError_t ct_rows(const SciLaunch& L, cudaStream_t s) {
-    sci_rows_ct<M><<<dim3((unsigned)((L.N + kCtRows - 1) / kCtRows), (unsigned)L.ctx.n_real), 256, ct_smem<M>(), s>>>(L);
+    sci_rows_ct<M><<<dim3((unsigned)((L.N + kCtRows - 1) / kCtRows + 1), (unsigned)L.ctx.n_real), 256, ct_smem<M>(), s>>>(L);
     return cudaGetLastError();
 }
 
@@ -354,7 +363,7 @@ cudaError_t launch_sci_rows(const SciLaunch& L, cudaStream_t s) {
     MCAO_SCI_CT_SIZES(MCAO_CT_ROWS)
 #undef MCAO_CT_ROWS
     size_t sm = fft_smem_bytes(L.M);
-    sci_rows_kernel<<<dim3((unsigned)((L.N + kRowsPerBlock - 1) / kRowsPerBlock), (unsigned)L.ctx.n_real), 256, sm, s>>>(L);
+    sci_rows_kernel<<<dim3((unsigned)((L.N + kRowsPerBlock - 1) / kRowsPerBlock + 1), (unsigned)L.ctx.n_real), 256, sm, s>>>(L);
     return cudaGetLastError();
 }
 
