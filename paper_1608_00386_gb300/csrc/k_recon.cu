@@ -237,8 +237,7 @@ __device__ __forceinline__ void stage_fma(const uint4 (&rv)[kTmaSeg / 32][kTmaRo
 // one warp), lane m adds slots m, m + 8, ... (all its loads in flight at once), then a fixed
 // shuffle tree; deterministic.  With the second-order controller:
 // c_{k+1} = a1 c_k + a2 c_{k-1} + b0 dc_k + b1 dc_{k-1}.  Without partials the update is read
-// from dc_in (batched product).  The partials are read from L2 (written by other SMs in the same
-// launch when the last slice applies the update).  Every lane of the warp must call it.
+// from dc_in (batched product).  Every lane of the warp must call it.
 __device__ __forceinline__ void reduce_row(const ReduceLaunch& L, long long row, int m, long long n_rows) {
     float a = 0.0f;
     if (row < n_rows) {
