@@ -369,7 +369,10 @@ mcao_status mcao_check_bounded_wait(mcao_sim* sim);
  * return at once: a closed loop can read each step's result without waiting for it.  The values
  * are in place after mcao_sync, or once the stream set by mcao_set_stream passes this point.
  * Host buffers should be pinned (cudaHostAlloc / page-locked) for the copies to overlap the
- * next steps; the caller keeps them alive until then.  Errors: MCAO_E_INVALID_ARG (both NULL),
+ * next steps; the caller keeps them alive until then.  The values are first snapshotted on the
+ * device (one small kernel after the queued steps, into one of 64 ring slots) and copied to the
+ * host from there on a stream of their own, so the next steps do not wait for the copies; a
+ * slot is reused once its earlier copy is done.  Errors: MCAO_E_INVALID_ARG (both NULL),
  * MCAO_E_STATE (commands before the DMs are loaded), MCAO_E_CUDA. */
 mcao_status mcao_read_async(mcao_sim* sim, float* commands, double* strehl);
 

@@ -6,6 +6,7 @@
 // The 2-D FFT runs as two passes of batched radix-4/5/2 Stockham FFTs in shared memory: rows of
 // the field (zero-padded) written transposed, then rows of the transposed array; the PSF
 // accumulator is therefore held transposed and unshifted, [kx][ky] (the host reorders it).
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -388,7 +389,27 @@ __global__ void strehl_out_kernel(const SciAcc* acc, int n_sci, double* out) {
     out[2 * q + 1] = a.sr_last;
 }
 
+// a step's readout into one slot of the device ring: the commands copied, the (long, last)
+// Strehl ratios of each science direction formed as strehl_out_kernel does
+__global__ void readout_kernel(const float* __restrict__ c, int n_cmd, const SciAcc* __restrict__ acc, int n_sci,
+                               float* __restrict__ ring_c, double* __restrict__ ring_s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_cmd) ring_c[i] = c[i];
+    if (i < n_sci) {
+        const SciAcc a = acc[i];
+        ring_s[2 * i] = a.n_sr ? a.sr_sum / (double)a.n_sr : 0.0;
+        ring_s[2 * i + 1] = a.sr_last;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_readout(const float* c, int n_cmd, const SciAcc* acc, int n_sci, float* ring_c, double* ring_s,
+                           cudaStream_t s) {
+    const int n = std::max(n_cmd, n_sci);
+    if (n > 0) readout_kernel<<<(n + 255) / 256, 256, 0, s>>>(c, n_cmd, acc, n_sci, ring_c, ring_s);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_strehl_out(const SciAcc* acc, int n_sci, double* out, cudaStream_t s) {
     if (n_sci > 0) strehl_out_kernel<<<(n_sci + 63) / 64, 64, 0, s>>>(acc, n_sci, out);

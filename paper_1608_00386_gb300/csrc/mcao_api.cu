@@ -91,6 +91,15 @@ struct mcao_sim {
     bool user_set = false;
     std::vector<cudaEvent_t> ev_pool;     // dependency events used while capturing
     cudaEvent_t ev_user = nullptr, ev_done = nullptr;
+    // per-step readout (mcao_read_async): each read takes one slot of a device ring on s0 (a
+    // small kernel after the queued steps), and the copies to the host run from that slot on
+    // s_read, so that the next step does not wait behind them
+    cudaStream_t s_read = nullptr;
+    float* d_ring_c = nullptr;            // [kReadRing][ring_ncmd]
+    double* d_ring_s = nullptr;           // [kReadRing][2 ring_nsci]
+    int ring_ncmd = -1, ring_nsci = -1, ring_pos = 0;
+    std::vector<cudaEvent_t> ring_ready, ring_free;   // per slot: snapshot written / copied out
+    std::vector<char> ring_busy;
 
     // wfs
     WfsDev* d_wfs = nullptr;
@@ -686,6 +695,7 @@ mcao_status signal_user(mcao_sim* S) {
 
 mcao_status sync_all(mcao_sim* S) {
     for (cudaStream_t st : {S->s0, S->s1, S->s2, S->s3}) CK(cudaStreamSynchronize(st));
+    if (S->s_read) CK(cudaStreamSynchronize(S->s_read));
     if (S->d_err) {
         int e = 0;
         CK(cudaMemcpy(&e, S->d_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -726,7 +736,10 @@ void destroy_all(mcao_sim* S) {
     for (auto e : S->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : {S->ev_user, S->ev_done})
         if (e) cudaEventDestroy(e);
-    for (cudaStream_t st : {S->s0, S->s1, S->s2, S->s3})
+    dfree(S->d_ring_c); dfree(S->d_ring_s);
+    for (auto e : S->ring_ready) cudaEventDestroy(e);
+    for (auto e : S->ring_free) cudaEventDestroy(e);
+    for (cudaStream_t st : {S->s0, S->s1, S->s2, S->s3, S->s_read})
         if (st) cudaStreamDestroy(st);
     delete S;
 }
@@ -838,6 +851,7 @@ mcao_status mcao_sim_create(const mcao_config* cfg, mcao_sim** out) {
     CKC(cudaStreamCreateWithPriority(&S->s0, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
     CKC(cudaStreamCreateWithPriority(&S->s1, cudaStreamNonBlocking, (prio_lo + prio_hi) / 2));
     CKC(cudaStreamCreateWithPriority(&S->s2, cudaStreamNonBlocking, prio_lo));
+    CKC(cudaStreamCreateWithPriority(&S->s_read, cudaStreamNonBlocking, prio_lo));
     CKC(cudaEventCreateWithFlags(&S->ev_user, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&S->ev_done, cudaEventDisableTiming));
     CKC(wfs_prepare());
@@ -2060,20 +2074,54 @@ mcao_status mcao_check_bounded_wait(mcao_sim* S) {
     return sync_all(S);   // reports the expired wait as MCAO_E_TIMEOUT and clears the flag
 }
 
+constexpr int kReadRing = 64;   // readout slots in flight at most
+
 mcao_status mcao_read_async(mcao_sim* S, float* commands, double* strehl) {
     if (!S || (!commands && !strehl)) return MCAO_E_INVALID_ARG;
     if (commands && !S->dms_loaded) return fail(S, MCAO_E_STATE, "DMs not loaded");
     CK(cudaSetDevice(S->device));
+    const int n_cmd = S->dms_loaded ? S->n_cmd : 0, n_sci = (int)S->sci.size();
+    if (S->ring_ncmd != n_cmd || S->ring_nsci != n_sci) {
+        // (re)size the ring after every earlier read has completed
+        if (S->s_read) CK(cudaStreamSynchronize(S->s_read));
+        dfree(S->d_ring_c);
+        dfree(S->d_ring_s);
+        CK(dalloc(&S->d_ring_c, (size_t)kReadRing * std::max(n_cmd, 1)));
+        CK(dalloc(&S->d_ring_s, (size_t)kReadRing * 2 * std::max(n_sci, 1)));
+        while ((int)S->ring_ready.size() < kReadRing) {
+            cudaEvent_t a = nullptr, b = nullptr;
+            CK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+            S->ring_ready.push_back(a);
+            S->ring_free.push_back(b);
+        }
+        S->ring_busy.assign(kReadRing, 0);
+        S->ring_ncmd = n_cmd;
+        S->ring_nsci = n_sci;
+        S->ring_pos = 0;
+    }
     mcao_status r = order_after_user(S);
     if (r != MCAO_OK) return r;
-    if (commands && S->n_cmd > 0)
-        CK(cudaMemcpyAsync(commands, S->d_c + (size_t)S->cur * S->n_cmd, sizeof(float) * S->n_cmd,
-                           cudaMemcpyDeviceToHost, S->s0));
-    if (strehl && !S->sci.empty()) {
-        CK(launch_strehl_out(S->d_acc + (size_t)S->cur * S->sci.size(), (int)S->sci.size(), S->d_sr_out, S->s0));
-        CK(cudaMemcpyAsync(strehl, S->d_sr_out, sizeof(double) * 2 * S->sci.size(), cudaMemcpyDeviceToHost, S->s0));
-    }
-    return signal_user(S);
+    const int slot = S->ring_pos;
+    S->ring_pos = (S->ring_pos + 1) % kReadRing;
+    float* rc = S->d_ring_c + (size_t)slot * std::max(n_cmd, 1);
+    double* rs = S->d_ring_s + (size_t)slot * 2 * std::max(n_sci, 1);
+    // the slot's previous copy to the host is done before the snapshot overwrites it
+    if (S->ring_busy[slot]) CK(cudaStreamWaitEvent(S->s0, S->ring_free[slot], 0));
+    const int nc = (commands && n_cmd > 0) ? n_cmd : 0, ns = strehl ? n_sci : 0;
+    CK(launch_readout(S->d_c + (size_t)S->cur * std::max(n_cmd, 1), nc, S->d_acc + (size_t)S->cur * std::max(n_sci, 1),
+                      ns, rc, rs, S->s0));
+    CK(cudaEventRecord(S->ring_ready[slot], S->s0));
+    CK(cudaStreamWaitEvent(S->s_read, S->ring_ready[slot], 0));
+    if (nc) CK(cudaMemcpyAsync(commands, rc, sizeof(float) * nc, cudaMemcpyDeviceToHost, S->s_read));
+    if (ns) CK(cudaMemcpyAsync(strehl, rs, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, S->s_read));
+    CK(cudaEventRecord(S->ring_free[slot], S->s_read));
+    S->ring_busy[slot] = 1;
+    r = signal_user(S);
+    if (r != MCAO_OK) return r;
+    // work queued on the caller's stream afterwards also sees the host copies
+    if (S->user_set) CK(cudaStreamWaitEvent(S->user, S->ring_free[slot], 0));
+    return MCAO_OK;
 }
 
 mcao_status mcao_get_marechal(mcao_sim* S, int sci, double* sr_long, double* sr_last) {

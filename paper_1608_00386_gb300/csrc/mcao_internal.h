@@ -336,6 +336,10 @@ cudaError_t launch_phase_adjoint(const ProjLaunch& L, float* g_phase, long long 
 
 // per science direction: (long-exposure, instantaneous) Strehl ratio into out[2 q], out[2 q + 1]
 cudaError_t launch_strehl_out(const SciAcc* acc, int n_sci, double* out, cudaStream_t s);
+// one readout slot: ring_c[0..n_cmd) = c, ring_s[2q], ring_s[2q+1] = (long, last) Strehl of
+// science direction q (n_cmd or n_sci may be 0)
+cudaError_t launch_readout(const float* c, int n_cmd, const SciAcc* acc, int n_sci, float* ring_c, double* ring_s,
+                           cudaStream_t s);
 
 // twiddles of a science FFT of size M in the layout its kernels read (stage-major for the sizes
 // with a compile-time transform, exp(-2 pi i m / M) otherwise)
