@@ -89,3 +89,34 @@ def test_read_async_matches_synchronous_reads():
         assert ring_s[k, 0, 0].item() == sl and ring_s[k, 0, 1].item() == sn
     with pytest.raises(mcao.McaoError):
         g.read_async(None, None)
+
+
+def test_read_async_ring_reuse_and_partial_reads():
+    """More reads in flight than the 64 device ring slots (a slot is reused once its copy is
+    done) and reads of the commands or the Strehl ratios alone: every value equals the
+    synchronous reads of a twin run."""
+    import torch
+    cfg, screens, R = scao_tiny_inputs()
+    cfg = dict(cfg, noise=True)
+    g = mcao.make_sim(cfg, screens, R)
+    n = g.query(mcao.Q_COMMANDS)
+    steps = 150
+    ring_c = torch.zeros((steps, n), dtype=torch.float32).pin_memory()
+    ring_s = torch.zeros((steps, 1, 2), dtype=torch.float64).pin_memory()
+    for k in range(steps):
+        g.step(1)
+        if k % 3 == 0:
+            g.read_async(ring_c[k], ring_s[k])
+        elif k % 3 == 1:
+            g.read_async(ring_c[k], None)
+        else:
+            g.read_async(None, ring_s[k])
+    g.sync()
+    h = mcao.make_sim(cfg, screens, R)
+    for k in range(steps):
+        h.step(1)
+        _, sl, sn = h.psf(0, with_image=False)
+        if k % 3 != 2:
+            assert np.array_equal(ring_c[k].numpy(), h.commands()), k
+        if k % 3 != 1:
+            assert ring_s[k, 0, 0].item() == sl and ring_s[k, 0, 1].item() == sn, k
