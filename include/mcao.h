@@ -477,7 +477,7 @@ mcao_status mcao_tikhonov_reconstructor(const float* D, int n_slopes, int n_cmd,
 
 /* Launch shapes ("tuning") of a simulation, in this order (values per MCAO_TUNE_*):
  *   MCAO_TUNE_SENSE_BLOCKS_PER_SM  warp-per-subaperture sensing launches: blocks per SM, [1, 8] (4)
- *   MCAO_TUNE_RECON_CTAS_PCT       reconstructor slices: blocks per SM x 100, [25, 400] (100); the
+ *   MCAO_TUNE_RECON_CTAS_PCT       reconstructor slices: blocks per SM x 100, [25, 400] (85); the
  *                                  step's last slice, which runs after the last sensor, takes at
  *                                  least one block per SM
  *   MCAO_TUNE_SCIENCE_AFTER_AUX    science waits for the block-per-subaperture sensors, 0 or 1 (1)

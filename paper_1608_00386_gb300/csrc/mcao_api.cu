@@ -1876,7 +1876,7 @@ mcao_status mcao_autotune(mcao_sim* S, int steps_per_trial, int* values, int n, 
     const bool batched = S->n_real > 1;
     std::vector<std::pair<int, std::vector<int>>> knobs;
     if (acf) knobs.push_back({0, {2, 3, 4, 6}});
-    if (!batched) knobs.push_back({1, {50, 75, 100, 125}});
+    if (!batched) knobs.push_back({1, {50, 75, 80, 85, 90, 95, 100, 125}});
     if (!S->sci.empty() && fft) knobs.push_back({2, {0, 1}});
     if (batched && S->tc) knobs.push_back({3, {4, 8, 16}});
     if (batched && !S->tc) knobs.push_back({4, {1, 2}});

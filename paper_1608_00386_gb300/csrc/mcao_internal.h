@@ -15,7 +15,7 @@ constexpr int kMaxEntries = 16;   // layers + DMs sampled along one direction
 // changes a result except tc_chunk, which regroups the tensor-core product's float32 sums.
 struct Tuning {
     int sense_blocks_per_sm = 4;    // warp-per-subaperture sensing: grid cap, blocks per SM
-    int recon_ctas_pct = 100;       // reconstructor slices: blocks per SM x 100
+    int recon_ctas_pct = 85;        // reconstructor slices: blocks per SM x 100
     int science_after_aux = 1;      // science waits for the block-per-subaperture sensors
     int tc_chunk = 8;               // tensor-core product: k-blocks per TMEM accumulator
     int multi_blocks_per_sm = 2;    // batched float32 product: blocks per SM
